@@ -1,0 +1,1149 @@
+// FP64 CPU oracle for backward Monte Carlo path tracing of generalized rays.
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes or
+// calls this file; only tests/, __graft_entry__.smoke() and bench.py's
+// cpu_baseline / reference arm use it (through oracle/oracle.py).  It shares no
+// header, helper, constant table or generator with the CUDA path: the two agree
+// only on the plain input arrays written by the seeded scene generator and on
+// the published definitions both follow (Philox4x32-10, the duff ONB, the
+// paper's equations).
+//
+// Everything here is plain, slow, double precision, written step by step in the
+// order of the paper's rendering algorithm (Algorithm 1, with the interactive
+// simplifications of Sec. 7.2):
+//   source a generalized ray from the pixel          (Eq. MC_sourcing)
+//   propagate it (closest hit, footprint update)     (Eq. K_free_space_propagation)
+//   measure it against light sources                 (Eq. measurement_operator)
+//   interact with the wavevector reversed            (Eq. action_time_reversal)
+//     grating orders                                 (Eq. K_grating)
+//     rough-surface lobe                             (Eq. K_surface_HS)
+//     smooth reflection with Fresnel weight          (Eq. K_reflection_refraction)
+//   sample the scattered distribution, update weight (Eq. MC_light_transport_Q1)
+// plus next-event estimation and Russian roulette (Sec. 7.2, implementation
+// details).  Where the paper leaves a quantity open, the reading used is stated
+// in the comment at that line; the same list of readings is kept with the
+// project's design notes.
+//
+// Units: scene geometry in metres; optical lengths (wavelength, grating period
+// and height, roughness, correlation and coherence lengths, beta) in
+// micrometres.  |k| = 2*pi/lambda in 1/um (refractive index 1, Sec. 3.1).
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+namespace {
+
+const double PI = 3.14159265358979323846;
+
+// ---------------------------------------------------------------- vectors
+struct V3 {
+  double x, y, z;
+};
+V3 v3(double x, double y, double z) { return V3{x, y, z}; }
+V3 operator+(V3 a, V3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
+V3 operator-(V3 a, V3 b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
+V3 operator*(double s, V3 a) { return v3(s * a.x, s * a.y, s * a.z); }
+V3 neg(V3 a) { return v3(-a.x, -a.y, -a.z); }
+double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+V3 cross(V3 a, V3 b) {
+  return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+double length(V3 a) { return std::sqrt(dot(a, a)); }
+V3 normalize(V3 a) { return (1.0 / length(a)) * a; }
+
+// Orthonormal basis around a unit vector n: the branchless construction of
+// Duff, Burgess, Christensen, Hery, Kensler, Liani, Villemin, "Building an
+// Orthonormal Basis, Revisited", JCGT 6(1), 2017.  The choice of basis fixes
+// how the two Gaussian random numbers of a transverse sample map to space.
+void onb(V3 n, V3* e1, V3* e2) {
+  double sign = std::copysign(1.0, n.z);
+  double a = -1.0 / (sign + n.z);
+  double b = n.x * n.y * a;
+  *e1 = v3(1.0 + sign * n.x * n.x * a, sign * b, -sign * n.x);
+  *e2 = v3(b, sign + n.y * n.y * a, -n.y);
+}
+
+// ---------------------------------------------------------------- RNG
+// Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw,
+// "Parallel random numbers: as easy as 1, 2, 3", SC'11): ten rounds of the
+// 4x32 Philox S-box, multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key bumps
+// 0x9E3779B9 / 0xBB67AE85, the key bumped before every round but the first.
+void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0;
+    c1 = n1;
+    c2 = n2;
+    c3 = n3;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+// Random-number addressing (fixed convention of this project, both sides):
+//   key     = (seed, view index)
+//   counter = (pixel index y*W+x, sample index, (segment << 4) | call, 0)
+// segment = number of surface interactions before the current ray segment
+// (0 for the camera ray); the call identifies the use at the vertex that ends
+// that segment.  Each 32-bit word maps to u = (x >> 8) * 2^-24 in [0,1), which
+// is exact in both float and double.
+enum Call { CALL_JITTER = 0, CALL_EMIT_FOOT = 1, CALL_LOBE = 2, CALL_NEE_DIR = 3, CALL_NEE_FOOT = 4, CALL_RR = 5 };
+
+struct Rng {
+  uint32_t key[2];
+  uint32_t pixel;
+  uint32_t sample;
+  void draw(int segment, int call, double u[4]) const {
+    uint32_t ctr[4] = {pixel, sample, ((uint32_t)segment << 4) | (uint32_t)call, 0u};
+    uint32_t x[4];
+    philox4x32_10(ctr, key, x);
+    for (int i = 0; i < 4; ++i) u[i] = (double)(x[i] >> 8) * (1.0 / 16777216.0);
+  }
+};
+
+// Two independent standard normals from two uniforms (Box & Muller 1958).
+// 1-u is used so the logarithm's argument lies in (0, 1].
+void box_muller(double u0, double u1, double* z0, double* z1) {
+  double r = std::sqrt(-2.0 * std::log(1.0 - u0));
+  double phi = 2.0 * PI * u1;
+  *z0 = r * std::cos(phi);
+  *z1 = r * std::sin(phi);
+}
+
+// ---------------------------------------------------------------- special functions
+// Bessel function of the first kind of integer order, by its power series
+// J_n(x) = sum_m (-1)^m (x/2)^(2m+n) / (m! (m+n)!)   (A&S 9.1.10).
+double bessel_j(int n, double x) {
+  double sgn = 1.0;
+  if (n < 0) {
+    n = -n;
+    if (n & 1) sgn = -1.0;  // J_{-n} = (-1)^n J_n
+  }
+  double half = 0.5 * x;
+  double term = 1.0;
+  for (int i = 1; i <= n; ++i) term *= half / i;  // (x/2)^n / n!
+  double sum = term;
+  for (int m = 1; m < 200; ++m) {
+    term *= -(half * half) / ((double)m * (double)(m + n));
+    sum += term;
+    if (std::fabs(term) < 1e-18 * std::fabs(sum) && m > 2) break;
+  }
+  return sgn * sum;
+}
+
+// von Mises-Fisher density on the unit sphere about mean direction mu with
+// concentration kappa (reading of the angular Gaussian measurement lobe on the
+// sphere): kappa / (2 pi (1 - e^{-2 kappa})) * exp(-kappa |w - mu|^2 / 2).
+double vmf(V3 w, V3 mu, double kappa) {
+  if (kappa < 1e-8) return 1.0 / (4.0 * PI);
+  V3 d = w - mu;
+  return kappa / (2.0 * PI * (-std::expm1(-2.0 * kappa))) * std::exp(-0.5 * kappa * dot(d, d));
+}
+
+// Sample a direction from the vMF about mu (Wood 1994 / Jakob 2012 form):
+// 1 - cos(theta) = -log(u' + (1-u') e^{-2 kappa}) / kappa with u' = 1-u0.
+V3 vmf_sample(V3 mu, double kappa, double u0, double u1) {
+  double up = 1.0 - u0;
+  double v = -std::log(up + (1.0 - up) * std::exp(-2.0 * kappa)) / kappa;  // 1 - cos
+  double sin_t = std::sqrt(std::max(0.0, v * (2.0 - v)));
+  double phi = 2.0 * PI * u1;
+  V3 e1, e2;
+  onb(mu, &e1, &e2);
+  return normalize((sin_t * std::cos(phi)) * e1 + (sin_t * std::sin(phi)) * e2 + (1.0 - v) * mu);
+}
+
+// ---------------------------------------------------------------- scene
+enum MatType { MAT_ABSORBER = 0, MAT_GRATING = 1, MAT_ROUGH = 2, MAT_MIRROR = 3, MAT_EMITTER = 4 };
+
+struct Material {
+  int type;
+  int fresnel;  // 0: unit reflectance (Mueller identity), 1: conductor (n + i kappa)
+  double n_re, n_im;
+  double period_um, height_um;
+  V3 gdir;
+  double sigma_h_um, corr_len_um;
+  double Le, coh_len_um;
+};
+
+struct Light {
+  int type;  // 0: distant source, 1: constant environment
+  V3 dir;    // unit vector toward the source
+  double E;
+  double coh_len_um;
+};
+
+struct Tri {
+  V3 v0, v1, v2;
+  int mat;
+};
+
+struct Box {
+  V3 lo, hi;
+};
+
+struct BvhNode {
+  Box box;
+  int left, right;  // children (internal) or -1
+  int first, count; // triangle range in order[] (leaf)
+};
+
+struct Scene {
+  std::vector<Tri> tris;
+  std::vector<Material> mats;
+  std::vector<Light> lights;
+  // Emitters: an emitter is the planar set of triangles that share one emitter
+  // material (a quad is two triangles); emitters[i] lists triangle ids and
+  // emitter_of_mat maps a material id to its emitter index (or -1).
+  std::vector<std::vector<int>> emitters;
+  std::vector<int> emitter_of_mat;
+  std::vector<BvhNode> nodes;
+  std::vector<int> order;
+};
+
+Box tri_box(const Tri& t) {
+  Box b;
+  b.lo = v3(std::min({t.v0.x, t.v1.x, t.v2.x}), std::min({t.v0.y, t.v1.y, t.v2.y}),
+            std::min({t.v0.z, t.v1.z, t.v2.z}));
+  b.hi = v3(std::max({t.v0.x, t.v1.x, t.v2.x}), std::max({t.v0.y, t.v1.y, t.v2.y}),
+            std::max({t.v0.z, t.v1.z, t.v2.z}));
+  return b;
+}
+
+// Plain median-split bounding-volume hierarchy over triangle centroids
+// (longest axis of the centroid bounds, leaves of at most 4 triangles).  It is
+// only an accelerator for the oracle's own closest-hit query, checked against
+// an exhaustive scan by the tests.
+int build_bvh(Scene& S, int first, int count) {
+  BvhNode node;
+  Box b = tri_box(S.tris[S.order[first]]);
+  for (int i = first + 1; i < first + count; ++i) {
+    Box t = tri_box(S.tris[S.order[i]]);
+    b.lo = v3(std::min(b.lo.x, t.lo.x), std::min(b.lo.y, t.lo.y), std::min(b.lo.z, t.lo.z));
+    b.hi = v3(std::max(b.hi.x, t.hi.x), std::max(b.hi.y, t.hi.y), std::max(b.hi.z, t.hi.z));
+  }
+  node.box = b;
+  node.left = node.right = -1;
+  node.first = first;
+  node.count = count;
+  int idx = (int)S.nodes.size();
+  S.nodes.push_back(node);
+  if (count <= 4) return idx;
+  auto centroid = [&](int t) {
+    const Tri& tr = S.tris[t];
+    return (1.0 / 3.0) * (tr.v0 + tr.v1 + tr.v2);
+  };
+  V3 clo = centroid(S.order[first]), chi = clo;
+  for (int i = first; i < first + count; ++i) {
+    V3 c = centroid(S.order[i]);
+    clo = v3(std::min(clo.x, c.x), std::min(clo.y, c.y), std::min(clo.z, c.z));
+    chi = v3(std::max(chi.x, c.x), std::max(chi.y, c.y), std::max(chi.z, c.z));
+  }
+  V3 ext = chi - clo;
+  int axis = (ext.x >= ext.y && ext.x >= ext.z) ? 0 : (ext.y >= ext.z ? 1 : 2);
+  auto key = [&](int t) {
+    V3 c = centroid(t);
+    return axis == 0 ? c.x : (axis == 1 ? c.y : c.z);
+  };
+  int mid = first + count / 2;
+  std::nth_element(S.order.begin() + first, S.order.begin() + mid, S.order.begin() + first + count,
+                   [&](int a, int b2) {
+                     double ka = key(a), kb = key(b2);
+                     return ka < kb || (ka == kb && a < b2);
+                   });
+  int l = build_bvh(S, first, mid - first);
+  int r = build_bvh(S, mid, first + count - mid);
+  S.nodes[idx].left = l;
+  S.nodes[idx].right = r;
+  S.nodes[idx].count = 0;
+  return idx;
+}
+
+// Ray-triangle intersection (Moller & Trumbore 1997), double precision, edges
+// inclusive.  Returns the distance t or -1.
+double intersect_tri(const Tri& T, V3 o, V3 d) {
+  V3 e1 = T.v1 - T.v0, e2 = T.v2 - T.v0;
+  V3 p = cross(d, e2);
+  double det = dot(e1, p);
+  if (det == 0.0) return -1.0;
+  double inv = 1.0 / det;
+  V3 s = o - T.v0;
+  double u = dot(s, p) * inv;
+  if (u < 0.0 || u > 1.0) return -1.0;
+  V3 q = cross(s, e1);
+  double v = dot(d, q) * inv;
+  if (v < 0.0 || u + v > 1.0) return -1.0;
+  return dot(e2, q) * inv;
+}
+
+// Self-intersection guard shared by the convention of both implementations:
+// hits closer than T_MIN metres, and the primitive just left, are ignored.
+const double T_MIN = 1e-5;
+
+bool box_hit(const Box& b, V3 o, V3 d, double tmax) {
+  double t0 = 0.0, t1 = tmax;
+  double oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+  double lo[3] = {b.lo.x, b.lo.y, b.lo.z}, hi[3] = {b.hi.x, b.hi.y, b.hi.z};
+  for (int a = 0; a < 3; ++a) {
+    if (dd[a] == 0.0) {
+      if (oo[a] < lo[a] || oo[a] > hi[a]) return false;
+      continue;
+    }
+    double ta = (lo[a] - oo[a]) / dd[a], tb = (hi[a] - oo[a]) / dd[a];
+    if (ta > tb) std::swap(ta, tb);
+    // widen by a relative margin so the box test never rejects a triangle hit
+    double pad = 1e-9 * (std::fabs(ta) + std::fabs(tb)) + 1e-12;
+    ta -= pad;
+    tb += pad;
+    t0 = std::max(t0, ta);
+    t1 = std::min(t1, tb);
+    if (t0 > t1) return false;
+  }
+  return true;
+}
+
+// Closest hit with t > T_MIN, excluding one primitive; equal distances resolve
+// to the lower primitive id.
+bool closest_hit(const Scene& S, V3 o, V3 d, int exclude, bool use_bvh, double* t_out, int* prim_out) {
+  double best = 1e300;
+  int bi = -1;
+  auto test = [&](int i) {
+    if (i == exclude) return;
+    double t = intersect_tri(S.tris[i], o, d);
+    if (t > T_MIN && (t < best || (t == best && i < bi))) {
+      best = t;
+      bi = i;
+    }
+  };
+  if (!use_bvh || S.nodes.empty()) {
+    for (int i = 0; i < (int)S.tris.size(); ++i) test(i);
+  } else {
+    std::vector<int> stack;
+    stack.push_back(0);
+    while (!stack.empty()) {
+      int ni = stack.back();
+      stack.pop_back();
+      const BvhNode& n = S.nodes[ni];
+      if (!box_hit(n.box, o, d, best)) continue;
+      if (n.left < 0) {
+        for (int k = n.first; k < n.first + n.count; ++k) test(S.order[k]);
+      } else {
+        stack.push_back(n.left);
+        stack.push_back(n.right);
+      }
+    }
+  }
+  if (bi < 0) return false;
+  *t_out = best;
+  *prim_out = bi;
+  return true;
+}
+
+V3 tri_normal(const Tri& T) { return normalize(cross(T.v1 - T.v0, T.v2 - T.v0)); }
+
+// ---------------------------------------------------------------- view
+struct View {
+  V3 eye, look, up;
+  double vfov_deg;
+  int W, H;
+  double p_pix_um, f_beta;
+  double lmin_um, lmax_um;
+  int n_bins, n_stokes, max_depth;
+  long spp, first_sample;
+  uint32_t view_index;
+  int ortho;
+  double ortho_half_m;
+};
+
+// Wavelength of bin b: lambda_b = lambda_min + b (lambda_max - lambda_min)/(n_bins - 1)
+// (reading of the hero wavelength as one discrete bin per path, stratified by
+// sample index: b = s mod n_bins).
+double bin_lambda(const View& V, int b) {
+  if (V.n_bins <= 1) return V.lmin_um;
+  return V.lmin_um + (double)b * (V.lmax_um - V.lmin_um) / (double)(V.n_bins - 1);
+}
+
+// ---------------------------------------------------------------- free-space propagation
+// Eq. K_free_space_propagation with zbar = z/|k0| (z in um):
+//   beta_o^2 = beta^2 + 2 zbar rho + zbar^2 (1 + rho^2) / beta^2
+//   rho_o    = rho + zbar (1 + rho^2) / beta^2
+void propagate(double* beta2, double* rho, double zbar) {
+  double b2 = *beta2, r = *rho;
+  double b2o = b2 + 2.0 * zbar * r + zbar * zbar * (1.0 + r * r) / b2;
+  double ro = r + zbar * (1.0 + r * r) / b2;
+  *beta2 = b2o;
+  *rho = ro;
+}
+
+// ---------------------------------------------------------------- polarisation
+typedef std::complex<double> cplx;
+
+// Fresnel amplitude reflection coefficients of a smooth conductor with
+// complex index n = n_re + i n_im (Born & Wolf, Sec. 1.5 / 14.2 sign choice, so
+// that r_p = -r_s at normal incidence):
+//   r_s = (cos_i - n cos_t) / (cos_i + n cos_t),  r_p = (n cos_i - cos_t) / (n cos_i + cos_t)
+// with n cos_t = sqrt(n^2 - sin_i^2) (principal branch).
+void fresnel_conductor(double cos_i, double n_re, double n_im, cplx* rs, cplx* rp) {
+  cplx n(n_re, n_im);
+  double sin2 = std::max(0.0, 1.0 - cos_i * cos_i);
+  cplx n_cos_t = std::sqrt(n * n - sin2);
+  cplx cos_t = n_cos_t / n;
+  *rs = (cos_i - n_cos_t) / (cos_i + n_cos_t);
+  *rp = (n * cos_i - cos_t) / (n * cos_i + cos_t);
+}
+
+struct M4 {
+  double m[4][4];
+};
+M4 m4_identity() {
+  M4 r;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) r.m[i][j] = (i == j) ? 1.0 : 0.0;
+  return r;
+}
+M4 m4_mul(const M4& a, const M4& b) {
+  M4 r;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 4; ++k) s += a.m[i][k] * b.m[k][j];
+      r.m[i][j] = s;
+    }
+  return r;
+}
+
+// Mueller matrix of the Jones matrix diag(a, b) in an (s, p) basis, Stokes
+// convention S = (|Es|^2+|Ep|^2, |Es|^2-|Ep|^2, 2 Re(Es Ep*), -2 Im(Es Ep*)).
+M4 mueller_diag(cplx a, cplx b) {
+  double A = std::norm(a), B = std::norm(b);
+  cplx c = a * std::conj(b);
+  M4 r;
+  std::memset(&r, 0, sizeof r);
+  r.m[0][0] = 0.5 * (A + B);
+  r.m[0][1] = 0.5 * (A - B);
+  r.m[1][0] = 0.5 * (A - B);
+  r.m[1][1] = 0.5 * (A + B);
+  r.m[2][2] = c.real();
+  r.m[2][3] = c.imag();
+  r.m[3][2] = -c.imag();
+  r.m[3][3] = c.real();
+  return r;
+}
+
+// Rotation of the Stokes reference frame: frame B's x axis at angle phi from
+// frame A's x axis (counter-clockwise about the common propagation direction).
+M4 stokes_rotation(double phi) {
+  M4 r = m4_identity();
+  double c = std::cos(2.0 * phi), s = std::sin(2.0 * phi);
+  r.m[1][1] = c;
+  r.m[1][2] = s;
+  r.m[2][1] = -s;
+  r.m[2][2] = c;
+  return r;
+}
+
+// Angle of frame B's x axis measured in frame A = (xa, ya).
+double frame_angle(V3 xa, V3 ya, V3 xb) { return std::atan2(dot(xb, ya), dot(xb, xa)); }
+
+// s vector of a plane of incidence for light propagating along k at a surface
+// with normal n: normalize(n x k); near normal incidence it is undefined and the
+// fallback vector (orthogonalised against k) is used instead.
+V3 s_vector(V3 n, V3 k, V3 fallback) {
+  V3 s = cross(n, k);
+  double l = length(s);
+  if (l > 1e-7) return (1.0 / l) * s;
+  V3 f = fallback - dot(fallback, k) * k;
+  return normalize(f);
+}
+
+// ---------------------------------------------------------------- path state
+struct PathState {
+  V3 o, d;         // mean position (m) and unit propagation direction of the ray
+  double beta2;    // beta^2 (um^2)
+  double rho;
+  double k;        // |k0| (1/um)
+  double lambda;   // um
+  double s_ray2;   // invariant angular variance (sigma_k/|k|)^2 (rad^2)
+  int prev_prim;
+  // throughput: scalar (n_stokes == 1) or Mueller matrix with frame x axis
+  double t;
+  M4 T;
+  V3 xf;
+  // MIS bookkeeping for the vertex that produced the current segment
+  bool prev_delta;  // true after the camera, a specular lobe, a grating order or a mirror
+  double prev_pdf;  // solid-angle density of the current direction at that vertex
+};
+
+struct Ctx {
+  const Scene* S;
+  const View* V;
+  int flags;
+  Rng rng;
+};
+const int FLAG_NEE = 1, FLAG_RR = 2, FLAG_NO_RENORM = 4;
+
+// Angular spread of a source of coherence length lc (Eq. coherence_diffusivity
+// read per axis with Theta = lc^2): s_src = lambda / lc; lc = 0 means spatially
+// coherent (s_src = 0).
+double source_spread2(double lambda, double lc) {
+  if (lc <= 0.0) return 0.0;
+  double s = lambda / lc;
+  return s * s;
+}
+
+// Measurement operator (Eq. measurement_operator) for a distant source: the
+// k-marginal of the generalized ray (Gaussian of angular variance s_ray^2)
+// convolved with the source's angular spread, evaluated on the sphere as a vMF
+// of concentration 1/(s_ray^2 + s_src^2) about the source direction.
+double measure_distant(const Light& L, V3 d, double lambda, double s_ray2) {
+  if (L.type == 1) return L.E;  // constant environment
+  double kappa = 1.0 / (s_ray2 + source_spread2(lambda, L.coh_len_um));
+  return L.E * vmf(d, L.dir, kappa);
+}
+
+// Measurement operator for an emissive triangle hit by the ray (Eq.
+// measurement_operator restricted to the source's support, Sec. 7.2 emissive
+// geometry): one transverse point x ~ N(0, beta^2/2) of the footprint is drawn,
+// projected along d onto the emitter plane and tested for coverage; the local
+// mean direction there is shifted by rho x / (beta^2 |k|) (the conditional
+// mean of the phase-space Gaussian given position) with residual angular
+// variance 1/(2 beta^2 |k|^2); the source emits a Gaussian lobe of spread
+// s_src about its normal.
+double measure_emitter(const Scene& S, int prim, V3 hit, V3 d, double beta2, double rho, double k, double lambda,
+                       double ua, double ub) {
+  const Tri& T = S.tris[prim];
+  const Material& M = S.mats[T.mat];
+  V3 ne = tri_normal(T);
+  if (dot(d, ne) >= 0.0) return 0.0;  // one-sided: only the front face emits
+  double z0, z1;
+  box_muller(ua, ub, &z0, &z1);
+  double sigma = std::sqrt(0.5 * beta2);  // um
+  V3 e1, e2;
+  onb(d, &e1, &e2);
+  V3 x_um = (sigma * z0) * e1 + (sigma * z1) * e2;
+  V3 p = hit + 1e-6 * x_um;
+  double tp = dot(T.v0 - p, ne) / dot(d, ne);
+  V3 q = p + tp * d;
+  // coverage: q inside any triangle of the emitter (barycentric test, edges
+  // inclusive); the emitter's triangles are coplanar
+  bool covered = false;
+  for (int ti : S.emitters[S.emitter_of_mat[T.mat]]) {
+    const Tri& E = S.tris[ti];
+    V3 a = E.v1 - E.v0, b = E.v2 - E.v0, c = q - E.v0;
+    double daa = dot(a, a), dab = dot(a, b), dbb = dot(b, b), dca = dot(c, a), dcb = dot(c, b);
+    double den = daa * dbb - dab * dab;
+    double bu = (dbb * dca - dab * dcb) / den;
+    double bv = (daa * dcb - dab * dca) / den;
+    if (bu >= 0.0 && bv >= 0.0 && bu + bv <= 1.0) {
+      covered = true;
+      break;
+    }
+  }
+  if (!covered) return 0.0;
+  V3 mu = (rho / (beta2 * k)) * x_um;
+  V3 dl = normalize(d + mu);
+  double sc2 = 1.0 / (2.0 * beta2 * k * k);
+  double kappa = 1.0 / (sc2 + source_spread2(lambda, M.coh_len_um));
+  return M.Le * vmf(neg(dl), ne, kappa);
+}
+
+// ---------------------------------------------------------------- interactions
+// Diffraction grating (Eq. K_grating): orders j with weight J_j(h k / 2)^2 and
+// tangential direction cosines t_j = t_in + j (lambda/Lambda) g (the grating
+// equation sin(theta_o) = sin(theta_i) - j lambda/Lambda, written in the
+// conical vector form; the sign of j is immaterial as J_{-j}^2 = J_j^2).
+// Evanescent orders (|t_j| >= 1) are dropped and the weights renormalised over
+// the propagating ones (reading; FLAG_NO_RENORM keeps the raw weights).
+struct Lobes {
+  int n;
+  int order[128];
+  double w[128];
+  V3 dir[128];
+  double total;
+};
+void grating_lobes(const Material& M, V3 d_in, V3 n, double lambda, bool renorm, Lobes* L) {
+  V3 t_in = d_in - dot(d_in, n) * n;
+  V3 g = M.gdir - dot(M.gdir, n) * n;
+  if (length(g) < 1e-9) {
+    V3 e1, e2;
+    onb(n, &e1, &e2);
+    g = e1;
+  }
+  g = normalize(g);
+  double x = PI * M.height_um / lambda;  // h k / 2
+  double step = lambda / M.period_um;
+  int jmax = (int)std::floor(2.0 / step) + 1;
+  if (jmax > 63) jmax = 63;
+  L->n = 0;
+  L->total = 0.0;
+  for (int j = -jmax; j <= jmax; ++j) {
+    V3 t = t_in + (j * step) * g;
+    double tt = dot(t, t);
+    if (tt >= 1.0) continue;
+    double J = bessel_j(j, x);
+    int i = L->n++;
+    L->order[i] = j;
+    L->w[i] = J * J;
+    L->dir[i] = t + std::sqrt(1.0 - tt) * n;
+    L->total += J * J;
+  }
+  if (!renorm) L->total = 1.0;
+}
+
+// Rough surface lobe (Eq. K_surface_HS with the Harvey-Shack f_HS read as the
+// Kirchhoff series of a Gaussian-correlated surface, Beckmann & Spizzichino
+// 1963): roughness parameter g = (2 |k| sigma_h cos(theta_i))^2; specular part
+// with weight e^{-g}; term m >= 1 (Poisson weight e^{-g} g^m / m!) is a 2D
+// Gaussian in tangential direction cosines about the mirror direction with
+// per-axis variance 2m / (|k| l)^2.  For g > 50 the series is replaced by its
+// continuous limit, a single Gaussian with m = g and no specular part.
+// Samples landing at |t| >= 1 are evanescent and carry no energy (weight 0).
+const double G_CONT = 50.0;
+
+double gauss2(V3 delta, double var) { return std::exp(-0.5 * dot(delta, delta) / var) / (2.0 * PI * var); }
+
+// Density of the diffuse (m >= 1) part in tangential direction cosines.
+double rough_diffuse_density(double g, double k, double ell, V3 delta) {
+  double kl2 = (k * ell) * (k * ell);
+  if (g > G_CONT) return gauss2(delta, 2.0 * g / kl2);
+  double p = std::exp(-g);
+  double cdf = p;
+  double sum = 0.0;
+  // include every m the sampler can return (until the Poisson CDF passes 1 - 2^-24)
+  for (int m = 1; m < 1000; ++m) {
+    p *= g / m;
+    cdf += p;
+    sum += p * gauss2(delta, 2.0 * m / kl2);
+    if (cdf > 1.0 - 1.0 / 16777216.0 && p < 1e-12) break;
+  }
+  return sum;
+}
+
+// ---------------------------------------------------------------- one path sample
+void add_vec(double* acc, int ns, const double* v, double s) {
+  for (int i = 0; i < ns; ++i) acc[i] += v[i] * s;
+}
+
+// Throughput applied to an unpolarised source of unit intensity: first column.
+void throughput_column(const PathState& P, int ns, double* out) {
+  if (ns == 1) {
+    out[0] = P.t;
+    return;
+  }
+  for (int i = 0; i < 4; ++i) out[i] = P.T.m[i][0];
+}
+
+void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
+  const Scene& S = *C.S;
+  const View& V = *C.V;
+  const int ns = V.n_stokes;
+  for (int i = 0; i < 4; ++i) result[i] = 0.0;
+  Rng rng = C.rng;
+  rng.pixel = (uint32_t)(py * V.W + px);
+  rng.sample = (uint32_t)sample;
+
+  // --- sourcing (Eq. MC_sourcing; Sec. 7.2): position uniform on the pixel,
+  // rho = 0, beta = f_beta * pixel pitch, alpha = 1, wavelength of bin s mod B.
+  double u[4];
+  rng.draw(0, CALL_JITTER, u);
+  int bin = (int)(sample % V.n_bins);
+  PathState P;
+  P.lambda = bin_lambda(V, bin);
+  P.k = 2.0 * PI / P.lambda;
+  double beta0 = V.f_beta * V.p_pix_um;
+  P.beta2 = beta0 * beta0;
+  P.rho = 0.0;
+  P.s_ray2 = (1.0 + P.rho * P.rho) / (2.0 * P.beta2) / (P.k * P.k);
+  V3 fw = normalize(V.look - V.eye);
+  V3 right = normalize(cross(fw, V.up));
+  V3 upc = cross(right, fw);
+  double aspect = (double)V.W / (double)V.H;
+  double fx = (px + u[0]) / V.W, fy = (py + u[1]) / V.H;
+  if (V.ortho) {
+    P.o = V.eye + ((2.0 * fx - 1.0) * V.ortho_half_m * aspect) * right + ((1.0 - 2.0 * fy) * V.ortho_half_m) * upc;
+    P.d = fw;
+  } else {
+    double th = std::tan(0.5 * V.vfov_deg * PI / 180.0);
+    double sx = (2.0 * fx - 1.0) * th * aspect;
+    double sy = (1.0 - 2.0 * fy) * th;
+    P.o = V.eye;
+    P.d = normalize(fw + sx * right + sy * upc);
+  }
+  P.prev_prim = -1;
+  P.t = 1.0;
+  P.T = m4_identity();
+  P.xf = normalize(right - dot(right, P.d) * P.d);
+  P.prev_delta = true;
+  P.prev_pdf = 0.0;
+  const int n_emit = (int)S.emitters.size();
+
+  for (int seg = 0;; ++seg) {
+    // --- propagation: closest hit along d (point-hit assumption, Sec. 7.2)
+    double th;
+    int prim;
+    bool hit = closest_hit(S, P.o, P.d, P.prev_prim, true, &th, &prim);
+    double col[4];
+    throughput_column(P, ns, col);
+    if (!hit) {
+      // --- measurement of distant sources on escape
+      double m = 0.0;
+      for (const Light& L : S.lights) m += measure_distant(L, P.d, P.lambda, P.s_ray2);
+      add_vec(result, ns, col, m);
+      return;
+    }
+    // footprint update over the segment (z in um)
+    propagate(&P.beta2, &P.rho, th * 1e6 / P.k);
+    V3 x = P.o + th * P.d;
+    const Tri& T = S.tris[prim];
+    const Material& M = S.mats[T.mat];
+    if (M.type == MAT_EMITTER) {
+      rng.draw(seg, CALL_EMIT_FOOT, u);
+      double m = measure_emitter(S, prim, x, P.d, P.beta2, P.rho, P.k, P.lambda, u[0], u[1]);
+      double w = 1.0;
+      if ((C.flags & FLAG_NEE) && !P.prev_delta && n_emit > 0) {
+        V3 ne = tri_normal(T);
+        double kap = 1.0 / (P.s_ray2 + source_spread2(P.lambda, M.coh_len_um));
+        double pn = vmf(neg(P.d), ne, kap) / n_emit;
+        double pb = P.prev_pdf;
+        w = pb * pb / (pb * pb + pn * pn);
+      }
+      add_vec(result, ns, col, m * w);
+      return;
+    }
+    if (M.type == MAT_ABSORBER) return;
+    if (seg >= V.max_depth) return;  // no interactions left
+    // Russian roulette before interaction seg+1 once 3 interactions are done
+    if ((C.flags & FLAG_RR) && seg >= 3) {
+      double q = std::min(1.0, std::max(0.05, ns == 1 ? P.t : P.T.m[0][0]));
+      rng.draw(seg, CALL_RR, u);
+      if (u[0] >= q) return;
+      if (ns == 1)
+        P.t /= q;
+      else
+        for (int i = 0; i < 4; ++i)
+          for (int j = 0; j < 4; ++j) P.T.m[i][j] /= q;
+    }
+
+    // --- light-matter interaction with the wavevector reversed (Eq.
+    // action_time_reversal): the surface normal is oriented against d.
+    V3 n = tri_normal(T);
+    if (dot(n, P.d) > 0.0) n = neg(n);
+    double cos_i = -dot(P.d, n);
+    V3 d_in = P.d;
+
+    // Fresnel weight (Eq. K_reflection_refraction), as a Mueller matrix in the
+    // s-p frames at the incidence angle of the arriving ray; diffractive lobes
+    // are scaled by the same matrix (reading).
+    M4 MF = m4_identity();
+    if (M.fresnel == 1) {
+      cplx rs, rp;
+      fresnel_conductor(cos_i, M.n_re, M.n_im, &rs, &rp);
+      MF = mueller_diag(rs, rp);
+    }
+    // frame of the outgoing light of the forward problem (propagation -d_in)
+    V3 k_o = neg(d_in);
+    V3 s_o = s_vector(n, k_o, P.xf);
+    V3 p_o = cross(k_o, s_o);
+    V3 y_cur = cross(k_o, P.xf);
+    M4 Rot = stokes_rotation(frame_angle(s_o, p_o, P.xf));  // frame o -> current frame
+    (void)y_cur;
+    M4 TRM = m4_mul(m4_mul(P.T, Rot), MF);
+    double t_new = P.t * MF.m[0][0];
+    double c_nee[4];
+    if (ns == 1)
+      c_nee[0] = t_new;
+    else
+      for (int i = 0; i < 4; ++i) c_nee[i] = TRM.m[i][0];
+
+    // --- sample the scattered distribution (Eq. MC_light_transport_Q1)
+    rng.draw(seg, CALL_LOBE, u);
+    V3 d_out;
+    bool delta = true;
+    double pdf = 0.0;
+    bool alive = true;
+    double g_r = 0.0;
+    V3 t_mir = d_in - dot(d_in, n) * n;
+    if (M.type == MAT_GRATING) {
+      Lobes L;
+      grating_lobes(M, d_in, n, P.lambda, !(C.flags & FLAG_NO_RENORM), &L);
+      if (L.n == 0) return;
+      // first order (ascending j) whose cumulative weight exceeds u * total
+      double target = u[0] * L.total;
+      double cum = 0.0;
+      int pick = -1;
+      for (int i = 0; i < L.n; ++i) {
+        cum += L.w[i];
+        if (cum > target) {
+          pick = i;
+          break;
+        }
+      }
+      if (pick < 0) return;  // only possible without renormalisation
+      d_out = L.dir[pick];
+    } else if (M.type == MAT_MIRROR) {
+      d_out = d_in + (2.0 * cos_i) * n;
+    } else {  // MAT_ROUGH
+      g_r = std::pow(2.0 * P.k * M.sigma_h_um * cos_i, 2);
+      double m;
+      if (g_r > G_CONT) {
+        m = g_r;
+      } else {
+        // Poisson(g) by sequential inversion: first m with CDF(m) > u
+        double p = std::exp(-g_r), cdf = p;
+        int mi = 0;
+        while (u[0] >= cdf && mi < 1000) {
+          ++mi;
+          p *= g_r / mi;
+          cdf += p;
+        }
+        m = mi;
+      }
+      if (m == 0.0) {
+        d_out = d_in + (2.0 * cos_i) * n;
+      } else {
+        delta = false;
+        double kl = P.k * M.corr_len_um;
+        double sig = std::sqrt(2.0 * m / (kl * kl));
+        double z0, z1;
+        box_muller(u[1], u[2], &z0, &z1);
+        V3 e1, e2;
+        onb(n, &e1, &e2);
+        V3 delta_t = (sig * z0) * e1 + (sig * z1) * e2;
+        V3 t_out = t_mir + delta_t;
+        double tt = dot(t_out, t_out);
+        if (tt >= 1.0) {
+          alive = false;  // evanescent: no propagating energy
+        } else {
+          d_out = t_out + std::sqrt(1.0 - tt) * n;
+          pdf = rough_diffuse_density(g_r, P.k, M.corr_len_um, delta_t) * std::sqrt(1.0 - tt);
+        }
+      }
+    }
+
+    // --- next-event estimation toward an emissive triangle (rough lobes only:
+    // grating orders and mirror reflection are delta lobes)
+    if (M.type == MAT_ROUGH && (C.flags & FLAG_NEE) && n_emit > 0) {
+      double un[4], uf[4];
+      rng.draw(seg, CALL_NEE_DIR, un);
+      int ei = std::min(n_emit - 1, (int)(un[0] * n_emit));
+      const Tri& ET = S.tris[S.emitters[ei][0]];
+      const int emat = ET.mat;
+      const Material& EM = S.mats[emat];
+      V3 ne = tri_normal(ET);
+      double kap = 1.0 / (P.s_ray2 + source_spread2(P.lambda, EM.coh_len_um));
+      V3 w = vmf_sample(neg(ne), kap, un[1], un[2]);
+      double cos_o = dot(w, n);
+      if (cos_o > 0.0) {
+        double ts;
+        int sp;
+        if (closest_hit(S, x, w, prim, true, &ts, &sp) && S.tris[sp].mat == emat) {
+          V3 delta_t = (w - dot(w, n) * n) - t_mir;
+          double f = (g_r > 0.0 ? rough_diffuse_density(g_r, P.k, M.corr_len_um, delta_t) : 0.0) * cos_o;
+          double pn = vmf(w, neg(ne), kap) / n_emit;
+          if (f > 0.0 && pn > 0.0) {
+            double b2 = P.beta2, r = P.rho;
+            propagate(&b2, &r, ts * 1e6 / P.k);
+            rng.draw(seg, CALL_NEE_FOOT, uf);
+            double m = measure_emitter(S, sp, x + ts * w, w, b2, r, P.k, P.lambda, uf[0], uf[1]);
+            double wmis = pn * pn / (pn * pn + f * f);
+            add_vec(result, ns, c_nee, m * f / pn * wmis);
+          }
+        }
+      }
+    }
+    if (!alive) return;
+
+    // --- continue the path with the sampled generalized ray: position and
+    // (beta, rho) unchanged by the interaction (Eq. K_reflection_refraction;
+    // rho growth at the grating ignored, Eq. K_grating).
+    if (ns == 1) {
+      P.t = t_new;
+    } else {
+      P.T = TRM;
+      V3 k_i = neg(d_out);
+      P.xf = s_vector(n, k_i, s_o);
+    }
+    P.o = x;
+    P.d = d_out;
+    P.prev_prim = prim;
+    P.prev_delta = delta;
+    P.prev_pdf = pdf;
+  }
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+int oracle_abi_version() { return 1; }
+
+void oracle_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) { philox4x32_10(ctr, key, out); }
+
+double oracle_bessel_j(int n, double x) { return bessel_j(n, x); }
+
+double oracle_vmf(const double* w, const double* mu, double kappa) {
+  return vmf(v3(w[0], w[1], w[2]), v3(mu[0], mu[1], mu[2]), kappa);
+}
+
+void oracle_vmf_sample(const double* mu, double kappa, double u0, double u1, double* out) {
+  V3 r = vmf_sample(v3(mu[0], mu[1], mu[2]), kappa, u0, u1);
+  out[0] = r.x;
+  out[1] = r.y;
+  out[2] = r.z;
+}
+
+void oracle_onb(const double* n, double* e1, double* e2) {
+  V3 a, b;
+  onb(v3(n[0], n[1], n[2]), &a, &b);
+  e1[0] = a.x; e1[1] = a.y; e1[2] = a.z;
+  e2[0] = b.x; e2[1] = b.y; e2[2] = b.z;
+}
+
+void oracle_propagate(double beta2, double rho, double zbar, double* out) {
+  propagate(&beta2, &rho, zbar);
+  out[0] = beta2;
+  out[1] = rho;
+}
+
+// Material parameter vector (float32[16]) and light vector (float32[8]) layout:
+// see oracle/oracle.py.
+static Material read_material(const float* m) {
+  Material M;
+  M.type = (int)m[0];
+  M.fresnel = (int)m[1];
+  M.n_re = m[2];
+  M.n_im = m[3];
+  M.period_um = m[4];
+  M.height_um = m[5];
+  M.gdir = v3(m[6], m[7], m[8]);
+  M.sigma_h_um = m[9];
+  M.corr_len_um = m[10];
+  M.Le = m[11];
+  M.coh_len_um = m[12];
+  return M;
+}
+
+// Grating lobes for one incidence (test access).  Returns the number of
+// propagating orders written (orders[i], weights[i] normalised by the total,
+// dirs[3i..3i+2]).
+int oracle_grating_lobes(const float* mat, const double* d_in, const double* n, double lambda_um, int renorm,
+                         int cap, int* orders, double* weights, double* dirs) {
+  Material M = read_material(mat);
+  Lobes L;
+  grating_lobes(M, v3(d_in[0], d_in[1], d_in[2]), v3(n[0], n[1], n[2]), lambda_um, renorm != 0, &L);
+  int k = std::min(cap, L.n);
+  for (int i = 0; i < k; ++i) {
+    orders[i] = L.order[i];
+    weights[i] = L.w[i] / L.total;
+    dirs[3 * i] = L.dir[i].x;
+    dirs[3 * i + 1] = L.dir[i].y;
+    dirs[3 * i + 2] = L.dir[i].z;
+  }
+  return L.n;
+}
+
+double oracle_rough_density(double g, double k, double ell, double dx, double dy) {
+  return rough_diffuse_density(g, k, ell, v3(dx, dy, 0.0));
+}
+
+void oracle_fresnel_mueller(double cos_i, double n_re, double n_im, double* out16, double* rs_rp4) {
+  cplx rs, rp;
+  fresnel_conductor(cos_i, n_re, n_im, &rs, &rp);
+  M4 M = mueller_diag(rs, rp);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) out16[4 * i + j] = M.m[i][j];
+  if (rs_rp4) {
+    rs_rp4[0] = rs.real();
+    rs_rp4[1] = rs.imag();
+    rs_rp4[2] = rp.real();
+    rs_rp4[3] = rp.imag();
+  }
+}
+
+void oracle_stokes_rotation(double phi, double* out16) {
+  M4 M = stokes_rotation(phi);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) out16[4 * i + j] = M.m[i][j];
+}
+
+void* oracle_scene_create(int n_tris, const float* verts, const int* tri_mat, int n_mats, const float* mats,
+                          int n_lights, const float* lights) {
+  Scene* S = new Scene();
+  S->tris.resize(n_tris);
+  for (int i = 0; i < n_tris; ++i) {
+    const float* v = verts + 9 * i;
+    S->tris[i].v0 = v3(v[0], v[1], v[2]);
+    S->tris[i].v1 = v3(v[3], v[4], v[5]);
+    S->tris[i].v2 = v3(v[6], v[7], v[8]);
+    S->tris[i].mat = tri_mat[i];
+  }
+  for (int i = 0; i < n_mats; ++i) S->mats.push_back(read_material(mats + 16 * i));
+  for (int i = 0; i < n_lights; ++i) {
+    const float* l = lights + 8 * i;
+    Light L;
+    L.type = (int)l[0];
+    L.dir = v3(l[1], l[2], l[3]);
+    if (L.type == 0) L.dir = normalize(L.dir);
+    L.E = l[4];
+    L.coh_len_um = l[5];
+    S->lights.push_back(L);
+  }
+  S->emitter_of_mat.assign(n_mats, -1);
+  for (int i = 0; i < n_tris; ++i) {
+    int m = S->tris[i].mat;
+    if (S->mats[m].type != MAT_EMITTER) continue;
+    if (S->emitter_of_mat[m] < 0) {
+      S->emitter_of_mat[m] = (int)S->emitters.size();
+      S->emitters.push_back(std::vector<int>());
+    }
+    S->emitters[S->emitter_of_mat[m]].push_back(i);
+  }
+  if (n_tris > 0) {
+    S->order.resize(n_tris);
+    for (int i = 0; i < n_tris; ++i) S->order[i] = i;
+    build_bvh(*S, 0, n_tris);
+  }
+  return S;
+}
+
+void oracle_scene_destroy(void* s) { delete (Scene*)s; }
+
+int oracle_closest_hit(void* s, const double* o, const double* d, int exclude, int use_bvh, double* t, int* prim) {
+  Scene* S = (Scene*)s;
+  double tt = 0.0;
+  int pp = -1;
+  bool h = closest_hit(*S, v3(o[0], o[1], o[2]), v3(d[0], d[1], d[2]), exclude, use_bvh != 0, &tt, &pp);
+  *t = h ? tt : -1.0;
+  *prim = h ? pp : -1;
+  return h ? 1 : 0;
+}
+
+// View parameter vector (double[24]):
+//  0-2 eye, 3-5 look_at, 6-8 up, 9 vfov_deg, 10 W, 11 H, 12 p_pix_um, 13 f_beta,
+//  14 lambda_min_um, 15 lambda_max_um, 16 n_bins, 17 n_stokes, 18 max_depth,
+//  19 spp, 20 first_sample, 21 view_index, 22 ortho (0/1), 23 ortho half height (m)
+static View read_view(const double* p) {
+  View V;
+  V.eye = v3(p[0], p[1], p[2]);
+  V.look = v3(p[3], p[4], p[5]);
+  V.up = v3(p[6], p[7], p[8]);
+  V.vfov_deg = p[9];
+  V.W = (int)p[10];
+  V.H = (int)p[11];
+  V.p_pix_um = p[12];
+  V.f_beta = p[13];
+  V.lmin_um = p[14];
+  V.lmax_um = p[15];
+  V.n_bins = (int)p[16];
+  V.n_stokes = (int)p[17];
+  V.max_depth = (int)p[18];
+  V.spp = (long)p[19];
+  V.first_sample = (long)p[20];
+  V.view_index = (uint32_t)p[21];
+  V.ortho = (int)p[22];
+  V.ortho_half_m = p[23];
+  return V;
+}
+
+// One path sample's contribution (n_stokes values) for tests.
+void oracle_trace_sample(void* s, const double* view, uint32_t seed, int flags, int px, int py, long sample,
+                         double* out4) {
+  Scene* S = (Scene*)s;
+  View V = read_view(view);
+  Ctx C;
+  C.S = S;
+  C.V = &V;
+  C.flags = flags;
+  C.rng.key[0] = seed;
+  C.rng.key[1] = V.view_index;
+  trace_sample(C, px, py, sample, out4);
+}
+
+// Render the pixels of the crop [x0,x1) x [y0,y1): for every pixel and bin, the
+// mean over the samples s in [first_sample, first_sample + spp) with
+// s mod n_bins == bin, summed in sample order with compensated (Neumaier)
+// summation.  out_mean: [crop_h][crop_w][n_bins][n_stokes]; out_var (optional):
+// the per-sample variance of the same values.  Returns the number of samples.
+long oracle_render(void* s, const double* view, uint32_t seed, int flags, int x0, int y0, int x1, int y1,
+                   int n_threads, double* out_mean, double* out_var) {
+  Scene* S = (Scene*)s;
+  View V = read_view(view);
+  Ctx C;
+  C.S = S;
+  C.V = &V;
+  C.flags = flags;
+  C.rng.key[0] = seed;
+  C.rng.key[1] = V.view_index;
+  const int cw = x1 - x0, ch = y1 - y0;
+  const int nb = V.n_bins, ns = V.n_stokes;
+  std::atomic<int> next_row(0);
+  auto worker = [&]() {
+    std::vector<double> sum(nb * 4), comp(nb * 4), sq(nb * 4);
+    std::vector<long> cnt(nb);
+    for (;;) {
+      int r = next_row.fetch_add(1);
+      if (r >= ch) break;
+      int py = y0 + r;
+      for (int px = x0; px < x1; ++px) {
+        std::fill(sum.begin(), sum.end(), 0.0);
+        std::fill(comp.begin(), comp.end(), 0.0);
+        std::fill(sq.begin(), sq.end(), 0.0);
+        std::fill(cnt.begin(), cnt.end(), 0L);
+        for (long si = 0; si < V.spp; ++si) {
+          long smp = V.first_sample + si;
+          double c[4];
+          trace_sample(C, px, py, smp, c);
+          int b = (int)(smp % nb);
+          cnt[b]++;
+          for (int k = 0; k < ns; ++k) {
+            // Neumaier compensated summation
+            double a = sum[b * 4 + k], v = c[k];
+            double t = a + v;
+            if (std::fabs(a) >= std::fabs(v))
+              comp[b * 4 + k] += (a - t) + v;
+            else
+              comp[b * 4 + k] += (v - t) + a;
+            sum[b * 4 + k] = t;
+            sq[b * 4 + k] += v * v;
+          }
+        }
+        size_t base = ((size_t)r * cw + (px - x0)) * nb * ns;
+        for (int b = 0; b < nb; ++b)
+          for (int k = 0; k < ns; ++k) {
+            double tot = sum[b * 4 + k] + comp[b * 4 + k];
+            double mean = cnt[b] ? tot / cnt[b] : 0.0;
+            out_mean[base + b * ns + k] = mean;
+            if (out_var) out_var[base + b * ns + k] = cnt[b] ? sq[b * 4 + k] / cnt[b] - mean * mean : 0.0;
+          }
+      }
+    }
+  };
+  int nt = std::max(1, n_threads);
+  std::vector<std::thread> th;
+  for (int i = 0; i < nt; ++i) th.emplace_back(worker);
+  for (auto& t : th) t.join();
+  return (long)cw * ch * V.spp;
+}
+
+}  // extern "C"
