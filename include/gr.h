@@ -1,0 +1,216 @@
+/* gr.h -- C ABI of the GB300 generalized-ray path tracer (libgr.so).
+ *
+ * Backward (sensor-to-source) Monte Carlo transport of generalized rays,
+ * "A Generalized Ray Formulation For Wave-Optics Rendering" (Steinberg et al.,
+ * arXiv 2303.15762):
+ *   - a pixel sources generalized rays {r0, k0, beta, rho = 0}      (Sec. 4.1, Eq. MC_sourcing;
+ *     detector as coherent states, Sec. 3.2, Eq. wdf_coherent_states)
+ *   - rays propagate by ray tracing, their footprint per Eq. K_free_space_propagation
+ *     (interactive simplification, Sec. 7.2)
+ *   - at a surface the interaction acts on the wavevector-reversed ray  (Eq. action_time_reversal)
+ *     and one child ray is sampled                                      (Eq. MC_light_transport_Q1):
+ *     grating orders (Eq. K_grating), rough-surface lobe (Eq. K_surface_HS),
+ *     smooth reflection with a Fresnel Mueller weight (Eq. K_reflection_refraction)
+ *   - light sources are integrated by the measurement operator          (Eq. measurement_operator)
+ *   - the per-pixel intensity is the sample mean                        (Algorithm 1)
+ * The output is the intensity per detector element: per view, pixel, spectral
+ * bin and Stokes component.
+ *
+ * Conventions (all calls):
+ *   - every call returns gr_status; out-pointers are written only on GR_OK;
+ *     gr_last_error() gives a thread-local message for the last failure;
+ *     no C++ exception crosses this boundary.
+ *   - host pointers are read during the call only (the caller keeps ownership);
+ *     device pointers passed in are borrowed until the work enqueued on the
+ *     given stream completes.
+ *   - stream arguments are cudaStream_t values passed as void* (NULL = the
+ *     legacy default stream); work is enqueued asynchronously and the caller
+ *     synchronises on its own stream.
+ *   - units: scene geometry in metres; optical lengths (wavelengths, grating
+ *     period and height, roughness, correlation and coherence lengths, pixel
+ *     pitch) in micrometres.
+ */
+#ifndef GR_H
+#define GR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GR_OK = 0,
+  GR_E_INVALID = 1, /* bad argument or descriptor */
+  GR_E_OOM = 2,     /* device allocation failed */
+  GR_E_CUDA = 3,    /* a CUDA runtime call failed */
+  GR_E_TIMEOUT = 4, /* the render loop exceeded its iteration limit */
+  GR_E_BUSY = 5     /* object in use */
+} gr_status;
+
+typedef struct gr_scene gr_scene;
+typedef struct gr_frame gr_frame;
+
+/* Material kinds (interaction operators, Sec. 6). */
+enum {
+  GR_MAT_ABSORBER = 0, /* black: terminates paths */
+  GR_MAT_GRATING = 1,  /* sinusoidal grating, Eq. K_grating */
+  GR_MAT_ROUGH = 2,    /* Gaussian-statistics rough surface, Eq. K_surface_HS */
+  GR_MAT_MIRROR = 3,   /* smooth reflector, Eq. K_reflection_refraction */
+  GR_MAT_EMITTER = 4   /* emissive geometry light source (Sec. 7.2) */
+};
+
+/* One material, 64 bytes.  fresnel: 0 = unit reflectance (Mueller identity),
+ * 1 = conductor with complex index n_re + i n_im (Fresnel Mueller matrix at the
+ * incidence angle, also scaling diffractive lobes).
+ * Grating: period_um (Lambda), height_um (h, peak to peak; order weights
+ * J_j(h k / 2)^2), gdir = grating vector direction in world space (projected
+ * onto the surface tangent plane at the hit).
+ * Rough: sigma_h_um (RMS height), corr_len_um (Gaussian correlation length).
+ * Emitter: Le (exitance), coh_len_um (coherence length; angular spread
+ * lambda / coh_len per axis, Eq. coherence_diffusivity; 0 = coherent).  An
+ * emitter is the planar set of triangles carrying the same emitter material;
+ * only its front face (counter-clockwise winding) emits. */
+typedef struct {
+  int32_t type;
+  int32_t fresnel;
+  float n_re, n_im;
+  float period_um, height_um;
+  float gdir[3];
+  float sigma_h_um, corr_len_um;
+  float Le, coh_len_um;
+  float reserved[3];
+} gr_material;
+
+/* Light sources measured on escape (Sec. 7.2): distant source of irradiance E
+ * toward unit direction dir with coherence length coh_len_um (0 = spatially
+ * coherent), or a constant environment of radiance E (dir ignored). 32 bytes. */
+enum { GR_LIGHT_DISTANT = 0, GR_LIGHT_ENV = 1 };
+typedef struct {
+  int32_t type;
+  float dir[3];
+  float E;
+  float coh_len_um;
+  float reserved[2];
+} gr_light;
+
+/* Scene description (host memory, read during gr_scene_create only).
+ * verts: float32 [n_tris][3][3] (three vertices, xyz); tri_mat: int32 [n_tris]
+ * material index per triangle.  n_tris may be 0 (every ray escapes). */
+typedef struct {
+  int32_t n_tris;
+  const float* verts;
+  const int32_t* tri_mat;
+  int32_t n_mats;
+  const gr_material* mats;
+  int32_t n_lights;
+  const gr_light* lights;
+} gr_scene_desc;
+
+/* A detector (Sec. 3.2 detector distribution D): a pinhole camera (or an
+ * orthographic one, ortho = 1) of width x height pixels, each sourcing
+ * generalized rays with beta = f_beta * p_pix_um, rho = 0, alpha = 1 and one
+ * wavelength per path from n_bins bins spanning [lambda_min_um, lambda_max_um]
+ * (bin b = sample mod n_bins).  n_stokes is 1 (unpolarised intensity) or 4
+ * (Stokes vector in the camera's right/up frame).  max_depth counts surface
+ * interactions.  A render adds the samples [first_sample, first_sample + spp)
+ * of every pixel.  view_index keys the random stream; scene_index selects the
+ * scene in gr_render's scene list.  100 bytes. */
+typedef struct {
+  float eye[3], look_at[3], up[3];
+  float vfov_deg;
+  int32_t width, height;
+  float p_pix_um, f_beta;
+  float lambda_min_um, lambda_max_um;
+  int32_t n_bins, n_stokes, max_depth;
+  int32_t spp, first_sample;
+  int32_t view_index, scene_index;
+  int32_t ortho;
+  float ortho_half_m;
+} gr_view_desc;
+
+/* Render options.  flags: GR_FLAG_NEE next-event estimation toward emitters
+ * with power-heuristic MIS; GR_FLAG_RR Russian roulette after 3 interactions;
+ * GR_FLAG_NO_RENORM keeps raw grating order weights (no renormalisation over
+ * propagating orders).  table_dtype: storage of the grating order tables
+ * (GR_TABLE_F32 / F16 / BF16); arithmetic is FP32 either way.  pool_size:
+ * wavefront slots (0 = default); block: threads per block (0 = default). */
+enum { GR_FLAG_NEE = 1, GR_FLAG_RR = 2, GR_FLAG_NO_RENORM = 4 };
+enum { GR_TABLE_F32 = 0, GR_TABLE_F16 = 1, GR_TABLE_BF16 = 2 };
+typedef struct {
+  uint32_t seed;
+  int32_t flags;
+  int32_t table_dtype;
+  int32_t pool_size;
+  int32_t block;
+  int32_t use_graph;     /* 1: replay the wavefront iteration as a CUDA graph */
+  int32_t max_iterations; /* 0 = default bound; exceeding it returns GR_E_TIMEOUT */
+  int32_t reserved;
+} gr_render_opts;
+
+/* Render statistics of the last gr_render on a frame (device-side counters,
+ * read after the stream is synchronised). */
+typedef struct {
+  int64_t samples;        /* path samples completed */
+  int64_t segments;       /* ray segments traced (camera + continuation) */
+  int64_t shadow_rays;    /* NEE shadow rays traced */
+  int64_t refine64_hits;  /* ray-triangle tests decided in FP64 */
+  int64_t refine64_lobes; /* grating / Poisson choices decided in FP64 */
+  int64_t iterations;     /* wavefront iterations */
+  int64_t kernel_launches;
+} gr_stats;
+
+/* Upload a scene and build its BVH (Karras LBVH, 30-bit Morton codes; integer
+ * topology and FP32 bounds are deterministic).  desc arrays are host memory
+ * and are copied; the library owns the device copy until gr_scene_destroy.
+ * Errors: GR_E_INVALID (null/negative sizes, material index out of range,
+ * unknown material or light type), GR_E_OOM, GR_E_CUDA. */
+gr_status gr_scene_create(const gr_scene_desc* desc, void* cuda_stream, gr_scene** out);
+gr_status gr_scene_destroy(gr_scene* scene);
+
+/* Frame = device accumulators for n_views views: for each view, float32 sum
+ * and Kahan compensation per [bin][y][x][stokes], plus per-bin sample counts
+ * (host side).  Library-owned device memory, zero-initialised on stream.
+ * Errors: GR_E_INVALID, GR_E_OOM, GR_E_CUDA. */
+gr_status gr_frame_create(const gr_view_desc* views, int32_t n_views, void* cuda_stream, gr_frame** out);
+gr_status gr_frame_reset(gr_frame* frame, void* cuda_stream);
+gr_status gr_frame_release(gr_frame* frame);
+
+/* Enqueue the samples [first_sample, first_sample + spp) of every view on the
+ * stream, adding them into frame (which must have been created for views of
+ * the same shapes).  scenes[view.scene_index] supplies each view's scene.
+ * Accumulation is per pixel and bin in sample order (deterministic).
+ * Errors: GR_E_INVALID (shape mismatch, bad scene index, bad options),
+ * GR_E_OOM, GR_E_CUDA, GR_E_TIMEOUT (iteration bound exceeded; the frame's
+ * accumulators are then incomplete). */
+gr_status gr_render(gr_scene* const* scenes, int32_t n_scenes, const gr_view_desc* views, int32_t n_views,
+                    const gr_render_opts* opts, gr_frame* frame, void* cuda_stream);
+
+/* Copy view `view`'s mean image, float32 [height][width][n_bins][n_stokes]
+ * (sum / count per bin, 0 where a bin has no samples), to dst (device memory
+ * if dst_is_device, else host memory; host copies complete before return).
+ * dst_bytes must be at least the image size.  Errors: GR_E_INVALID, GR_E_CUDA. */
+gr_status gr_readback(gr_frame* frame, int32_t view, float* dst, size_t dst_bytes, int32_t dst_is_device,
+                      void* cuda_stream);
+
+/* Statistics of the last gr_render on this frame (synchronises the stream). */
+gr_status gr_frame_stats(gr_frame* frame, void* cuda_stream, gr_stats* out);
+
+/* Inspection of a scene's BVH for bit-exact tests (host buffers, may be NULL
+ * to query sizes): sorted 64-bit keys (morton << 32 | triangle id) [n],
+ * internal nodes as int32 [n-1][2] child references (bit 31 set = leaf slot),
+ * and float32 [n-1][12] child boxes (left lo xyz, left hi xyz, right lo, right
+ * hi).  Returns the triangle count in *n_out. */
+gr_status gr_scene_bvh(gr_scene* scene, int32_t* n_out, uint64_t* keys, int32_t* children, float* boxes);
+
+/* Thread-local description of the last error (never NULL). */
+const char* gr_last_error(void);
+
+/* Library ABI version (this header: 1). */
+int32_t gr_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GR_H */

@@ -1,1 +1,25 @@
-"""GB300-native backward path tracing of generalized rays (arXiv 2303.15762)."""
+"""GB300-native backward path tracing of generalized rays (arXiv 2303.15762).
+
+The compute path is libgr.so (hand-written CUDA for sm_103a, C ABI in
+include/gr.h); this package is its thin binding (``_native``), the seeded input
+generators (``scenegen``) and the build script (``build``).  The binding is
+loaded lazily so that importing the input generators needs neither torch nor a
+GPU.
+"""
+from . import scenegen  # noqa: F401
+
+_NATIVE_NAMES = ("Scene", "Frame", "render", "render_image", "make_opts", "GrError", "lib_handle",
+                 "FLAG_NEE", "FLAG_RR", "FLAG_NO_RENORM", "pack_views", "current_stream")
+
+
+def load():
+    """Load libgr.so (raises if it is missing or no CUDA device is present)."""
+    from . import _native
+    return _native.lib_handle()
+
+
+def __getattr__(name):
+    if name in _NATIVE_NAMES:
+        from . import _native
+        return getattr(_native, name)
+    raise AttributeError(name)

@@ -1,0 +1,285 @@
+"""ctypes binding of libgr.so (include/gr.h): argument marshalling only.
+
+Every step of rendering runs in the library's CUDA kernels; this module packs
+the scene generator's arrays into the C structs, passes PyTorch's current CUDA
+stream, and unpacks results.  There is no CPU fallback: without a CUDA device
+or without the built library every call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgr.so")
+
+GR_OK, GR_E_INVALID, GR_E_OOM, GR_E_CUDA, GR_E_TIMEOUT, GR_E_BUSY = range(6)
+FLAG_NEE, FLAG_RR, FLAG_NO_RENORM = 1, 2, 4
+TABLE_DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
+
+EXPORTED = ["gr_scene_create", "gr_scene_destroy", "gr_frame_create", "gr_frame_reset", "gr_frame_release",
+            "gr_render", "gr_readback", "gr_frame_stats", "gr_scene_bvh", "gr_last_error", "gr_abi_version"]
+
+
+class GrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("gr status %d: %s" % (status, msg))
+        self.status = status
+
+
+class gr_material(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("fresnel", ctypes.c_int32), ("n_re", ctypes.c_float),
+                ("n_im", ctypes.c_float), ("period_um", ctypes.c_float), ("height_um", ctypes.c_float),
+                ("gdir", ctypes.c_float * 3), ("sigma_h_um", ctypes.c_float), ("corr_len_um", ctypes.c_float),
+                ("Le", ctypes.c_float), ("coh_len_um", ctypes.c_float), ("reserved", ctypes.c_float * 3)]
+
+
+class gr_light(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("dir", ctypes.c_float * 3), ("E", ctypes.c_float),
+                ("coh_len_um", ctypes.c_float), ("reserved", ctypes.c_float * 2)]
+
+
+class gr_scene_desc(ctypes.Structure):
+    _fields_ = [("n_tris", ctypes.c_int32), ("verts", ctypes.c_void_p), ("tri_mat", ctypes.c_void_p),
+                ("n_mats", ctypes.c_int32), ("mats", ctypes.c_void_p), ("n_lights", ctypes.c_int32),
+                ("lights", ctypes.c_void_p)]
+
+
+class gr_view_desc(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("look_at", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
+                ("vfov_deg", ctypes.c_float), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("p_pix_um", ctypes.c_float), ("f_beta", ctypes.c_float), ("lambda_min_um", ctypes.c_float),
+                ("lambda_max_um", ctypes.c_float), ("n_bins", ctypes.c_int32), ("n_stokes", ctypes.c_int32),
+                ("max_depth", ctypes.c_int32), ("spp", ctypes.c_int32), ("first_sample", ctypes.c_int32),
+                ("view_index", ctypes.c_int32), ("scene_index", ctypes.c_int32), ("ortho", ctypes.c_int32),
+                ("ortho_half_m", ctypes.c_float)]
+
+
+class gr_render_opts(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint32), ("flags", ctypes.c_int32), ("table_dtype", ctypes.c_int32),
+                ("pool_size", ctypes.c_int32), ("block", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("max_iterations", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class gr_stats(ctypes.Structure):
+    _fields_ = [("samples", ctypes.c_int64), ("segments", ctypes.c_int64), ("shadow_rays", ctypes.c_int64),
+                ("refine64_hits", ctypes.c_int64), ("refine64_lobes", ctypes.c_int64),
+                ("iterations", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib_handle(require_gpu=True):
+    """Load libgr.so.  With require_gpu (the default for every compute call)
+    a CUDA device must be present."""
+    global _lib
+    if require_gpu:
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libgr needs a CUDA device; there is no CPU fallback")
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libgr.so is not built (run __graft_entry__.build() or "
+                           "python -m paper_2303_15762_gb300.build)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I32 = ctypes.c_void_p, ctypes.c_int32
+    L.gr_scene_create.argtypes = [P, P, P]
+    L.gr_scene_destroy.argtypes = [P]
+    L.gr_frame_create.argtypes = [P, I32, P, P]
+    L.gr_frame_reset.argtypes = [P, P]
+    L.gr_frame_release.argtypes = [P]
+    L.gr_render.argtypes = [P, I32, P, I32, P, P, P]
+    L.gr_readback.argtypes = [P, I32, P, ctypes.c_size_t, I32, P]
+    L.gr_frame_stats.argtypes = [P, P, P]
+    L.gr_scene_bvh.argtypes = [P, P, P, P, P]
+    L.gr_last_error.restype = ctypes.c_char_p
+    L.gr_abi_version.restype = I32
+    for name in EXPORTED:
+        if name not in ("gr_last_error", "gr_abi_version"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != GR_OK:
+        raise GrError(status, _lib.gr_last_error().decode(errors="replace"))
+
+
+def current_stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def pack_view(v):
+    d = gr_view_desc()
+    d.eye[:] = v["eye"]
+    d.look_at[:] = v["look_at"]
+    d.up[:] = v["up"]
+    d.vfov_deg = v["vfov_deg"]
+    d.width, d.height = v["width"], v["height"]
+    d.p_pix_um, d.f_beta = v["p_pix_um"], v["f_beta"]
+    d.lambda_min_um, d.lambda_max_um = v["lambda_min_um"], v["lambda_max_um"]
+    d.n_bins, d.n_stokes, d.max_depth = v["n_bins"], v["n_stokes"], v["max_depth"]
+    d.spp, d.first_sample = v["spp"], v.get("first_sample", 0)
+    d.view_index, d.scene_index = v.get("view_index", 0), v.get("scene_index", 0)
+    d.ortho, d.ortho_half_m = v.get("ortho", 0), v.get("ortho_half_m", 0.0)
+    return d
+
+
+def pack_views(views):
+    arr = (gr_view_desc * len(views))()
+    for i, v in enumerate(views):
+        arr[i] = pack_view(v)
+    return arr
+
+
+def _pack_materials(rows):
+    rows = np.asarray(rows, dtype=np.float32).reshape(-1, 16)
+    arr = (gr_material * max(1, len(rows)))()
+    for i, r in enumerate(rows):
+        m = arr[i]
+        m.type, m.fresnel = int(r[0]), int(r[1])
+        m.n_re, m.n_im, m.period_um, m.height_um = float(r[2]), float(r[3]), float(r[4]), float(r[5])
+        m.gdir[:] = [float(x) for x in r[6:9]]
+        m.sigma_h_um, m.corr_len_um, m.Le, m.coh_len_um = float(r[9]), float(r[10]), float(r[11]), float(r[12])
+    return arr, len(rows)
+
+
+def _pack_lights(rows):
+    rows = np.asarray(rows, dtype=np.float32).reshape(-1, 8)
+    arr = (gr_light * max(1, len(rows)))()
+    for i, r in enumerate(rows):
+        L = arr[i]
+        L.type = int(r[0])
+        L.dir[:] = [float(x) for x in r[1:4]]
+        L.E, L.coh_len_um = float(r[4]), float(r[5])
+    return arr, len(rows)
+
+
+class Scene:
+    """Device copy of a scene (triangles, materials, lights) with its BVH."""
+
+    def __init__(self, scene, stream=None):
+        L = lib_handle()
+        self._h = ctypes.c_void_p()
+        verts = np.ascontiguousarray(scene["verts"], dtype=np.float32).reshape(-1, 9)
+        tri_mat = np.ascontiguousarray(scene["tri_mat"], dtype=np.int32)
+        mats, n_mats = _pack_materials(scene["mats"])
+        lights, n_lights = _pack_lights(scene["lights"])
+        desc = gr_scene_desc(len(tri_mat), _ptr(verts), _ptr(tri_mat), n_mats,
+                             ctypes.cast(mats, ctypes.c_void_p), n_lights, ctypes.cast(lights, ctypes.c_void_p))
+        self.n_tris = len(tri_mat)
+        self.host_bytes = verts.nbytes + tri_mat.nbytes + n_mats * 64 + n_lights * 32
+        _check(L.gr_scene_create(ctypes.byref(desc), stream or current_stream(), ctypes.byref(self._h)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def bvh(self):
+        n = ctypes.c_int32()
+        _check(_lib.gr_scene_bvh(self._h, ctypes.byref(n), None, None, None))
+        n = n.value
+        keys = np.zeros(max(n, 1), dtype=np.uint64)
+        ch = np.zeros((max(n - 1, 1), 2), dtype=np.int32)
+        bx = np.zeros((max(n - 1, 1), 12), dtype=np.float32)
+        _check(_lib.gr_scene_bvh(self._h, ctypes.byref(ctypes.c_int32()), _ptr(keys), _ptr(ch), _ptr(bx)))
+        return keys[:n], ch[: max(n - 1, 0)], bx[: max(n - 1, 0)]
+
+    def close(self):
+        if self._h:
+            _lib.gr_scene_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Frame:
+    """Resident per-view accumulators (sum + Kahan compensation)."""
+
+    def __init__(self, views, stream=None):
+        L = lib_handle()
+        self.views = [dict(v) for v in views]
+        self._h = ctypes.c_void_p()
+        arr = pack_views(self.views)
+        _check(L.gr_frame_create(arr, len(self.views), stream or current_stream(), ctypes.byref(self._h)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def reset(self, stream=None):
+        _check(_lib.gr_frame_reset(self._h, stream or current_stream()))
+
+    def readback(self, view=0, out=None, stream=None):
+        """Mean image float32 [H][W][n_bins][n_stokes]: a numpy array (host),
+        or written into `out` if it is a CUDA torch tensor."""
+        v = self.views[view]
+        shape = (v["height"], v["width"], v["n_bins"], v["n_stokes"])
+        if out is not None:
+            assert out.is_cuda and out.is_contiguous() and out.numel() >= int(np.prod(shape))
+            _check(_lib.gr_readback(self._h, view, ctypes.c_void_p(out.data_ptr()), out.numel() * 4, 1,
+                                    stream or current_stream()))
+            return out
+        host = np.empty(shape, dtype=np.float32)
+        _check(_lib.gr_readback(self._h, view, _ptr(host), host.nbytes, 0, stream or current_stream()))
+        return host
+
+    def stats(self, stream=None):
+        s = gr_stats()
+        _check(_lib.gr_frame_stats(self._h, stream or current_stream(), ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in gr_stats._fields_}
+
+    def close(self):
+        if self._h:
+            _lib.gr_frame_release(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_opts(seed=1, flags=0, table_dtype="f32", pool_size=0, block=0, use_graph=False, max_iterations=0):
+    o = gr_render_opts()
+    o.seed = int(seed) & 0xFFFFFFFF
+    o.flags = int(flags)
+    o.table_dtype = TABLE_DTYPES[table_dtype] if isinstance(table_dtype, str) else int(table_dtype)
+    o.pool_size, o.block = int(pool_size), int(block)
+    o.use_graph = int(bool(use_graph))
+    o.max_iterations = int(max_iterations)
+    return o
+
+
+def render(scenes, views, frame, stream=None, **opts):
+    """Enqueue the samples of every view into `frame` (asynchronous)."""
+    L = lib_handle()
+    sc = (ctypes.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    arr = pack_views(views)
+    o = make_opts(**opts)
+    _check(L.gr_render(sc, len(scenes), arr, len(views), ctypes.byref(o), frame.handle, stream or current_stream()))
+
+
+def render_image(scene, view, **opts):
+    """Convenience: one scene dict + one view dict -> mean image (numpy)."""
+    s = Scene(scene)
+    f = Frame([view])
+    try:
+        render([s], [dict(view, scene_index=0)], f, **opts)
+        return f.readback(0)
+    finally:
+        f.close()
+        s.close()

@@ -1,0 +1,350 @@
+// C ABI entry points of libgr.so (declared and documented in include/gr.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gr_build.h"
+
+namespace gr {
+gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc* vd, int n_views,
+                      const gr_render_opts& o, gr_frame* f, cudaStream_t st, std::string& err);
+cudaError_t readback_impl(gr_frame* f, int v, float* dst_dev, const float* inv_count_dev, cudaStream_t st);
+}  // namespace gr
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+gr_status fail(gr_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+gr_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? GR_E_OOM : GR_E_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+extern "C" {
+
+int32_t gr_abi_version(void) { return 1; }
+
+const char* gr_last_error(void) { return g_err.c_str(); }
+
+gr_status gr_scene_create(const gr_scene_desc* desc, void* cuda_stream, gr_scene** out) {
+  if (!desc || !out) return fail(GR_E_INVALID, "gr_scene_create: null argument");
+  const int n = desc->n_tris;
+  if (n < 0 || desc->n_mats < 0 || desc->n_lights < 0) return fail(GR_E_INVALID, "gr_scene_create: negative count");
+  if (n > 0 && (!desc->verts || !desc->tri_mat)) return fail(GR_E_INVALID, "gr_scene_create: null triangle arrays");
+  if (desc->n_mats > 0 && !desc->mats) return fail(GR_E_INVALID, "gr_scene_create: null materials");
+  if (desc->n_lights > 0 && !desc->lights) return fail(GR_E_INVALID, "gr_scene_create: null lights");
+  if (n > (1 << 28)) return fail(GR_E_INVALID, "gr_scene_create: too many triangles");
+  for (int i = 0; i < desc->n_mats; ++i) {
+    const gr_material& M = desc->mats[i];
+    if (M.type < GR_MAT_ABSORBER || M.type > GR_MAT_EMITTER || M.fresnel < 0 || M.fresnel > 1)
+      return fail(GR_E_INVALID, "gr_scene_create: bad material " + std::to_string(i));
+    if (M.type == GR_MAT_GRATING && !(M.period_um > 0.0f))
+      return fail(GR_E_INVALID, "gr_scene_create: grating period must be > 0");
+    if (M.type == GR_MAT_ROUGH && !(M.corr_len_um > 0.0f))
+      return fail(GR_E_INVALID, "gr_scene_create: correlation length must be > 0");
+  }
+  for (int i = 0; i < desc->n_lights; ++i) {
+    const gr_light& L = desc->lights[i];
+    if (L.type != GR_LIGHT_DISTANT && L.type != GR_LIGHT_ENV)
+      return fail(GR_E_INVALID, "gr_scene_create: bad light " + std::to_string(i));
+  }
+  for (int i = 0; i < n; ++i)
+    if (desc->tri_mat[i] < 0 || desc->tri_mat[i] >= desc->n_mats)
+      return fail(GR_E_INVALID, "gr_scene_create: material index out of range at triangle " + std::to_string(i));
+
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  gr_scene* S = new (std::nothrow) gr_scene();
+  if (!S) return fail(GR_E_OOM, "gr_scene_create: host allocation");
+  cudaGetDevice(&S->device);
+  S->n_tris = n;
+  S->mats.assign(desc->mats, desc->mats + desc->n_mats);
+
+  // emitters: triangles grouped by emitter material (host bookkeeping)
+  std::vector<int> emitter_of_mat(std::max(desc->n_mats, 1), -1);
+  std::vector<std::vector<int>> groups;
+  for (int i = 0; i < n; ++i) {
+    int m = desc->tri_mat[i];
+    if (desc->mats[m].type != GR_MAT_EMITTER) continue;
+    if (emitter_of_mat[m] < 0) {
+      emitter_of_mat[m] = (int)groups.size();
+      groups.emplace_back();
+    }
+    groups[emitter_of_mat[m]].push_back(i);
+  }
+  std::vector<gr::DevEmitter> emit;
+  std::vector<float4> etris;
+  for (size_t g = 0; g < groups.size(); ++g) {
+    gr::DevEmitter E;
+    E.mat = desc->tri_mat[groups[g][0]];
+    E.first = (int)(etris.size() / 3);
+    E.count = (int)groups[g].size();
+    E.pad = 0;
+    for (int t : groups[g])
+      for (int k = 0; k < 3; ++k) {
+        const float* v = desc->verts + 9 * t + 3 * k;
+        etris.push_back(make_float4(v[0], v[1], v[2], 0.0f));
+      }
+    emit.push_back(E);
+  }
+
+  // one device allocation for every persistent array
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = off;
+    off = align_up(off + std::max<size_t>(bytes, 1), 256);
+    return r;
+  };
+  const size_t o_tri = take(sizeof(float4) * 3 * (size_t)n);
+  const size_t o_tmat = take(sizeof(int) * (size_t)n);
+  const size_t o_nodes = take(sizeof(float) * 16 * (size_t)std::max(n - 1, 0));
+  const size_t o_mats = take(sizeof(gr_material) * desc->n_mats);
+  const size_t o_lights = take(sizeof(gr_light) * desc->n_lights);
+  const size_t o_emit = take(sizeof(gr::DevEmitter) * emit.size());
+  const size_t o_eom = take(sizeof(int) * emitter_of_mat.size());
+  const size_t o_etri = take(sizeof(float4) * etris.size());
+  const size_t o_keys = take(sizeof(unsigned long long) * (size_t)n);
+  cudaError_t e = cudaMallocAsync(&S->mem, off, st);
+  if (e != cudaSuccess) {
+    delete S;
+    return cuda_fail(e, "gr_scene_create: device allocation");
+  }
+  unsigned char* b = (unsigned char*)S->mem;
+  float* verts_d = nullptr;
+  int* tmat_in = nullptr;
+  gr_status status = GR_OK;
+  do {
+    if (n > 0) {
+      if ((e = cudaMallocAsync(&verts_d, sizeof(float) * 9 * (size_t)n, st)) != cudaSuccess) break;
+      if ((e = cudaMallocAsync(&tmat_in, sizeof(int) * (size_t)n, st)) != cudaSuccess) break;
+      if ((e = cudaMemcpyAsync(verts_d, desc->verts, sizeof(float) * 9 * (size_t)n, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+      if ((e = cudaMemcpyAsync(tmat_in, desc->tri_mat, sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+    }
+    if (desc->n_mats && (e = cudaMemcpyAsync(b + o_mats, desc->mats, sizeof(gr_material) * desc->n_mats, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+    if (desc->n_lights && (e = cudaMemcpyAsync(b + o_lights, desc->lights, sizeof(gr_light) * desc->n_lights, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+    if (!emit.empty() && (e = cudaMemcpyAsync(b + o_emit, emit.data(), sizeof(gr::DevEmitter) * emit.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(b + o_eom, emitter_of_mat.data(), sizeof(int) * emitter_of_mat.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+    if (!etris.empty() && (e = cudaMemcpyAsync(b + o_etri, etris.data(), sizeof(float4) * etris.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+    if (n > 0) {
+      e = gr::build_lbvh(verts_d, tmat_in, n, (float4*)(b + o_tri), (int*)(b + o_tmat), (float*)(b + o_nodes),
+                         (unsigned long long*)(b + o_keys), st);
+      if (e != cudaSuccess) break;
+    }
+    // host arrays are pageable: make sure every copy has consumed them
+    e = cudaStreamSynchronize(st);
+  } while (0);
+  if (verts_d) cudaFreeAsync(verts_d, st);
+  if (tmat_in) cudaFreeAsync(tmat_in, st);
+  if (e != cudaSuccess) {
+    status = cuda_fail(e, "gr_scene_create");
+    cudaFreeAsync(S->mem, st);
+    delete S;
+    return status;
+  }
+  gr::DevScene& D = S->dev;
+  D.n_tris = n;
+  D.n_mats = desc->n_mats;
+  D.n_lights = desc->n_lights;
+  D.n_emitters = (int)emit.size();
+  D.tri = (const float4*)(b + o_tri);
+  D.tri_mat = (const int*)(b + o_tmat);
+  D.nodes = (const float4*)(b + o_nodes);
+  D.mats = (const gr_material*)(b + o_mats);
+  D.lights = (const gr_light*)(b + o_lights);
+  D.emitters = (const gr::DevEmitter*)(b + o_emit);
+  D.emitter_of_mat = (const int*)(b + o_eom);
+  D.emitter_tris = (const float4*)(b + o_etri);
+  S->keys = (unsigned long long*)(b + o_keys);
+  *out = S;
+  return GR_OK;
+}
+
+gr_status gr_scene_destroy(gr_scene* scene) {
+  if (!scene) return fail(GR_E_INVALID, "gr_scene_destroy: null scene");
+  if (scene->mem) cudaFree(scene->mem);
+  delete scene;
+  return GR_OK;
+}
+
+gr_status gr_scene_bvh(gr_scene* scene, int32_t* n_out, uint64_t* keys, int32_t* children, float* boxes) {
+  if (!scene || !n_out) return fail(GR_E_INVALID, "gr_scene_bvh: null argument");
+  const int n = scene->n_tris;
+  *n_out = n;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "gr_scene_bvh");
+  if (keys && n > 0) {
+    e = cudaMemcpy(keys, scene->keys, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "gr_scene_bvh keys");
+  }
+  if ((children || boxes) && n > 1) {
+    std::vector<float> nodes((size_t)16 * (n - 1));
+    e = cudaMemcpy(nodes.data(), scene->dev.nodes, sizeof(float) * nodes.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "gr_scene_bvh nodes");
+    for (int i = 0; i < n - 1; ++i) {
+      if (children) {
+        std::memcpy(children + 2 * i, &nodes[16 * (size_t)i + 12], 8);
+      }
+      if (boxes) std::memcpy(boxes + 12 * (size_t)i, &nodes[16 * (size_t)i], 48);
+    }
+  }
+  return GR_OK;
+}
+
+gr_status gr_frame_create(const gr_view_desc* views, int32_t n_views, void* cuda_stream, gr_frame** out) {
+  if (!views || !out || n_views <= 0) return fail(GR_E_INVALID, "gr_frame_create: bad arguments");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  gr_frame* F = new (std::nothrow) gr_frame();
+  if (!F) return fail(GR_E_OOM, "gr_frame_create: host allocation");
+  cudaGetDevice(&F->device);
+  F->n_views = n_views;
+  size_t total = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const gr_view_desc& d = views[v];
+    if (d.width <= 0 || d.height <= 0 || d.n_bins <= 0 || d.n_bins > 4096 || (d.n_stokes != 1 && d.n_stokes != 4)) {
+      delete F;
+      return fail(GR_E_INVALID, "gr_frame_create: bad view shape " + std::to_string(v));
+    }
+    if ((long long)d.width * d.height * d.n_bins >= (1LL << 31)) {
+      delete F;
+      return fail(GR_E_INVALID, "gr_frame_create: view too large " + std::to_string(v));
+    }
+    F->shapes.push_back(gr_view_shape{d.width, d.height, d.n_bins, d.n_stokes});
+    F->offsets.push_back(total);
+    total += (size_t)d.width * d.height * d.n_bins * d.n_stokes;
+    F->counts.emplace_back(d.n_bins, 0LL);
+  }
+  F->acc_floats = total;
+  cudaError_t e = cudaMallocAsync(&F->acc, sizeof(float) * total * 2, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(F->acc, 0, sizeof(float) * total * 2, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&F->ctr, sizeof(gr::Counters), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(F->ctr, 0, sizeof(gr::Counters), st);
+  if (e == cudaSuccess) e = cudaHostAlloc(&F->ctr_host, sizeof(gr::Counters) * 2, cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    if (F->acc) cudaFreeAsync(F->acc, st);
+    if (F->ctr) cudaFreeAsync(F->ctr, st);
+    delete F;
+    return cuda_fail(e, "gr_frame_create");
+  }
+  std::memset(F->ctr_host, 0, sizeof(gr::Counters) * 2);
+  *out = F;
+  return GR_OK;
+}
+
+gr_status gr_frame_reset(gr_frame* f, void* cuda_stream) {
+  if (!f) return fail(GR_E_INVALID, "gr_frame_reset: null frame");
+  cudaError_t e = cudaMemsetAsync(f->acc, 0, sizeof(float) * f->acc_floats * 2, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_frame_reset");
+  for (auto& c : f->counts) std::fill(c.begin(), c.end(), 0LL);
+  return GR_OK;
+}
+
+gr_status gr_frame_release(gr_frame* f) {
+  if (!f) return fail(GR_E_INVALID, "gr_frame_release: null frame");
+  cudaDeviceSynchronize();
+  if (f->acc) cudaFree(f->acc);
+  if (f->scratch) cudaFree(f->scratch);
+  if (f->ctr) cudaFree(f->ctr);
+  if (f->ctr_host) cudaFreeHost(f->ctr_host);
+  delete f;
+  return GR_OK;
+}
+
+gr_status gr_render(gr_scene* const* scenes, int32_t n_scenes, const gr_view_desc* views, int32_t n_views,
+                    const gr_render_opts* opts, gr_frame* frame, void* cuda_stream) {
+  if (!scenes || !views || !opts || !frame || n_views <= 0 || n_scenes <= 0)
+    return fail(GR_E_INVALID, "gr_render: null or empty argument");
+  if (n_views != frame->n_views) return fail(GR_E_INVALID, "gr_render: view count differs from the frame's");
+  for (int i = 0; i < n_scenes; ++i)
+    if (!scenes[i]) return fail(GR_E_INVALID, "gr_render: null scene " + std::to_string(i));
+  if (opts->table_dtype < GR_TABLE_F32 || opts->table_dtype > GR_TABLE_BF16)
+    return fail(GR_E_INVALID, "gr_render: bad table dtype");
+  if (opts->pool_size < 0 || opts->block < 0 || (opts->block && (opts->block % 32 || opts->block > 256)))
+    return fail(GR_E_INVALID, "gr_render: bad pool size or block (block must be a multiple of 32, <= 256)");
+  const int ns = views[0].n_stokes;
+  for (int v = 0; v < n_views; ++v) {
+    const gr_view_desc& d = views[v];
+    const gr_view_shape& s = frame->shapes[v];
+    if (d.width != s.W || d.height != s.H || d.n_bins != s.nb || d.n_stokes != s.ns)
+      return fail(GR_E_INVALID, "gr_render: view " + std::to_string(v) + " does not match the frame");
+    if (d.n_stokes != ns) return fail(GR_E_INVALID, "gr_render: all views of one call need the same n_stokes");
+    if (d.scene_index < 0 || d.scene_index >= n_scenes)
+      return fail(GR_E_INVALID, "gr_render: scene index out of range in view " + std::to_string(v));
+    if (d.spp < 0 || d.first_sample < 0 || (long long)d.first_sample + d.spp >= (1LL << 31))
+      return fail(GR_E_INVALID, "gr_render: bad sample range in view " + std::to_string(v));
+    if ((long long)d.spp / d.n_bins + 1 >= 65536)
+      return fail(GR_E_INVALID, "gr_render: more than 65535 samples per pixel and bin in one call");
+    if (d.max_depth < 0 || d.max_depth > 250) return fail(GR_E_INVALID, "gr_render: max_depth out of [0, 250]");
+    if (!(d.lambda_min_um > 0.0f) || d.lambda_max_um < d.lambda_min_um || !(d.p_pix_um > 0.0f) || !(d.f_beta > 0.0f))
+      return fail(GR_E_INVALID, "gr_render: bad spectral range or pixel footprint in view " + std::to_string(v));
+    if (!(d.vfov_deg > 0.0f && d.vfov_deg < 180.0f) && !d.ortho)
+      return fail(GR_E_INVALID, "gr_render: bad field of view in view " + std::to_string(v));
+  }
+  std::string err;
+  gr_status s = gr::render_impl(scenes, n_scenes, views, n_views, *opts, frame, (cudaStream_t)cuda_stream, err);
+  if (s != GR_OK) return fail(s, "gr_render: " + err);
+  for (int v = 0; v < n_views; ++v) {
+    const gr_view_desc& d = views[v];
+    for (int b = 0; b < d.n_bins; ++b) {
+      long long r = ((long long)b - d.first_sample) % d.n_bins;
+      if (r < 0) r += d.n_bins;
+      long long s0 = d.first_sample + r, end = (long long)d.first_sample + d.spp;
+      frame->counts[v][b] += s0 < end ? (end - 1 - s0) / d.n_bins + 1 : 0;
+    }
+  }
+  return GR_OK;
+}
+
+gr_status gr_readback(gr_frame* f, int32_t view, float* dst, size_t dst_bytes, int32_t dst_is_device, void* cuda_stream) {
+  if (!f || !dst) return fail(GR_E_INVALID, "gr_readback: null argument");
+  if (view < 0 || view >= f->n_views) return fail(GR_E_INVALID, "gr_readback: view out of range");
+  const gr_view_shape& s = f->shapes[view];
+  const size_t n = (size_t)s.W * s.H * s.nb * s.ns;
+  if (dst_bytes < n * sizeof(float)) return fail(GR_E_INVALID, "gr_readback: destination too small");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  std::vector<float> inv(s.nb);
+  for (int b = 0; b < s.nb; ++b) inv[b] = f->counts[view][b] > 0 ? 1.0f / (float)f->counts[view][b] : 0.0f;
+  float* inv_d = nullptr;
+  float* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync(&inv_d, sizeof(float) * s.nb, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(inv_d, inv.data(), sizeof(float) * s.nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !dst_is_device) e = cudaMallocAsync(&tmp, n * sizeof(float), st);
+  if (e == cudaSuccess) e = gr::readback_impl(f, view, dst_is_device ? dst : tmp, inv_d, st);
+  if (e == cudaSuccess && !dst_is_device) e = cudaMemcpyAsync(dst, tmp, n * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (inv_d) cudaFreeAsync(inv_d, st);
+  if (tmp) cudaFreeAsync(tmp, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // inv[] is pageable host memory; host dst must be complete
+  if (e != cudaSuccess) return cuda_fail(e, "gr_readback");
+  return GR_OK;
+}
+
+gr_status gr_frame_stats(gr_frame* f, void* cuda_stream, gr_stats* out) {
+  if (!f || !out) return fail(GR_E_INVALID, "gr_frame_stats: null argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  gr::Counters c;
+  cudaError_t e = cudaMemcpyAsync(&c, f->ctr, sizeof c, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_frame_stats");
+  out->samples = (int64_t)c.samples;
+  out->segments = (int64_t)c.segments;
+  out->shadow_rays = (int64_t)c.shadow;
+  out->refine64_hits = (int64_t)c.ref_hit;
+  out->refine64_lobes = (int64_t)c.ref_lobe;
+  out->iterations = (int64_t)c.iters;
+  out->kernel_launches = f->launches;
+  return GR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "gr.h"
+#include "gr_device.cuh"
+
+namespace gr {
+
+cudaError_t build_lbvh(const float* verts, const int* tri_mat, int n, float4* tri, int* tmat, float* nodes,
+                       unsigned long long* keys_out, cudaStream_t st);
+
+// Wavefront slot pool: per-slot path state in structure-of-arrays form.
+struct Pool {
+  float4* od0;   // o.xyz, beta^2 (um^2)
+  float4* od1;   // d.xyz, rho
+  float4* tp[4]; // throughput: scalar in tp[0].x, or Mueller rows 0..3
+  float4* xf;    // Stokes frame x axis, MIS density of the current direction
+  float4* part;  // contribution of the current sample
+  float4* accS;  // ticket sums (Kahan)
+  float4* accC;  // ticket compensations
+  float4* shd;   // NEE direction xyz, (emitter index | vertex segment << 16)
+  float4* shc;   // NEE weight (Stokes vector)
+  float2* hit;   // t, leaf slot
+  int4* meta;    // view, local ticket, (sample k | seg << 16 | state << 24 | delta << 26), previous leaf slot
+  int* tq;       // trace queue
+  int* sq;       // shadow queue
+};
+
+struct Counters {
+  unsigned long long next_ticket;
+  unsigned long long total_tickets;
+  int tq_count;
+  int sq_count;
+  int last_active;
+  int err;
+  unsigned long long samples, segments, shadow, ref_hit, ref_lobe, iters;
+};
+
+struct RenderParams {
+  const DevView* views;
+  int n_views;
+  const DevScene* scenes;
+  uint32_t seed;
+  int flags;
+  const TableRow* rows;
+  const void* table_vals;
+  int table_dtype;
+  int table_smem;        // 1 if the order table is staged in shared memory
+  int table_rows;
+  int table_vals_count;
+  Pool pool;
+  int P;
+  Counters* ctr;
+};
+
+}  // namespace gr
+
+struct gr_scene {
+  gr::DevScene dev;
+  void* mem = nullptr;            // single device allocation holding every array
+  unsigned long long* keys = nullptr;
+  int n_tris = 0;
+  std::vector<gr_material> mats;  // host copy (order tables)
+  int device = 0;
+};
+
+struct gr_view_shape {
+  int W, H, nb, ns;
+};
+
+struct gr_frame {
+  int n_views = 0;
+  std::vector<gr_view_shape> shapes;
+  std::vector<size_t> offsets;           // float offset of each view's sum plane
+  float* acc = nullptr;                  // sums then compensations
+  size_t acc_floats = 0;                 // floats per plane set (sum part)
+  std::vector<std::vector<long long>> counts;  // [view][bin] samples accumulated
+  // scratch kept between renders
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  gr::Counters* ctr = nullptr;           // device counters
+  gr::Counters* ctr_host = nullptr;      // pinned mirror
+  long long launches = 0;
+  long long iterations = 0;
+  int device = 0;
+};

@@ -1,0 +1,414 @@
+// Device-side building blocks of the generalized-ray path tracer (sm_103a).
+// Everything on the render path is FP32 except the decision refinements and the
+// footprint quadratic form at emitters, which run in FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "gr.h"
+
+namespace gr {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr double kPiD = 3.14159265358979323846;
+// Hits closer than this (metres) are ignored, besides the primitive just left.
+constexpr float kTMin = 1e-5f;
+// Roughness above which the Poisson series is replaced by its continuous limit.
+constexpr float kGCont = 50.0f;
+// Largest grating order magnitude kept in the order tables.
+constexpr int kMaxOrder = 40;
+constexpr int kStackDepth = 64;
+
+// Random-number uses at a path vertex (word 2 of the Philox counter is
+// (segment << 4) | call).
+enum Call { kCallJitter = 0, kCallEmitFoot = 1, kCallLobe = 2, kCallNeeDir = 3, kCallNeeFoot = 4, kCallRR = 5 };
+
+// ------------------------------------------------------------------ device scene
+struct DevEmitter {
+  int mat;    // emitter material id
+  int first;  // first triangle in emitter_tris
+  int count;  // number of triangles
+  int pad;
+};
+
+struct DevScene {
+  int n_tris;
+  int n_mats;
+  int n_lights;
+  int n_emitters;
+  const float4* tri;         // [n][3] vertices in BVH leaf order; tri[3i].w = original id (int bits)
+  const int* tri_mat;        // [n] material of leaf slot i
+  const float4* nodes;       // [n-1][4] internal nodes (child boxes + child refs)
+  const gr_material* mats;   // [n_mats]
+  const gr_light* lights;    // [n_lights]
+  const DevEmitter* emitters;     // [n_emitters]
+  const int* emitter_of_mat;      // [n_mats] -> emitter index or -1
+  const float4* emitter_tris;     // [m][3] vertices of emitter triangles
+};
+
+struct DevView {
+  float3 eye, fw, right, upc;
+  float th, aspect;
+  int W, H, nb, ns, max_depth, spp, first_sample, view_index, scene_index, ortho;
+  float ortho_half;
+  float lmin, lmax, beta0;
+  long long ticket_base;  // first global ticket of this view
+  long long n_tickets;    // nb * W * H
+  float* acc_sum;         // [nb][H][W][ns]
+  float* acc_comp;
+  int table_base;         // first table row of this view ((view, material, bin) rows)
+  int pad;
+};
+
+// Per-(view, material, bin) row of the grating order table: J_j(h k/2)^2 for
+// j = 0..jmax, stored from `offset` in the value array.
+struct TableRow {
+  int offset;
+  int jmax;
+};
+
+// ------------------------------------------------------------------ small vector math
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return f3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 normalize(float3 a) { return rsqrtf(dot(a, a)) * a; }
+__device__ __forceinline__ float3 xyz(float4 a) { return f3(a.x, a.y, a.z); }
+
+struct d3 {
+  double x, y, z;
+};
+__device__ __forceinline__ d3 D3(float3 a) { return d3{a.x, a.y, a.z}; }
+__device__ __forceinline__ d3 dadd(d3 a, d3 b) { return d3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ d3 dsub(d3 a, d3 b) { return d3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ d3 dmul(double s, d3 a) { return d3{s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ double ddot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ d3 dcross(d3 a, d3 b) {
+  return d3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ d3 dnormalize(d3 a) { return dmul(1.0 / sqrt(ddot(a, a)), a); }
+
+// Branchless orthonormal basis (Duff et al., JCGT 2017).
+__device__ __forceinline__ void onb(float3 n, float3& e1, float3& e2) {
+  float sign = copysignf(1.0f, n.z);
+  float a = -1.0f / (sign + n.z);
+  float b = n.x * n.y * a;
+  e1 = f3(1.0f + sign * n.x * n.x * a, sign * b, -sign * n.x);
+  e2 = f3(b, sign + n.y * n.y * a, -n.y);
+}
+__device__ __forceinline__ void onb_d(d3 n, d3& e1, d3& e2) {
+  double sign = copysign(1.0, n.z);
+  double a = -1.0 / (sign + n.z);
+  double b = n.x * n.y * a;
+  e1 = d3{1.0 + sign * n.x * n.x * a, sign * b, -sign * n.x};
+  e2 = d3{b, sign + n.y * n.y * a, -n.y};
+}
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon et al., SC'11: 10 rounds; multipliers 0xD2511F53 / 0xCD9E8D57, key
+// schedule 0x9E3779B9 / 0xBB67AE85, applied between rounds.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Four uniforms in [0,1) on the 2^-24 grid for (pixel, sample, segment, call).
+__device__ __forceinline__ float4 rng4(uint32_t seed, uint32_t view, uint32_t pixel, uint32_t sample, int seg,
+                                       int call) {
+  uint4 x = philox10(make_uint4(pixel, sample, ((uint32_t)seg << 4) | (uint32_t)call, 0u), seed, view);
+  const float s = 5.9604644775390625e-8f;  // 2^-24
+  return make_float4((float)(x.x >> 8) * s, (float)(x.y >> 8) * s, (float)(x.z >> 8) * s, (float)(x.w >> 8) * s);
+}
+
+__device__ __forceinline__ void box_muller(float u0, float u1, float& z0, float& z1) {
+  float r = sqrtf(-2.0f * logf(1.0f - u0));
+  float s, c;
+  sincospif(2.0f * u1, &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+
+// vMF density about mu with concentration kappa (angular Gaussian on the sphere).
+__device__ __forceinline__ float vmf(float3 w, float3 mu, float kappa) {
+  if (kappa < 1e-8f) return 0.25f / kPi;
+  float3 d = w - mu;
+  return kappa / (2.0f * kPi * (-expm1f(-2.0f * kappa))) * expf(-0.5f * kappa * dot(d, d));
+}
+__device__ __forceinline__ double vmf_d(d3 w, d3 mu, double kappa) {
+  if (kappa < 1e-8) return 0.25 / kPiD;
+  d3 d = dsub(w, mu);
+  return kappa / (2.0 * kPiD * (-expm1(-2.0 * kappa))) * exp(-0.5 * kappa * ddot(d, d));
+}
+
+__device__ __forceinline__ float3 vmf_sample(float3 mu, float kappa, float u0, float u1) {
+  float up = 1.0f - u0;
+  float v = -logf(up + (1.0f - up) * expf(-2.0f * kappa)) / kappa;  // 1 - cos(theta)
+  float sin_t = sqrtf(fmaxf(0.0f, v * (2.0f - v)));
+  float s, c;
+  sincospif(2.0f * u1, &s, &c);
+  float3 e1, e2;
+  onb(mu, e1, e2);
+  return normalize((sin_t * c) * e1 + (sin_t * s) * e2 + (1.0f - v) * mu);
+}
+
+// ------------------------------------------------------------------ Bessel J_n (power series)
+__device__ __forceinline__ double bessel_j_d(int n, double x) {
+  if (n < 0) n = -n;  // only squares are used
+  double half = 0.5 * x, term = 1.0;
+  for (int i = 1; i <= n; ++i) term *= half / i;
+  double sum = term;
+  for (int m = 1; m < 200; ++m) {
+    term *= -(half * half) / ((double)m * (double)(m + n));
+    sum += term;
+    if (fabs(term) < 1e-18 * fabs(sum) && m > 2) break;
+  }
+  return sum;
+}
+
+// ------------------------------------------------------------------ intersection
+struct RayPre {
+  float3 o, d, inv;
+  int kx, ky, kz;
+  float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ float comp(float3 v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : v.z); }
+
+__device__ __forceinline__ RayPre ray_pre(float3 o, float3 d) {
+  RayPre r;
+  r.o = o;
+  r.d = d;
+  r.inv = f3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+  float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+  int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+  int kx = kz + 1 == 3 ? 0 : kz + 1;
+  int ky = kx + 1 == 3 ? 0 : kx + 1;
+  if (comp(d, kz) < 0.0f) {
+    int t = kx;
+    kx = ky;
+    ky = t;
+  }
+  r.kx = kx;
+  r.ky = ky;
+  r.kz = kz;
+  float dz = comp(d, kz);
+  r.Sx = comp(d, kx) / dz;
+  r.Sy = comp(d, ky) / dz;
+  r.Sz = 1.0f / dz;
+  return r;
+}
+
+// Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2(1), 2013) in FP32;
+// when an edge function is within its rounding margin the edge functions are
+// recomputed in FP64 from the same inputs ("FP64 refinement").  Edges count as
+// inside.  Returns t (metres) or -1.
+__device__ __forceinline__ float isect_tri(const RayPre& r, float3 v0, float3 v1, float3 v2, unsigned long long* refine_ctr) {
+  const float3 A = v0 - r.o, B = v1 - r.o, C = v2 - r.o;
+  const float Az_ = comp(A, r.kz), Bz_ = comp(B, r.kz), Cz_ = comp(C, r.kz);
+  const float Ax = comp(A, r.kx) - r.Sx * Az_, Ay = comp(A, r.ky) - r.Sy * Az_;
+  const float Bx = comp(B, r.kx) - r.Sx * Bz_, By = comp(B, r.ky) - r.Sy * Bz_;
+  const float Cx = comp(C, r.kx) - r.Sx * Cz_, Cy = comp(C, r.ky) - r.Sy * Cz_;
+  float U = Cx * By - Cy * Bx;
+  float V = Ax * Cy - Ay * Cx;
+  float W = Bx * Ay - By * Ax;
+  const float eps = 2e-6f;
+  bool refine = fabsf(U) <= eps * (fabsf(Cx * By) + fabsf(Cy * Bx)) ||
+                fabsf(V) <= eps * (fabsf(Ax * Cy) + fabsf(Ay * Cx)) ||
+                fabsf(W) <= eps * (fabsf(Bx * Ay) + fabsf(By * Ax));
+  if (refine) {
+    // FP64 edge functions from the FP32 vertices and ray
+    double Sx = (double)comp(r.d, r.kx) / (double)comp(r.d, r.kz);
+    double Sy = (double)comp(r.d, r.ky) / (double)comp(r.d, r.kz);
+    d3 o = D3(r.o);
+    d3 a = dsub(D3(v0), o), b = dsub(D3(v1), o), c = dsub(D3(v2), o);
+    double az = r.kz == 0 ? a.x : (r.kz == 1 ? a.y : a.z);
+    double bz = r.kz == 0 ? b.x : (r.kz == 1 ? b.y : b.z);
+    double cz = r.kz == 0 ? c.x : (r.kz == 1 ? c.y : c.z);
+    auto cx_ = [&](d3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); };
+    double ax = cx_(a, r.kx) - Sx * az, ay = cx_(a, r.ky) - Sy * az;
+    double bx = cx_(b, r.kx) - Sx * bz, by = cx_(b, r.ky) - Sy * bz;
+    double cxx = cx_(c, r.kx) - Sx * cz, cy = cx_(c, r.ky) - Sy * cz;
+    double Ud = cxx * by - cy * bx, Vd = ax * cy - ay * cxx, Wd = bx * ay - by * ax;
+    U = (float)Ud;
+    V = (float)Vd;
+    W = (float)Wd;
+    // keep exact signs of tiny values
+    if (Ud != 0.0 && U == 0.0f) U = Ud > 0 ? 1e-38f : -1e-38f;
+    if (Vd != 0.0 && V == 0.0f) V = Vd > 0 ? 1e-38f : -1e-38f;
+    if (Wd != 0.0 && W == 0.0f) W = Wd > 0 ? 1e-38f : -1e-38f;
+    if (refine_ctr) atomicAdd(refine_ctr, 1ull);
+  }
+  if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return -1.0f;
+  float det = U + V + W;
+  if (det == 0.0f) return -1.0f;
+  float T = U * (r.Sz * Az_) + V * (r.Sz * Bz_) + W * (r.Sz * Cz_);
+  return T / det;
+}
+
+// Slab test of a child box; returns the entry distance or +inf on a miss.
+// The far distance is widened by 2*gamma(3) (Ize 2013) so no box containing a
+// triangle hit is rejected by rounding.
+__device__ __forceinline__ float box_entry(const RayPre& r, float3 lo, float3 hi, float tbest) {
+  float tx0 = (lo.x - r.o.x) * r.inv.x, tx1 = (hi.x - r.o.x) * r.inv.x;
+  float ty0 = (lo.y - r.o.y) * r.inv.y, ty1 = (hi.y - r.o.y) * r.inv.y;
+  float tz0 = (lo.z - r.o.z) * r.inv.z, tz1 = (hi.z - r.o.z) * r.inv.z;
+  float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+  float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+  tf = fminf(tf * 1.0000004f, tbest);
+  return tn <= tf ? tn : __int_as_float(0x7f800000);
+}
+
+struct Hit {
+  float t;
+  int slot;  // leaf slot (BVH order) or -1
+};
+
+// Closest hit along (o, d) with t > kTMin, skipping leaf slot `exclude`;
+// equal distances resolve to the lower original triangle id.  Stack-based
+// traversal of the binary LBVH, nearer child first.  *err is set if the stack
+// would overflow (the traversal then stops early).
+__device__ __forceinline__ Hit closest_hit(const DevScene& S, float3 o, float3 d, int exclude,
+                                           unsigned long long* refine_ctr, int* err) {
+  Hit h;
+  h.t = __int_as_float(0x7f800000);
+  h.slot = -1;
+  int best_id = 0x7fffffff;
+  if (S.n_tris == 0) return h;
+  RayPre r = ray_pre(o, d);
+  auto test_leaf = [&](int slot) {
+    if (slot == exclude) return;
+    const float4 a = __ldg(&S.tri[3 * slot]);
+    const float4 b = __ldg(&S.tri[3 * slot + 1]);
+    const float4 c = __ldg(&S.tri[3 * slot + 2]);
+    float t = isect_tri(r, xyz(a), xyz(b), xyz(c), refine_ctr);
+    int id = __float_as_int(a.w);
+    if (t > kTMin && (t < h.t || (t == h.t && id < best_id))) {
+      h.t = t;
+      h.slot = slot;
+      best_id = id;
+    }
+  };
+  if (S.n_tris == 1) {
+    test_leaf(0);
+    return h;
+  }
+  int stack[kStackDepth];
+  int sp = 0;
+  int node = 0;
+  // a binary tree of n leaves has n-1 internal nodes: a traversal never visits
+  // more, so the bound only trips on a corrupt hierarchy
+  int guard = S.n_tris + 8;
+  for (;;) {
+    if (--guard < 0) {
+      if (err) *err = 2;
+      break;
+    }
+    const float4* N = S.nodes + 4 * node;
+    const float4 n0 = __ldg(N), n1 = __ldg(N + 1), n2 = __ldg(N + 2), n3 = __ldg(N + 3);
+    const int lref = __float_as_int(n3.x), rref = __float_as_int(n3.y);
+    float tl = box_entry(r, f3(n0.x, n0.y, n0.z), f3(n0.w, n1.x, n1.y), h.t);
+    float tr = box_entry(r, f3(n1.z, n1.w, n2.x), f3(n2.y, n2.z, n2.w), h.t);
+    bool hl = tl <= h.t, hr = tr <= h.t;
+    int next = -1;
+    // leaves are tested immediately; internal children are descended/pushed
+    if (hl && lref < 0) {
+      test_leaf(lref & 0x7fffffff);
+      hl = false;
+    }
+    if (hr && rref < 0) {
+      test_leaf(rref & 0x7fffffff);
+      hr = false;
+    }
+    if (hl && hr) {
+      int nearer = tl <= tr ? lref : rref;
+      int farther = tl <= tr ? rref : lref;
+      if (sp < kStackDepth) {
+        stack[sp++] = farther;
+      } else if (err) {
+        *err = 1;
+      }
+      next = nearer;
+    } else if (hl) {
+      next = lref;
+    } else if (hr) {
+      next = rref;
+    }
+    if (next < 0) {
+      // pop until an internal node whose box still overlaps [0, best]
+      if (sp == 0) break;
+      next = stack[--sp];
+    }
+    node = next;
+  }
+  return h;
+}
+
+// ------------------------------------------------------------------ small complex (FP32)
+struct cf {
+  float re, im;
+};
+__device__ __forceinline__ cf cadd(cf a, cf b) { return cf{a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cf csub(cf a, cf b) { return cf{a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ cf cmul(cf a, cf b) { return cf{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ cf cdiv(cf a, cf b) {
+  float den = b.re * b.re + b.im * b.im;
+  return cf{(a.re * b.re + a.im * b.im) / den, (a.im * b.re - a.re * b.im) / den};
+}
+__device__ __forceinline__ cf csqrt(cf z) {
+  // principal square root
+  float m = sqrtf(z.re * z.re + z.im * z.im);
+  float re = sqrtf(fmaxf(0.0f, 0.5f * (m + z.re)));
+  float im = copysignf(sqrtf(fmaxf(0.0f, 0.5f * (m - z.re))), z.im);
+  return cf{re, im};
+}
+
+// Fresnel reflection of a smooth conductor (n = n_re + i n_im): Mueller
+// entries of diag(r_s, r_p) in s-p frames: a = (|rs|^2+|rp|^2)/2,
+// b = (|rs|^2-|rp|^2)/2, cr + i ci = rs conj(rp).
+struct FresnelM {
+  float a, b, cr, ci;
+};
+__device__ __forceinline__ FresnelM fresnel_conductor(float cos_i, float n_re, float n_im) {
+  cf n{n_re, n_im};
+  float sin2 = fmaxf(0.0f, 1.0f - cos_i * cos_i);
+  cf n2 = cmul(n, n);
+  cf ncos_t = csqrt(cf{n2.re - sin2, n2.im});
+  cf cos_t = cdiv(ncos_t, n);
+  cf ci{cos_i, 0.0f};
+  cf rs = cdiv(csub(ci, ncos_t), cadd(ci, ncos_t));
+  cf nci = cmul(n, ci);
+  cf rp = cdiv(csub(nci, cos_t), cadd(nci, cos_t));
+  float A = rs.re * rs.re + rs.im * rs.im, B = rp.re * rp.re + rp.im * rp.im;
+  FresnelM m;
+  m.a = 0.5f * (A + B);
+  m.b = 0.5f * (A - B);
+  m.cr = rs.re * rp.re + rs.im * rp.im;   // Re(rs conj(rp))
+  m.ci = rs.im * rp.re - rs.re * rp.im;   // Im(rs conj(rp))
+  return m;
+}
+
+// s vector of the plane of incidence for propagation k at normal n; falls back
+// to `fb` (orthogonalised against k) near normal incidence.
+__device__ __forceinline__ float3 s_vector(float3 n, float3 k, float3 fb) {
+  float3 s = cross(n, k);
+  float l2 = dot(s, s);
+  if (l2 > 1e-14f) return rsqrtf(l2) * s;
+  return normalize(fb - dot(fb, k) * k);
+}
+
+}  // namespace gr

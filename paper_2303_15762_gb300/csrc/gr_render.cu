@@ -1,0 +1,1128 @@
+// Wavefront integrator for backward path tracing of generalized rays.
+//
+// Work decomposition.  A ticket is one (view, spectral bin, pixel); it owns the
+// samples s in [first_sample, first_sample + spp) with s mod n_bins == bin,
+// which one pool slot traces one after another and sums (Kahan) in sample
+// order, so every pixel value is deterministic whatever the schedule.  A fixed
+// pool of P slots persists across iterations; each iteration is four kernels:
+//   regen  : fold finished samples, start the ticket's next sample (camera
+//            generalized ray, Eq. MC_sourcing), or claim new tickets with one
+//            warp-aggregated atomic per warp; compact live slots into the
+//            trace queue (ballot + popc)
+//   trace  : closest hit of every queued ray (BVH, stack traversal)
+//   shade  : footprint update (Eq. K_free_space_propagation), measurement on
+//            escape / emitter hit (Eq. measurement_operator), interaction with
+//            the reversed wavevector (Eq. action_time_reversal) and sampling of
+//            one child ray (Eq. MC_light_transport_Q1): grating orders
+//            (Eq. K_grating, order tables staged in shared memory), rough lobe
+//            (Eq. K_surface_HS), smooth reflection (Eq. K_reflection_refraction)
+//            with Fresnel Mueller weights; NEE shadow requests are queued
+//   shadow : trace NEE shadow rays, measure the emitter, add the MIS-weighted
+//            contribution
+// All launches have fixed shapes (grid-stride loops over device-side queue
+// counts), so a batch of iterations can be replayed as one CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "gr_build.h"
+
+namespace gr {
+
+enum { ST_IDLE = 0, ST_ACTIVE = 1, ST_DONE = 2 };
+
+__device__ __forceinline__ int meta_k(int z) { return z & 0xffff; }
+__device__ __forceinline__ int meta_seg(int z) { return (z >> 16) & 0xff; }
+__device__ __forceinline__ int meta_state(int z) { return (z >> 24) & 3; }
+__device__ __forceinline__ int meta_delta(int z) { return (z >> 26) & 1; }
+__device__ __forceinline__ int meta_pack(int k, int seg, int st, int delta) {
+  return k | (seg << 16) | (st << 24) | (delta << 26);
+}
+
+__device__ __forceinline__ int bin_first_sample(const DevView& V, int bin) {
+  int r = (bin - V.first_sample) % V.nb;
+  if (r < 0) r += V.nb;
+  return V.first_sample + r;
+}
+__device__ __forceinline__ int bin_samples(const DevView& V, int bin) {
+  int s0 = bin_first_sample(V, bin);
+  int end = V.first_sample + V.spp;
+  return s0 < end ? (end - 1 - s0) / V.nb + 1 : 0;
+}
+__device__ __forceinline__ float bin_lambda(const DevView& V, int b) {
+  if (V.nb <= 1) return V.lmin;
+  return V.lmin + (float)b * (V.lmax - V.lmin) / (float)(V.nb - 1);
+}
+__device__ __forceinline__ double bin_lambda_d(const DevView& V, int b) {
+  if (V.nb <= 1) return (double)V.lmin;
+  return (double)V.lmin + (double)b * ((double)V.lmax - (double)V.lmin) / (double)(V.nb - 1);
+}
+// Angular variance of a source of coherence length lc (um): (lambda/lc)^2.
+__device__ __forceinline__ float src_spread2(float lambda, float lc) {
+  if (lc <= 0.0f) return 0.0f;
+  float s = lambda / lc;
+  return s * s;
+}
+
+__device__ __forceinline__ int find_view(const RenderParams& p, unsigned long long t) {
+  int lo = 0, hi = p.n_views - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if ((unsigned long long)p.views[mid].ticket_base <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename TT>
+__device__ __forceinline__ float table_load(const TT* v, int i);
+template <>
+__device__ __forceinline__ float table_load<float>(const float* v, int i) {
+  return v[i];
+}
+template <>
+__device__ __forceinline__ float table_load<__half>(const __half* v, int i) {
+  return __half2float(v[i]);
+}
+template <>
+__device__ __forceinline__ float table_load<__nv_bfloat16>(const __nv_bfloat16* v, int i) {
+  return __bfloat162float(v[i]);
+}
+
+// ------------------------------------------------------------------ sourcing
+template <int NS>
+__device__ __forceinline__ void start_sample(const RenderParams& p, int slot, int view, int local, int k) {
+  const DevView& V = p.views[view];
+  const int WH = V.W * V.H;
+  const int bin = local / WH;
+  const int pixel = local - bin * WH;
+  const int py = pixel / V.W, px = pixel - py * V.W;
+  const int s = bin_first_sample(V, bin) + k * V.nb;
+  float4 u = rng4(p.seed, (uint32_t)V.view_index, (uint32_t)pixel, (uint32_t)s, 0, kCallJitter);
+  float fx = ((float)px + u.x) / (float)V.W, fy = ((float)py + u.y) / (float)V.H;
+  float3 o, d;
+  if (V.ortho) {
+    o = V.eye + ((2.0f * fx - 1.0f) * V.ortho_half * V.aspect) * V.right + ((1.0f - 2.0f * fy) * V.ortho_half) * V.upc;
+    d = V.fw;
+  } else {
+    float sx = (2.0f * fx - 1.0f) * V.th * V.aspect;
+    float sy = (1.0f - 2.0f * fy) * V.th;
+    o = V.eye;
+    d = normalize(V.fw + sx * V.right + sy * V.upc);
+  }
+  const Pool& P = p.pool;
+  P.od0[slot] = make_float4(o.x, o.y, o.z, V.beta0 * V.beta0);
+  P.od1[slot] = make_float4(d.x, d.y, d.z, 0.0f);
+  if (NS == 1) {
+    P.tp[0][slot] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+  } else {
+    P.tp[0][slot] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+    P.tp[1][slot] = make_float4(0.0f, 1.0f, 0.0f, 0.0f);
+    P.tp[2][slot] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+    P.tp[3][slot] = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+    float3 xf = normalize(V.right - dot(V.right, d) * d);
+    P.xf[slot] = make_float4(xf.x, xf.y, xf.z, 0.0f);
+  }
+  if (NS == 1) P.xf[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  P.part[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  P.meta[slot] = make_int4(view, local, meta_pack(k, 0, ST_ACTIVE, 1), -1);
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  float y = v - c;
+  float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// ------------------------------------------------------------------ regen
+template <int NS>
+__global__ void __launch_bounds__(256) k_regen(RenderParams p) {
+  const Pool& P = p.pool;
+  const int lane = threadIdx.x & 31;
+  const int stride = gridDim.x * blockDim.x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    p.ctr->sq_count = 0;
+    p.ctr->iters += 1;
+  }
+  int finished = 0;
+  for (int base = blockIdx.x * blockDim.x; base < p.P; base += stride) {
+    const int slot = base + threadIdx.x;
+    const bool valid = slot < p.P;
+    bool need = false, active = false;
+    int4 m = valid ? P.meta[slot] : make_int4(0, 0, 0, 0);
+    const int st = meta_state(m.z);
+    if (valid && st == ST_DONE) {
+      ++finished;
+      const DevView& V = p.views[m.x];
+      float4 s = P.accS[slot], c = P.accC[slot], v = P.part[slot];
+      kahan_add(s.x, c.x, v.x);
+      if (NS == 4) {
+        kahan_add(s.y, c.y, v.y);
+        kahan_add(s.z, c.z, v.z);
+        kahan_add(s.w, c.w, v.w);
+      }
+      const int WH = V.W * V.H;
+      const int bin = m.y / WH;
+      const int k = meta_k(m.z) + 1;
+      if (k < bin_samples(V, bin)) {
+        P.accS[slot] = s;
+        P.accC[slot] = c;
+        start_sample<NS>(p, slot, m.x, m.y, k);
+        active = true;
+      } else {
+        // ticket complete: add its sum into the frame accumulator (Kahan)
+        const size_t idx = (size_t)m.y * NS;
+        float tot[4] = {s.x - c.x, s.y - c.y, s.z - c.z, s.w - c.w};
+        for (int q = 0; q < NS; ++q) {
+          float a = V.acc_sum[idx + q], e = V.acc_comp[idx + q];
+          kahan_add(a, e, tot[q]);
+          V.acc_sum[idx + q] = a;
+          V.acc_comp[idx + q] = e;
+        }
+        need = true;
+      }
+    } else if (valid && st == ST_IDLE) {
+      need = true;
+    } else if (valid && st == ST_ACTIVE) {
+      active = true;
+    }
+    // claim tickets, one atomic per warp
+    while (__any_sync(0xffffffffu, need)) {
+      unsigned mask = __ballot_sync(0xffffffffu, need);
+      unsigned long long first = 0;
+      int leader = __ffs(mask) - 1;
+      if (lane == leader) first = atomicAdd(&p.ctr->next_ticket, (unsigned long long)__popc(mask));
+      first = __shfl_sync(0xffffffffu, first, leader);
+      if (need) {
+        unsigned long long t = first + __popc(mask & ((1u << lane) - 1u));
+        if (t >= p.ctr->total_tickets) {
+          need = false;
+          P.meta[slot] = make_int4(0, 0, meta_pack(0, 0, ST_IDLE, 0), -1);
+        } else {
+          int view = find_view(p, t);
+          const DevView& V = p.views[view];
+          int local = (int)(t - (unsigned long long)V.ticket_base);
+          int bin = local / (V.W * V.H);
+          if (bin_samples(V, bin) > 0) {
+            P.accS[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            P.accC[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            start_sample<NS>(p, slot, view, local, 0);
+            active = true;
+            need = false;
+          }
+        }
+      }
+    }
+    unsigned amask = __ballot_sync(0xffffffffu, active);
+    if (amask) {
+      int leader = __ffs(amask) - 1;
+      int first = 0;
+      if (lane == leader) first = atomicAdd(&p.ctr->tq_count, __popc(amask));
+      first = __shfl_sync(0xffffffffu, first, leader);
+      if (active) P.tq[first + __popc(amask & ((1u << lane) - 1u))] = slot;
+    }
+  }
+  // per-warp sum of completed samples
+  for (int off = 16; off > 0; off >>= 1) finished += __shfl_down_sync(0xffffffffu, finished, off);
+  if (lane == 0 && finished) atomicAdd(&p.ctr->samples, (unsigned long long)finished);
+}
+
+// ------------------------------------------------------------------ trace
+__global__ void __launch_bounds__(256) k_trace(RenderParams p) {
+  const Pool& P = p.pool;
+  const int n = *(volatile int*)&p.ctr->tq_count;
+  if (blockIdx.x == 0 && threadIdx.x == 0) p.ctr->segments += (unsigned long long)n;
+  int err = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int slot = P.tq[i];
+    const int4 m = P.meta[slot];
+    const DevView& V = p.views[m.x];
+    const DevScene& S = p.scenes[V.scene_index];
+    const float4 a = P.od0[slot], b = P.od1[slot];
+    Hit h = closest_hit(S, xyz(a), xyz(b), m.w, &p.ctr->ref_hit, &err);
+    P.hit[slot] = make_float2(h.t, __int_as_float(h.slot));
+  }
+  if (err) atomicOr(&p.ctr->err, 1);
+}
+
+// ------------------------------------------------------------------ measurement
+// Emitter measurement (Eq. measurement_operator on an emissive triangle set):
+// one footprint point x ~ N(0, beta^2/2) transverse to d, projected along d
+// onto the emitter plane and tested for coverage; the local mean direction is
+// shifted by rho x / (beta^2 |k|) with residual angular variance
+// 1/(2 beta^2 |k|^2); the source emits a Gaussian lobe of spread lambda/lc
+// about its normal.  The lobe's quadratic form is evaluated in FP64.
+__device__ float measure_emitter(const DevScene& S, int ei, float3 hit, float3 d, float beta2, float rho, float k,
+                                 float lambda, float u0, float u1) {
+  const DevEmitter E = S.emitters[ei];
+  const gr_material& M = S.mats[E.mat];
+  const float4 t0 = S.emitter_tris[3 * E.first], t1 = S.emitter_tris[3 * E.first + 1],
+               t2 = S.emitter_tris[3 * E.first + 2];
+  d3 ned = dnormalize(dcross(dsub(D3(xyz(t1)), D3(xyz(t0))), dsub(D3(xyz(t2)), D3(xyz(t0)))));
+  float3 ne = f3((float)ned.x, (float)ned.y, (float)ned.z);
+  if (dot(d, ne) >= 0.0f) return 0.0f;
+  float z0, z1;
+  box_muller(u0, u1, z0, z1);
+  const float sigma = sqrtf(0.5f * beta2);
+  float3 e1, e2;
+  onb(d, e1, e2);
+  const float3 x_um = (sigma * z0) * e1 + (sigma * z1) * e2;
+  const float3 pt = hit + 1e-6f * x_um;
+  const float tp = dot(xyz(t0) - pt, ne) / dot(d, ne);
+  const float3 q = pt + tp * d;
+  bool covered = false;
+  for (int i = 0; i < E.count && !covered; ++i) {
+    const float3 v0 = xyz(S.emitter_tris[3 * (E.first + i)]);
+    const float3 a = xyz(S.emitter_tris[3 * (E.first + i) + 1]) - v0;
+    const float3 b = xyz(S.emitter_tris[3 * (E.first + i) + 2]) - v0;
+    const float3 c = q - v0;
+    const float daa = dot(a, a), dab = dot(a, b), dbb = dot(b, b), dca = dot(c, a), dcb = dot(c, b);
+    const float den = daa * dbb - dab * dab;
+    const float bu = (dbb * dca - dab * dcb) / den;
+    const float bv = (daa * dcb - dab * dca) / den;
+    covered = bu >= 0.0f && bv >= 0.0f && bu + bv <= 1.0f;
+  }
+  if (!covered) return 0.0f;
+  const float3 mu = (rho / (beta2 * k)) * x_um;
+  // FP64 quadratic form of the measured lobe
+  const d3 dl = dnormalize(dadd(D3(d), D3(mu)));
+  const d3 w = d3{-dl.x, -dl.y, -dl.z};
+  const d3 diff = dsub(w, ned);
+  const double sc2 = 1.0 / (2.0 * (double)beta2 * (double)k * (double)k);
+  double s2 = 0.0;
+  if (M.coh_len_um > 0.0f) {
+    double s = (double)lambda / (double)M.coh_len_um;
+    s2 = s * s;
+  }
+  const double kappa = 1.0 / (sc2 + s2);
+  const double q2 = 0.5 * kappa * ddot(diff, diff);
+  const float kf = (float)kappa;
+  const float pref = kf < 1e-8f ? 0.25f / kPi : kf / (2.0f * kPi * (-expm1f(-2.0f * kf)));
+  return M.Le * pref * expf(-(float)q2);
+}
+
+__device__ __forceinline__ float3 emitter_normal(const DevScene& S, int ei) {
+  const DevEmitter E = S.emitters[ei];
+  const float4 t0 = S.emitter_tris[3 * E.first], t1 = S.emitter_tris[3 * E.first + 1],
+               t2 = S.emitter_tris[3 * E.first + 2];
+  d3 n = dnormalize(dcross(dsub(D3(xyz(t1)), D3(xyz(t0))), dsub(D3(xyz(t2)), D3(xyz(t0)))));
+  return f3((float)n.x, (float)n.y, (float)n.z);
+}
+
+// Density of the m >= 1 part of the rough lobe in tangential direction cosines.
+__device__ float rough_density(float g, float k, float ell, float3 delta) {
+  const float kl2 = (k * ell) * (k * ell);
+  const float r2 = dot(delta, delta);
+  if (g > kGCont) {
+    const float var = 2.0f * g / kl2;
+    return expf(-0.5f * r2 / var) / (2.0f * kPi * var);
+  }
+  float pm = expf(-g), sum = 0.0f;
+  const int mmax = (int)(g + 12.0f * sqrtf(g) + 20.0f);
+  for (int m = 1; m <= mmax; ++m) {
+    pm *= g / (float)m;
+    const float var = 2.0f * (float)m / kl2;
+    sum += pm * expf(-0.5f * r2 / var) / (2.0f * kPi * var);
+  }
+  return sum;
+}
+
+// ------------------------------------------------------------------ shade
+template <int NS, typename TT>
+__global__ void __launch_bounds__(256) k_shade(RenderParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const TableRow* rows = p.rows;
+  const TT* tvals = (const TT*)p.table_vals;
+  if (p.table_smem) {
+    TableRow* srows = (TableRow*)smem;
+    TT* svals = (TT*)(smem + sizeof(TableRow) * p.table_rows);
+    for (int i = threadIdx.x; i < p.table_rows; i += blockDim.x) srows[i] = p.rows[i];
+    for (int i = threadIdx.x; i < p.table_vals_count; i += blockDim.x) svals[i] = ((const TT*)p.table_vals)[i];
+    __syncthreads();
+    rows = srows;
+    tvals = svals;
+  }
+  const Pool& P = p.pool;
+  const int n = *(volatile int*)&p.ctr->tq_count;
+  const int lane = threadIdx.x & 31;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int i = base + threadIdx.x;
+    bool want_shadow = false;
+    int slot = -1;
+    if (i < n) {
+      slot = P.tq[i];
+      int4 m = P.meta[slot];
+      const DevView& V = p.views[m.x];
+      const DevScene& S = p.scenes[V.scene_index];
+      float4 a0 = P.od0[slot], a1 = P.od1[slot];
+      const float2 hh = P.hit[slot];
+      float3 o = xyz(a0), d = xyz(a1);
+      float beta2 = a0.w, rho = a1.w;
+      const int kk = meta_k(m.z), seg = meta_seg(m.z), prev_delta = meta_delta(m.z);
+      const int WH = V.W * V.H;
+      const int bin = m.y / WH;
+      const int pixel = m.y - bin * WH;
+      const int smp = bin_first_sample(V, bin) + kk * V.nb;
+      const float lambda = bin_lambda(V, bin);
+      const float kw = 2.0f * kPi / lambda;
+      const float s_ray2 = 1.0f / (2.0f * V.beta0 * V.beta0 * kw * kw);
+      float T[4][4];
+      if (NS == 1) {
+        T[0][0] = P.tp[0][slot].x;
+      } else {
+        for (int r = 0; r < 4; ++r) {
+          float4 v = P.tp[r][slot];
+          T[r][0] = v.x;
+          T[r][1] = v.y;
+          T[r][2] = v.z;
+          T[r][3] = v.w;
+        }
+      }
+      float4 xfv = P.xf[slot];
+      float4 pt = P.part[slot];
+      const int hslot = __float_as_int(hh.y);
+      bool done = false;
+      auto add_col = [&](float val) {
+        pt.x += T[0][0] * val;
+        if (NS == 4) {
+          pt.y += T[1][0] * val;
+          pt.z += T[2][0] * val;
+          pt.w += T[3][0] * val;
+        }
+      };
+      if (hslot < 0) {
+        float msum = 0.0f;
+        for (int l = 0; l < S.n_lights; ++l) {
+          const gr_light L = S.lights[l];
+          if (L.type == GR_LIGHT_ENV) {
+            msum += L.E;
+          } else {
+            const float kap = 1.0f / (s_ray2 + src_spread2(lambda, L.coh_len_um));
+            msum += L.E * vmf(d, f3(L.dir[0], L.dir[1], L.dir[2]), kap);
+          }
+        }
+        add_col(msum);
+        done = true;
+      } else {
+        const float t = hh.x;
+        // footprint update, Eq. K_free_space_propagation (z in um)
+        {
+          const float zbar = t * 1e6f / kw;
+          const float b2 = beta2 + 2.0f * zbar * rho + zbar * zbar * (1.0f + rho * rho) / beta2;
+          const float ro = rho + zbar * (1.0f + rho * rho) / beta2;
+          beta2 = b2;
+          rho = ro;
+        }
+        const float3 x = o + t * d;
+        const int mat = S.tri_mat[hslot];
+        const gr_material M = S.mats[mat];
+        if (M.type == GR_MAT_EMITTER) {
+          const int ei = S.emitter_of_mat[mat];
+          float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallEmitFoot);
+          float val = measure_emitter(S, ei, x, d, beta2, rho, kw, lambda, u.x, u.y);
+          float w = 1.0f;
+          if ((p.flags & GR_FLAG_NEE) && !prev_delta && S.n_emitters > 0 && val > 0.0f) {
+            const float3 ne = emitter_normal(S, ei);
+            const float kap = 1.0f / (s_ray2 + src_spread2(lambda, M.coh_len_um));
+            const float pn = vmf(-d, ne, kap) / (float)S.n_emitters;
+            const float pb = xfv.w;
+            w = pb * pb / (pb * pb + pn * pn);
+          }
+          add_col(val * w);
+          done = true;
+        } else if (M.type == GR_MAT_ABSORBER || seg >= V.max_depth) {
+          done = true;
+        } else {
+          if ((p.flags & GR_FLAG_RR) && seg >= 3) {
+            const float q = fminf(1.0f, fmaxf(0.05f, T[0][0]));
+            float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallRR);
+            if (u.x >= q) {
+              done = true;
+            } else {
+              const float iq = 1.0f / q;
+              for (int r = 0; r < (NS == 1 ? 1 : 4); ++r)
+                for (int c = 0; c < (NS == 1 ? 1 : 4); ++c) T[r][c] *= iq;
+            }
+          }
+          if (!done) {
+            // --- interaction with the reversed wavevector
+            const float4 v0 = __ldg(&S.tri[3 * hslot]), v1 = __ldg(&S.tri[3 * hslot + 1]),
+                         v2 = __ldg(&S.tri[3 * hslot + 2]);
+            float3 nrm = normalize(cross(xyz(v1) - xyz(v0), xyz(v2) - xyz(v0)));
+            if (dot(nrm, d) > 0.0f) nrm = -nrm;
+            const float cos_i = -dot(d, nrm);
+            FresnelM F{1.0f, 0.0f, 1.0f, 0.0f};
+            if (M.fresnel == 1) F = fresnel_conductor(cos_i, M.n_re, M.n_im);
+            float cn[4];
+            float3 s_o = f3(0.f, 0.f, 0.f);
+            if (NS == 1) {
+              T[0][0] *= F.a;
+              cn[0] = T[0][0];
+            } else {
+              const float3 k_o = -d;
+              const float3 xf = xyz(xfv);
+              s_o = s_vector(nrm, k_o, xf);
+              const float3 p_o = cross(k_o, s_o);
+              const float cphi = dot(xf, s_o), sphi = dot(xf, p_o);
+              const float r2 = cphi * cphi + sphi * sphi;
+              const float c2 = (cphi * cphi - sphi * sphi) / r2, s2 = 2.0f * cphi * sphi / r2;
+              for (int r = 0; r < 4; ++r) {
+                const float X0 = T[r][0], X3 = T[r][3];
+                const float X1 = T[r][1] * c2 - T[r][2] * s2;
+                const float X2 = T[r][1] * s2 + T[r][2] * c2;
+                T[r][0] = F.a * X0 + F.b * X1;
+                T[r][1] = F.b * X0 + F.a * X1;
+                T[r][2] = F.cr * X2 - F.ci * X3;
+                T[r][3] = F.ci * X2 + F.cr * X3;
+                cn[r] = T[r][0];
+              }
+            }
+            // --- sample the scattered distribution
+            const float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallLobe);
+            const float3 t_mir = d - dot(d, nrm) * nrm;
+            float3 d_out = d;
+            int delta = 1;
+            float pdf = 0.0f;
+            bool alive = true;
+            float g_r = 0.0f;
+            if (M.type == GR_MAT_GRATING) {
+              float3 gt = f3(M.gdir[0], M.gdir[1], M.gdir[2]);
+              gt = gt - dot(gt, nrm) * nrm;
+              if (dot(gt, gt) < 1e-12f) {
+                float3 e1, e2;
+                onb(nrm, e1, e2);
+                gt = e1;
+              }
+              gt = normalize(gt);
+              const float step = lambda / M.period_um;
+              const TableRow row = rows[V.table_base + mat * V.nb + bin];
+              const int jm = row.jmax;
+              const bool renorm = !(p.flags & GR_FLAG_NO_RENORM);
+              float total = 0.0f;
+              for (int j = -jm; j <= jm; ++j) {
+                const float3 tj = t_mir + ((float)j * step) * gt;
+                if (dot(tj, tj) < 1.0f) total += table_load<TT>(tvals, row.offset + (j < 0 ? -j : j));
+              }
+              if (!renorm) total = 1.0f;
+              const float target = u.x * total;
+              float cum = 0.0f, prev = 0.0f;
+              int pick = 0x7fffffff;
+              for (int j = -jm; j <= jm; ++j) {
+                const float3 tj = t_mir + ((float)j * step) * gt;
+                if (dot(tj, tj) < 1.0f) {
+                  prev = cum;
+                  cum += table_load<TT>(tvals, row.offset + (j < 0 ? -j : j));
+                  if (cum > target) {
+                    pick = j;
+                    break;
+                  }
+                }
+              }
+              // FP64 decision near a CDF boundary (tables are approximate)
+              const float eps = (p.table_dtype == GR_TABLE_F32 ? 2e-6f : (p.table_dtype == GR_TABLE_F16 ? 2e-3f : 2e-2f)) *
+                                fmaxf(total, 1e-30f);
+              if ((pick != 0x7fffffff && (cum - target < eps || target - prev < eps)) ||
+                  (pick == 0x7fffffff && renorm)) {
+                atomicAdd(&p.ctr->ref_lobe, 1ull);
+                const double lam_d = bin_lambda_d(V, bin);
+                const double xarg = kPiD * (double)M.height_um / lam_d;
+                double tot_d = 0.0;
+                for (int j = -jm; j <= jm; ++j) {
+                  const float3 tj = t_mir + ((float)j * step) * gt;
+                  if (dot(tj, tj) < 1.0f) {
+                    double J = bessel_j_d(j, xarg);
+                    tot_d += J * J;
+                  }
+                }
+                if (!renorm) tot_d = 1.0;
+                const double tgt = (double)u.x * tot_d;
+                double cd = 0.0;
+                pick = 0x7fffffff;
+                for (int j = -jm; j <= jm; ++j) {
+                  const float3 tj = t_mir + ((float)j * step) * gt;
+                  if (dot(tj, tj) < 1.0f) {
+                    double J = bessel_j_d(j, xarg);
+                    cd += J * J;
+                    if (cd > tgt) {
+                      pick = j;
+                      break;
+                    }
+                  }
+                }
+              }
+              if (pick == 0x7fffffff) {
+                alive = false;
+              } else {
+                const float3 tj = t_mir + ((float)pick * step) * gt;
+                d_out = tj + sqrtf(fmaxf(0.0f, 1.0f - dot(tj, tj))) * nrm;
+              }
+            } else if (M.type == GR_MAT_MIRROR) {
+              d_out = d + (2.0f * cos_i) * nrm;
+            } else {  // rough
+              g_r = 2.0f * kw * M.sigma_h_um * cos_i;
+              g_r *= g_r;
+              float mreal;
+              if (g_r > kGCont) {
+                mreal = g_r;
+              } else {
+                float pm = expf(-g_r), cdf = pm;
+                int mi = 0;
+                while (u.x >= cdf && mi < 1000) {
+                  ++mi;
+                  pm *= g_r / (float)mi;
+                  cdf += pm;
+                }
+                const float eps = 4e-6f + 2e-7f * (float)mi;
+                if (fabsf(u.x - cdf) < eps || (mi > 0 && fabsf(u.x - (cdf - pm)) < eps) || mi >= 1000) {
+                  atomicAdd(&p.ctr->ref_lobe, 1ull);
+                  const double lam_d = bin_lambda_d(V, bin);
+                  const double kd = 2.0 * kPiD / lam_d;
+                  double gd = 2.0 * kd * (double)M.sigma_h_um * (double)cos_i;
+                  gd *= gd;
+                  double pd = exp(-gd), cd = pd;
+                  mi = 0;
+                  while ((double)u.x >= cd && mi < 1000) {
+                    ++mi;
+                    pd *= gd / mi;
+                    cd += pd;
+                  }
+                }
+                mreal = (float)mi;
+              }
+              if (mreal == 0.0f) {
+                d_out = d + (2.0f * cos_i) * nrm;
+              } else {
+                delta = 0;
+                const float kl = kw * M.corr_len_um;
+                const float sig = sqrtf(2.0f * mreal) / kl;
+                float z0, z1;
+                box_muller(u.y, u.z, z0, z1);
+                float3 e1, e2;
+                onb(nrm, e1, e2);
+                const float3 dt = (sig * z0) * e1 + (sig * z1) * e2;
+                const float3 to = t_mir + dt;
+                const float tt = dot(to, to);
+                if (tt >= 1.0f) {
+                  alive = false;
+                } else {
+                  const float cz = sqrtf(1.0f - tt);
+                  d_out = to + cz * nrm;
+                  if (p.flags & GR_FLAG_NEE) pdf = rough_density(g_r, kw, M.corr_len_um, dt) * cz;
+                }
+              }
+            }
+            // --- next-event estimation toward an emitter (rough lobes only)
+            if (M.type == GR_MAT_ROUGH && (p.flags & GR_FLAG_NEE) && S.n_emitters > 0) {
+              const float4 un = rng4(p.seed, V.view_index, pixel, smp, seg, kCallNeeDir);
+              const int ne_cnt = S.n_emitters;
+              int ei = (int)(un.x * (float)ne_cnt);
+              if (ei > ne_cnt - 1) ei = ne_cnt - 1;
+              const float3 nE = emitter_normal(S, ei);
+              const gr_material EM = S.mats[S.emitters[ei].mat];
+              const float kap = 1.0f / (s_ray2 + src_spread2(lambda, EM.coh_len_um));
+              const float3 w = vmf_sample(-nE, kap, un.y, un.z);
+              const float cos_o = dot(w, nrm);
+              if (cos_o > 0.0f) {
+                const float3 dtn = (w - dot(w, nrm) * nrm) - t_mir;
+                const float f = (g_r > 0.0f ? rough_density(g_r, kw, M.corr_len_um, dtn) : 0.0f) * cos_o;
+                const float pn = vmf(w, -nE, kap) / (float)ne_cnt;
+                if (f > 0.0f && pn > 0.0f) {
+                  const float wm = pn * pn / (pn * pn + f * f) * (f / pn);
+                  P.shd[slot] = make_float4(w.x, w.y, w.z, __int_as_float(ei | (seg << 16)));
+                  P.shc[slot] = make_float4(cn[0] * wm, NS == 4 ? cn[1] * wm : 0.0f, NS == 4 ? cn[2] * wm : 0.0f,
+                                            NS == 4 ? cn[3] * wm : 0.0f);
+                  want_shadow = true;
+                }
+              }
+            }
+            // the vertex becomes the ray origin; (beta, rho) are unchanged by
+            // the interaction (Eq. K_reflection_refraction, Eq. K_grating)
+            P.od0[slot] = make_float4(x.x, x.y, x.z, beta2);
+            if (alive) {
+              P.od1[slot] = make_float4(d_out.x, d_out.y, d_out.z, rho);
+              if (NS == 1) {
+                P.tp[0][slot] = make_float4(T[0][0], 0.0f, 0.0f, 0.0f);
+                P.xf[slot] = make_float4(0.0f, 0.0f, 0.0f, pdf);
+              } else {
+                for (int r = 0; r < 4; ++r) P.tp[r][slot] = make_float4(T[r][0], T[r][1], T[r][2], T[r][3]);
+                const float3 xn = s_vector(nrm, -d_out, s_o);
+                P.xf[slot] = make_float4(xn.x, xn.y, xn.z, pdf);
+              }
+              P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg + 1, ST_ACTIVE, delta), hslot);
+            } else {
+              P.od1[slot] = make_float4(d.x, d.y, d.z, rho);
+              P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg, ST_DONE, 0), hslot);
+            }
+          }
+        }
+      }
+      P.part[slot] = pt;
+      if (done) P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg, ST_DONE, 0), m.w);
+    }
+    unsigned smask = __ballot_sync(0xffffffffu, want_shadow);
+    if (smask) {
+      int leader = __ffs(smask) - 1;
+      int first = 0;
+      if (lane == leader) first = atomicAdd(&p.ctr->sq_count, __popc(smask));
+      first = __shfl_sync(0xffffffffu, first, leader);
+      if (want_shadow) P.sq[first + __popc(smask & ((1u << lane) - 1u))] = slot;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ shadow
+template <int NS>
+__global__ void __launch_bounds__(256) k_shadow(RenderParams p) {
+  const Pool& P = p.pool;
+  const int n = *(volatile int*)&p.ctr->sq_count;
+  int err = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int slot = P.sq[i];
+    const int4 m = P.meta[slot];
+    const DevView& V = p.views[m.x];
+    const DevScene& S = p.scenes[V.scene_index];
+    const float4 a0 = P.od0[slot], a1 = P.od1[slot], sd = P.shd[slot];
+    const int tag = __float_as_int(sd.w);
+    const int ei = tag & 0xffff, seg = tag >> 16;
+    const float3 x = xyz(a0), w = xyz(sd);
+    Hit h = closest_hit(S, x, w, m.w, &p.ctr->ref_hit, &err);
+    if (h.slot < 0 || S.tri_mat[h.slot] != S.emitters[ei].mat) continue;
+    const int WH = V.W * V.H;
+    const int bin = m.y / WH;
+    const int pixel = m.y - bin * WH;
+    const int smp = bin_first_sample(V, bin) + meta_k(m.z) * V.nb;
+    const float lambda = bin_lambda(V, bin);
+    const float kw = 2.0f * kPi / lambda;
+    float beta2 = a0.w, rho = a1.w;
+    const float zbar = h.t * 1e6f / kw;
+    const float b2 = beta2 + 2.0f * zbar * rho + zbar * zbar * (1.0f + rho * rho) / beta2;
+    const float ro = rho + zbar * (1.0f + rho * rho) / beta2;
+    const float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallNeeFoot);
+    const float val = measure_emitter(S, ei, x + h.t * w, w, b2, ro, kw, lambda, u.x, u.y);
+    if (val != 0.0f) {
+      const float4 c = P.shc[slot];
+      float4 pt = P.part[slot];
+      pt.x += c.x * val;
+      if (NS == 4) {
+        pt.y += c.y * val;
+        pt.z += c.z * val;
+        pt.w += c.w * val;
+      }
+      P.part[slot] = pt;
+    }
+  }
+  if (err) atomicOr(&p.ctr->err, 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    p.ctr->shadow += (unsigned long long)n;
+    p.ctr->last_active = p.ctr->tq_count;
+    p.ctr->tq_count = 0;
+  }
+}
+
+// ------------------------------------------------------------------ order tables
+struct TableBuildRow {
+  int offset, jmax, view, bin;
+  float height_um;
+  int pad[3];
+};
+
+template <typename TT>
+__global__ void k_tables(const TableBuildRow* rows, int n_rows, const DevView* views, TT* vals) {
+  int r = blockIdx.x;
+  if (r >= n_rows) return;
+  const TableBuildRow R = rows[r];
+  const DevView& V = views[R.view];
+  const double lam = bin_lambda_d(V, R.bin);
+  const double x = kPiD * (double)R.height_um / lam;  // h k / 2
+  for (int j = threadIdx.x; j <= R.jmax; j += blockDim.x) {
+    double J = bessel_j_d(j, x);
+    float v = (float)(J * J);
+    if constexpr (sizeof(TT) == 4)
+      vals[R.offset + j] = v;
+    else if constexpr (std::is_same<TT, __half>::value)
+      vals[R.offset + j] = __float2half_rn(v);
+    else
+      vals[R.offset + j] = __float2bfloat16_rn(v);
+  }
+}
+
+// ------------------------------------------------------------------ readback
+__global__ void k_readback(const float* __restrict__ sum, const float* __restrict__ comp, int W, int H, int nb, int ns,
+                           const float* __restrict__ inv_count, float* __restrict__ out) {
+  const long long n = (long long)W * H * nb * ns;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    // out layout [y][x][bin][stokes]; accumulator layout [bin][y][x][stokes]
+    const int s = (int)(i % ns);
+    long long r = i / ns;
+    const int b = (int)(r % nb);
+    const long long pix = r / nb;
+    const long long a = ((long long)b * W * H + pix) * ns + s;
+    out[i] = (sum[a] - comp[a]) * inv_count[b];
+  }
+}
+
+// Camera basis of every view from its descriptor (pinhole: forward, right =
+// forward x up, up' = right x forward, tan of half the vertical FOV).
+__global__ void k_views(const gr_view_desc* __restrict__ vd, DevView* views, int n) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const gr_view_desc d = vd[v];
+  DevView& V = views[v];
+  const float3 eye = f3(d.eye[0], d.eye[1], d.eye[2]);
+  const float3 fw = normalize(f3(d.look_at[0], d.look_at[1], d.look_at[2]) - eye);
+  const float3 rt = normalize(cross(fw, f3(d.up[0], d.up[1], d.up[2])));
+  V.eye = eye;
+  V.fw = fw;
+  V.right = rt;
+  V.upc = cross(rt, fw);
+  V.th = tanf(0.5f * d.vfov_deg * kPi / 180.0f);
+  V.aspect = (float)d.width / (float)d.height;
+}
+
+// ================================================================== host side
+namespace {
+
+int sm_count(int dev) {
+  int n = 0;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+template <int NS, typename TT>
+cudaError_t launch_iteration(const RenderParams& p, int grid_regen, int grid_trace, int grid_shade, int grid_shadow,
+                             int block, size_t smem, cudaStream_t st) {
+  k_regen<NS><<<grid_regen, block, 0, st>>>(p);
+  k_trace<<<grid_trace, block, 0, st>>>(p);
+  k_shade<NS, TT><<<grid_shade, block, smem, st>>>(p);
+  k_shadow<NS><<<grid_shadow, block, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct RenderPlan {
+  std::vector<DevView> views;
+  std::vector<DevScene> scenes;
+  std::vector<TableRow> rows;
+  std::vector<TableBuildRow> build_rows;
+  int vals_count = 0;
+  unsigned long long total_tickets = 0;
+};
+
+// Called by gr_render after argument validation.
+gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc* vd, int n_views,
+                      const gr_render_opts& o, gr_frame* f, cudaStream_t st, std::string& err) {
+  const int NSv = vd[0].n_stokes;
+  RenderPlan plan;
+  plan.scenes.resize(n_scenes);
+  for (int i = 0; i < n_scenes; ++i) plan.scenes[i] = scenes[i]->dev;
+  const size_t tsize = o.table_dtype == GR_TABLE_F32 ? 4 : 2;
+  for (int v = 0; v < n_views; ++v) {
+    const gr_view_desc& d = vd[v];
+    DevView V;
+    std::memset(&V, 0, sizeof V);
+    // camera basis (eye, fw, right, upc, th, aspect) is filled by k_views
+    V.W = d.width;
+    V.H = d.height;
+    V.nb = d.n_bins;
+    V.ns = d.n_stokes;
+    V.max_depth = d.max_depth;
+    V.spp = d.spp;
+    V.first_sample = d.first_sample;
+    V.view_index = d.view_index;
+    V.scene_index = d.scene_index;
+    V.ortho = d.ortho;
+    V.ortho_half = d.ortho_half_m;
+    V.lmin = d.lambda_min_um;
+    V.lmax = d.lambda_max_um;
+    V.beta0 = d.f_beta * d.p_pix_um;
+    V.ticket_base = (long long)plan.total_tickets;
+    V.n_tickets = (long long)d.n_bins * d.width * d.height;
+    plan.total_tickets += (unsigned long long)V.n_tickets;
+    V.acc_sum = f->acc + f->offsets[v];
+    V.acc_comp = f->acc + f->acc_floats + f->offsets[v];
+    // grating order table rows for every (material, bin) of this view
+    const gr_scene* sc = scenes[d.scene_index];
+    V.table_base = (int)plan.rows.size();
+    for (size_t m = 0; m < sc->mats.size(); ++m) {
+      for (int b = 0; b < d.n_bins; ++b) {
+        TableRow r{0, -1};
+        const gr_material& M = sc->mats[m];
+        if (M.type == GR_MAT_GRATING) {
+          double lam = d.n_bins <= 1 ? (double)d.lambda_min_um
+                                     : (double)d.lambda_min_um + (double)b * ((double)d.lambda_max_um - (double)d.lambda_min_um) /
+                                                                     (double)(d.n_bins - 1);
+          int jm = (int)std::floor(2.0 * (double)M.period_um / lam) + 2;
+          if (jm > kMaxOrder) jm = kMaxOrder;
+          r.offset = plan.vals_count;
+          r.jmax = jm;
+          plan.vals_count += jm + 1;
+          TableBuildRow br{};
+          br.offset = r.offset;
+          br.jmax = jm;
+          br.view = v;
+          br.bin = b;
+          br.height_um = M.height_um;
+          plan.build_rows.push_back(br);
+        }
+        plan.rows.push_back(r);
+      }
+    }
+    plan.views.push_back(V);
+  }
+  // ---- scratch layout
+  int P = o.pool_size > 0 ? o.pool_size : 1 << 20;
+  if ((unsigned long long)P > plan.total_tickets) P = (int)std::max<unsigned long long>(plan.total_tickets, 1ull);
+  P = (P + 255) / 256 * 256;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = off;
+    off = align_up(off + bytes, 256);
+    return r;
+  };
+  const size_t o_views = take(sizeof(DevView) * n_views);
+  const size_t o_vdesc = take(sizeof(gr_view_desc) * n_views);
+  const size_t o_scenes = take(sizeof(DevScene) * n_scenes);
+  const size_t o_rows = take(sizeof(TableRow) * std::max<size_t>(plan.rows.size(), 1));
+  const size_t o_brows = take(sizeof(TableBuildRow) * std::max<size_t>(plan.build_rows.size(), 1));
+  const size_t o_vals = take(tsize * std::max(plan.vals_count, 1));
+  const size_t o_f4 = take(sizeof(float4) * (size_t)P * 13);
+  const size_t o_hit = take(sizeof(float2) * (size_t)P);
+  const size_t o_meta = take(sizeof(int4) * (size_t)P);
+  const size_t o_tq = take(sizeof(int) * (size_t)P);
+  const size_t o_sq = take(sizeof(int) * (size_t)P);
+  const size_t total = off;
+  if (f->scratch_bytes < total) {
+    if (f->scratch) cudaFreeAsync(f->scratch, st);
+    f->scratch = nullptr;
+    f->scratch_bytes = 0;
+    if (cudaMallocAsync(&f->scratch, total, st) != cudaSuccess) {
+      err = "scratch allocation failed";
+      return GR_E_OOM;
+    }
+    f->scratch_bytes = total;
+  }
+  unsigned char* base = (unsigned char*)f->scratch;
+  RenderParams p;
+  std::memset(&p, 0, sizeof p);
+  p.views = (const DevView*)(base + o_views);
+  p.n_views = n_views;
+  p.scenes = (const DevScene*)(base + o_scenes);
+  p.seed = o.seed;
+  p.flags = o.flags;
+  p.rows = (const TableRow*)(base + o_rows);
+  p.table_vals = base + o_vals;
+  p.table_dtype = o.table_dtype;
+  p.table_rows = (int)plan.rows.size();
+  p.table_vals_count = plan.vals_count;
+  float4* f4 = (float4*)(base + o_f4);
+  p.pool.od0 = f4;
+  p.pool.od1 = f4 + (size_t)P;
+  for (int r = 0; r < 4; ++r) p.pool.tp[r] = f4 + (size_t)P * (2 + r);
+  p.pool.xf = f4 + (size_t)P * 6;
+  p.pool.part = f4 + (size_t)P * 7;
+  p.pool.accS = f4 + (size_t)P * 8;
+  p.pool.accC = f4 + (size_t)P * 9;
+  p.pool.shd = f4 + (size_t)P * 10;
+  p.pool.shc = f4 + (size_t)P * 11;
+  p.pool.hit = (float2*)(base + o_hit);
+  p.pool.meta = (int4*)(base + o_meta);
+  p.pool.tq = (int*)(base + o_tq);
+  p.pool.sq = (int*)(base + o_sq);
+  p.P = P;
+  p.ctr = f->ctr;
+  const size_t smem_table = sizeof(TableRow) * plan.rows.size() + tsize * plan.vals_count;
+  p.table_smem = smem_table <= 40 * 1024 ? 1 : 0;
+  const size_t smem = p.table_smem ? align_up(smem_table, 16) : 0;
+
+  cudaError_t e;
+#define GR_CK(x)                                 \
+  do {                                           \
+    e = (x);                                     \
+    if (e != cudaSuccess) {                      \
+      err = std::string(#x) + ": " + cudaGetErrorString(e); \
+      return GR_E_CUDA;                          \
+    }                                            \
+  } while (0)
+  GR_CK(cudaMemcpyAsync(base + o_views, plan.views.data(), sizeof(DevView) * n_views, cudaMemcpyHostToDevice, st));
+  GR_CK(cudaMemcpyAsync(base + o_vdesc, vd, sizeof(gr_view_desc) * n_views, cudaMemcpyHostToDevice, st));
+  k_views<<<(n_views + 63) / 64, 64, 0, st>>>((const gr_view_desc*)(base + o_vdesc), (DevView*)(base + o_views), n_views);
+  f->launches += 1;
+  GR_CK(cudaMemcpyAsync(base + o_scenes, plan.scenes.data(), sizeof(DevScene) * n_scenes, cudaMemcpyHostToDevice, st));
+  if (!plan.rows.empty())
+    GR_CK(cudaMemcpyAsync(base + o_rows, plan.rows.data(), sizeof(TableRow) * plan.rows.size(), cudaMemcpyHostToDevice, st));
+  if (!plan.build_rows.empty()) {
+    GR_CK(cudaMemcpyAsync(base + o_brows, plan.build_rows.data(), sizeof(TableBuildRow) * plan.build_rows.size(),
+                          cudaMemcpyHostToDevice, st));
+    const TableBuildRow* br = (const TableBuildRow*)(base + o_brows);
+    const int nr = (int)plan.build_rows.size();
+    if (o.table_dtype == GR_TABLE_F32)
+      k_tables<float><<<nr, 64, 0, st>>>(br, nr, p.views, (float*)(base + o_vals));
+    else if (o.table_dtype == GR_TABLE_F16)
+      k_tables<__half><<<nr, 64, 0, st>>>(br, nr, p.views, (__half*)(base + o_vals));
+    else
+      k_tables<__nv_bfloat16><<<nr, 64, 0, st>>>(br, nr, p.views, (__nv_bfloat16*)(base + o_vals));
+    f->launches += 1;
+  }
+  GR_CK(cudaMemsetAsync(p.pool.meta, 0, sizeof(int4) * (size_t)P, st));
+  Counters c0;
+  std::memset(&c0, 0, sizeof c0);
+  c0.total_tickets = plan.total_tickets;
+  GR_CK(cudaMemcpyAsync(f->ctr, &c0, sizeof c0, cudaMemcpyHostToDevice, st));
+  GR_CK(cudaGetLastError());
+
+  // ---- launch shapes
+  const int dev = f->device;
+  const int sms = sm_count(dev);
+  const int block = o.block > 0 ? o.block : 256;
+  auto grid_for = [&](const void* fn, size_t dyn) {
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, block, dyn);
+    if (per < 1) per = 1;
+    return sms * per;
+  };
+  int g_regen, g_trace, g_shade, g_shadow;
+  const void* shade_fn;
+  if (NSv == 1) {
+    g_regen = grid_for((const void*)k_regen<1>, 0);
+    g_shadow = grid_for((const void*)k_shadow<1>, 0);
+    shade_fn = o.table_dtype == GR_TABLE_F32 ? (const void*)k_shade<1, float>
+               : o.table_dtype == GR_TABLE_F16 ? (const void*)k_shade<1, __half>
+                                               : (const void*)k_shade<1, __nv_bfloat16>;
+  } else {
+    g_regen = grid_for((const void*)k_regen<4>, 0);
+    g_shadow = grid_for((const void*)k_shadow<4>, 0);
+    shade_fn = o.table_dtype == GR_TABLE_F32 ? (const void*)k_shade<4, float>
+               : o.table_dtype == GR_TABLE_F16 ? (const void*)k_shade<4, __half>
+                                               : (const void*)k_shade<4, __nv_bfloat16>;
+  }
+  g_trace = grid_for((const void*)k_trace, 0);
+  g_shade = grid_for(shade_fn, smem);
+  // never more blocks than the pool needs
+  const int gmax = (P + block - 1) / block;
+  g_regen = std::min(g_regen, gmax);
+  g_trace = std::min(g_trace, gmax);
+  g_shade = std::min(g_shade, gmax);
+  g_shadow = std::min(g_shadow, gmax);
+
+  auto launch = [&]() -> cudaError_t {
+    if (NSv == 1) {
+      if (o.table_dtype == GR_TABLE_F32) return launch_iteration<1, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st);
+      if (o.table_dtype == GR_TABLE_F16) return launch_iteration<1, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st);
+      return launch_iteration<1, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st);
+    }
+    if (o.table_dtype == GR_TABLE_F32) return launch_iteration<4, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st);
+    if (o.table_dtype == GR_TABLE_F16) return launch_iteration<4, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st);
+    return launch_iteration<4, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st);
+  };
+
+  // ---- iteration loop: batches of B iterations; the host watches the
+  // device's live-slot count of the batch before the last one
+  const int B = 8;
+  // Worst case of the schedule: each slot runs ceil(T/P) tickets one after the
+  // other, each of at most n samples taking at most max_depth + 2 iterations.
+  long long worst = 0;
+  {
+    long long n_max = 1, d_max = 0;
+    for (int v = 0; v < n_views; ++v) {
+      n_max = std::max<long long>(n_max, (long long)vd[v].spp / vd[v].n_bins + 1);
+      d_max = std::max<long long>(d_max, vd[v].max_depth);
+    }
+    long long rounds = (long long)((plan.total_tickets + P - 1) / P) + 1;
+    worst = rounds * n_max * (d_max + 3) + 4 * B;
+  }
+  const long long max_iter = o.max_iterations > 0 ? o.max_iterations : 2 * worst;
+  cudaGraphExec_t gexec = nullptr;
+  if (o.use_graph) {
+    cudaGraph_t g;
+    GR_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < B; ++i) {
+      cudaError_t le = launch();
+      if (le != cudaSuccess) {
+        cudaStreamEndCapture(st, &g);
+        err = std::string("graph capture launch: ") + cudaGetErrorString(le);
+        return GR_E_CUDA;
+      }
+    }
+    GR_CK(cudaStreamEndCapture(st, &g));
+    e = cudaGraphInstantiate(&gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+      return GR_E_CUDA;
+    }
+  }
+  cudaEvent_t ev[2];
+  cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+  Counters* hc = f->ctr_host;
+  long long it = 0;
+  int batch = 0;
+  gr_status status = GR_OK;
+  for (;;) {
+    if (gexec) {
+      e = cudaGraphLaunch(gexec, st);
+    } else {
+      for (int i = 0; i < B && e == cudaSuccess; ++i) e = launch();
+    }
+    if (e != cudaSuccess) {
+      err = std::string("launch: ") + cudaGetErrorString(e);
+      status = GR_E_CUDA;
+      break;
+    }
+    it += B;
+    f->launches += 4LL * B;
+    // copy the counters of this batch into pinned slot (batch & 1)
+    e = cudaMemcpyAsync(hc + (batch & 1), f->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[batch & 1], st);
+    if (e != cudaSuccess) {
+      err = std::string("counter copy: ") + cudaGetErrorString(e);
+      status = GR_E_CUDA;
+      break;
+    }
+    if (batch >= 1) {
+      // wait for the previous batch while this one runs
+      e = cudaEventSynchronize(ev[(batch - 1) & 1]);
+      if (e != cudaSuccess) {
+        err = std::string("event sync: ") + cudaGetErrorString(e);
+        status = GR_E_CUDA;
+        break;
+      }
+      const Counters& c = hc[(batch - 1) & 1];
+      if (c.err) {
+        err = c.err == 1 ? "traversal stack overflow" : "corrupt BVH (traversal bound exceeded)";
+        status = GR_E_INVALID;
+        break;
+      }
+      if (c.last_active == 0 && c.next_ticket >= c.total_tickets) break;
+    }
+    ++batch;
+    if (it > max_iter) {
+      err = "render exceeded its iteration bound";
+      status = GR_E_TIMEOUT;
+      break;
+    }
+  }
+  f->iterations += it;
+  if (gexec) cudaGraphExecDestroy(gexec);
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  return status;
+#undef GR_CK
+}
+
+cudaError_t readback_impl(gr_frame* f, int v, float* dst_dev, const float* inv_count_dev, cudaStream_t st) {
+  const gr_view_shape& s = f->shapes[v];
+  const long long n = (long long)s.W * s.H * s.nb * s.ns;
+  int blocks = (int)std::min<long long>((n + 255) / 256, 65535);
+  k_readback<<<blocks, 256, 0, st>>>(f->acc + f->offsets[v], f->acc + f->acc_floats + f->offsets[v], s.W, s.H, s.nb,
+                                      s.ns, inv_count_dev, dst_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace gr

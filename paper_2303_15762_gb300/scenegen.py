@@ -69,13 +69,16 @@ def light(type_, direction=(0.0, 0.0, 1.0), E=1.0, coh_len_um=0.0):
 def view(eye, look_at, up=(0.0, 1.0, 0.0), vfov_deg=28.0, width=64, height=64, p_pix_um=2.0,
          f_beta=0.5, lambda_min_um=0.4, lambda_max_um=0.7, n_bins=16, n_stokes=1, max_depth=1,
          spp=64, first_sample=0, view_index=0, scene_index=0, ortho=0, ortho_half_m=0.0):
-    return dict(eye=tuple(float(x) for x in eye), look_at=tuple(float(x) for x in look_at),
-                up=tuple(float(x) for x in up), vfov_deg=float(vfov_deg), width=int(width),
-                height=int(height), p_pix_um=float(p_pix_um), f_beta=float(f_beta),
-                lambda_min_um=float(lambda_min_um), lambda_max_um=float(lambda_max_um),
+    # float fields are rounded to float32 here: the C ABI carries float32, and
+    # both implementations must see identical input values
+    f = lambda x: float(np.float32(x))  # noqa: E731
+    return dict(eye=tuple(f(x) for x in eye), look_at=tuple(f(x) for x in look_at),
+                up=tuple(f(x) for x in up), vfov_deg=f(vfov_deg), width=int(width),
+                height=int(height), p_pix_um=f(p_pix_um), f_beta=f(f_beta),
+                lambda_min_um=f(lambda_min_um), lambda_max_um=f(lambda_max_um),
                 n_bins=int(n_bins), n_stokes=int(n_stokes), max_depth=int(max_depth), spp=int(spp),
                 first_sample=int(first_sample), view_index=int(view_index),
-                scene_index=int(scene_index), ortho=int(ortho), ortho_half_m=float(ortho_half_m))
+                scene_index=int(scene_index), ortho=int(ortho), ortho_half_m=f(ortho_half_m))
 
 
 def _quad(c, a, b):
