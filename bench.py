@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Throughput of backward generalized-ray path tracing on one GB300 (or N
+independent replicas), in path samples per second.
+
+Workload (default): the procedural scene -- ground plane plus 64 objects,
+~92k triangles, rough Gaussian-statistics conductors and gratings, 1-4
+partially coherent emissive quads -- seen by a 512x512 camera at 256 samples
+per pixel, 32 spectral bins (400-700 nm), full Stokes vector, up to 3
+interactions, next-event estimation with MIS.  One step renders all
+512*512*256 = 67.1M path samples.  Inputs are synthetic (seeded generator); the
+paper's own scenes are not available.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded crop of the same workload instead.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gen-ray path Msamples/s at <=1e-3 rel-L2 vs FP64 oracle; p50/p99 frame ms"
+UNIT = "Msamples/s"
+FP32_PEAK_TFLOPS = 2 * 152 * 128 * 2.070e9 / 1e12  # FMA = 2 FLOP, 152 SMs x 128 lanes at 2070 MHz
+# Algorithmic FP32 FLOPs (FMA = 2) of the traversal units, counted from the
+# operations the closest-hit query needs: a node visit tests two child boxes
+# (6 slab FMAs + 11 min/max + 3 for the far-distance widening, compare and
+# clip = 26 per box); a watertight triangle test (9 subtractions, 6 shear
+# FMAs, 3 edge functions of 1 mul + 1 FMA, 2 adds, 3 mul + 2 FMA for T, 1
+# division) = 41.
+FLOP_PER_NODE = 52
+FLOP_PER_TRI = 41
+KERNELS = ["k_regen", "k_trace", "k_shade", "k_shadow"]
+# DRAM traffic per launch of the dominant kernel from one ncu capture, valid only
+# for the kernel sources whose hash is recorded with it (else reported null).
+NCU_TRAFFIC = {}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ["gr_device.cuh", "gr_render.cu", "gr_build.h"]:
+        with open(os.path.join(ROOT, "paper_2303_15762_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--spp", type=int, default=256)
+    ap.add_argument("--size", type=int, default=512)
+    ap.add_argument("--table", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--pool", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-crop", type=int, default=128, help="side of the oracle's centre crop")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(args, rank):
+    from paper_2303_15762_gb300 import scenegen as sg
+    scene = sg.procedural_scene(seed=2)
+    view = sg.procedural_view(width=args.size, height=args.size, spp=args.spp, view_index=rank)
+    return scene, view
+
+
+def workload_name(args, scene):
+    return ("procedural scene, %d tris, %dx%d, %d spp, 32 bins 400-700 nm, 4 Stokes, depth<=3, NEE+MIS"
+            % (len(scene["tri_mat"]), args.size, args.size, args.spp))
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.p = None
+        self.gpu = gpu_index
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_reference(args):
+    """FP64 CPU oracle on a bounded crop of the same workload."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    scene, view = workload(args, 0)
+    S = orc.Scene(scene)
+    crop = 32
+    x0 = args.size // 2 - crop // 2
+    box = (x0, x0, x0 + crop, x0 + crop)
+    samples = crop * crop * args.spp
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        S.render(view, 2, orc.FLAG_NEE, crop=box, n_threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        S.render(view, 2, orc.FLAG_NEE, crop=box, n_threads=cores)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    value = samples / (ms * 1e-3) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args, scene), "sample": "%dx%d centre crop" % (crop, crop)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%dx%d centre crop x %d spp per step" % (crop, crop, args.spp)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    world, rank, local = dist_setup()
+    import numpy as np
+    import torch
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    import paper_2303_15762_gb300 as gr
+    gr.load()
+    scene, view = workload(args, rank)
+    samples = view["width"] * view["height"] * view["spp"]
+    flags = gr.FLAG_NEE
+    S = gr.Scene(scene)
+    F = gr.Frame([view])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+
+    def step(profile):
+        F.reset()
+        gr.render([S], [view], F, seed=2, flags=flags, table_dtype=args.table, pool_size=args.pool, profile=profile)
+
+    for _ in range(max(3, args.warmup)):
+        step(False)
+    torch.cuda.synchronize()
+    launches0 = F.stats()["kernel_launches"]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    step_ms, kms, kcnt = [], [0.0] * 4, [0] * 4
+    visits = tests = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(True)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = F.stats()
+        for k in range(4):
+            kms[k] += st["kernel_ms"][k]
+            kcnt[k] += st["kernel_count"][k]
+        visits += st["node_visits"]
+        tests += st["tri_tests"]
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    stats = F.stats()
+    launches = stats["kernel_launches"] - launches0
+    mean_ms = statistics.mean(step_ms)
+    t_max = mean_ms
+    if world > 1:
+        t = torch.tensor([mean_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * samples / (t_max * 1e-3) / 1e6
+    img = F.readback(0)
+
+    # ---- roofline of the dominant kernel (device time share from live events)
+    dom = int(np.argmax(kms))
+    per_launch_ms = kms[dom] / max(1, kcnt[dom])
+    if dom in (1, 3):
+        # traversal kernels: ALU-bound; counts of node visits / triangle tests
+        # are summed over trace and shadow, so attribute by time share
+        flops = (visits * FLOP_PER_NODE + tests * FLOP_PER_TRI) / args.steps
+        trav_ms = (kms[1] + kms[3]) / args.steps
+        achieved = flops / (trav_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": KERNELS[dom] + "+k_shadow" if dom == 1 else KERNELS[dom],
+                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                "traffic": NCU_TRAFFIC.get((KERNELS[dom], source_hash())),
+                "per_launch_ms": per_launch_ms}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+        # slot state read and written by regen / shade per processed slot
+        bytes_per_launch = None
+        roof = {"bound": "hbm", "kernel": KERNELS[dom], "achieved": None, "peak": peaks.get("hbm_gbs", 6800.0),
+                "unit": "GB/s", "frac": None, "traffic": NCU_TRAFFIC.get((KERNELS[dom], source_hash())),
+                "per_launch_ms": per_launch_ms, "note": "bytes per launch not yet derived", "bytes": bytes_per_launch}
+    roof["kernel_ms_share"] = {KERNELS[k]: kms[k] / max(sum(kms), 1e-9) for k in range(4)}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if rank == 0 and args.e2e_steps > 0:
+        pinned = {}
+        for key in ("verts", "tri_mat", "mats", "lights"):
+            a = np.ascontiguousarray(scene[key])
+            t = torch.from_numpy(a.copy()).pin_memory()
+            pinned[key] = t.numpy()
+        h2d = sum(pinned[k].nbytes for k in pinned) + 100  # + one view descriptor
+        host_img = torch.empty(img.size, dtype=torch.float32).pin_memory().numpy().reshape(img.shape)
+        d2h = host_img.nbytes
+        times = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s2 = gr.Scene(pinned)
+            f2 = gr.Frame([view])
+            gr.render([s2], [view], f2, seed=2, flags=flags, table_dtype=args.table, pool_size=args.pool)
+            _lib = gr.lib_handle()
+            from paper_2303_15762_gb300 import _native as nat
+            nat._check(_lib.gr_readback(f2.handle, 0, host_img.ctypes.data_as(nat.ctypes.c_void_p),
+                                        host_img.nbytes, 0, nat.current_stream()))
+            f2.close()
+            s2.close()
+            torch.cuda.synchronize()
+            if i > 0:
+                times.append(time.perf_counter() - t0)
+        e2e_ms = 1e3 * statistics.mean(times)
+        e2e = {"value": world * samples / (e2e_ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
+               "includes": "scene upload + BVH build, frame alloc, render, readback to pinned host"}
+
+    # ---- CPU oracle baseline on a centre crop, and the accuracy of this run there
+    cpu = None
+    rel = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import oracle as orc
+        c = min(args.cpu_crop, args.size)
+        x0 = args.size // 2 - c // 2
+        O = orc.Scene(scene)
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        ref = O.render(view, 2, orc.FLAG_NEE, crop=(x0, x0, x0 + c, x0 + c), n_threads=cores)
+        dt = time.perf_counter() - t0
+        cpu = {"value": c * c * view["spp"] / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%dx%d centre crop of the same view, %d spp (%d samples), %.1f s" % (
+                   c, c, view["spp"], c * c * view["spp"], dt)}
+        crop = img[x0:x0 + c, x0:x0 + c].astype(np.float64)
+        rel = float(np.linalg.norm(crop - ref) / max(np.linalg.norm(ref), 1e-300))
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": workload_name(args, scene), "tables": args.table,
+                           "parallelism": "replicas x%d" % world,
+                           "l2": "flushed before every timed step (256 MB write)",
+                           "p50_frame_ms": float(np.percentile(step_ms, 50)),
+                           "p99_frame_ms": float(np.percentile(step_ms, 99))},
+                "rel_l2_vs_oracle": rel, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk,
+                "stats": {"iterations_per_step": stats["iterations"], "segments": stats["segments"],
+                          "shadow_rays": stats["shadow_rays"], "refine64_hits": stats["refine64_hits"],
+                          "refine64_lobes": stats["refine64_lobes"],
+                          "node_visits_per_step": visits / args.steps, "tri_tests_per_step": tests / args.steps}}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -146,7 +146,8 @@ typedef struct {
   int32_t block;
   int32_t use_graph;     /* 1: replay the wavefront iteration as a CUDA graph */
   int32_t max_iterations; /* 0 = default bound; exceeding it returns GR_E_TIMEOUT */
-  int32_t reserved;
+  int32_t profile;        /* 1: time every kernel with CUDA events on the render stream
+                             (not with use_graph); the call then waits for completion */
 } gr_render_opts;
 
 /* Render statistics of the last gr_render on a frame (device-side counters,
@@ -159,6 +160,12 @@ typedef struct {
   int64_t refine64_lobes; /* grating / Poisson choices decided in FP64 */
   int64_t iterations;     /* wavefront iterations */
   int64_t kernel_launches;
+  int64_t node_visits;    /* BVH internal nodes visited (trace + shadow) */
+  int64_t tri_tests;      /* ray-triangle tests (trace + shadow) */
+  /* last render with profile = 1: device ms and launches per kernel
+     (0 regen, 1 trace, 2 shade, 3 shadow) */
+  double kernel_ms[4];
+  int64_t kernel_count[4];
 } gr_stats;
 
 /* Upload a scene and build its BVH (Karras LBVH, 30-bit Morton codes; integer
@@ -203,6 +210,13 @@ gr_status gr_frame_stats(gr_frame* frame, void* cuda_stream, gr_stats* out);
  * and float32 [n-1][12] child boxes (left lo xyz, left hi xyz, right lo, right
  * hi).  Returns the triangle count in *n_out. */
 gr_status gr_scene_bvh(gr_scene* scene, int32_t* n_out, uint64_t* keys, int32_t* children, float* boxes);
+
+/* Inspection of the device random stream for bit-exact tests: the raw
+ * Philox4x32-10 words of key (seed, view_index) and counters (pixel,
+ * sample + i, (segment << 4) | call, 0) for i in [0, n), written to host
+ * out_u32 [n][4].  Runs one kernel on the stream and synchronises it. */
+gr_status gr_debug_rng(uint32_t seed, uint32_t view_index, uint32_t pixel, uint32_t sample, int32_t segment,
+                       int32_t call, int32_t n, uint32_t* out_u32, void* cuda_stream);
 
 /* Thread-local description of the last error (never NULL). */
 const char* gr_last_error(void);

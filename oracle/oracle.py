@@ -21,7 +21,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "gr_oracle.cpp")
+_SRCS = [os.path.join(_HERE, "gr_oracle.cpp"), os.path.join(_HERE, "lbvh_ref.cpp")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
@@ -36,11 +36,11 @@ def build(force=False):
     """Compile the oracle shared library (plain g++, no CUDA)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
     cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread",
-           "-ffp-contract=off", "-o", tmp, _SRC]
+           "-ffp-contract=off", "-o", tmp] + _SRCS
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -51,7 +51,7 @@ def build_cmd_popen():
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
     cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread",
-           "-ffp-contract=off", "-o", tmp, _SRC]
+           "-ffp-contract=off", "-o", tmp] + _SRCS
     return subprocess.Popen(cmd), tmp, _LIB_PATH
 
 
@@ -84,6 +84,8 @@ def lib():
     L.oracle_trace_sample.argtypes = [P, P, U32, I, I, I, L_, P]
     L.oracle_render.argtypes = [P, P, U32, I, I, I, I, I, I, P, P]
     L.oracle_render.restype = L_
+    L.oracle_lbvh_build.argtypes = [I, P, P, P, P]
+    L.oracle_lbvh_build.restype = I
     _lib = L
     return L
 
@@ -158,6 +160,17 @@ def stokes_rotation(phi):
     m = np.zeros(16)
     lib().oracle_stokes_rotation(float(phi), _p(m))
     return m.reshape(4, 4)
+
+
+def lbvh_build(verts):
+    """CPU LBVH of float32 triangles [n][3][3]: (sorted keys, child refs, child boxes)."""
+    v = np.ascontiguousarray(np.asarray(verts, dtype=np.float32).reshape(-1, 9))
+    n = len(v)
+    keys = np.zeros(max(n, 1), dtype=np.uint64)
+    ch = np.zeros((max(n - 1, 1), 2), dtype=np.int32)
+    bx = np.zeros((max(n - 1, 1), 12), dtype=np.float32)
+    lib().oracle_lbvh_build(n, _p(v), _p(keys), _p(ch), _p(bx))
+    return keys[:n], ch[: max(n - 1, 0)], bx[: max(n - 1, 0)]
 
 
 # ------------------------------------------------------------------ scenes

@@ -18,7 +18,8 @@ FLAG_NEE, FLAG_RR, FLAG_NO_RENORM = 1, 2, 4
 TABLE_DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
 
 EXPORTED = ["gr_scene_create", "gr_scene_destroy", "gr_frame_create", "gr_frame_reset", "gr_frame_release",
-            "gr_render", "gr_readback", "gr_frame_stats", "gr_scene_bvh", "gr_last_error", "gr_abi_version"]
+            "gr_render", "gr_readback", "gr_frame_stats", "gr_scene_bvh", "gr_debug_rng", "gr_last_error",
+            "gr_abi_version"]
 
 
 class GrError(RuntimeError):
@@ -58,13 +59,15 @@ class gr_view_desc(ctypes.Structure):
 class gr_render_opts(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint32), ("flags", ctypes.c_int32), ("table_dtype", ctypes.c_int32),
                 ("pool_size", ctypes.c_int32), ("block", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("max_iterations", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("max_iterations", ctypes.c_int32), ("profile", ctypes.c_int32)]
 
 
 class gr_stats(ctypes.Structure):
     _fields_ = [("samples", ctypes.c_int64), ("segments", ctypes.c_int64), ("shadow_rays", ctypes.c_int64),
                 ("refine64_hits", ctypes.c_int64), ("refine64_lobes", ctypes.c_int64),
-                ("iterations", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+                ("iterations", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("node_visits", ctypes.c_int64), ("tri_tests", ctypes.c_int64),
+                ("kernel_ms", ctypes.c_double * 4), ("kernel_count", ctypes.c_int64 * 4)]
 
 
 _lib = None
@@ -94,6 +97,8 @@ def lib_handle(require_gpu=True):
     L.gr_readback.argtypes = [P, I32, P, ctypes.c_size_t, I32, P]
     L.gr_frame_stats.argtypes = [P, P, P]
     L.gr_scene_bvh.argtypes = [P, P, P, P, P]
+    U32 = ctypes.c_uint32
+    L.gr_debug_rng.argtypes = [U32, U32, U32, U32, I32, I32, I32, P, P]
     L.gr_last_error.restype = ctypes.c_char_p
     L.gr_abi_version.restype = I32
     for name in EXPORTED:
@@ -239,7 +244,10 @@ class Frame:
     def stats(self, stream=None):
         s = gr_stats()
         _check(_lib.gr_frame_stats(self._h, stream or current_stream(), ctypes.byref(s)))
-        return {k: getattr(s, k) for k, _ in gr_stats._fields_}
+        out = {k: getattr(s, k) for k, _ in gr_stats._fields_}
+        out["kernel_ms"] = list(s.kernel_ms)
+        out["kernel_count"] = list(s.kernel_count)
+        return out
 
     def close(self):
         if self._h:
@@ -253,7 +261,8 @@ class Frame:
             pass
 
 
-def make_opts(seed=1, flags=0, table_dtype="f32", pool_size=0, block=0, use_graph=False, max_iterations=0):
+def make_opts(seed=1, flags=0, table_dtype="f32", pool_size=0, block=0, use_graph=False, max_iterations=0,
+              profile=False):
     o = gr_render_opts()
     o.seed = int(seed) & 0xFFFFFFFF
     o.flags = int(flags)
@@ -261,6 +270,7 @@ def make_opts(seed=1, flags=0, table_dtype="f32", pool_size=0, block=0, use_grap
     o.pool_size, o.block = int(pool_size), int(block)
     o.use_graph = int(bool(use_graph))
     o.max_iterations = int(max_iterations)
+    o.profile = int(bool(profile))
     return o
 
 
@@ -271,6 +281,15 @@ def render(scenes, views, frame, stream=None, **opts):
     arr = pack_views(views)
     o = make_opts(**opts)
     _check(L.gr_render(sc, len(scenes), arr, len(views), ctypes.byref(o), frame.handle, stream or current_stream()))
+
+
+def debug_rng(seed, view_index, pixel, sample, segment, call, n, stream=None):
+    """Raw device Philox words [n][4] for samples sample..sample+n-1."""
+    L = lib_handle()
+    out = np.zeros((n, 4), dtype=np.uint32)
+    _check(L.gr_debug_rng(seed & 0xFFFFFFFF, view_index, pixel, sample, segment, call, n, _ptr(out),
+                          stream or current_stream()))
+    return out
 
 
 def render_image(scene, view, **opts):

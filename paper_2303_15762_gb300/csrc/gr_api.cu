@@ -14,6 +14,8 @@ namespace gr {
 gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc* vd, int n_views,
                       const gr_render_opts& o, gr_frame* f, cudaStream_t st, std::string& err);
 cudaError_t readback_impl(gr_frame* f, int v, float* dst_dev, const float* inv_count_dev, cudaStream_t st);
+cudaError_t debug_rng_impl(uint32_t seed, uint32_t view, uint32_t pixel, uint32_t sample, int seg, int call, int n,
+                           uint32_t* host_out, cudaStream_t st);
 }  // namespace gr
 
 namespace {
@@ -344,6 +346,22 @@ gr_status gr_frame_stats(gr_frame* f, void* cuda_stream, gr_stats* out) {
   out->refine64_lobes = (int64_t)c.ref_lobe;
   out->iterations = (int64_t)c.iters;
   out->kernel_launches = f->launches;
+  out->node_visits = (int64_t)c.node_visits;
+  out->tri_tests = (int64_t)c.tri_tests;
+  for (int k = 0; k < 4; ++k) {
+    out->kernel_ms[k] = f->kernel_ms[k];
+    out->kernel_count[k] = f->kernel_launches[k];
+  }
+  return GR_OK;
+}
+
+gr_status gr_debug_rng(uint32_t seed, uint32_t view_index, uint32_t pixel, uint32_t sample, int32_t segment,
+                       int32_t call, int32_t n, uint32_t* out_u32, void* cuda_stream) {
+  if (!out_u32 || n <= 0 || segment < 0 || segment > 0x0fffffff || call < 0 || call > 15)
+    return fail(GR_E_INVALID, "gr_debug_rng: bad arguments");
+  cudaError_t e = gr::debug_rng_impl(seed, view_index, pixel, sample, segment, call, n, out_u32,
+                                     (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_debug_rng");
   return GR_OK;
 }
 

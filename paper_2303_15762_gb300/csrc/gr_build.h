@@ -38,7 +38,7 @@ struct Counters {
   int sq_count;
   int last_active;
   int err;
-  unsigned long long samples, segments, shadow, ref_hit, ref_lobe, iters;
+  unsigned long long samples, segments, shadow, ref_hit, ref_lobe, iters, node_visits, tri_tests;
 };
 
 struct RenderParams {
@@ -87,5 +87,7 @@ struct gr_frame {
   gr::Counters* ctr_host = nullptr;      // pinned mirror
   long long launches = 0;
   long long iterations = 0;
+  double kernel_ms[4] = {0, 0, 0, 0};       // last profiled render: regen, trace, shade, shadow
+  long long kernel_launches[4] = {0, 0, 0, 0};
   int device = 0;
 };

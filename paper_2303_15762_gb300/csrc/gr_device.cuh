@@ -213,11 +213,15 @@ __device__ __forceinline__ RayPre ray_pre(float3 o, float3 d) {
   return r;
 }
 
-// Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2(1), 2013) in FP32;
-// when an edge function is within its rounding margin the edge functions are
-// recomputed in FP64 from the same inputs ("FP64 refinement").  Edges count as
-// inside.  Returns t (metres) or -1.
-__device__ __forceinline__ float isect_tri(const RayPre& r, float3 v0, float3 v1, float3 v2, unsigned long long* refine_ctr) {
+// Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2(1), 2013) in FP32.
+// When an edge function lies within its FP32 rounding bound the three edge
+// functions are recomputed in FP64 from the same FP32 inputs ("FP64
+// refinement"), so the inside/outside decision is exact for the ray as stored.
+// The bound: the sheared coordinates carry an absolute error of a few ulps of
+// the largest vertex offset M, so |dU| <= c * u * M * (|Bx|+|By|+|Cx|+|Cy|) plus
+// the rounding of the products themselves.  Edges count as inside.
+// Returns t (metres) or -1; *refined counts FP64 recomputations.
+__device__ __forceinline__ float isect_tri(const RayPre& r, float3 v0, float3 v1, float3 v2, int* refined) {
   const float3 A = v0 - r.o, B = v1 - r.o, C = v2 - r.o;
   const float Az_ = comp(A, r.kz), Bz_ = comp(B, r.kz), Cz_ = comp(C, r.kz);
   const float Ax = comp(A, r.kx) - r.Sx * Az_, Ay = comp(A, r.ky) - r.Sy * Az_;
@@ -226,41 +230,39 @@ __device__ __forceinline__ float isect_tri(const RayPre& r, float3 v0, float3 v1
   float U = Cx * By - Cy * Bx;
   float V = Ax * Cy - Ay * Cx;
   float W = Bx * Ay - By * Ax;
-  const float eps = 2e-6f;
-  bool refine = fabsf(U) <= eps * (fabsf(Cx * By) + fabsf(Cy * Bx)) ||
-                fabsf(V) <= eps * (fabsf(Ax * Cy) + fabsf(Ay * Cx)) ||
-                fabsf(W) <= eps * (fabsf(Bx * Ay) + fabsf(By * Ax));
+  const float M = fmaxf(fmaxf(fmaxf(fabsf(A.x), fabsf(A.y)), fmaxf(fabsf(A.z), fabsf(B.x))),
+                        fmaxf(fmaxf(fabsf(B.y), fabsf(B.z)), fmaxf(fmaxf(fabsf(C.x), fabsf(C.y)), fabsf(C.z))));
+  const float e = 8.0f * 5.9604645e-8f * M * (1.0f + fabsf(r.Sx) + fabsf(r.Sy));
+  const bool refine = fabsf(U) <= e * (fabsf(Bx) + fabsf(By) + fabsf(Cx) + fabsf(Cy)) + 4e-7f * (fabsf(Cx * By) + fabsf(Cy * Bx)) ||
+                      fabsf(V) <= e * (fabsf(Ax) + fabsf(Ay) + fabsf(Cx) + fabsf(Cy)) + 4e-7f * (fabsf(Ax * Cy) + fabsf(Ay * Cx)) ||
+                      fabsf(W) <= e * (fabsf(Ax) + fabsf(Ay) + fabsf(Bx) + fabsf(By)) + 4e-7f * (fabsf(Bx * Ay) + fabsf(By * Ax));
   if (refine) {
     // FP64 edge functions from the FP32 vertices and ray
-    double Sx = (double)comp(r.d, r.kx) / (double)comp(r.d, r.kz);
-    double Sy = (double)comp(r.d, r.ky) / (double)comp(r.d, r.kz);
-    d3 o = D3(r.o);
-    d3 a = dsub(D3(v0), o), b = dsub(D3(v1), o), c = dsub(D3(v2), o);
-    double az = r.kz == 0 ? a.x : (r.kz == 1 ? a.y : a.z);
-    double bz = r.kz == 0 ? b.x : (r.kz == 1 ? b.y : b.z);
-    double cz = r.kz == 0 ? c.x : (r.kz == 1 ? c.y : c.z);
-    auto cx_ = [&](d3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); };
-    double ax = cx_(a, r.kx) - Sx * az, ay = cx_(a, r.ky) - Sy * az;
-    double bx = cx_(b, r.kx) - Sx * bz, by = cx_(b, r.ky) - Sy * bz;
-    double cxx = cx_(c, r.kx) - Sx * cz, cy = cx_(c, r.ky) - Sy * cz;
-    double Ud = cxx * by - cy * bx, Vd = ax * cy - ay * cxx, Wd = bx * ay - by * ax;
-    U = (float)Ud;
-    V = (float)Vd;
-    W = (float)Wd;
-    // keep exact signs of tiny values
-    if (Ud != 0.0 && U == 0.0f) U = Ud > 0 ? 1e-38f : -1e-38f;
-    if (Vd != 0.0 && V == 0.0f) V = Vd > 0 ? 1e-38f : -1e-38f;
-    if (Wd != 0.0 && W == 0.0f) W = Wd > 0 ? 1e-38f : -1e-38f;
-    if (refine_ctr) atomicAdd(refine_ctr, 1ull);
+    const double dz = (double)comp(r.d, r.kz);
+    const double Sx = (double)comp(r.d, r.kx) / dz;
+    const double Sy = (double)comp(r.d, r.ky) / dz;
+    const d3 o = D3(r.o);
+    const d3 a = dsub(D3(v0), o), b = dsub(D3(v1), o), c = dsub(D3(v2), o);
+    auto cm = [&](d3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); };
+    const double ax = cm(a, r.kx) - Sx * cm(a, r.kz), ay = cm(a, r.ky) - Sy * cm(a, r.kz);
+    const double bx = cm(b, r.kx) - Sx * cm(b, r.kz), by = cm(b, r.ky) - Sy * cm(b, r.kz);
+    const double cx = cm(c, r.kx) - Sx * cm(c, r.kz), cy = cm(c, r.ky) - Sy * cm(c, r.kz);
+    const double Ud = cx * by - cy * bx, Vd = ax * cy - ay * cx, Wd = bx * ay - by * ax;
+    // keep the exact signs; magnitudes only feed t below
+    U = Ud == 0.0 ? 0.0f : (fabs(Ud) < 1e-37 ? copysignf(1e-37f, (float)Ud) : (float)Ud);
+    V = Vd == 0.0 ? 0.0f : (fabs(Vd) < 1e-37 ? copysignf(1e-37f, (float)Vd) : (float)Vd);
+    W = Wd == 0.0 ? 0.0f : (fabs(Wd) < 1e-37 ? copysignf(1e-37f, (float)Wd) : (float)Wd);
+    ++*refined;
   }
   if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return -1.0f;
-  float det = U + V + W;
+  const float det = U + V + W;
   if (det == 0.0f) return -1.0f;
-  float T = U * (r.Sz * Az_) + V * (r.Sz * Bz_) + W * (r.Sz * Cz_);
+  const float T = U * (r.Sz * Az_) + V * (r.Sz * Bz_) + W * (r.Sz * Cz_);
   return T / det;
 }
 
-// Slab test of a child box; returns the entry distance or +inf on a miss.
+// Slab test of a child box; returns the entry distance (>= 0), or -1 when the
+// box is missed or starts beyond tbest.
 // The far distance is widened by 2*gamma(3) (Ize 2013) so no box containing a
 // triangle hit is rejected by rounding.
 __device__ __forceinline__ float box_entry(const RayPre& r, float3 lo, float3 hi, float tbest) {
@@ -270,7 +272,7 @@ __device__ __forceinline__ float box_entry(const RayPre& r, float3 lo, float3 hi
   float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
   float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
   tf = fminf(tf * 1.0000004f, tbest);
-  return tn <= tf ? tn : __int_as_float(0x7f800000);
+  return tn <= tf ? tn : -1.0f;
 }
 
 struct Hit {
@@ -282,8 +284,8 @@ struct Hit {
 // equal distances resolve to the lower original triangle id.  Stack-based
 // traversal of the binary LBVH, nearer child first.  *err is set if the stack
 // would overflow (the traversal then stops early).
-__device__ __forceinline__ Hit closest_hit(const DevScene& S, float3 o, float3 d, int exclude,
-                                           unsigned long long* refine_ctr, int* err) {
+__device__ __forceinline__ Hit closest_hit(const DevScene& S, float3 o, float3 d, int exclude, int* refined,
+                                           int* visits, int* tests, int* err) {
   Hit h;
   h.t = __int_as_float(0x7f800000);
   h.slot = -1;
@@ -295,7 +297,8 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& S, float3 o, float3 d
     const float4 a = __ldg(&S.tri[3 * slot]);
     const float4 b = __ldg(&S.tri[3 * slot + 1]);
     const float4 c = __ldg(&S.tri[3 * slot + 2]);
-    float t = isect_tri(r, xyz(a), xyz(b), xyz(c), refine_ctr);
+    ++*tests;
+    float t = isect_tri(r, xyz(a), xyz(b), xyz(c), refined);
     int id = __float_as_int(a.w);
     if (t > kTMin && (t < h.t || (t == h.t && id < best_id))) {
       h.t = t;
@@ -318,12 +321,13 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& S, float3 o, float3 d
       if (err) *err = 2;
       break;
     }
+    ++*visits;
     const float4* N = S.nodes + 4 * node;
     const float4 n0 = __ldg(N), n1 = __ldg(N + 1), n2 = __ldg(N + 2), n3 = __ldg(N + 3);
     const int lref = __float_as_int(n3.x), rref = __float_as_int(n3.y);
     float tl = box_entry(r, f3(n0.x, n0.y, n0.z), f3(n0.w, n1.x, n1.y), h.t);
     float tr = box_entry(r, f3(n1.z, n1.w, n2.x), f3(n2.y, n2.z, n2.w), h.t);
-    bool hl = tl <= h.t, hr = tr <= h.t;
+    bool hl = tl >= 0.0f, hr = tr >= 0.0f;
     int next = -1;
     // leaves are tested immediately; internal children are descended/pushed
     if (hl && lref < 0) {

@@ -130,6 +130,12 @@ __device__ __forceinline__ void start_sample(const RenderParams& p, int slot, in
   P.meta[slot] = make_int4(view, local, meta_pack(k, 0, ST_ACTIVE, 1), -1);
 }
 
+// Sum a per-thread count over the warp and add it with one atomic.
+__device__ __forceinline__ void warp_count(unsigned long long* ctr, int v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(ctr, (unsigned long long)v);
+}
+
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
   float y = v - c;
   float t = s + y;
@@ -235,17 +241,20 @@ __global__ void __launch_bounds__(256) k_trace(RenderParams p) {
   const Pool& P = p.pool;
   const int n = *(volatile int*)&p.ctr->tq_count;
   if (blockIdx.x == 0 && threadIdx.x == 0) p.ctr->segments += (unsigned long long)n;
-  int err = 0;
+  int err = 0, refined = 0, visits = 0, tests = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int slot = P.tq[i];
     const int4 m = P.meta[slot];
     const DevView& V = p.views[m.x];
     const DevScene& S = p.scenes[V.scene_index];
     const float4 a = P.od0[slot], b = P.od1[slot];
-    Hit h = closest_hit(S, xyz(a), xyz(b), m.w, &p.ctr->ref_hit, &err);
+    Hit h = closest_hit(S, xyz(a), xyz(b), m.w, &refined, &visits, &tests, &err);
     P.hit[slot] = make_float2(h.t, __int_as_float(h.slot));
   }
-  if (err) atomicOr(&p.ctr->err, 1);
+  warp_count(&p.ctr->ref_hit, refined);
+  warp_count(&p.ctr->node_visits, visits);
+  warp_count(&p.ctr->tri_tests, tests);
+  if (err) atomicOr(&p.ctr->err, err);
 }
 
 // ------------------------------------------------------------------ measurement
@@ -678,7 +687,7 @@ template <int NS>
 __global__ void __launch_bounds__(256) k_shadow(RenderParams p) {
   const Pool& P = p.pool;
   const int n = *(volatile int*)&p.ctr->sq_count;
-  int err = 0;
+  int err = 0, refined = 0, visits = 0, tests = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int slot = P.sq[i];
     const int4 m = P.meta[slot];
@@ -688,7 +697,7 @@ __global__ void __launch_bounds__(256) k_shadow(RenderParams p) {
     const int tag = __float_as_int(sd.w);
     const int ei = tag & 0xffff, seg = tag >> 16;
     const float3 x = xyz(a0), w = xyz(sd);
-    Hit h = closest_hit(S, x, w, m.w, &p.ctr->ref_hit, &err);
+    Hit h = closest_hit(S, x, w, m.w, &refined, &visits, &tests, &err);
     if (h.slot < 0 || S.tri_mat[h.slot] != S.emitters[ei].mat) continue;
     const int WH = V.W * V.H;
     const int bin = m.y / WH;
@@ -714,7 +723,10 @@ __global__ void __launch_bounds__(256) k_shadow(RenderParams p) {
       P.part[slot] = pt;
     }
   }
-  if (err) atomicOr(&p.ctr->err, 1);
+  warp_count(&p.ctr->ref_hit, refined);
+  warp_count(&p.ctr->node_visits, visits);
+  warp_count(&p.ctr->tri_tests, tests);
+  if (err) atomicOr(&p.ctr->err, err);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     p.ctr->shadow += (unsigned long long)n;
     p.ctr->last_active = p.ctr->tq_count;
@@ -782,6 +794,26 @@ __global__ void k_views(const gr_view_desc* __restrict__ vd, DevView* views, int
   V.aspect = (float)d.width / (float)d.height;
 }
 
+__global__ void k_debug_rng(uint32_t seed, uint32_t view, uint32_t pixel, uint32_t sample, int seg, int call, int n,
+                            uint4* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = philox10(make_uint4(pixel, sample + (uint32_t)i, ((uint32_t)seg << 4) | (uint32_t)call, 0u), seed, view);
+}
+
+cudaError_t debug_rng_impl(uint32_t seed, uint32_t view, uint32_t pixel, uint32_t sample, int seg, int call, int n,
+                           uint32_t* host_out, cudaStream_t st) {
+  uint4* d = nullptr;
+  cudaError_t e = cudaMallocAsync(&d, sizeof(uint4) * (size_t)n, st);
+  if (e != cudaSuccess) return e;
+  k_debug_rng<<<(n + 255) / 256, 256, 0, st>>>(seed, view, pixel, sample, seg, call, n, d);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, d, sizeof(uint4) * (size_t)n, cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
 // ================================================================== host side
 namespace {
 
@@ -791,13 +823,21 @@ int sm_count(int dev) {
   return n > 0 ? n : 1;
 }
 
+// One wavefront iteration.  With `ev` (profiling) an event is recorded before
+// each kernel and after the last, so each kernel's device time is measured on
+// the stream it runs on.
 template <int NS, typename TT>
 cudaError_t launch_iteration(const RenderParams& p, int grid_regen, int grid_trace, int grid_shade, int grid_shadow,
-                             int block, size_t smem, cudaStream_t st) {
+                             int block, size_t smem, cudaStream_t st, cudaEvent_t* ev) {
+  if (ev) cudaEventRecord(ev[0], st);
   k_regen<NS><<<grid_regen, block, 0, st>>>(p);
+  if (ev) cudaEventRecord(ev[1], st);
   k_trace<<<grid_trace, block, 0, st>>>(p);
+  if (ev) cudaEventRecord(ev[2], st);
   k_shade<NS, TT><<<grid_shade, block, smem, st>>>(p);
+  if (ev) cudaEventRecord(ev[3], st);
   k_shadow<NS><<<grid_shadow, block, 0, st>>>(p);
+  if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError();
 }
 
@@ -1010,15 +1050,27 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   g_shade = std::min(g_shade, gmax);
   g_shadow = std::min(g_shadow, gmax);
 
+  const bool profile = o.profile && !o.use_graph;
+  std::vector<cudaEvent_t> pev;
   auto launch = [&]() -> cudaError_t {
-    if (NSv == 1) {
-      if (o.table_dtype == GR_TABLE_F32) return launch_iteration<1, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st);
-      if (o.table_dtype == GR_TABLE_F16) return launch_iteration<1, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st);
-      return launch_iteration<1, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st);
+    cudaEvent_t* ev = nullptr;
+    if (profile) {
+      size_t b = pev.size();
+      for (int i = 0; i < 5; ++i) {
+        cudaEvent_t e2;
+        cudaEventCreate(&e2);
+        pev.push_back(e2);
+      }
+      ev = pev.data() + b;
     }
-    if (o.table_dtype == GR_TABLE_F32) return launch_iteration<4, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st);
-    if (o.table_dtype == GR_TABLE_F16) return launch_iteration<4, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st);
-    return launch_iteration<4, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st);
+    if (NSv == 1) {
+      if (o.table_dtype == GR_TABLE_F32) return launch_iteration<1, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
+      if (o.table_dtype == GR_TABLE_F16) return launch_iteration<1, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
+      return launch_iteration<1, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
+    }
+    if (o.table_dtype == GR_TABLE_F32) return launch_iteration<4, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
+    if (o.table_dtype == GR_TABLE_F16) return launch_iteration<4, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
+    return launch_iteration<4, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
   };
 
   // ---- iteration loop: batches of B iterations; the host watches the
@@ -1109,6 +1161,24 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     }
   }
   f->iterations += it;
+  if (profile) {
+    // per-kernel device time of this render
+    for (int k = 0; k < 4; ++k) {
+      f->kernel_ms[k] = 0.0;
+      f->kernel_launches[k] = 0;
+    }
+    if (status == GR_OK && !pev.empty()) cudaEventSynchronize(pev.back());
+    for (size_t i = 0; i + 4 < pev.size(); i += 5) {
+      for (int k = 0; k < 4; ++k) {
+        float ms = 0.0f;
+        if (status == GR_OK && cudaEventElapsedTime(&ms, pev[i + k], pev[i + k + 1]) == cudaSuccess) {
+          f->kernel_ms[k] += ms;
+          f->kernel_launches[k] += 1;
+        }
+      }
+    }
+    for (auto e3 : pev) cudaEventDestroy(e3);
+  }
   if (gexec) cudaGraphExecDestroy(gexec);
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);

@@ -64,8 +64,10 @@ def test_ragged_and_degenerate_shapes(gr, oracle):
         v["max_depth"] = c.get("max_depth", 1)
         img = gr.render_image(scene, v, seed=5)
         ref = oracle.Scene(scene).render(v, 5, 0)
-        if np.linalg.norm(ref) == 0:
-            assert np.all(img == 0)
+        if np.linalg.norm(ref) < 1e-30:
+            # e.g. escaping rays far outside a coherent source's lobe: the FP64
+            # values (~1e-118) underflow to 0 in FP32
+            assert np.linalg.norm(img) < 1e-30
         else:
             assert rel_l2(img, ref) <= TOL, c
 
