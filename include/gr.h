@@ -218,6 +218,42 @@ gr_status gr_scene_bvh(gr_scene* scene, int32_t* n_out, uint64_t* keys, int32_t*
 gr_status gr_debug_rng(uint32_t seed, uint32_t view_index, uint32_t pixel, uint32_t sample, int32_t segment,
                        int32_t call, int32_t n, uint32_t* out_u32, void* cuda_stream);
 
+/* ---- Rendering without device allocation (no counterpart in the paper).
+ *
+ * For callers that must not allocate device memory while rendering: a
+ * serving process that sizes all of its GPU memory once at start-up and keeps
+ * it under its own allocator, code that runs where an allocation would stall
+ * or fail (cudaMalloc and cudaFree synchronise the device; a caching allocator
+ * can be empty under memory pressure), or a host framework that forbids
+ * libraries from allocating behind its back.  gr_render allocates its
+ * wavefront scratch on the stream; gr_render_static runs the same kernels with
+ * the scratch in a fixed device array compiled into the library
+ * (GR_STATIC_SCRATCH_BYTES; every GPU that loads the library holds it until
+ * the process exits) and writes caller-owned accumulators.  It calls no
+ * cudaMalloc, cudaFree, event, graph or allocating library routine.
+ *
+ * scenes/views/opts are as for gr_render (opts.use_graph and opts.profile
+ * must be 0).  accum: caller-owned device buffer of 2 * T float32, where T is
+ * the sum over views of width * height * n_bins * n_stokes; the first T floats
+ * are the per-view sums laid out view after view as [bin][y][x][stokes], the
+ * next T their Kahan compensations.  Samples are added (Kahan) into it, so a
+ * zeroed buffer gives a fresh image; the mean of a pixel and bin is
+ * (sum - compensation) / count, count = number of rendered samples s with
+ * s mod n_bins == bin.  The call waits for its work on the stream.
+ *
+ * Scratch limits: the views' descriptors and grating order tables, plus the
+ * slot pool, must fit in GR_STATIC_SCRATCH_BYTES; opts.pool_size (0 = as many
+ * slots as fit, about 270k) above that capacity is rejected with GR_E_INVALID
+ * and a message naming the limit.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call reuses the same
+ * array and resets what must start at zero; calls that overlap on the GPU
+ * (other streams or threads) race on it and must be serialised by the caller.
+ * Errors: as gr_render. */
+#define GR_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+gr_status gr_render_static(gr_scene* const* scenes, int32_t n_scenes, const gr_view_desc* views, int32_t n_views,
+                           const gr_render_opts* opts, float* accum, void* cuda_stream);
+
 /* Thread-local description of the last error (never NULL). */
 const char* gr_last_error(void);
 

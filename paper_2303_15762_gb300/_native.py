@@ -18,8 +18,8 @@ FLAG_NEE, FLAG_RR, FLAG_NO_RENORM = 1, 2, 4
 TABLE_DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
 
 EXPORTED = ["gr_scene_create", "gr_scene_destroy", "gr_frame_create", "gr_frame_reset", "gr_frame_release",
-            "gr_render", "gr_readback", "gr_frame_stats", "gr_scene_bvh", "gr_debug_rng", "gr_last_error",
-            "gr_abi_version"]
+            "gr_render", "gr_readback", "gr_frame_stats", "gr_scene_bvh", "gr_debug_rng", "gr_render_static",
+            "gr_last_error", "gr_abi_version"]
 
 
 class GrError(RuntimeError):
@@ -99,6 +99,7 @@ def lib_handle(require_gpu=True):
     L.gr_scene_bvh.argtypes = [P, P, P, P, P]
     U32 = ctypes.c_uint32
     L.gr_debug_rng.argtypes = [U32, U32, U32, U32, I32, I32, I32, P, P]
+    L.gr_render_static.argtypes = [P, I32, P, I32, P, P, P]
     L.gr_last_error.restype = ctypes.c_char_p
     L.gr_abi_version.restype = I32
     for name in EXPORTED:

@@ -16,6 +16,8 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
 cudaError_t readback_impl(gr_frame* f, int v, float* dst_dev, const float* inv_count_dev, cudaStream_t st);
 cudaError_t debug_rng_impl(uint32_t seed, uint32_t view, uint32_t pixel, uint32_t sample, int seg, int call, int n,
                            uint32_t* host_out, cudaStream_t st);
+gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc* vd, int n_views,
+                             const gr_render_opts& o, float* accum, cudaStream_t st, std::string& err);
 }  // namespace gr
 
 namespace {
@@ -352,6 +354,42 @@ gr_status gr_frame_stats(gr_frame* f, void* cuda_stream, gr_stats* out) {
     out->kernel_ms[k] = f->kernel_ms[k];
     out->kernel_count[k] = f->kernel_launches[k];
   }
+  return GR_OK;
+}
+
+gr_status gr_render_static(gr_scene* const* scenes, int32_t n_scenes, const gr_view_desc* views, int32_t n_views,
+                           const gr_render_opts* opts, float* accum, void* cuda_stream) {
+  if (!scenes || !views || !opts || !accum || n_views <= 0 || n_scenes <= 0)
+    return fail(GR_E_INVALID, "gr_render_static: null or empty argument");
+  if (opts->use_graph || opts->profile)
+    return fail(GR_E_INVALID, "gr_render_static: use_graph and profile are not available without allocation");
+  for (int i = 0; i < n_scenes; ++i)
+    if (!scenes[i]) return fail(GR_E_INVALID, "gr_render_static: null scene " + std::to_string(i));
+  if (opts->table_dtype < GR_TABLE_F32 || opts->table_dtype > GR_TABLE_BF16)
+    return fail(GR_E_INVALID, "gr_render_static: bad table dtype");
+  if (opts->pool_size < 0 || opts->block < 0 || (opts->block && (opts->block % 32 || opts->block > 256)))
+    return fail(GR_E_INVALID, "gr_render_static: bad pool size or block (block must be a multiple of 32, <= 256)");
+  const int ns = views[0].n_stokes;
+  for (int v = 0; v < n_views; ++v) {
+    const gr_view_desc& d = views[v];
+    if (d.width <= 0 || d.height <= 0 || d.n_bins <= 0 || d.n_bins > 4096 || (d.n_stokes != 1 && d.n_stokes != 4) ||
+        (long long)d.width * d.height * d.n_bins >= (1LL << 31))
+      return fail(GR_E_INVALID, "gr_render_static: bad view shape " + std::to_string(v));
+    if (d.n_stokes != ns) return fail(GR_E_INVALID, "gr_render_static: all views of one call need the same n_stokes");
+    if (d.scene_index < 0 || d.scene_index >= n_scenes)
+      return fail(GR_E_INVALID, "gr_render_static: scene index out of range in view " + std::to_string(v));
+    if (d.spp < 0 || d.first_sample < 0 || (long long)d.first_sample + d.spp >= (1LL << 31) ||
+        (long long)d.spp / d.n_bins + 1 >= 65536)
+      return fail(GR_E_INVALID, "gr_render_static: bad sample range in view " + std::to_string(v));
+    if (d.max_depth < 0 || d.max_depth > 250) return fail(GR_E_INVALID, "gr_render_static: max_depth out of [0, 250]");
+    if (!(d.lambda_min_um > 0.0f) || d.lambda_max_um < d.lambda_min_um || !(d.p_pix_um > 0.0f) || !(d.f_beta > 0.0f))
+      return fail(GR_E_INVALID, "gr_render_static: bad spectral range or pixel footprint in view " + std::to_string(v));
+    if (!(d.vfov_deg > 0.0f && d.vfov_deg < 180.0f) && !d.ortho)
+      return fail(GR_E_INVALID, "gr_render_static: bad field of view in view " + std::to_string(v));
+  }
+  std::string err;
+  gr_status s = gr::render_static_impl(scenes, n_scenes, views, n_views, *opts, accum, (cudaStream_t)cuda_stream, err);
+  if (s != GR_OK) return fail(s, "gr_render_static: " + err);
   return GR_OK;
 }
 

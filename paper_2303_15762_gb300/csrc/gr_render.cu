@@ -1186,6 +1186,271 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
 #undef GR_CK
 }
 
+
+// ================================================================== no-allocation variant
+// gr_render_static runs the same four wavefront kernels, but its scratch (slot
+// pool, queues, counters, view and table descriptors) lives in the fixed
+// device array below instead of memory obtained from the CUDA allocator, and
+// the accumulators are caller-owned device memory.  The array is part of the
+// module image: every GPU that loads the library holds it until the process
+// exits.  All calls share it, so calls that overlap on the GPU (two streams,
+// two host threads) race on it; calls must be ordered.
+static __device__ __align__(256) unsigned char g_static_scratch[GR_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void* g_static_addr[kMaxDevices] = {};  // device address of g_static_scratch, per device
+}  // namespace
+
+gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc* vd, int n_views,
+                             const gr_render_opts& o, float* accum, cudaStream_t st, std::string& err) {
+  // --- per-device set-up: the host-side name of the array is not a device
+  // address; ask the runtime for it, with the calling thread's device current
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    err = "cannot determine the current device";
+    return GR_E_CUDA;
+  }
+  if (!g_static_addr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess || !ptr) {
+      err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      return GR_E_CUDA;
+    }
+    g_static_addr[dev] = ptr;
+  }
+  unsigned char* base = (unsigned char*)g_static_addr[dev];
+
+  const int NSv = vd[0].n_stokes;
+  const size_t tsize = o.table_dtype == GR_TABLE_F32 ? 4 : 2;
+  std::vector<DevView> views;
+  std::vector<DevScene> sc(n_scenes);
+  std::vector<TableRow> rows;
+  std::vector<TableBuildRow> brows;
+  int vals = 0;
+  unsigned long long total_tickets = 0;
+  size_t acc_off = 0, acc_total = 0;
+  for (int v = 0; v < n_views; ++v) acc_total += (size_t)vd[v].width * vd[v].height * vd[v].n_bins * vd[v].n_stokes;
+  for (int i = 0; i < n_scenes; ++i) sc[i] = scenes[i]->dev;
+  for (int v = 0; v < n_views; ++v) {
+    const gr_view_desc& d = vd[v];
+    DevView V;
+    std::memset(&V, 0, sizeof V);
+    V.W = d.width;
+    V.H = d.height;
+    V.nb = d.n_bins;
+    V.ns = d.n_stokes;
+    V.max_depth = d.max_depth;
+    V.spp = d.spp;
+    V.first_sample = d.first_sample;
+    V.view_index = d.view_index;
+    V.scene_index = d.scene_index;
+    V.ortho = d.ortho;
+    V.ortho_half = d.ortho_half_m;
+    V.lmin = d.lambda_min_um;
+    V.lmax = d.lambda_max_um;
+    V.beta0 = d.f_beta * d.p_pix_um;
+    V.ticket_base = (long long)total_tickets;
+    V.n_tickets = (long long)d.n_bins * d.width * d.height;
+    total_tickets += (unsigned long long)V.n_tickets;
+    V.acc_sum = accum + acc_off;
+    V.acc_comp = accum + acc_total + acc_off;
+    acc_off += (size_t)d.width * d.height * d.n_bins * d.n_stokes;
+    const gr_scene* S = scenes[d.scene_index];
+    V.table_base = (int)rows.size();
+    for (size_t m = 0; m < S->mats.size(); ++m)
+      for (int b = 0; b < d.n_bins; ++b) {
+        TableRow r{0, -1};
+        const gr_material& M = S->mats[m];
+        if (M.type == GR_MAT_GRATING) {
+          double lam = d.n_bins <= 1 ? (double)d.lambda_min_um
+                                     : (double)d.lambda_min_um + (double)b * ((double)d.lambda_max_um - (double)d.lambda_min_um) /
+                                                                     (double)(d.n_bins - 1);
+          int jm = std::min(kMaxOrder, (int)std::floor(2.0 * (double)M.period_um / lam) + 2);
+          r.offset = vals;
+          r.jmax = jm;
+          vals += jm + 1;
+          TableBuildRow br{};
+          br.offset = r.offset;
+          br.jmax = jm;
+          br.view = v;
+          br.bin = b;
+          br.height_um = M.height_um;
+          brows.push_back(br);
+        }
+        rows.push_back(r);
+      }
+    views.push_back(V);
+  }
+  // --- carve the fixed array; anything that does not fit is rejected
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = off;
+    off = align_up(off + std::max<size_t>(bytes, 1), 256);
+    return r;
+  };
+  const size_t o_ctr = take(sizeof(Counters));
+  const size_t o_views = take(sizeof(DevView) * n_views);
+  const size_t o_vdesc = take(sizeof(gr_view_desc) * n_views);
+  const size_t o_scenes = take(sizeof(DevScene) * n_scenes);
+  const size_t o_rows = take(sizeof(TableRow) * rows.size());
+  const size_t o_brows = take(sizeof(TableBuildRow) * brows.size());
+  const size_t o_vals = take(tsize * (size_t)std::max(vals, 1));
+  const size_t fixed = off;
+  const size_t per_slot = sizeof(float4) * 13 + sizeof(float2) + sizeof(int4) + 2 * sizeof(int);
+  if (fixed + per_slot * 256 > (size_t)GR_STATIC_SCRATCH_BYTES) {
+    err = "views and order tables need " + std::to_string(fixed) + " bytes; the static scratch holds " +
+          std::to_string((size_t)GR_STATIC_SCRATCH_BYTES);
+    return GR_E_INVALID;
+  }
+  const long long p_max = (long long)(((size_t)GR_STATIC_SCRATCH_BYTES - fixed - 6 * 256) / per_slot) / 256 * 256;
+  if (o.pool_size > p_max) {
+    err = "pool_size " + std::to_string(o.pool_size) + " exceeds the static scratch capacity of " +
+          std::to_string(p_max) + " slots";
+    return GR_E_INVALID;
+  }
+  long long P = o.pool_size > 0 ? o.pool_size : p_max;
+  P = std::min<long long>(P, (long long)std::max<unsigned long long>(total_tickets, 1ull));
+  P = (P + 255) / 256 * 256;
+  if (P > p_max) P = p_max;
+  const size_t o_f4 = take(sizeof(float4) * (size_t)P * 13);
+  const size_t o_hit = take(sizeof(float2) * (size_t)P);
+  const size_t o_meta = take(sizeof(int4) * (size_t)P);
+  const size_t o_tq = take(sizeof(int) * (size_t)P);
+  const size_t o_sq = take(sizeof(int) * (size_t)P);
+  if (off > (size_t)GR_STATIC_SCRATCH_BYTES) {
+    err = "static scratch layout overflow";
+    return GR_E_INVALID;
+  }
+  RenderParams p;
+  std::memset(&p, 0, sizeof p);
+  p.views = (const DevView*)(base + o_views);
+  p.n_views = n_views;
+  p.scenes = (const DevScene*)(base + o_scenes);
+  p.seed = o.seed;
+  p.flags = o.flags;
+  p.rows = (const TableRow*)(base + o_rows);
+  p.table_vals = base + o_vals;
+  p.table_dtype = o.table_dtype;
+  p.table_rows = (int)rows.size();
+  p.table_vals_count = vals;
+  float4* f4 = (float4*)(base + o_f4);
+  p.pool.od0 = f4;
+  p.pool.od1 = f4 + (size_t)P;
+  for (int r = 0; r < 4; ++r) p.pool.tp[r] = f4 + (size_t)P * (2 + r);
+  p.pool.xf = f4 + (size_t)P * 6;
+  p.pool.part = f4 + (size_t)P * 7;
+  p.pool.accS = f4 + (size_t)P * 8;
+  p.pool.accC = f4 + (size_t)P * 9;
+  p.pool.shd = f4 + (size_t)P * 10;
+  p.pool.shc = f4 + (size_t)P * 11;
+  p.pool.hit = (float2*)(base + o_hit);
+  p.pool.meta = (int4*)(base + o_meta);
+  p.pool.tq = (int*)(base + o_tq);
+  p.pool.sq = (int*)(base + o_sq);
+  p.P = (int)P;
+  p.ctr = (Counters*)(base + o_ctr);
+  const size_t smem_table = sizeof(TableRow) * rows.size() + tsize * vals;
+  p.table_smem = smem_table <= 40 * 1024 ? 1 : 0;
+  const size_t smem = p.table_smem ? align_up(smem_table, 16) : 0;
+#define GR_SK(x)                                               \
+  do {                                                         \
+    e = (x);                                                   \
+    if (e != cudaSuccess) {                                    \
+      err = std::string(#x) + ": " + cudaGetErrorString(e);    \
+      return GR_E_CUDA;                                        \
+    }                                                          \
+  } while (0)
+  // the array keeps the previous call's contents: the counters and the slot
+  // states (0 = idle) must start at zero
+  Counters c0;
+  std::memset(&c0, 0, sizeof c0);
+  c0.total_tickets = total_tickets;
+  GR_SK(cudaMemcpyAsync(base + o_ctr, &c0, sizeof c0, cudaMemcpyHostToDevice, st));
+  GR_SK(cudaMemsetAsync(p.pool.meta, 0, sizeof(int4) * (size_t)P, st));
+  GR_SK(cudaMemcpyAsync(base + o_views, views.data(), sizeof(DevView) * n_views, cudaMemcpyHostToDevice, st));
+  GR_SK(cudaMemcpyAsync(base + o_vdesc, vd, sizeof(gr_view_desc) * n_views, cudaMemcpyHostToDevice, st));
+  GR_SK(cudaMemcpyAsync(base + o_scenes, sc.data(), sizeof(DevScene) * n_scenes, cudaMemcpyHostToDevice, st));
+  if (!rows.empty()) GR_SK(cudaMemcpyAsync(base + o_rows, rows.data(), sizeof(TableRow) * rows.size(), cudaMemcpyHostToDevice, st));
+  k_views<<<(n_views + 63) / 64, 64, 0, st>>>((const gr_view_desc*)(base + o_vdesc), (DevView*)(base + o_views), n_views);
+  if (!brows.empty()) {
+    GR_SK(cudaMemcpyAsync(base + o_brows, brows.data(), sizeof(TableBuildRow) * brows.size(), cudaMemcpyHostToDevice, st));
+    const TableBuildRow* br = (const TableBuildRow*)(base + o_brows);
+    const int nr = (int)brows.size();
+    if (o.table_dtype == GR_TABLE_F32)
+      k_tables<float><<<nr, 64, 0, st>>>(br, nr, p.views, (float*)(base + o_vals));
+    else if (o.table_dtype == GR_TABLE_F16)
+      k_tables<__half><<<nr, 64, 0, st>>>(br, nr, p.views, (__half*)(base + o_vals));
+    else
+      k_tables<__nv_bfloat16><<<nr, 64, 0, st>>>(br, nr, p.views, (__nv_bfloat16*)(base + o_vals));
+  }
+  GR_SK(cudaGetLastError());
+  // --- launch shapes (same rule as gr_render)
+  const int sms = sm_count(dev);
+  const int block = o.block > 0 ? o.block : 256;
+  auto grid_for = [&](const void* fn, size_t dyn) {
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, block, dyn);
+    return sms * std::max(per, 1);
+  };
+  const void* shade_fn = NSv == 1 ? (o.table_dtype == GR_TABLE_F32 ? (const void*)k_shade<1, float>
+                                     : o.table_dtype == GR_TABLE_F16 ? (const void*)k_shade<1, __half>
+                                                                     : (const void*)k_shade<1, __nv_bfloat16>)
+                                  : (o.table_dtype == GR_TABLE_F32 ? (const void*)k_shade<4, float>
+                                     : o.table_dtype == GR_TABLE_F16 ? (const void*)k_shade<4, __half>
+                                                                     : (const void*)k_shade<4, __nv_bfloat16>);
+  const int gmax = (int)((P + block - 1) / block);
+  const int g_regen = std::min(gmax, grid_for(NSv == 1 ? (const void*)k_regen<1> : (const void*)k_regen<4>, 0));
+  const int g_trace = std::min(gmax, grid_for((const void*)k_trace, 0));
+  const int g_shade = std::min(gmax, grid_for(shade_fn, smem));
+  const int g_shadow = std::min(gmax, grid_for(NSv == 1 ? (const void*)k_shadow<1> : (const void*)k_shadow<4>, 0));
+  // --- iteration loop; the host reads the device counters into a stack copy
+  // after every batch (no events, no pinned buffer)
+  long long n_max = 1, d_max = 0;
+  for (int v = 0; v < n_views; ++v) {
+    n_max = std::max<long long>(n_max, (long long)vd[v].spp / vd[v].n_bins + 1);
+    d_max = std::max<long long>(d_max, vd[v].max_depth);
+  }
+  const int B = 8;
+  const long long worst = ((long long)((total_tickets + P - 1) / P) + 1) * n_max * (d_max + 3) + 4 * B;
+  const long long max_iter = o.max_iterations > 0 ? o.max_iterations : 2 * worst;
+  long long it = 0;
+  for (;;) {
+    for (int i = 0; i < B; ++i) {
+      if (NSv == 1) {
+        if (o.table_dtype == GR_TABLE_F32) e = launch_iteration<1, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
+        else if (o.table_dtype == GR_TABLE_F16) e = launch_iteration<1, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
+        else e = launch_iteration<1, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
+      } else {
+        if (o.table_dtype == GR_TABLE_F32) e = launch_iteration<4, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
+        else if (o.table_dtype == GR_TABLE_F16) e = launch_iteration<4, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
+        else e = launch_iteration<4, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
+      }
+      if (e != cudaSuccess) {
+        err = std::string("launch: ") + cudaGetErrorString(e);
+        return GR_E_CUDA;
+      }
+    }
+    it += B;
+    Counters hc;
+    GR_SK(cudaMemcpyAsync(&hc, base + o_ctr, sizeof hc, cudaMemcpyDeviceToHost, st));
+    GR_SK(cudaStreamSynchronize(st));
+    if (hc.err) {
+      err = hc.err == 1 ? "traversal stack overflow" : "corrupt BVH (traversal bound exceeded)";
+      return GR_E_INVALID;
+    }
+    if (hc.last_active == 0 && hc.next_ticket >= hc.total_tickets) break;
+    if (it > max_iter) {
+      err = "render exceeded its iteration bound";
+      return GR_E_TIMEOUT;
+    }
+  }
+#undef GR_SK
+  return GR_OK;
+}
+
 cudaError_t readback_impl(gr_frame* f, int v, float* dst_dev, const float* inv_count_dev, cudaStream_t st) {
   const gr_view_shape& s = f->shapes[v];
   const long long n = (long long)s.W * s.H * s.nb * s.ns;
