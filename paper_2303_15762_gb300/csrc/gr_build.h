@@ -19,12 +19,14 @@ struct Pool {
   float4* od0;   // o.xyz, beta^2 (um^2)
   float4* od1;   // d.xyz, rho
   float4* tp[4]; // throughput: scalar in tp[0].x, or Mueller rows 0..3
-  float4* xf;    // Stokes frame x axis, MIS density of the current direction
+  float4* xf;    // Stokes frame x axis (w unused)
   float4* part;  // contribution of the current sample
   float4* accS;  // ticket sums (Kahan)
   float4* accC;  // ticket compensations
   float4* shd;   // NEE direction xyz, (emitter index | vertex segment << 16)
-  float4* shc;   // NEE weight (Stokes vector)
+  float4* shc;   // NEE throughput column (Stokes vector)
+  float4* shm;   // NEE lobe terms: squared offset, g, (k l)^2, cos
+  float4* mis;   // lobe terms of the vertex that sampled the current direction
   float2* hit;   // t, leaf slot
   int4* meta;    // view, local ticket, (sample k | seg << 16 | state << 24 | delta << 26), previous leaf slot
   int* tq;       // trace queue

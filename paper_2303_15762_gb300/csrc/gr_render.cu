@@ -321,20 +321,21 @@ __device__ __forceinline__ float3 emitter_normal(const DevScene& S, int ei) {
   return f3((float)n.x, (float)n.y, (float)n.z);
 }
 
-// Density of the m >= 1 part of the rough lobe in tangential direction cosines.
-__device__ float rough_density(float g, float k, float ell, float3 delta) {
-  const float kl2 = (k * ell) * (k * ell);
-  const float r2 = dot(delta, delta);
+// Density of the m >= 1 part of the rough lobe in tangential direction
+// cosines at squared offset r2 from the mirror direction, kl2 = (|k| l)^2.
+// Evaluated only where it is needed (MIS weights of paths that actually reach
+// an emitter), not at every rough vertex.
+__device__ float rough_density(float g, float kl2, float r2) {
   if (g > kGCont) {
     const float var = 2.0f * g / kl2;
-    return expf(-0.5f * r2 / var) / (2.0f * kPi * var);
+    return __expf(-0.5f * r2 / var) / (2.0f * kPi * var);
   }
-  float pm = expf(-g), sum = 0.0f;
+  float pm = __expf(-g), sum = 0.0f;
   const int mmax = (int)(g + 12.0f * sqrtf(g) + 20.0f);
   for (int m = 1; m <= mmax; ++m) {
     pm *= g / (float)m;
     const float var = 2.0f * (float)m / kl2;
-    sum += pm * expf(-0.5f * r2 / var) / (2.0f * kPi * var);
+    sum += pm * __expf(-0.5f * r2 / var) / (2.0f * kPi * var);
   }
   return sum;
 }
@@ -437,7 +438,8 @@ __global__ void __launch_bounds__(256) k_shade(RenderParams p) {
             const float3 ne = emitter_normal(S, ei);
             const float kap = 1.0f / (s_ray2 + src_spread2(lambda, M.coh_len_um));
             const float pn = vmf(-d, ne, kap) / (float)S.n_emitters;
-            const float pb = xfv.w;
+            const float4 mi = P.mis[slot];  // (r2, g, kl2, cos) of the rough vertex that sampled d
+            const float pb = rough_density(mi.y, mi.z, mi.x) * mi.w;
             w = pb * pb / (pb * pb + pn * pn);
           }
           add_col(val * w);
@@ -494,7 +496,7 @@ __global__ void __launch_bounds__(256) k_shade(RenderParams p) {
             const float3 t_mir = d - dot(d, nrm) * nrm;
             float3 d_out = d;
             int delta = 1;
-            float pdf = 0.0f;
+            float4 mis_rec = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
             bool alive = true;
             float g_r = 0.0f;
             if (M.type == GR_MAT_GRATING) {
@@ -619,7 +621,7 @@ __global__ void __launch_bounds__(256) k_shade(RenderParams p) {
                 } else {
                   const float cz = sqrtf(1.0f - tt);
                   d_out = to + cz * nrm;
-                  if (p.flags & GR_FLAG_NEE) pdf = rough_density(g_r, kw, M.corr_len_um, dt) * cz;
+                  mis_rec = make_float4(dot(dt, dt), g_r, kl * kl, cz);
                 }
               }
             }
@@ -634,17 +636,15 @@ __global__ void __launch_bounds__(256) k_shade(RenderParams p) {
               const float kap = 1.0f / (s_ray2 + src_spread2(lambda, EM.coh_len_um));
               const float3 w = vmf_sample(-nE, kap, un.y, un.z);
               const float cos_o = dot(w, nrm);
-              if (cos_o > 0.0f) {
+              if (cos_o > 0.0f && g_r > 0.0f) {
+                // the lobe density, the MIS weight and the measurement are
+                // evaluated by k_shadow once the shadow ray reaches the emitter
                 const float3 dtn = (w - dot(w, nrm) * nrm) - t_mir;
-                const float f = (g_r > 0.0f ? rough_density(g_r, kw, M.corr_len_um, dtn) : 0.0f) * cos_o;
-                const float pn = vmf(w, -nE, kap) / (float)ne_cnt;
-                if (f > 0.0f && pn > 0.0f) {
-                  const float wm = pn * pn / (pn * pn + f * f) * (f / pn);
-                  P.shd[slot] = make_float4(w.x, w.y, w.z, __int_as_float(ei | (seg << 16)));
-                  P.shc[slot] = make_float4(cn[0] * wm, NS == 4 ? cn[1] * wm : 0.0f, NS == 4 ? cn[2] * wm : 0.0f,
-                                            NS == 4 ? cn[3] * wm : 0.0f);
-                  want_shadow = true;
-                }
+                const float kl = kw * M.corr_len_um;
+                P.shd[slot] = make_float4(w.x, w.y, w.z, __int_as_float(ei | (seg << 16)));
+                P.shc[slot] = make_float4(cn[0], NS == 4 ? cn[1] : 0.0f, NS == 4 ? cn[2] : 0.0f, NS == 4 ? cn[3] : 0.0f);
+                P.shm[slot] = make_float4(dot(dtn, dtn), g_r, kl * kl, cos_o);
+                want_shadow = true;
               }
             }
             // the vertex becomes the ray origin; (beta, rho) are unchanged by
@@ -654,12 +654,12 @@ __global__ void __launch_bounds__(256) k_shade(RenderParams p) {
               P.od1[slot] = make_float4(d_out.x, d_out.y, d_out.z, rho);
               if (NS == 1) {
                 P.tp[0][slot] = make_float4(T[0][0], 0.0f, 0.0f, 0.0f);
-                P.xf[slot] = make_float4(0.0f, 0.0f, 0.0f, pdf);
               } else {
                 for (int r = 0; r < 4; ++r) P.tp[r][slot] = make_float4(T[r][0], T[r][1], T[r][2], T[r][3]);
                 const float3 xn = s_vector(nrm, -d_out, s_o);
-                P.xf[slot] = make_float4(xn.x, xn.y, xn.z, pdf);
+                P.xf[slot] = make_float4(xn.x, xn.y, xn.z, 0.0f);
               }
+              if (!delta) P.mis[slot] = mis_rec;
               P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg + 1, ST_ACTIVE, delta), hslot);
             } else {
               P.od1[slot] = make_float4(d.x, d.y, d.z, rho);
@@ -712,15 +712,26 @@ __global__ void __launch_bounds__(256) k_shadow(RenderParams p) {
     const float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallNeeFoot);
     const float val = measure_emitter(S, ei, x + h.t * w, w, b2, ro, kw, lambda, u.x, u.y);
     if (val != 0.0f) {
-      const float4 c = P.shc[slot];
-      float4 pt = P.part[slot];
-      pt.x += c.x * val;
-      if (NS == 4) {
-        pt.y += c.y * val;
-        pt.z += c.z * val;
-        pt.w += c.w * val;
+      // lobe density toward w and the power-heuristic weight against the
+      // emitter's direction sampler
+      const float4 sm = P.shm[slot];
+      const float f = rough_density(sm.y, sm.z, sm.x) * sm.w;
+      const float3 nE = emitter_normal(S, ei);
+      const float s_ray2 = 1.0f / (2.0f * V.beta0 * V.beta0 * kw * kw);
+      const float kap = 1.0f / (s_ray2 + src_spread2(lambda, S.mats[S.emitters[ei].mat].coh_len_um));
+      const float pn = vmf(w, -nE, kap) / (float)S.n_emitters;
+      if (f > 0.0f && pn > 0.0f) {
+        const float wm = pn * pn / (pn * pn + f * f) * (f / pn) * val;
+        const float4 c = P.shc[slot];
+        float4 pt = P.part[slot];
+        pt.x += c.x * wm;
+        if (NS == 4) {
+          pt.y += c.y * wm;
+          pt.z += c.z * wm;
+          pt.w += c.w * wm;
+        }
+        P.part[slot] = pt;
       }
-      P.part[slot] = pt;
     }
   }
   warp_count(&p.ctr->ref_hit, refined);
@@ -931,7 +942,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const size_t o_rows = take(sizeof(TableRow) * std::max<size_t>(plan.rows.size(), 1));
   const size_t o_brows = take(sizeof(TableBuildRow) * std::max<size_t>(plan.build_rows.size(), 1));
   const size_t o_vals = take(tsize * std::max(plan.vals_count, 1));
-  const size_t o_f4 = take(sizeof(float4) * (size_t)P * 13);
+  const size_t o_f4 = take(sizeof(float4) * (size_t)P * 14);
   const size_t o_hit = take(sizeof(float2) * (size_t)P);
   const size_t o_meta = take(sizeof(int4) * (size_t)P);
   const size_t o_tq = take(sizeof(int) * (size_t)P);
@@ -970,6 +981,8 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   p.pool.accC = f4 + (size_t)P * 9;
   p.pool.shd = f4 + (size_t)P * 10;
   p.pool.shc = f4 + (size_t)P * 11;
+  p.pool.shm = f4 + (size_t)P * 12;
+  p.pool.mis = f4 + (size_t)P * 13;
   p.pool.hit = (float2*)(base + o_hit);
   p.pool.meta = (int4*)(base + o_meta);
   p.pool.tq = (int*)(base + o_tq);
@@ -1299,7 +1312,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   const size_t o_brows = take(sizeof(TableBuildRow) * brows.size());
   const size_t o_vals = take(tsize * (size_t)std::max(vals, 1));
   const size_t fixed = off;
-  const size_t per_slot = sizeof(float4) * 13 + sizeof(float2) + sizeof(int4) + 2 * sizeof(int);
+  const size_t per_slot = sizeof(float4) * 14 + sizeof(float2) + sizeof(int4) + 2 * sizeof(int);
   if (fixed + per_slot * 256 > (size_t)GR_STATIC_SCRATCH_BYTES) {
     err = "views and order tables need " + std::to_string(fixed) + " bytes; the static scratch holds " +
           std::to_string((size_t)GR_STATIC_SCRATCH_BYTES);
@@ -1315,7 +1328,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   P = std::min<long long>(P, (long long)std::max<unsigned long long>(total_tickets, 1ull));
   P = (P + 255) / 256 * 256;
   if (P > p_max) P = p_max;
-  const size_t o_f4 = take(sizeof(float4) * (size_t)P * 13);
+  const size_t o_f4 = take(sizeof(float4) * (size_t)P * 14);
   const size_t o_hit = take(sizeof(float2) * (size_t)P);
   const size_t o_meta = take(sizeof(int4) * (size_t)P);
   const size_t o_tq = take(sizeof(int) * (size_t)P);
@@ -1346,6 +1359,8 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   p.pool.accC = f4 + (size_t)P * 9;
   p.pool.shd = f4 + (size_t)P * 10;
   p.pool.shc = f4 + (size_t)P * 11;
+  p.pool.shm = f4 + (size_t)P * 12;
+  p.pool.mis = f4 + (size_t)P * 13;
   p.pool.hit = (float2*)(base + o_hit);
   p.pool.meta = (int4*)(base + o_meta);
   p.pool.tq = (int*)(base + o_tq);
