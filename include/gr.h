@@ -130,7 +130,7 @@ typedef struct {
   float ortho_half_m;
 } gr_view_desc;
 
-/* Render options.  flags: GR_FLAG_NEE next-event estimation toward emitters
+/* Render options (36 bytes).  flags: GR_FLAG_NEE next-event estimation toward emitters
  * with power-heuristic MIS; GR_FLAG_RR Russian roulette after 3 interactions;
  * GR_FLAG_NO_RENORM keeps raw grating order weights (no renormalisation over
  * propagating orders).  table_dtype: storage of the grating order tables
@@ -144,10 +144,18 @@ typedef struct {
   int32_t table_dtype;
   int32_t pool_size;
   int32_t block;
-  int32_t use_graph;     /* 1: replay the wavefront iteration as a CUDA graph */
+  int32_t use_graph;     /* 1: run the whole render as ONE graph launch: a CUDA graph
+                             whose conditional while-node repeats the wavefront iteration
+                             until every ticket is done (device-side loop, bounded by the
+                             iteration limit); the instantiated graph is cached in the
+                             frame and reused while the launch shapes are unchanged; the
+                             call waits for completion */
   int32_t max_iterations; /* 0 = default bound; exceeding it returns GR_E_TIMEOUT */
   int32_t profile;        /* 1: time every kernel with CUDA events on the render stream
                              (not with use_graph); the call then waits for completion */
+  int32_t regen_threshold_pct; /* 0: refill idle slots every iteration; p > 0: claim new
+                                  tickets only once at least p% of the pool is idle (fresh
+                                  camera rays then enter in coherent groups) */
 } gr_render_opts;
 
 /* Render statistics of the last gr_render on a frame (device-side counters,
@@ -193,6 +201,16 @@ gr_status gr_frame_release(gr_frame* frame);
  * accumulators are then incomplete). */
 gr_status gr_render(gr_scene* const* scenes, int32_t n_scenes, const gr_view_desc* views, int32_t n_views,
                     const gr_render_opts* opts, gr_frame* frame, void* cuda_stream);
+
+/* Continuous batching: one render over views whose accumulators live in
+ * different frames (e.g. one resident frame per request of a progressive
+ * service).  View v adds into view frame_view[v] of frames[v] (shapes must
+ * match; no two views may target the same frame view).  The scratch, counters
+ * and cached render graph of frames[0] serve the call.  Otherwise as
+ * gr_render.  Errors: as gr_render. */
+gr_status gr_render_multi(gr_scene* const* scenes, int32_t n_scenes, const gr_view_desc* views, int32_t n_views,
+                          const gr_render_opts* opts, gr_frame* const* frames, const int32_t* frame_view,
+                          void* cuda_stream);
 
 /* Copy view `view`'s mean image, float32 [height][width][n_bins][n_stokes]
  * (sum / count per bin, 0 where a bin has no samples), to dst (device memory

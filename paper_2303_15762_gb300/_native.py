@@ -18,7 +18,7 @@ FLAG_NEE, FLAG_RR, FLAG_NO_RENORM = 1, 2, 4
 TABLE_DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
 
 EXPORTED = ["gr_scene_create", "gr_scene_destroy", "gr_frame_create", "gr_frame_reset", "gr_frame_release",
-            "gr_render", "gr_readback", "gr_frame_stats", "gr_scene_bvh", "gr_debug_rng", "gr_render_static",
+            "gr_render", "gr_readback", "gr_frame_stats", "gr_scene_bvh", "gr_debug_rng", "gr_render_static", "gr_render_multi",
             "gr_last_error", "gr_abi_version"]
 
 
@@ -59,7 +59,8 @@ class gr_view_desc(ctypes.Structure):
 class gr_render_opts(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint32), ("flags", ctypes.c_int32), ("table_dtype", ctypes.c_int32),
                 ("pool_size", ctypes.c_int32), ("block", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("max_iterations", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("max_iterations", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("regen_threshold_pct", ctypes.c_int32)]
 
 
 class gr_stats(ctypes.Structure):
@@ -100,6 +101,7 @@ def lib_handle(require_gpu=True):
     U32 = ctypes.c_uint32
     L.gr_debug_rng.argtypes = [U32, U32, U32, U32, I32, I32, I32, P, P]
     L.gr_render_static.argtypes = [P, I32, P, I32, P, P, P]
+    L.gr_render_multi.argtypes = [P, I32, P, I32, P, P, P, P]
     L.gr_last_error.restype = ctypes.c_char_p
     L.gr_abi_version.restype = I32
     for name in EXPORTED:
@@ -263,7 +265,7 @@ class Frame:
 
 
 def make_opts(seed=1, flags=0, table_dtype="f32", pool_size=0, block=0, use_graph=False, max_iterations=0,
-              profile=False):
+              profile=False, regen_threshold_pct=0):
     o = gr_render_opts()
     o.seed = int(seed) & 0xFFFFFFFF
     o.flags = int(flags)
@@ -272,6 +274,7 @@ def make_opts(seed=1, flags=0, table_dtype="f32", pool_size=0, block=0, use_grap
     o.use_graph = int(bool(use_graph))
     o.max_iterations = int(max_iterations)
     o.profile = int(bool(profile))
+    o.regen_threshold_pct = int(regen_threshold_pct)
     return o
 
 
@@ -282,6 +285,18 @@ def render(scenes, views, frame, stream=None, **opts):
     arr = pack_views(views)
     o = make_opts(**opts)
     _check(L.gr_render(sc, len(scenes), arr, len(views), ctypes.byref(o), frame.handle, stream or current_stream()))
+
+
+def render_multi(scenes, views, frames, frame_view, stream=None, **opts):
+    """One render over views accumulating into different frames
+    (continuous batching): view i adds into frames[i]'s view frame_view[i]."""
+    L = lib_handle()
+    sc = (ctypes.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    arr = pack_views(views)
+    fr = (ctypes.c_void_p * len(frames))(*[f.handle.value for f in frames])
+    fv = (ctypes.c_int32 * len(frame_view))(*[int(x) for x in frame_view])
+    o = make_opts(**opts)
+    _check(L.gr_render_multi(sc, len(scenes), arr, len(views), ctypes.byref(o), fr, fv, stream or current_stream()))
 
 
 def debug_rng(seed, view_index, pixel, sample, segment, call, n, stream=None):

@@ -1,0 +1,60 @@
+"""Autotuner for the wavefront render's launch parameters.
+
+Coordinate descent over the slot-pool size, the block size and the
+regeneration threshold on a reduced-sample probe of the actual workload (the
+same scenes and views, fewer samples per pixel), timed with CUDA events on the
+render stream.  The result is a dict of gr_render options.
+"""
+import statistics
+
+POOLS = (1 << 18, 1 << 19, 1 << 20, 1 << 21, 1 << 22)
+BLOCKS = (128, 256)
+THRESHOLDS = (0, 25, 50, 75)
+
+
+def _time_render(gr, scenes, views, frame, opts, repeats=2):
+    import torch
+    stream = torch.cuda.current_stream()
+    times = []
+    for r in range(repeats + 1):
+        frame.reset()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gr.render(scenes, views, frame, **opts)
+        e1.record(stream)
+        e1.synchronize()
+        if r > 0:  # the first run builds and caches the render graph
+            times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
+
+
+def autotune(gr, scenes, views, base_opts, probe_spp=None, pools=POOLS, blocks=BLOCKS, thresholds=THRESHOLDS,
+             log=None):
+    """Return (best_opts, trials).  base_opts are fixed options (seed, flags,
+    table dtype, use_graph); probe_spp reduces every view's samples."""
+    probe = [dict(v, spp=probe_spp if probe_spp else v["spp"]) for v in views]
+    frame = gr.Frame(probe)
+    trials = []
+    best = dict(base_opts, pool_size=1 << 20, block=256, regen_threshold_pct=0)
+
+    def run(cand):
+        ms = _time_render(gr, scenes, probe, frame, cand)
+        trials.append((dict(pool_size=cand["pool_size"], block=cand["block"],
+                            regen_threshold_pct=cand["regen_threshold_pct"]), ms))
+        if log:
+            log("autotune pool=%d block=%d thr=%d: %.2f ms" % (cand["pool_size"], cand["block"],
+                                                              cand["regen_threshold_pct"], ms))
+        return ms
+
+    best_ms = run(best)
+    for key, values in (("pool_size", pools), ("block", blocks), ("regen_threshold_pct", thresholds)):
+        for v in values:
+            if v == best[key]:
+                continue
+            cand = dict(best, **{key: v})
+            ms = run(cand)
+            if ms < best_ms:
+                best, best_ms = cand, ms
+    frame.close()
+    return best, trials

@@ -12,7 +12,8 @@
 
 namespace gr {
 gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc* vd, int n_views,
-                      const gr_render_opts& o, gr_frame* f, cudaStream_t st, std::string& err);
+                      const gr_render_opts& o, gr_frame* f, const std::vector<float*>& acc_sum,
+                      const std::vector<float*>& acc_comp, cudaStream_t st, std::string& err);
 cudaError_t readback_impl(gr_frame* f, int v, float* dst_dev, const float* inv_count_dev, cudaStream_t st);
 cudaError_t debug_rng_impl(uint32_t seed, uint32_t view, uint32_t pixel, uint32_t sample, int seg, int call, int n,
                            uint32_t* host_out, cudaStream_t st);
@@ -262,52 +263,108 @@ gr_status gr_frame_release(gr_frame* f) {
   if (f->scratch) cudaFree(f->scratch);
   if (f->ctr) cudaFree(f->ctr);
   if (f->ctr_host) cudaFreeHost(f->ctr_host);
+  if (f->graph_exec) cudaGraphExecDestroy(f->graph_exec);
+  if (f->capture_stream) cudaStreamDestroy(f->capture_stream);
   delete f;
   return GR_OK;
 }
 
-gr_status gr_render(gr_scene* const* scenes, int32_t n_scenes, const gr_view_desc* views, int32_t n_views,
-                    const gr_render_opts* opts, gr_frame* frame, void* cuda_stream) {
-  if (!scenes || !views || !opts || !frame || n_views <= 0 || n_scenes <= 0)
-    return fail(GR_E_INVALID, "gr_render: null or empty argument");
-  if (n_views != frame->n_views) return fail(GR_E_INVALID, "gr_render: view count differs from the frame's");
+namespace {
+
+// Checks shared by gr_render and gr_render_multi: options, scene indices,
+// sample ranges, spectral and camera parameters, and the frame view each view
+// accumulates into.
+gr_status check_render_args(const char* who, gr_scene* const* scenes, int32_t n_scenes, const gr_view_desc* views,
+                            int32_t n_views, const gr_render_opts* opts, gr_frame* const* frames,
+                            const int32_t* frame_view) {
+  const std::string w(who);
+  if (!scenes || !views || !opts || !frames || n_views <= 0 || n_scenes <= 0)
+    return fail(GR_E_INVALID, w + ": null or empty argument");
   for (int i = 0; i < n_scenes; ++i)
-    if (!scenes[i]) return fail(GR_E_INVALID, "gr_render: null scene " + std::to_string(i));
+    if (!scenes[i]) return fail(GR_E_INVALID, w + ": null scene " + std::to_string(i));
   if (opts->table_dtype < GR_TABLE_F32 || opts->table_dtype > GR_TABLE_BF16)
-    return fail(GR_E_INVALID, "gr_render: bad table dtype");
+    return fail(GR_E_INVALID, w + ": bad table dtype");
   if (opts->pool_size < 0 || opts->block < 0 || (opts->block && (opts->block % 32 || opts->block > 256)))
-    return fail(GR_E_INVALID, "gr_render: bad pool size or block (block must be a multiple of 32, <= 256)");
+    return fail(GR_E_INVALID, w + ": bad pool size or block (block must be a multiple of 32, <= 256)");
+  if (opts->regen_threshold_pct < 0 || opts->regen_threshold_pct > 100)
+    return fail(GR_E_INVALID, w + ": regen_threshold_pct out of [0, 100]");
   const int ns = views[0].n_stokes;
   for (int v = 0; v < n_views; ++v) {
     const gr_view_desc& d = views[v];
-    const gr_view_shape& s = frame->shapes[v];
+    const gr_frame* fr = frames[v];
+    const int fv = frame_view ? frame_view[v] : v;
+    if (!fr || fv < 0 || fv >= fr->n_views)
+      return fail(GR_E_INVALID, w + ": view " + std::to_string(v) + " has no frame view");
+    const gr_view_shape& s = fr->shapes[fv];
     if (d.width != s.W || d.height != s.H || d.n_bins != s.nb || d.n_stokes != s.ns)
-      return fail(GR_E_INVALID, "gr_render: view " + std::to_string(v) + " does not match the frame");
-    if (d.n_stokes != ns) return fail(GR_E_INVALID, "gr_render: all views of one call need the same n_stokes");
+      return fail(GR_E_INVALID, w + ": view " + std::to_string(v) + " does not match its frame view");
+    if (d.n_stokes != ns) return fail(GR_E_INVALID, w + ": all views of one call need the same n_stokes");
     if (d.scene_index < 0 || d.scene_index >= n_scenes)
-      return fail(GR_E_INVALID, "gr_render: scene index out of range in view " + std::to_string(v));
+      return fail(GR_E_INVALID, w + ": scene index out of range in view " + std::to_string(v));
     if (d.spp < 0 || d.first_sample < 0 || (long long)d.first_sample + d.spp >= (1LL << 31))
-      return fail(GR_E_INVALID, "gr_render: bad sample range in view " + std::to_string(v));
+      return fail(GR_E_INVALID, w + ": bad sample range in view " + std::to_string(v));
     if ((long long)d.spp / d.n_bins + 1 >= 65536)
-      return fail(GR_E_INVALID, "gr_render: more than 65535 samples per pixel and bin in one call");
-    if (d.max_depth < 0 || d.max_depth > 250) return fail(GR_E_INVALID, "gr_render: max_depth out of [0, 250]");
+      return fail(GR_E_INVALID, w + ": more than 65535 samples per pixel and bin in one call");
+    if (d.max_depth < 0 || d.max_depth > 250) return fail(GR_E_INVALID, w + ": max_depth out of [0, 250]");
     if (!(d.lambda_min_um > 0.0f) || d.lambda_max_um < d.lambda_min_um || !(d.p_pix_um > 0.0f) || !(d.f_beta > 0.0f))
-      return fail(GR_E_INVALID, "gr_render: bad spectral range or pixel footprint in view " + std::to_string(v));
+      return fail(GR_E_INVALID, w + ": bad spectral range or pixel footprint in view " + std::to_string(v));
     if (!(d.vfov_deg > 0.0f && d.vfov_deg < 180.0f) && !d.ortho)
-      return fail(GR_E_INVALID, "gr_render: bad field of view in view " + std::to_string(v));
+      return fail(GR_E_INVALID, w + ": bad field of view in view " + std::to_string(v));
+  }
+  // two views must not accumulate into the same frame view in one call
+  for (int a = 0; a < n_views; ++a)
+    for (int b = a + 1; b < n_views && n_views <= 4096; ++b)
+      if (frames[a] == frames[b] && (frame_view ? frame_view[a] == frame_view[b] : a == b))
+        return fail(GR_E_INVALID, w + ": two views accumulate into the same frame view");
+  return GR_OK;
+}
+
+void add_counts(gr_frame* fr, int fv, const gr_view_desc& d) {
+  for (int b = 0; b < d.n_bins; ++b) {
+    long long r = ((long long)b - d.first_sample) % d.n_bins;
+    if (r < 0) r += d.n_bins;
+    long long s0 = d.first_sample + r, end = (long long)d.first_sample + d.spp;
+    fr->counts[fv][b] += s0 < end ? (end - 1 - s0) / d.n_bins + 1 : 0;
+  }
+}
+
+}  // namespace
+
+gr_status gr_render(gr_scene* const* scenes, int32_t n_scenes, const gr_view_desc* views, int32_t n_views,
+                    const gr_render_opts* opts, gr_frame* frame, void* cuda_stream) {
+  if (!frame) return fail(GR_E_INVALID, "gr_render: null frame");
+  if (n_views != frame->n_views) return fail(GR_E_INVALID, "gr_render: view count differs from the frame's");
+  std::vector<gr_frame*> frames(std::max(n_views, 1), frame);
+  gr_status s = check_render_args("gr_render", scenes, n_scenes, views, n_views, opts, frames.data(), nullptr);
+  if (s != GR_OK) return s;
+  std::vector<float*> as(n_views), ac(n_views);
+  for (int v = 0; v < n_views; ++v) {
+    as[v] = frame->acc + frame->offsets[v];
+    ac[v] = frame->acc + frame->acc_floats + frame->offsets[v];
   }
   std::string err;
-  gr_status s = gr::render_impl(scenes, n_scenes, views, n_views, *opts, frame, (cudaStream_t)cuda_stream, err);
+  s = gr::render_impl(scenes, n_scenes, views, n_views, *opts, frame, as, ac, (cudaStream_t)cuda_stream, err);
   if (s != GR_OK) return fail(s, "gr_render: " + err);
+  for (int v = 0; v < n_views; ++v) add_counts(frame, v, views[v]);
+  return GR_OK;
+}
+
+gr_status gr_render_multi(gr_scene* const* scenes, int32_t n_scenes, const gr_view_desc* views, int32_t n_views,
+                          const gr_render_opts* opts, gr_frame* const* frames, const int32_t* frame_view,
+                          void* cuda_stream) {
+  if (!frame_view) return fail(GR_E_INVALID, "gr_render_multi: null frame_view");
+  gr_status s = check_render_args("gr_render_multi", scenes, n_scenes, views, n_views, opts, frames, frame_view);
+  if (s != GR_OK) return s;
+  std::vector<float*> as(n_views), ac(n_views);
   for (int v = 0; v < n_views; ++v) {
-    const gr_view_desc& d = views[v];
-    for (int b = 0; b < d.n_bins; ++b) {
-      long long r = ((long long)b - d.first_sample) % d.n_bins;
-      if (r < 0) r += d.n_bins;
-      long long s0 = d.first_sample + r, end = (long long)d.first_sample + d.spp;
-      frame->counts[v][b] += s0 < end ? (end - 1 - s0) / d.n_bins + 1 : 0;
-    }
+    gr_frame* fr = frames[v];
+    as[v] = fr->acc + fr->offsets[frame_view[v]];
+    ac[v] = fr->acc + fr->acc_floats + fr->offsets[frame_view[v]];
   }
+  std::string err;
+  s = gr::render_impl(scenes, n_scenes, views, n_views, *opts, frames[0], as, ac, (cudaStream_t)cuda_stream, err);
+  if (s != GR_OK) return fail(s, "gr_render_multi: " + err);
+  for (int v = 0; v < n_views; ++v) add_counts(frames[v], frame_view[v], views[v]);
   return GR_OK;
 }
 

@@ -57,6 +57,7 @@ struct RenderParams {
   int table_vals_count;
   Pool pool;
   int P;
+  int regen_thr;         // regeneration threshold, percent of idle slots (0 = always)
   Counters* ctr;
 };
 
@@ -89,6 +90,10 @@ struct gr_frame {
   gr::Counters* ctr_host = nullptr;      // pinned mirror
   long long launches = 0;
   long long iterations = 0;
+  // cached single-launch render graph and the launch parameters it was built for
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t capture_stream = nullptr;   // private stream used only to record the graph
+  std::vector<unsigned char> graph_key;
   double kernel_ms[4] = {0, 0, 0, 0};       // last profiled render: regen, trace, shade, shadow
   long long kernel_launches[4] = {0, 0, 0, 0};
   int device = 0;

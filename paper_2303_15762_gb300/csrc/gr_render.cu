@@ -154,6 +154,11 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
     p.ctr->iters += 1;
   }
   int finished = 0;
+  // regeneration threshold: new tickets are claimed only while enough of the
+  // pool was idle after the previous iteration (or when nothing is active)
+  const int active_prev = *(volatile int*)&p.ctr->last_active;
+  const bool may_claim = p.regen_thr <= 0 || active_prev == 0 ||
+                         (long long)(p.P - active_prev) * 100 >= (long long)p.regen_thr * p.P;
   for (int base = blockIdx.x * blockDim.x; base < p.P; base += stride) {
     const int slot = base + threadIdx.x;
     const bool valid = slot < p.P;
@@ -194,6 +199,10 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
       need = true;
     } else if (valid && st == ST_ACTIVE) {
       active = true;
+    }
+    if (need && !may_claim) {
+      need = false;
+      P.meta[slot] = make_int4(0, 0, meta_pack(0, 0, ST_IDLE, 0), -1);
     }
     // claim tickets, one atomic per warp
     while (__any_sync(0xffffffffu, need)) {
@@ -787,6 +796,18 @@ __global__ void k_readback(const float* __restrict__ sum, const float* __restric
   }
 }
 
+// Condition of the single-launch render graph: repeat the iteration while any
+// slot is live or tickets remain; stop (and flag) at the iteration bound.
+__global__ void k_loop_cond(Counters* ctr, cudaGraphConditionalHandle h, long long max_iter) {
+  bool more = !(ctr->last_active == 0 && ctr->next_ticket >= ctr->total_tickets);
+  if (more && (long long)ctr->iters >= max_iter) {
+    ctr->err = 3;
+    more = false;
+  }
+  if (ctr->err) more = false;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 // Camera basis of every view from its descriptor (pinhole: forward, right =
 // forward x up, up' = right x forward, tan of half the vertical FOV).
 __global__ void k_views(const gr_view_desc* __restrict__ vd, DevView* views, int n) {
@@ -866,8 +887,11 @@ struct RenderPlan {
 };
 
 // Called by gr_render after argument validation.
+// acc_sum[v] / acc_comp[v]: view v's accumulator planes; f supplies the
+// scratch, counters and graph cache of the call.
 gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc* vd, int n_views,
-                      const gr_render_opts& o, gr_frame* f, cudaStream_t st, std::string& err) {
+                      const gr_render_opts& o, gr_frame* f, const std::vector<float*>& acc_sum,
+                      const std::vector<float*>& acc_comp, cudaStream_t st, std::string& err) {
   const int NSv = vd[0].n_stokes;
   RenderPlan plan;
   plan.scenes.resize(n_scenes);
@@ -895,8 +919,8 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     V.ticket_base = (long long)plan.total_tickets;
     V.n_tickets = (long long)d.n_bins * d.width * d.height;
     plan.total_tickets += (unsigned long long)V.n_tickets;
-    V.acc_sum = f->acc + f->offsets[v];
-    V.acc_comp = f->acc + f->acc_floats + f->offsets[v];
+    V.acc_sum = acc_sum[v];
+    V.acc_comp = acc_comp[v];
     // grating order table rows for every (material, bin) of this view
     const gr_scene* sc = scenes[d.scene_index];
     V.table_base = (int)plan.rows.size();
@@ -988,6 +1012,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   p.pool.tq = (int*)(base + o_tq);
   p.pool.sq = (int*)(base + o_sq);
   p.P = P;
+  p.regen_thr = o.regen_threshold_pct;
   p.ctr = f->ctr;
   const size_t smem_table = sizeof(TableRow) * plan.rows.size() + tsize * plan.vals_count;
   p.table_smem = smem_table <= 40 * 1024 ? 1 : 0;
@@ -1065,6 +1090,16 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
 
   const bool profile = o.profile && !o.use_graph;
   std::vector<cudaEvent_t> pev;
+  auto launch_on = [&](cudaStream_t ls) -> cudaError_t {
+    if (NSv == 1) {
+      if (o.table_dtype == GR_TABLE_F32) return launch_iteration<1, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
+      if (o.table_dtype == GR_TABLE_F16) return launch_iteration<1, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
+      return launch_iteration<1, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
+    }
+    if (o.table_dtype == GR_TABLE_F32) return launch_iteration<4, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
+    if (o.table_dtype == GR_TABLE_F16) return launch_iteration<4, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
+    return launch_iteration<4, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
+  };
   auto launch = [&]() -> cudaError_t {
     cudaEvent_t* ev = nullptr;
     if (profile) {
@@ -1102,25 +1137,66 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     worst = rounds * n_max * (d_max + 3) + 4 * B;
   }
   const long long max_iter = o.max_iterations > 0 ? o.max_iterations : 2 * worst;
-  cudaGraphExec_t gexec = nullptr;
   if (o.use_graph) {
-    cudaGraph_t g;
-    GR_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < B; ++i) {
-      cudaError_t le = launch();
-      if (le != cudaSuccess) {
-        cudaStreamEndCapture(st, &g);
-        err = std::string("graph capture launch: ") + cudaGetErrorString(le);
+    // ---- one graph launch: conditional while-node around one iteration
+    std::vector<unsigned char> key(sizeof(RenderParams) + 8 * sizeof(long long));
+    long long shape[8] = {g_regen, g_trace, g_shade, g_shadow, block, (long long)smem, NSv * 16 + o.table_dtype, max_iter};
+    std::memcpy(key.data(), &p, sizeof p);
+    std::memcpy(key.data() + sizeof p, shape, sizeof shape);
+    if (!f->graph_exec || f->graph_key != key) {
+      if (f->graph_exec) cudaGraphExecDestroy(f->graph_exec);
+      f->graph_exec = nullptr;
+      cudaGraph_t g = nullptr;
+      GR_CK(cudaGraphCreate(&g, 0));
+      cudaGraphConditionalHandle h;
+      e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+      cudaGraphNode_t cnode;
+      cudaGraphNodeParams np = {};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, g, nullptr, nullptr, 0, &np);
+      // the body is recorded on a private stream (capture is not allowed on
+      // the legacy default stream); the graph is then launched on `st`
+      if (e == cudaSuccess && !f->capture_stream) e = cudaStreamCreateWithFlags(&f->capture_stream, cudaStreamNonBlocking);
+      if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        cudaStream_t cs = f->capture_stream;
+        e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          cudaError_t le = launch_on(cs);
+          k_loop_cond<<<1, 1, 0, cs>>>(p.ctr, h, max_iter);
+          if (le == cudaSuccess) le = cudaGetLastError();
+          cudaGraph_t captured = nullptr;
+          e = cudaStreamEndCapture(cs, &captured);
+          if (e == cudaSuccess) e = le;
+        }
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&f->graph_exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        f->graph_exec = nullptr;
+        err = std::string("render graph: ") + cudaGetErrorString(e);
         return GR_E_CUDA;
       }
+      f->graph_key = key;
     }
-    GR_CK(cudaStreamEndCapture(st, &g));
-    e = cudaGraphInstantiate(&gexec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
-      return GR_E_CUDA;
+    GR_CK(cudaGraphLaunch(f->graph_exec, st));
+    Counters* hc = f->ctr_host;
+    GR_CK(cudaMemcpyAsync(hc, f->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    GR_CK(cudaStreamSynchronize(st));
+    f->iterations += (long long)hc->iters;
+    f->launches += 5LL * (long long)hc->iters + 1;
+    if (hc->err == 3) {
+      err = "render exceeded its iteration bound";
+      return GR_E_TIMEOUT;
     }
+    if (hc->err) {
+      err = hc->err == 1 ? "traversal stack overflow" : "corrupt BVH (traversal bound exceeded)";
+      return GR_E_INVALID;
+    }
+    return GR_OK;
   }
   cudaEvent_t ev[2];
   cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
@@ -1130,11 +1206,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   int batch = 0;
   gr_status status = GR_OK;
   for (;;) {
-    if (gexec) {
-      e = cudaGraphLaunch(gexec, st);
-    } else {
-      for (int i = 0; i < B && e == cudaSuccess; ++i) e = launch();
-    }
+    for (int i = 0; i < B && e == cudaSuccess; ++i) e = launch();
     if (e != cudaSuccess) {
       err = std::string("launch: ") + cudaGetErrorString(e);
       status = GR_E_CUDA;
@@ -1192,7 +1264,6 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     }
     for (auto e3 : pev) cudaEventDestroy(e3);
   }
-  if (gexec) cudaGraphExecDestroy(gexec);
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   return status;
@@ -1366,6 +1437,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   p.pool.tq = (int*)(base + o_tq);
   p.pool.sq = (int*)(base + o_sq);
   p.P = (int)P;
+  p.regen_thr = o.regen_threshold_pct;
   p.ctr = (Counters*)(base + o_ctr);
   const size_t smem_table = sizeof(TableRow) * rows.size() + tsize * vals;
   p.table_smem = smem_table <= 40 * 1024 ? 1 : 0;
