@@ -37,6 +37,9 @@ FP32_PEAK_TFLOPS = 2 * 152 * 128 * 2.070e9 / 1e12  # FMA = 2 FLOP, 152 SMs x 128
 # division) = 41.
 FLOP_PER_NODE = 52
 FLOP_PER_TRI = 41
+# a 4-wide quantised node: per child 6 slab FMAs + 11 min/max + 4 for widening
+# and compare (25), plus 9 for the node's affine decode (3 mul, 3 sub, 3 mul)
+FLOP_PER_WNODE = 109
 KERNELS = ["k_regen", "k_trace", "k_shade", "k_shadow"]
 # DRAM traffic per launch of the dominant kernel from one ncu capture, valid only
 # for the kernel sources whose hash is recorded with it (else reported null).
@@ -61,6 +64,7 @@ def parse():
     ap.add_argument("--size", type=int, default=512)
     ap.add_argument("--table", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--pool", type=int, default=0)
+    ap.add_argument("--wide", action="store_true", help="traverse the 4-wide quantised BVH")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-crop", type=int, default=128, help="side of the oracle's centre crop")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -298,7 +302,7 @@ def main():
     gr.load()
     scene, view = workload(args, rank)
     samples = view["width"] * view["height"] * view["spp"]
-    flags = gr.FLAG_NEE
+    flags = gr.FLAG_NEE | (gr.FLAG_WIDE_BVH if args.wide else 0)
     S = gr.Scene(scene)
     F = gr.Frame([view])
     stream = torch.cuda.current_stream()
@@ -354,7 +358,8 @@ def main():
     if dom in (1, 3):
         # traversal kernels: ALU-bound; counts of node visits / triangle tests
         # are summed over trace and shadow, so attribute by time share
-        flops = (visits * FLOP_PER_NODE + tests * FLOP_PER_TRI) / args.steps
+        per_node = FLOP_PER_WNODE if args.wide else FLOP_PER_NODE
+        flops = (visits * per_node + tests * FLOP_PER_TRI) / args.steps
         trav_ms = (kms[1] + kms[3]) / args.steps
         achieved = flops / (trav_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": KERNELS[dom] + "+k_shadow" if dom == 1 else KERNELS[dom],

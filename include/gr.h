@@ -133,10 +133,13 @@ typedef struct {
 /* Render options (36 bytes).  flags: GR_FLAG_NEE next-event estimation toward emitters
  * with power-heuristic MIS; GR_FLAG_RR Russian roulette after 3 interactions;
  * GR_FLAG_NO_RENORM keeps raw grating order weights (no renormalisation over
- * propagating orders).  table_dtype: storage of the grating order tables
+ * propagating orders); GR_FLAG_WIDE_BVH traverses the 4-wide BVH with 8-bit
+ * quantised child boxes instead of the default binary FP32 BVH (both give the
+ * same closest hits; the wide tree halves node visits but needs more
+ * registers per thread).  table_dtype: storage of the grating order tables
  * (GR_TABLE_F32 / F16 / BF16); arithmetic is FP32 either way.  pool_size:
  * wavefront slots (0 = default); block: threads per block (0 = default). */
-enum { GR_FLAG_NEE = 1, GR_FLAG_RR = 2, GR_FLAG_NO_RENORM = 4 };
+enum { GR_FLAG_NEE = 1, GR_FLAG_RR = 2, GR_FLAG_NO_RENORM = 4, GR_FLAG_WIDE_BVH = 8 };
 enum { GR_TABLE_F32 = 0, GR_TABLE_F16 = 1, GR_TABLE_BF16 = 2 };
 typedef struct {
   uint32_t seed;
@@ -176,8 +179,11 @@ typedef struct {
   int64_t kernel_count[4];
 } gr_stats;
 
-/* Upload a scene and build its BVH (Karras LBVH, 30-bit Morton codes; integer
- * topology and FP32 bounds are deterministic).  desc arrays are host memory
+/* Upload a scene and build its BVH on the device: 30-bit Morton order, then
+ * agglomerative clustering along that order (PLOC, window +-8, least merged
+ * surface area); topology and FP32 bounds are deterministic.  The binary tree
+ * is also collapsed into a 4-wide BVH with 8-bit quantised, conservatively
+ * rounded child boxes.  desc arrays are host memory
  * and are copied; the library owns the device copy until gr_scene_destroy.
  * Errors: GR_E_INVALID (null/negative sizes, material index out of range,
  * unknown material or light type), GR_E_OOM, GR_E_CUDA. */
@@ -222,9 +228,10 @@ gr_status gr_readback(gr_frame* frame, int32_t view, float* dst, size_t dst_byte
 /* Statistics of the last gr_render on this frame (synchronises the stream). */
 gr_status gr_frame_stats(gr_frame* frame, void* cuda_stream, gr_stats* out);
 
-/* Inspection of a scene's BVH for bit-exact tests (host buffers, may be NULL
- * to query sizes): sorted 64-bit keys (morton << 32 | triangle id) [n],
- * internal nodes as int32 [n-1][2] child references (bit 31 set = leaf slot),
+/* Inspection of a scene's binary BVH for bit-exact tests (host buffers, may
+ * be NULL to query sizes): sorted 64-bit keys (morton << 32 | triangle id) [n],
+ * internal nodes (root = 0) as int32 [n-1][2] child references (bit 31 set =
+ * leaf slot),
  * and float32 [n-1][12] child boxes (left lo xyz, left hi xyz, right lo, right
  * hi).  Returns the triangle count in *n_out. */
 gr_status gr_scene_bvh(gr_scene* scene, int32_t* n_out, uint64_t* keys, int32_t* children, float* boxes);

@@ -1,14 +1,19 @@
-// CPU reference build of a linear BVH (Karras, "Maximizing Parallelism in the
-// Construction of BVHs, Octrees, and k-d Trees", HPG 2012) -- TEST
-// INFRASTRUCTURE ONLY, used to check the GPU build bit for bit.  Written
-// independently of the CUDA code; the two agree because both follow the same
-// published algorithm on the same float32 inputs:
+// CPU reference build of the BVH -- TEST INFRASTRUCTURE ONLY, used to check
+// the GPU build bit for bit.  Written independently of the CUDA code; the two
+// agree because both follow the same published algorithms on the same float32
+// inputs:
 //   centroid  c = ((v0 + v1) + v2) / 3            (float32, no contraction)
 //   quantise  q = trunc(((c - lo) / (hi - lo)) * 1024), clamped to [0, 1023]
 //   Morton    interleave(qx, qy, qz) (x highest), key = morton << 32 | id
-//   sort keys ascending; internal node i of n-1: range, split (Karras),
-//   child reference = index, or index | 0x80000000 for a leaf;
-//   child boxes = exact float min/max of the subtree's triangle vertices.
+//   sort keys ascending (leaf slot i = i-th key)
+//   PLOC (Meister & Bittner, IEEE TVCG 2018) over the sorted leaves: every
+//   cluster's nearest neighbour within +-8 positions by least half surface
+//   area ((dx*dy + dy*dz) + dz*dx in float32) of the merged box, ties to the
+//   lower position; mutual pairs merge into a new node numbered
+//   (n-2) - (order of creation, positions ascending within a round), the
+//   clusters are compacted in order, until one remains (the root, node 0);
+//   child reference = node index, or slot | 0x80000000 for a leaf;
+//   child boxes = exact float min/max.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -21,19 +26,6 @@ uint32_t spread10(uint32_t v) {
   uint32_t r = 0;
   for (int k = 0; k < 10; ++k) r |= ((v >> k) & 1u) << (3 * k);
   return r;
-}
-
-int common_prefix(const std::vector<uint64_t>& keys, int i, int j) {
-  int n = (int)keys.size();
-  if (j < 0 || j >= n) return -1;
-  uint64_t x = keys[i] ^ keys[j];
-  if (x == 0) return 64;
-  int c = 0;
-  while (!(x & (1ull << 63))) {
-    x <<= 1;
-    ++c;
-  }
-  return c;
 }
 
 struct Box {
@@ -84,34 +76,6 @@ extern "C" int oracle_lbvh_build(int n, const float* verts, uint64_t* keys_out, 
   for (int i = 0; i < n; ++i) keys_out[i] = keys[i];
   if (n == 1) return 1;
   std::vector<int> lref(n - 1), rref(n - 1);
-  for (int i = 0; i < n - 1; ++i) {
-    int d = common_prefix(keys, i, i + 1) > common_prefix(keys, i, i - 1) ? 1 : -1;
-    int dmin = common_prefix(keys, i, i - d);
-    int lmax = 2;
-    while (common_prefix(keys, i, i + lmax * d) > dmin) lmax *= 2;
-    int l = 0;
-    for (int t = lmax / 2; t >= 1; t /= 2)
-      if (common_prefix(keys, i, i + (l + t) * d) > dmin) l += t;
-    int j = i + l * d;
-    int dnode = common_prefix(keys, i, j);
-    // binary search for the split: largest s with common prefix > dnode
-    int s = 0;
-    int t = l;
-    while (t > 1) {
-      t = (t + 1) / 2;
-      if (common_prefix(keys, i, i + (s + t) * d) > dnode) s += t;
-    }
-    if (l == 1) {
-      // single step: the search above never ran; the split is at i
-      s = 0;
-    }
-    int gamma = i + s * d + std::min(d, 0);
-    int first = std::min(i, j), last = std::max(i, j);
-    lref[i] = (first == gamma) ? (int)(0x80000000u | (uint32_t)gamma) : gamma;
-    rref[i] = (last == gamma + 1) ? (int)(0x80000000u | (uint32_t)(gamma + 1)) : gamma + 1;
-  }
-  // child boxes, bottom-up by recursion from the root (node 0)
-  std::vector<Box> node_box(n - 1);
   std::vector<Box> child_box(2 * (size_t)(n - 1));
   auto leaf_box = [&](int slot) {
     int id = (int)(keys[slot] & 0xffffffffu);
@@ -123,29 +87,66 @@ extern "C" int oracle_lbvh_build(int n, const float* verts, uint64_t* keys_out, 
     }
     return b;
   };
-  // iterative post-order
-  std::vector<std::pair<int, int>> stack;
-  stack.push_back({0, 0});
-  while (!stack.empty()) {
-    auto& top = stack.back();
-    int node = top.first;
-    if (top.second == 0) {
-      top.second = 1;
-      if (lref[node] >= 0) stack.push_back({lref[node], 0});
-      if (rref[node] >= 0) stack.push_back({rref[node], 0});
-      continue;
+  auto merged = [](const Box& a, const Box& b) {
+    Box r;
+    for (int k = 0; k < 3; ++k) {
+      r.lo[k] = std::min(a.lo[k], b.lo[k]);
+      r.hi[k] = std::max(a.hi[k], b.hi[k]);
     }
-    stack.pop_back();
-    Box L = lref[node] < 0 ? leaf_box(lref[node] & 0x7fffffff) : node_box[lref[node]];
-    Box R = rref[node] < 0 ? leaf_box(rref[node] & 0x7fffffff) : node_box[rref[node]];
-    child_box[2 * node] = L;
-    child_box[2 * node + 1] = R;
-    Box U;
-    for (int a = 0; a < 3; ++a) {
-      U.lo[a] = std::min(L.lo[a], R.lo[a]);
-      U.hi[a] = std::max(L.hi[a], R.hi[a]);
+    return r;
+  };
+  auto half_area = [](const Box& b) {
+    volatile float dx = b.hi[0] - b.lo[0], dy = b.hi[1] - b.lo[1], dz = b.hi[2] - b.lo[2];
+    volatile float p = dx * dy, q = dy * dz, r = dz * dx;
+    volatile float s1 = p + q;
+    volatile float s2 = s1 + r;
+    return (float)s2;
+  };
+  std::vector<Box> box(n);
+  std::vector<int> ref(n);
+  for (int i = 0; i < n; ++i) {
+    box[i] = leaf_box(i);
+    ref[i] = (int)(0x80000000u | (uint32_t)i);
+  }
+  const int R = 8;
+  int created = 0;
+  while (box.size() > 1) {
+    const int m = (int)box.size();
+    std::vector<int> nn(m);
+    for (int i = 0; i < m; ++i) {
+      int best = -1;
+      float ba = 3.4e38f;
+      for (int j = std::max(0, i - R); j <= std::min(m - 1, i + R); ++j) {
+        if (j == i) continue;
+        float a = half_area(merged(box[i], box[j]));
+        if (a < ba || (a == ba && j < best)) {
+          ba = a;
+          best = j;
+        }
+      }
+      nn[i] = best;
     }
-    node_box[node] = U;
+    std::vector<Box> nb;
+    std::vector<int> nr;
+    for (int i = 0; i < m; ++i) {
+      const int j = nn[i];
+      const bool mutual = j >= 0 && nn[j] == i;
+      if (mutual && j < i) continue;  // absorbed by its lower partner
+      if (mutual) {
+        const int x = (n - 2) - created++;
+        lref[x] = ref[i];
+        rref[x] = ref[j];
+        child_box[2 * x] = box[i];
+        child_box[2 * x + 1] = box[j];
+        nb.push_back(merged(box[i], box[j]));
+        nr.push_back(x);
+      } else {
+        nb.push_back(box[i]);
+        nr.push_back(ref[i]);
+      }
+    }
+    box.swap(nb);
+    ref.swap(nr);
   }
   for (int i = 0; i < n - 1; ++i) {
     children_out[2 * i] = lref[i];

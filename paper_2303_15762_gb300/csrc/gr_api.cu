@@ -122,6 +122,8 @@ gr_status gr_scene_create(const gr_scene_desc* desc, void* cuda_stream, gr_scene
   const size_t o_eom = take(sizeof(int) * emitter_of_mat.size());
   const size_t o_etri = take(sizeof(float4) * etris.size());
   const size_t o_keys = take(sizeof(unsigned long long) * (size_t)n);
+  const size_t o_wide = take(sizeof(uint4) * 4 * (size_t)std::max(n - 1, 1));
+  int n_wide = 0;
   cudaError_t e = cudaMallocAsync(&S->mem, off, st);
   if (e != cudaSuccess) {
     delete S;
@@ -147,6 +149,8 @@ gr_status gr_scene_create(const gr_scene_desc* desc, void* cuda_stream, gr_scene
       e = gr::build_lbvh(verts_d, tmat_in, n, (float4*)(b + o_tri), (int*)(b + o_tmat), (float*)(b + o_nodes),
                          (unsigned long long*)(b + o_keys), st);
       if (e != cudaSuccess) break;
+      e = gr::build_wide((const float*)(b + o_nodes), (const float4*)(b + o_tri), n, (uint4*)(b + o_wide), &n_wide, st);
+      if (e != cudaSuccess) break;
     }
     // host arrays are pageable: make sure every copy has consumed them
     e = cudaStreamSynchronize(st);
@@ -167,6 +171,9 @@ gr_status gr_scene_create(const gr_scene_desc* desc, void* cuda_stream, gr_scene
   D.tri = (const float4*)(b + o_tri);
   D.tri_mat = (const int*)(b + o_tmat);
   D.nodes = (const float4*)(b + o_nodes);
+  D.wnodes = (const uint4*)(b + o_wide);
+  D.n_wide = n_wide;
+  D.pad_w = 0;
   D.mats = (const gr_material*)(b + o_mats);
   D.lights = (const gr_light*)(b + o_lights);
   D.emitters = (const gr::DevEmitter*)(b + o_emit);

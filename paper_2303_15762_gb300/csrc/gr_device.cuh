@@ -42,6 +42,9 @@ struct DevScene {
   const float4* tri;         // [n][3] vertices in BVH leaf order; tri[3i].w = original id (int bits)
   const int* tri_mat;        // [n] material of leaf slot i
   const float4* nodes;       // [n-1][4] internal nodes (child boxes + child refs)
+  const uint4* wnodes;       // [n_wide][4] 4-wide quantised nodes (root = 0)
+  int n_wide;
+  int pad_w;
   const gr_material* mats;   // [n_mats]
   const gr_light* lights;    // [n_lights]
   const DevEmitter* emitters;     // [n_emitters]
@@ -354,6 +357,129 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& S, float3 o, float3 d
     }
     if (next < 0) {
       // pop until an internal node whose box still overlaps [0, best]
+      if (sp == 0) break;
+      next = stack[--sp];
+    }
+    node = next;
+  }
+  return h;
+}
+
+// Closest hit through the 4-wide quantised BVH: same contract as closest_hit
+// (t > kTMin, skip `exclude`, ties to the lower original id).  A node decodes
+// its child slabs as t = q * (2^e / d) + (P - o) / d, one FMA per bound; the
+// far distance is widened by 8 ulps and the near one narrowed, so rounding
+// can only add visits.
+__device__ __forceinline__ Hit closest_hit_wide(const DevScene& S, float3 o, float3 d, int exclude, int* refined,
+                                                int* visits, int* tests, int* err) {
+  Hit h;
+  h.t = __int_as_float(0x7f800000);
+  h.slot = -1;
+  int best_id = 0x7fffffff;
+  if (S.n_tris == 0) return h;
+  RayPre r = ray_pre(o, d);
+  auto test_leaf = [&](int slot) {
+    if (slot == exclude) return;
+    const float4 a = __ldg(&S.tri[3 * slot]);
+    const float4 b = __ldg(&S.tri[3 * slot + 1]);
+    const float4 c = __ldg(&S.tri[3 * slot + 2]);
+    ++*tests;
+    float t = isect_tri(r, xyz(a), xyz(b), xyz(c), refined);
+    int id = __float_as_int(a.w);
+    if (t > kTMin && (t < h.t || (t == h.t && id < best_id))) {
+      h.t = t;
+      h.slot = slot;
+      best_id = id;
+    }
+  };
+  if (S.n_tris == 1 || S.n_wide == 0) {
+    test_leaf(0);
+    return h;
+  }
+  int stack[kStackDepth];
+  int sp = 0;
+  int node = 0;
+  int guard = S.n_tris + 8;
+  for (;;) {
+    if (--guard < 0) {
+      if (err) *err = 2;
+      break;
+    }
+    ++*visits;
+    const uint4* N = S.wnodes + 4 * node;
+    const uint4 a = __ldg(N), b = __ldg(N + 1), c = __ldg(N + 2), e4 = __ldg(N + 3);
+    const int cnt = (int)(a.w >> 24);
+    const float sx = __int_as_float((int)(((a.w & 0xffu) - 128u + 127u) << 23));
+    const float sy = __int_as_float((int)((((a.w >> 8) & 0xffu) - 128u + 127u) << 23));
+    const float sz = __int_as_float((int)((((a.w >> 16) & 0xffu) - 128u + 127u) << 23));
+    const float Ax = sx * r.inv.x, Ay = sy * r.inv.y, Az = sz * r.inv.z;
+    const float Bx = (__uint_as_float(a.x) - r.o.x) * r.inv.x;
+    const float By = (__uint_as_float(a.y) - r.o.y) * r.inv.y;
+    const float Bz = (__uint_as_float(a.z) - r.o.z) * r.inv.z;
+    const int refs[4] = {(int)c.z, (int)c.w, (int)e4.x, (int)e4.y};
+    const float kInf = __int_as_float(0x7f800000);
+    // entry distance of each internal child hit (+inf otherwise), kept in
+    // fixed registers; leaves are tested on the spot
+    float tq[4] = {kInf, kInf, kInf, kInf};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (k < cnt) {
+        const unsigned sh = 8u * k;
+        const float lx = (float)((b.x >> sh) & 0xffu), ly = (float)((b.y >> sh) & 0xffu), lz = (float)((b.z >> sh) & 0xffu);
+        const float hx = (float)((b.w >> sh) & 0xffu), hy = (float)((c.x >> sh) & 0xffu), hz = (float)((c.y >> sh) & 0xffu);
+        const float tx0 = fmaf(lx, Ax, Bx), tx1 = fmaf(hx, Ax, Bx);
+        const float ty0 = fmaf(ly, Ay, By), ty1 = fmaf(hy, Ay, By);
+        const float tz0 = fmaf(lz, Az, Bz), tz1 = fmaf(hz, Az, Bz);
+        float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+        float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+        tn *= 0.999999f;
+        tf = fminf(tf * 1.000001f, h.t);
+        if (tn <= tf) {
+          if (refs[k] < 0)
+            test_leaf(refs[k] & 0x7fffffff);
+          else
+            tq[k] = tn;
+        }
+      }
+    }
+    // order the four (distance, child) pairs with a sorting network
+    float t0 = tq[0], t1 = tq[1], t2 = tq[2], t3 = tq[3];
+    int r0 = refs[0], r1 = refs[1], r2 = refs[2], r3 = refs[3];
+    auto cswap = [](float& ta, int& ra, float& tb, int& rb) {
+      if (tb < ta) {
+        float t = ta;
+        ta = tb;
+        tb = t;
+        int q = ra;
+        ra = rb;
+        rb = q;
+      }
+    };
+    cswap(t0, r0, t1, r1);
+    cswap(t2, r2, t3, r3);
+    cswap(t0, r0, t2, r2);
+    cswap(t1, r1, t3, r3);
+    cswap(t1, r1, t2, r2);
+    // nearest next; the others pushed farthest first (skipping those now
+    // beyond the best hit)
+    // (+inf marks "not an internal hit"; it must not pass as <= h.t = +inf)
+    int next = -1;
+    if (t0 < kInf && t0 <= h.t) {
+      next = r0;
+      if (t3 < kInf && t3 <= h.t) {
+        if (sp < kStackDepth) stack[sp++] = r3;
+        else if (err) *err = 1;
+      }
+      if (t2 < kInf && t2 <= h.t) {
+        if (sp < kStackDepth) stack[sp++] = r2;
+        else if (err) *err = 1;
+      }
+      if (t1 < kInf && t1 <= h.t) {
+        if (sp < kStackDepth) stack[sp++] = r1;
+        else if (err) *err = 1;
+      }
+    }
+    if (next < 0) {
       if (sp == 0) break;
       next = stack[--sp];
     }

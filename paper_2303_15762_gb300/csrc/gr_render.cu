@@ -31,6 +31,12 @@ namespace gr {
 
 enum { ST_IDLE = 0, ST_ACTIVE = 1, ST_DONE = 2 };
 
+// Minimum resident 256-thread blocks per SM requested for the traversal
+// kernels (register budget 65536 / (256 x blocks)).
+#ifndef GR_TRACE_MIN_BLOCKS
+#define GR_TRACE_MIN_BLOCKS 3
+#endif
+
 __device__ __forceinline__ int meta_k(int z) { return z & 0xffff; }
 __device__ __forceinline__ int meta_seg(int z) { return (z >> 16) & 0xff; }
 __device__ __forceinline__ int meta_state(int z) { return (z >> 24) & 3; }
@@ -246,7 +252,8 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
 }
 
 // ------------------------------------------------------------------ trace
-__global__ void __launch_bounds__(256) k_trace(RenderParams p) {
+template <bool WIDE>
+__global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_trace(RenderParams p) {
   const Pool& P = p.pool;
   const int n = *(volatile int*)&p.ctr->tq_count;
   if (blockIdx.x == 0 && threadIdx.x == 0) p.ctr->segments += (unsigned long long)n;
@@ -257,7 +264,8 @@ __global__ void __launch_bounds__(256) k_trace(RenderParams p) {
     const DevView& V = p.views[m.x];
     const DevScene& S = p.scenes[V.scene_index];
     const float4 a = P.od0[slot], b = P.od1[slot];
-    Hit h = closest_hit(S, xyz(a), xyz(b), m.w, &refined, &visits, &tests, &err);
+    Hit h = WIDE ? closest_hit_wide(S, xyz(a), xyz(b), m.w, &refined, &visits, &tests, &err)
+                 : closest_hit(S, xyz(a), xyz(b), m.w, &refined, &visits, &tests, &err);
     P.hit[slot] = make_float2(h.t, __int_as_float(h.slot));
   }
   warp_count(&p.ctr->ref_hit, refined);
@@ -692,8 +700,8 @@ __global__ void __launch_bounds__(256) k_shade(RenderParams p) {
 }
 
 // ------------------------------------------------------------------ shadow
-template <int NS>
-__global__ void __launch_bounds__(256) k_shadow(RenderParams p) {
+template <int NS, bool WIDE>
+__global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_shadow(RenderParams p) {
   const Pool& P = p.pool;
   const int n = *(volatile int*)&p.ctr->sq_count;
   int err = 0, refined = 0, visits = 0, tests = 0;
@@ -706,7 +714,8 @@ __global__ void __launch_bounds__(256) k_shadow(RenderParams p) {
     const int tag = __float_as_int(sd.w);
     const int ei = tag & 0xffff, seg = tag >> 16;
     const float3 x = xyz(a0), w = xyz(sd);
-    Hit h = closest_hit(S, x, w, m.w, &refined, &visits, &tests, &err);
+    Hit h = WIDE ? closest_hit_wide(S, x, w, m.w, &refined, &visits, &tests, &err)
+                 : closest_hit(S, x, w, m.w, &refined, &visits, &tests, &err);
     if (h.slot < 0 || S.tri_mat[h.slot] != S.emitters[ei].mat) continue;
     const int WH = V.W * V.H;
     const int bin = m.y / WH;
@@ -861,14 +870,21 @@ int sm_count(int dev) {
 template <int NS, typename TT>
 cudaError_t launch_iteration(const RenderParams& p, int grid_regen, int grid_trace, int grid_shade, int grid_shadow,
                              int block, size_t smem, cudaStream_t st, cudaEvent_t* ev) {
+  const bool wide = (p.flags & GR_FLAG_WIDE_BVH) != 0;
   if (ev) cudaEventRecord(ev[0], st);
   k_regen<NS><<<grid_regen, block, 0, st>>>(p);
   if (ev) cudaEventRecord(ev[1], st);
-  k_trace<<<grid_trace, block, 0, st>>>(p);
+  if (wide)
+    k_trace<true><<<grid_trace, block, 0, st>>>(p);
+  else
+    k_trace<false><<<grid_trace, block, 0, st>>>(p);
   if (ev) cudaEventRecord(ev[2], st);
   k_shade<NS, TT><<<grid_shade, block, smem, st>>>(p);
   if (ev) cudaEventRecord(ev[3], st);
-  k_shadow<NS><<<grid_shadow, block, 0, st>>>(p);
+  if (wide)
+    k_shadow<NS, true><<<grid_shadow, block, 0, st>>>(p);
+  else
+    k_shadow<NS, false><<<grid_shadow, block, 0, st>>>(p);
   if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError();
 }
@@ -1068,18 +1084,18 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const void* shade_fn;
   if (NSv == 1) {
     g_regen = grid_for((const void*)k_regen<1>, 0);
-    g_shadow = grid_for((const void*)k_shadow<1>, 0);
+    g_shadow = grid_for((const void*)k_shadow<1, false>, 0);
     shade_fn = o.table_dtype == GR_TABLE_F32 ? (const void*)k_shade<1, float>
                : o.table_dtype == GR_TABLE_F16 ? (const void*)k_shade<1, __half>
                                                : (const void*)k_shade<1, __nv_bfloat16>;
   } else {
     g_regen = grid_for((const void*)k_regen<4>, 0);
-    g_shadow = grid_for((const void*)k_shadow<4>, 0);
+    g_shadow = grid_for((const void*)k_shadow<4, false>, 0);
     shade_fn = o.table_dtype == GR_TABLE_F32 ? (const void*)k_shade<4, float>
                : o.table_dtype == GR_TABLE_F16 ? (const void*)k_shade<4, __half>
                                                : (const void*)k_shade<4, __nv_bfloat16>;
   }
-  g_trace = grid_for((const void*)k_trace, 0);
+  g_trace = grid_for((const void*)k_trace<false>, 0);
   g_shade = grid_for(shade_fn, smem);
   // never more blocks than the pool needs
   const int gmax = (P + block - 1) / block;
@@ -1490,9 +1506,9 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
                                                                      : (const void*)k_shade<4, __nv_bfloat16>);
   const int gmax = (int)((P + block - 1) / block);
   const int g_regen = std::min(gmax, grid_for(NSv == 1 ? (const void*)k_regen<1> : (const void*)k_regen<4>, 0));
-  const int g_trace = std::min(gmax, grid_for((const void*)k_trace, 0));
+  const int g_trace = std::min(gmax, grid_for((const void*)k_trace<false>, 0));
   const int g_shade = std::min(gmax, grid_for(shade_fn, smem));
-  const int g_shadow = std::min(gmax, grid_for(NSv == 1 ? (const void*)k_shadow<1> : (const void*)k_shadow<4>, 0));
+  const int g_shadow = std::min(gmax, grid_for(NSv == 1 ? (const void*)k_shadow<1, false> : (const void*)k_shadow<4, false>, 0));
   // --- iteration loop; the host reads the device counters into a stack copy
   // after every batch (no events, no pinned buffer)
   long long n_max = 1, d_max = 0;

@@ -1,6 +1,6 @@
 """Integer outputs of the CUDA path are bit-exact with independent CPU
-implementations: the Philox4x32-10 stream and the LBVH (keys, topology and the
-exact float min/max child boxes)."""
+implementations: the Philox4x32-10 stream and the BVH (Morton keys, PLOC
+topology and the exact float min/max child boxes)."""
 import numpy as np
 import pytest
 
@@ -19,7 +19,7 @@ def test_rng_stream_bit_exact(gr, oracle):
 
 
 @pytest.mark.parametrize("case", ["one", "two", "three", "grating", "small", "medium", "large"])
-def test_lbvh_bit_exact(gr, oracle, case):
+def test_bvh_bit_exact(gr, oracle, case):
     if case in ("one", "two", "three"):
         n = {"one": 1, "two": 2, "three": 3}[case]
         rng = np.random.default_rng(n)
