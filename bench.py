@@ -41,9 +41,12 @@ FLOP_PER_TRI = 41
 # and compare (25), plus 9 for the node's affine decode (3 mul, 3 sub, 3 mul)
 FLOP_PER_WNODE = 109
 KERNELS = ["k_regen", "k_trace", "k_shade", "k_shadow"]
-# DRAM traffic per launch of the dominant kernel from one ncu capture, valid only
-# for the kernel sources whose hash is recorded with it (else reported null).
-NCU_TRAFFIC = {}
+# DRAM traffic of the dominant kernel per unit (ray) from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of a full-queue launch of the
+# 256x256 x 64 spp case divided by the rays it traced; traffic grows with the
+# rays a launch processes), valid only for the kernel sources whose hash is
+# recorded with it (else reported null).
+NCU_TRAFFIC_PER_RAY = {("k_trace", "c1ec988e479046b2"): 68.8e6 / 1.0e6}
 
 
 def source_hash():
@@ -365,15 +368,19 @@ def main():
         roof = {"bound": "alu", "kernel": KERNELS[dom] + "+k_shadow" if dom == 1 else KERNELS[dom],
                 "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
-                "traffic": NCU_TRAFFIC.get((KERNELS[dom], source_hash())),
-                "per_launch_ms": per_launch_ms}
+                "traffic": None, "per_launch_ms": per_launch_ms}
+        tpr = NCU_TRAFFIC_PER_RAY.get((KERNELS[dom], source_hash()))
+        if tpr is not None:
+            rays_per_launch = stats["segments"] / max(1, stats["iterations"])
+            roof["traffic"] = tpr * rays_per_launch
+            roof["traffic_note"] = "ncu DRAM bytes per ray of a full-queue k_trace launch x rays per launch"
     else:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
         # slot state read and written by regen / shade per processed slot
         bytes_per_launch = None
         roof = {"bound": "hbm", "kernel": KERNELS[dom], "achieved": None, "peak": peaks.get("hbm_gbs", 6800.0),
-                "unit": "GB/s", "frac": None, "traffic": NCU_TRAFFIC.get((KERNELS[dom], source_hash())),
+                "unit": "GB/s", "frac": None, "traffic": None,
                 "per_launch_ms": per_launch_ms, "note": "bytes per launch not yet derived", "bytes": bytes_per_launch}
     roof["kernel_ms_share"] = {KERNELS[k]: kms[k] / max(sum(kms), 1e-9) for k in range(4)}
 
