@@ -89,6 +89,23 @@ def dist_setup():
     return world, rank, local
 
 
+def reduce_max(value, world):
+    """Max over ranks (the slowest replica sets the whole job's time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(samples_per_rank, t_max_ms, world):
+    """Whole-job Msamples/s: every rank renders its own replica (weak scaling)."""
+    return world * samples_per_rank / (t_max_ms * 1e-3) / 1e6
+
+
 def workload(args, rank):
     from paper_2303_15762_gb300 import scenegen as sg
     scene = sg.procedural_scene(seed=2)
@@ -347,12 +364,8 @@ def main():
     stats = F.stats()
     launches = stats["kernel_launches"] - launches0
     mean_ms = statistics.mean(step_ms)
-    t_max = mean_ms
-    if world > 1:
-        t = torch.tensor([mean_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * samples / (t_max * 1e-3) / 1e6
+    t_max = reduce_max(mean_ms, world)
+    value = job_throughput(samples, t_max, world)
     img = F.readback(0)
 
     # ---- roofline of the dominant kernel (device time share from live events)
