@@ -142,6 +142,48 @@ __device__ __forceinline__ void warp_count(unsigned long long* ctr, int v) {
   if ((threadIdx.x & 31) == 0 && v) atomicAdd(ctr, (unsigned long long)v);
 }
 
+// Block-wide queue reservation with one atomic per block: returns this
+// thread's slot in the queue for `want` entries (exclusive scan over the
+// block's warps).  Every thread of the block must call it (uniform control
+// flow); the trailing barrier lets the shared words be reused by the next call.
+template <typename CT>
+__device__ __forceinline__ CT block_reserve(CT* counter, bool want) {
+  __shared__ int s_warp[8];
+  __shared__ CT s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const unsigned m = __ballot_sync(0xffffffffu, want);
+  if (lane == 0) s_warp[warp] = __popc(m);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int c = s_warp[w];
+      s_warp[w] = tot;
+      tot += c;
+    }
+    s_base = tot ? atomicAdd(counter, (CT)tot) : (CT)0;
+  }
+  __syncthreads();
+  const CT off = s_base + (CT)(s_warp[warp] + __popc(m & ((1u << lane) - 1u)));
+  __syncthreads();
+  return off;
+}
+
+// Block-wide sum of a per-thread count added with one atomic per block.
+__device__ __forceinline__ void block_count(unsigned long long* ctr, int v) {
+  __shared__ int s_sum[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if (lane == 0) s_sum[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long tot = 0;
+    for (int w = 0; w < nw; ++w) tot += s_sum[w];
+    if (tot) atomicAdd(ctr, (unsigned long long)tot);
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
   float y = v - c;
   float t = s + y;
@@ -153,7 +195,6 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
 template <int NS>
 __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
   const Pool& P = p.pool;
-  const int lane = threadIdx.x & 31;
   const int stride = gridDim.x * blockDim.x;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     p.ctr->sq_count = 0;
@@ -210,15 +251,11 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
       need = false;
       P.meta[slot] = make_int4(0, 0, meta_pack(0, 0, ST_IDLE, 0), -1);
     }
-    // claim tickets, one atomic per warp
-    while (__any_sync(0xffffffffu, need)) {
-      unsigned mask = __ballot_sync(0xffffffffu, need);
-      unsigned long long first = 0;
-      int leader = __ffs(mask) - 1;
-      if (lane == leader) first = atomicAdd(&p.ctr->next_ticket, (unsigned long long)__popc(mask));
-      first = __shfl_sync(0xffffffffu, first, leader);
+    // claim tickets, one atomic per block (tickets without samples in this
+    // render are skipped by claiming again)
+    while (__syncthreads_or(need)) {
+      const unsigned long long t = block_reserve<unsigned long long>(&p.ctr->next_ticket, need);
       if (need) {
-        unsigned long long t = first + __popc(mask & ((1u << lane) - 1u));
         if (t >= p.ctr->total_tickets) {
           need = false;
           P.meta[slot] = make_int4(0, 0, meta_pack(0, 0, ST_IDLE, 0), -1);
@@ -237,18 +274,11 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
         }
       }
     }
-    unsigned amask = __ballot_sync(0xffffffffu, active);
-    if (amask) {
-      int leader = __ffs(amask) - 1;
-      int first = 0;
-      if (lane == leader) first = atomicAdd(&p.ctr->tq_count, __popc(amask));
-      first = __shfl_sync(0xffffffffu, first, leader);
-      if (active) P.tq[first + __popc(amask & ((1u << lane) - 1u))] = slot;
-    }
+    // compact live slots into the trace queue, one atomic per block
+    const int q = block_reserve<int>(&p.ctr->tq_count, active);
+    if (active) P.tq[q] = slot;
   }
-  // per-warp sum of completed samples
-  for (int off = 16; off > 0; off >>= 1) finished += __shfl_down_sync(0xffffffffu, finished, off);
-  if (lane == 0 && finished) atomicAdd(&p.ctr->samples, (unsigned long long)finished);
+  block_count(&p.ctr->samples, finished);
 }
 
 // ------------------------------------------------------------------ trace
@@ -268,9 +298,9 @@ __global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_trace(RenderParams
                  : closest_hit(S, xyz(a), xyz(b), m.w, &refined, &visits, &tests, &err);
     P.hit[slot] = make_float2(h.t, __int_as_float(h.slot));
   }
-  warp_count(&p.ctr->ref_hit, refined);
-  warp_count(&p.ctr->node_visits, visits);
-  warp_count(&p.ctr->tri_tests, tests);
+  block_count(&p.ctr->ref_hit, refined);
+  block_count(&p.ctr->node_visits, visits);
+  block_count(&p.ctr->tri_tests, tests);
   if (err) atomicOr(&p.ctr->err, err);
 }
 
@@ -374,7 +404,6 @@ __global__ void __launch_bounds__(256) k_shade(RenderParams p) {
   }
   const Pool& P = p.pool;
   const int n = *(volatile int*)&p.ctr->tq_count;
-  const int lane = threadIdx.x & 31;
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int i = base + threadIdx.x;
     bool want_shadow = false;
@@ -688,14 +717,8 @@ __global__ void __launch_bounds__(256) k_shade(RenderParams p) {
       P.part[slot] = pt;
       if (done) P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg, ST_DONE, 0), m.w);
     }
-    unsigned smask = __ballot_sync(0xffffffffu, want_shadow);
-    if (smask) {
-      int leader = __ffs(smask) - 1;
-      int first = 0;
-      if (lane == leader) first = atomicAdd(&p.ctr->sq_count, __popc(smask));
-      first = __shfl_sync(0xffffffffu, first, leader);
-      if (want_shadow) P.sq[first + __popc(smask & ((1u << lane) - 1u))] = slot;
-    }
+    const int q = block_reserve<int>(&p.ctr->sq_count, want_shadow);
+    if (want_shadow) P.sq[q] = slot;
   }
 }
 
@@ -752,9 +775,9 @@ __global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_shadow(RenderParam
       }
     }
   }
-  warp_count(&p.ctr->ref_hit, refined);
-  warp_count(&p.ctr->node_visits, visits);
-  warp_count(&p.ctr->tri_tests, tests);
+  block_count(&p.ctr->ref_hit, refined);
+  block_count(&p.ctr->node_visits, visits);
+  block_count(&p.ctr->tri_tests, tests);
   if (err) atomicOr(&p.ctr->err, err);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     p.ctr->shadow += (unsigned long long)n;
