@@ -41,6 +41,8 @@ struct Counters {
   int sq_count;
   int last_active;
   int err;
+  int trace_next;  // next unclaimed trace-queue entry (claimed in groups of 32)
+  int pad;
   unsigned long long samples, segments, shadow, ref_hit, ref_lobe, iters, node_visits, tri_tests;
 };
 

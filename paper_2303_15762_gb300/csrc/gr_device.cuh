@@ -283,85 +283,123 @@ struct Hit {
   int slot;  // leaf slot (BVH order) or -1
 };
 
+// Resumable traversal of the binary BVH for one ray: the state a lane keeps
+// between steps, so a warp can interleave rays that started at different
+// times.  One step visits one internal node (two slab tests, leaf children
+// tested at once) and picks the next node, nearer child first, the farther
+// one pushed; the order of visits and tests per ray does not depend on how
+// steps are scheduled, so neither does the result.
+struct BinTrav {
+  RayPre r;
+  float t;       // closest accepted distance so far (+inf: none)
+  int slot;      // leaf slot of that hit, or -1
+  int best_id;   // its original triangle id (ties go to the lower id)
+  int exclude;   // leaf slot never accepted (the surface the ray leaves)
+  int node, sp, guard;
+};
+
+__device__ __forceinline__ void bin_leaf(const float4* __restrict__ tri, BinTrav& s, int leaf, int* refined,
+                                         int* tests) {
+  if (leaf == s.exclude) return;
+  const float4 a = __ldg(&tri[3 * leaf]);
+  const float4 b = __ldg(&tri[3 * leaf + 1]);
+  const float4 c = __ldg(&tri[3 * leaf + 2]);
+  ++*tests;
+  const float t = isect_tri(s.r, xyz(a), xyz(b), xyz(c), refined);
+  const int id = __float_as_int(a.w);
+  if (t > kTMin && (t < s.t || (t == s.t && id < s.best_id))) {
+    s.t = t;
+    s.slot = leaf;
+    s.best_id = id;
+  }
+}
+
+// Starts a traversal; returns true if it is already complete (0 or 1 triangles).
+__device__ __forceinline__ bool bin_begin(int n_tris, const float4* __restrict__ tri, BinTrav& s, float3 o, float3 d,
+                                          int exclude, int* refined, int* tests) {
+  s.t = __int_as_float(0x7f800000);
+  s.slot = -1;
+  s.best_id = 0x7fffffff;
+  s.exclude = exclude;
+  s.node = 0;
+  s.sp = 0;
+  // a binary tree of n leaves has n-1 internal nodes: a traversal never visits
+  // more, so the bound only trips on a corrupt hierarchy
+  s.guard = n_tris + 8;
+  if (n_tris == 0) return true;
+  s.r = ray_pre(o, d);
+  if (n_tris == 1) {
+    bin_leaf(tri, s, 0, refined, tests);
+    return true;
+  }
+  return false;
+}
+
+// One node visit; returns true when the traversal is complete.  *err = 2 if
+// the visit bound trips, 1 if the stack would overflow (the traversal then
+// drops the farther child).
+// `stack` holds kStackDepth entries, kept outside BinTrav so that the ray
+// state stays in registers.
+__device__ __forceinline__ bool bin_step(const float4* __restrict__ nodes, const float4* __restrict__ tri, BinTrav& s,
+                                         int* stack, int* refined, int* visits, int* tests, int* err) {
+  if (--s.guard < 0) {
+    if (err) *err = 2;
+    return true;
+  }
+  ++*visits;
+  const float4* N = nodes + 4 * s.node;
+  const float4 n0 = __ldg(N), n1 = __ldg(N + 1), n2 = __ldg(N + 2), n3 = __ldg(N + 3);
+  const int lref = __float_as_int(n3.x), rref = __float_as_int(n3.y);
+  const float tl = box_entry(s.r, f3(n0.x, n0.y, n0.z), f3(n0.w, n1.x, n1.y), s.t);
+  const float tr = box_entry(s.r, f3(n1.z, n1.w, n2.x), f3(n2.y, n2.z, n2.w), s.t);
+  bool hl = tl >= 0.0f, hr = tr >= 0.0f;
+  // leaves are tested immediately; internal children are descended/pushed
+  if (hl && lref < 0) {
+    bin_leaf(tri, s, lref & 0x7fffffff, refined, tests);
+    hl = false;
+  }
+  if (hr && rref < 0) {
+    bin_leaf(tri, s, rref & 0x7fffffff, refined, tests);
+    hr = false;
+  }
+  int next = -1;
+  if (hl && hr) {
+    const int nearer = tl <= tr ? lref : rref;
+    const int farther = tl <= tr ? rref : lref;
+    if (s.sp < kStackDepth) {
+      stack[s.sp++] = farther;
+    } else if (err) {
+      *err = 1;
+    }
+    next = nearer;
+  } else if (hl) {
+    next = lref;
+  } else if (hr) {
+    next = rref;
+  }
+  if (next < 0) {
+    if (s.sp == 0) return true;
+    next = stack[--s.sp];
+  }
+  s.node = next;
+  return false;
+}
+
 // Closest hit along (o, d) with t > kTMin, skipping leaf slot `exclude`;
 // equal distances resolve to the lower original triangle id.  Stack-based
-// traversal of the binary LBVH, nearer child first.  *err is set if the stack
+// traversal of the binary BVH, nearer child first.  *err is set if the stack
 // would overflow (the traversal then stops early).
 __device__ __forceinline__ Hit closest_hit(const DevScene& S, float3 o, float3 d, int exclude, int* refined,
                                            int* visits, int* tests, int* err) {
-  Hit h;
-  h.t = __int_as_float(0x7f800000);
-  h.slot = -1;
-  int best_id = 0x7fffffff;
-  if (S.n_tris == 0) return h;
-  RayPre r = ray_pre(o, d);
-  auto test_leaf = [&](int slot) {
-    if (slot == exclude) return;
-    const float4 a = __ldg(&S.tri[3 * slot]);
-    const float4 b = __ldg(&S.tri[3 * slot + 1]);
-    const float4 c = __ldg(&S.tri[3 * slot + 2]);
-    ++*tests;
-    float t = isect_tri(r, xyz(a), xyz(b), xyz(c), refined);
-    int id = __float_as_int(a.w);
-    if (t > kTMin && (t < h.t || (t == h.t && id < best_id))) {
-      h.t = t;
-      h.slot = slot;
-      best_id = id;
-    }
-  };
-  if (S.n_tris == 1) {
-    test_leaf(0);
-    return h;
-  }
+  BinTrav s;
   int stack[kStackDepth];
-  int sp = 0;
-  int node = 0;
-  // a binary tree of n leaves has n-1 internal nodes: a traversal never visits
-  // more, so the bound only trips on a corrupt hierarchy
-  int guard = S.n_tris + 8;
-  for (;;) {
-    if (--guard < 0) {
-      if (err) *err = 2;
-      break;
+  if (!bin_begin(S.n_tris, S.tri, s, o, d, exclude, refined, tests)) {
+    while (!bin_step(S.nodes, S.tri, s, stack, refined, visits, tests, err)) {
     }
-    ++*visits;
-    const float4* N = S.nodes + 4 * node;
-    const float4 n0 = __ldg(N), n1 = __ldg(N + 1), n2 = __ldg(N + 2), n3 = __ldg(N + 3);
-    const int lref = __float_as_int(n3.x), rref = __float_as_int(n3.y);
-    float tl = box_entry(r, f3(n0.x, n0.y, n0.z), f3(n0.w, n1.x, n1.y), h.t);
-    float tr = box_entry(r, f3(n1.z, n1.w, n2.x), f3(n2.y, n2.z, n2.w), h.t);
-    bool hl = tl >= 0.0f, hr = tr >= 0.0f;
-    int next = -1;
-    // leaves are tested immediately; internal children are descended/pushed
-    if (hl && lref < 0) {
-      test_leaf(lref & 0x7fffffff);
-      hl = false;
-    }
-    if (hr && rref < 0) {
-      test_leaf(rref & 0x7fffffff);
-      hr = false;
-    }
-    if (hl && hr) {
-      int nearer = tl <= tr ? lref : rref;
-      int farther = tl <= tr ? rref : lref;
-      if (sp < kStackDepth) {
-        stack[sp++] = farther;
-      } else if (err) {
-        *err = 1;
-      }
-      next = nearer;
-    } else if (hl) {
-      next = lref;
-    } else if (hr) {
-      next = rref;
-    }
-    if (next < 0) {
-      // pop until an internal node whose box still overlaps [0, best]
-      if (sp == 0) break;
-      next = stack[--sp];
-    }
-    node = next;
   }
+  Hit h;
+  h.t = s.t;
+  h.slot = s.slot;
   return h;
 }
 

@@ -282,21 +282,88 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
 }
 
 // ------------------------------------------------------------------ trace
+#ifndef GR_TRACE_REFILL
+#define GR_TRACE_REFILL 8
+#endif
+// Trace-queue closest hits.  Binary tree: warps claim the queue in groups of
+// 32 entries from a shared cursor and keep their lanes busy across rays -- a
+// lane whose ray has finished stays idle until GR_TRACE_REFILL lanes are idle
+// (or every lane is), then the idle lanes take the next entries together, so
+// ray set-up runs once per batch rather than once per lane, the warp no longer
+// waits for the slowest ray of a fixed group of 32, and all warps advance
+// through the queue together (neighbouring rays share BVH nodes in L1).  Each
+// ray's visits and tests are those of closest_hit, in the same order.  The
+// 4-wide tree keeps one ray per thread per pass.
 template <bool WIDE>
 __global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_trace(RenderParams p) {
   const Pool& P = p.pool;
   const int n = *(volatile int*)&p.ctr->tq_count;
   if (blockIdx.x == 0 && threadIdx.x == 0) p.ctr->segments += (unsigned long long)n;
   int err = 0, refined = 0, visits = 0, tests = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int slot = P.tq[i];
-    const int4 m = P.meta[slot];
-    const DevView& V = p.views[m.x];
-    const DevScene& S = p.scenes[V.scene_index];
-    const float4 a = P.od0[slot], b = P.od1[slot];
-    Hit h = WIDE ? closest_hit_wide(S, xyz(a), xyz(b), m.w, &refined, &visits, &tests, &err)
-                 : closest_hit(S, xyz(a), xyz(b), m.w, &refined, &visits, &tests, &err);
-    P.hit[slot] = make_float2(h.t, __int_as_float(h.slot));
+  if (WIDE) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const int slot = P.tq[i];
+      const int4 m = P.meta[slot];
+      const DevView& V = p.views[m.x];
+      const DevScene& S = p.scenes[V.scene_index];
+      const float4 a = P.od0[slot], b = P.od1[slot];
+      const Hit h = closest_hit_wide(S, xyz(a), xyz(b), m.w, &refined, &visits, &tests, &err);
+      P.hit[slot] = make_float2(h.t, __int_as_float(h.slot));
+    }
+  } else {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    BinTrav s;
+    int stack[kStackDepth];
+    const float4* nodes = nullptr;
+    const float4* tri = nullptr;
+    int out = -1;
+    bool live = false;
+    // the warp's claimed group: its last `left` entries (from base + 32 - left) are unread
+    int base = 0, left = 0;
+    bool more = true;  // unclaimed groups may remain
+    for (;;) {
+      const unsigned idle = __ballot_sync(0xffffffffu, !live);
+      if (idle == 0xffffffffu && !more && left == 0) break;
+      const int nidle = __popc(idle);
+      if ((left > 0 || more) && (nidle >= GR_TRACE_REFILL || idle == 0xffffffffu)) {
+        const int rank = __popc(idle & below);
+        int take = rank < left ? base + 32 - left + rank : -1;
+        if (nidle <= left) {
+          left -= nidle;
+        } else {
+          const int from_old = left;
+          left = 0;
+          if (more) {
+            int nb = 0;
+            if (lane == 0) nb = atomicAdd(&p.ctr->trace_next, 32);
+            nb = __shfl_sync(0xffffffffu, nb, 0);
+            if (nb >= n) {
+              more = false;
+            } else {
+              if (rank >= from_old) take = nb + (rank - from_old);
+              base = nb;
+              left = 32 - (nidle - from_old);
+            }
+          }
+        }
+        if (!live && take >= 0 && take < n) {
+          const int slot = P.tq[take];
+          const int4 m = P.meta[slot];
+          const DevScene& S = p.scenes[p.views[m.x].scene_index];
+          const float4 a = P.od0[slot], b = P.od1[slot];
+          nodes = S.nodes;
+          tri = S.tri;
+          out = slot;
+          live = !bin_begin(S.n_tris, tri, s, xyz(a), xyz(b), m.w, &refined, &tests);
+          if (!live) P.hit[slot] = make_float2(s.t, __int_as_float(s.slot));
+        }
+      }
+      if (live && bin_step(nodes, tri, s, stack, &refined, &visits, &tests, &err)) {
+        P.hit[out] = make_float2(s.t, __int_as_float(s.slot));
+        live = false;
+      }
+    }
   }
   block_count(&p.ctr->ref_hit, refined);
   block_count(&p.ctr->node_visits, visits);
@@ -783,6 +850,7 @@ __global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_shadow(RenderParam
     p.ctr->shadow += (unsigned long long)n;
     p.ctr->last_active = p.ctr->tq_count;
     p.ctr->tq_count = 0;
+    p.ctr->trace_next = 0;
   }
 }
 
