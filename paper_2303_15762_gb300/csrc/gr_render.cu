@@ -36,6 +36,9 @@ enum { ST_IDLE = 0, ST_ACTIVE = 1, ST_DONE = 2 };
 #ifndef GR_TRACE_MIN_BLOCKS
 #define GR_TRACE_MIN_BLOCKS 3
 #endif
+#ifndef GR_SHADOW_MIN_BLOCKS
+#define GR_SHADOW_MIN_BLOCKS 3
+#endif
 
 __device__ __forceinline__ int meta_k(int z) { return z & 0xffff; }
 __device__ __forceinline__ int meta_seg(int z) { return (z >> 16) & 0xff; }
@@ -262,12 +265,17 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
         } else {
           int view = find_view(p, t);
           const DevView& V = p.views[view];
-          int local = (int)(t - (unsigned long long)V.ticket_base);
-          int bin = local / (V.W * V.H);
+          // tickets run pixel-major, wavelength bin fastest: neighbouring
+          // slots start the same pixel at neighbouring wavelengths, so a warp's
+          // camera rays (and grating orders) stay coherent.  The ticket's
+          // element is bin * W*H + pixel, whatever the claim order.
+          const int local = (int)(t - (unsigned long long)V.ticket_base);
+          const int pix = local / V.nb;
+          const int bin = local - pix * V.nb;
           if (bin_samples(V, bin) > 0) {
             P.accS[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             P.accC[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            start_sample<NS>(p, slot, view, local, 0);
+            start_sample<NS>(p, slot, view, bin * (V.W * V.H) + pix, 0);
             active = true;
             need = false;
           }
@@ -791,7 +799,7 @@ __global__ void __launch_bounds__(256) k_shade(RenderParams p) {
 
 // ------------------------------------------------------------------ shadow
 template <int NS, bool WIDE>
-__global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_shadow(RenderParams p) {
+__global__ void __launch_bounds__(256, GR_SHADOW_MIN_BLOCKS) k_shadow(RenderParams p) {
   const Pool& P = p.pool;
   const int n = *(volatile int*)&p.ctr->sq_count;
   int err = 0, refined = 0, visits = 0, tests = 0;
