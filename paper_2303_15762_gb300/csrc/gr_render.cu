@@ -39,6 +39,9 @@ enum { ST_IDLE = 0, ST_ACTIVE = 1, ST_DONE = 2 };
 #ifndef GR_SHADOW_MIN_BLOCKS
 #define GR_SHADOW_MIN_BLOCKS 3
 #endif
+#ifndef GR_SHADE_MIN_BLOCKS
+#define GR_SHADE_MIN_BLOCKS 3
+#endif
 
 __device__ __forceinline__ int meta_k(int z) { return z & 0xffff; }
 __device__ __forceinline__ int meta_seg(int z) { return (z >> 16) & 0xff; }
@@ -464,7 +467,7 @@ __device__ float rough_density(float g, float kl2, float r2) {
 
 // ------------------------------------------------------------------ shade
 template <int NS, typename TT>
-__global__ void __launch_bounds__(256) k_shade(RenderParams p) {
+__global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const TableRow* rows = p.rows;
   const TT* tvals = (const TT*)p.table_vals;
