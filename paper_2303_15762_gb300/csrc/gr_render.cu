@@ -466,6 +466,55 @@ __device__ float rough_density(float g, float kl2, float r2) {
 }
 
 // ------------------------------------------------------------------ shade
+// FP64 re-decisions, taken only when the FP32 pick lies within the tables'
+// rounding of a CDF boundary; kept out of line so the rare path costs the
+// common one neither code size nor registers.
+//
+// Grating order j (Eq. K_grating): cumulative J_j(pi h / lambda)^2 over the
+// propagating orders (|t_mir + j lambda/Lambda g|^2 < 1), renormalised unless
+// `renorm` is false; returns the first j whose cumulative sum exceeds
+// u * total, or 0x7fffffff if none does.
+__device__ __noinline__ int grating_pick_fp64(double lam_d, float height_um, int jm, float3 t_mir, float step,
+                                              float3 gt, bool renorm, float u) {
+  const double xarg = kPiD * (double)height_um / lam_d;
+  double tot_d = 0.0;
+  for (int j = -jm; j <= jm; ++j) {
+    const float3 tj = t_mir + ((float)j * step) * gt;
+    if (dot(tj, tj) < 1.0f) {
+      const double J = bessel_j_d(j, xarg);
+      tot_d += J * J;
+    }
+  }
+  if (!renorm) tot_d = 1.0;
+  const double tgt = (double)u * tot_d;
+  double cd = 0.0;
+  for (int j = -jm; j <= jm; ++j) {
+    const float3 tj = t_mir + ((float)j * step) * gt;
+    if (dot(tj, tj) < 1.0f) {
+      const double J = bessel_j_d(j, xarg);
+      cd += J * J;
+      if (cd > tgt) return j;
+    }
+  }
+  return 0x7fffffff;
+}
+
+// Rough-surface term count m ~ Poisson(g), g = (2 k sigma_h cos_i)^2: the
+// first m whose cumulative Poisson probability exceeds u (at most 1000).
+__device__ __noinline__ int poisson_pick_fp64(double lam_d, float sigma_h_um, float cos_i, float u) {
+  const double kd = 2.0 * kPiD / lam_d;
+  double gd = 2.0 * kd * (double)sigma_h_um * (double)cos_i;
+  gd *= gd;
+  double pd = exp(-gd), cd = pd;
+  int mi = 0;
+  while ((double)u >= cd && mi < 1000) {
+    ++mi;
+    pd *= gd / mi;
+    cd += pd;
+  }
+  return mi;
+}
+
 template <int NS, typename TT>
 __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -662,31 +711,7 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
               if ((pick != 0x7fffffff && (cum - target < eps || target - prev < eps)) ||
                   (pick == 0x7fffffff && renorm)) {
                 atomicAdd(&p.ctr->ref_lobe, 1ull);
-                const double lam_d = bin_lambda_d(V, bin);
-                const double xarg = kPiD * (double)M.height_um / lam_d;
-                double tot_d = 0.0;
-                for (int j = -jm; j <= jm; ++j) {
-                  const float3 tj = t_mir + ((float)j * step) * gt;
-                  if (dot(tj, tj) < 1.0f) {
-                    double J = bessel_j_d(j, xarg);
-                    tot_d += J * J;
-                  }
-                }
-                if (!renorm) tot_d = 1.0;
-                const double tgt = (double)u.x * tot_d;
-                double cd = 0.0;
-                pick = 0x7fffffff;
-                for (int j = -jm; j <= jm; ++j) {
-                  const float3 tj = t_mir + ((float)j * step) * gt;
-                  if (dot(tj, tj) < 1.0f) {
-                    double J = bessel_j_d(j, xarg);
-                    cd += J * J;
-                    if (cd > tgt) {
-                      pick = j;
-                      break;
-                    }
-                  }
-                }
+                pick = grating_pick_fp64(bin_lambda_d(V, bin), M.height_um, jm, t_mir, step, gt, renorm, u.x);
               }
               if (pick == 0x7fffffff) {
                 alive = false;
@@ -713,17 +738,7 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
                 const float eps = 4e-6f + 2e-7f * (float)mi;
                 if (fabsf(u.x - cdf) < eps || (mi > 0 && fabsf(u.x - (cdf - pm)) < eps) || mi >= 1000) {
                   atomicAdd(&p.ctr->ref_lobe, 1ull);
-                  const double lam_d = bin_lambda_d(V, bin);
-                  const double kd = 2.0 * kPiD / lam_d;
-                  double gd = 2.0 * kd * (double)M.sigma_h_um * (double)cos_i;
-                  gd *= gd;
-                  double pd = exp(-gd), cd = pd;
-                  mi = 0;
-                  while ((double)u.x >= cd && mi < 1000) {
-                    ++mi;
-                    pd *= gd / mi;
-                    cd += pd;
-                  }
+                  mi = poisson_pick_fp64(bin_lambda_d(V, bin), M.sigma_h_um, cos_i, u.x);
                 }
                 mreal = (float)mi;
               }
