@@ -335,13 +335,17 @@ __device__ __forceinline__ bool bin_begin(int n_tris, const float4* __restrict__
   return false;
 }
 
-// One node visit; returns true when the traversal is complete.  *err = 2 if
-// the visit bound trips, 1 if the stack would overflow (the traversal then
-// drops the farther child).
-// `stack` holds kStackDepth entries, kept outside BinTrav so that the ray
-// state stays in registers.
-__device__ __forceinline__ bool bin_step(const float4* __restrict__ nodes, const float4* __restrict__ tri, BinTrav& s,
-                                         int* stack, int* refined, int* visits, int* tests, int* err) {
+// One node visit; returns true when the traversal is complete.  Leaf
+// children whose boxes the ray enters go to leaf(slot), which tests them at
+// once or queues them: the closest hit is the least (t, original id) over the
+// tested triangles whatever the order of the tests, and a test only ever
+// lowers s.t, so a queued test only delays culling.  *err = 2 if the visit
+// bound trips, 1 if the stack would overflow (the traversal then drops the
+// farther child).  `stack` holds kStackDepth entries, kept outside BinTrav so
+// that the ray state stays in registers.
+template <class LeafFn>
+__device__ __forceinline__ bool bin_step(const float4* __restrict__ nodes, BinTrav& s, int* stack, int* visits,
+                                         int* err, LeafFn&& leaf) {
   if (--s.guard < 0) {
     if (err) *err = 2;
     return true;
@@ -353,13 +357,13 @@ __device__ __forceinline__ bool bin_step(const float4* __restrict__ nodes, const
   const float tl = box_entry(s.r, f3(n0.x, n0.y, n0.z), f3(n0.w, n1.x, n1.y), s.t);
   const float tr = box_entry(s.r, f3(n1.z, n1.w, n2.x), f3(n2.y, n2.z, n2.w), s.t);
   bool hl = tl >= 0.0f, hr = tr >= 0.0f;
-  // leaves are tested immediately; internal children are descended/pushed
+  // leaves go to `leaf`; internal children are descended/pushed
   if (hl && lref < 0) {
-    bin_leaf(tri, s, lref & 0x7fffffff, refined, tests);
+    leaf(lref & 0x7fffffff);
     hl = false;
   }
   if (hr && rref < 0) {
-    bin_leaf(tri, s, rref & 0x7fffffff, refined, tests);
+    leaf(rref & 0x7fffffff);
     hr = false;
   }
   int next = -1;
@@ -394,7 +398,9 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& S, float3 o, float3 d
   BinTrav s;
   int stack[kStackDepth];
   if (!bin_begin(S.n_tris, S.tri, s, o, d, exclude, refined, tests)) {
-    while (!bin_step(S.nodes, S.tri, s, stack, refined, visits, tests, err)) {
+    const float4* tri = S.tri;
+    auto test_now = [&](int leaf) { bin_leaf(tri, s, leaf, refined, tests); };
+    while (!bin_step(S.nodes, s, stack, visits, err, test_now)) {
     }
   }
   Hit h;

@@ -296,15 +296,25 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
 #ifndef GR_TRACE_REFILL
 #define GR_TRACE_REFILL 8
 #endif
+#ifndef GR_LEAF_BATCH
+#define GR_LEAF_BATCH 16
+#endif
+#ifndef GR_LEAF_BLOCKED
+#define GR_LEAF_BLOCKED 8
+#endif
 // Trace-queue closest hits.  Binary tree: warps claim the queue in groups of
 // 32 entries from a shared cursor and keep their lanes busy across rays -- a
 // lane whose ray has finished stays idle until GR_TRACE_REFILL lanes are idle
 // (or every lane is), then the idle lanes take the next entries together, so
 // ray set-up runs once per batch rather than once per lane, the warp no longer
 // waits for the slowest ray of a fixed group of 32, and all warps advance
-// through the queue together (neighbouring rays share BVH nodes in L1).  Each
-// ray's visits and tests are those of closest_hit, in the same order.  The
-// 4-wide tree keeps one ray per thread per pass.
+// through the queue together (neighbouring rays share BVH nodes in L1).
+// Leaf triangles are queued per lane (up to 3; a lane holding 2 stops walking)
+// and tested in warp-wide passes once GR_LEAF_BATCH lanes hold some, or
+// GR_LEAF_BLOCKED lanes are stopped, or no lane can walk: one test then serves
+// many lanes instead of two or three.  The hit equals closest_hit's (the least
+// (t, id) over the triangles whose boxes the ray enters); only the counts of
+// visits and tests differ.  The 4-wide tree keeps one ray per thread per pass.
 template <bool WIDE>
 __global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_trace(RenderParams p) {
   const Pool& P = p.pool;
@@ -329,7 +339,17 @@ __global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_trace(RenderParams
     const float4* nodes = nullptr;
     const float4* tri = nullptr;
     int out = -1;
-    bool live = false;
+    bool live = false;     // the lane holds a ray
+    bool walking = false;  // ... whose node walk has not ended
+    int np = 0, pl0 = 0, pl1 = 0, pl2 = 0;  // queued leaves (at most 3)
+    int exclude = -1;  // the ray's s.exclude, kept for the queueing test
+    auto queue_leaf = [&](int leaf) {
+      if (leaf == exclude) return;
+      if (np == 0) pl0 = leaf;
+      else if (np == 1) pl1 = leaf;
+      else pl2 = leaf;
+      ++np;
+    };
     // the warp's claimed group: its last `left` entries (from base + 32 - left) are unread
     int base = 0, left = 0;
     bool more = true;  // unclaimed groups may remain
@@ -366,13 +386,35 @@ __global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_trace(RenderParams
           nodes = S.nodes;
           tri = S.tri;
           out = slot;
-          live = !bin_begin(S.n_tris, tri, s, xyz(a), xyz(b), m.w, &refined, &tests);
+          np = 0;
+          exclude = m.w;
+          live = walking = !bin_begin(S.n_tris, tri, s, xyz(a), xyz(b), m.w, &refined, &tests);
           if (!live) P.hit[slot] = make_float2(s.t, __int_as_float(s.slot));
         }
       }
-      if (live && bin_step(nodes, tri, s, stack, &refined, &visits, &tests, &err)) {
-        P.hit[out] = make_float2(s.t, __int_as_float(s.slot));
-        live = false;
+      // leaf pass: the queued triangles of many lanes are tested together
+      const bool blocked = live && (np >= 2 || (!walking && np > 0));
+      const unsigned pend = __ballot_sync(0xffffffffu, live && np > 0);
+      const unsigned blk = __ballot_sync(0xffffffffu, blocked);
+      const unsigned can_walk = __ballot_sync(0xffffffffu, live && walking && np < 2);
+      if (pend && (__popc(pend) >= GR_LEAF_BATCH || __popc(blk) >= GR_LEAF_BLOCKED || can_walk == 0)) {
+        if (live && np > 0) {
+          bin_leaf(tri, s, pl0, &refined, &tests);
+          if (np > 1) bin_leaf(tri, s, pl1, &refined, &tests);
+          if (np > 2) bin_leaf(tri, s, pl2, &refined, &tests);
+          np = 0;
+          if (!walking) {
+            P.hit[out] = make_float2(s.t, __int_as_float(s.slot));
+            live = false;
+          }
+        }
+      }
+      if (live && walking && np < 2) {
+        walking = !bin_step(nodes, s, stack, &visits, &err, queue_leaf);
+        if (!walking && np == 0) {
+          P.hit[out] = make_float2(s.t, __int_as_float(s.slot));
+          live = false;
+        }
       }
     }
   }
