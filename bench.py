@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", choices=["procedural", "batched", "serving"], default="procedural",
                     help="procedural: the headline single-view workload; batched: 64 views/scenes, plain "
-                         "per-view FP32 form vs the autotuned FP16-table single-graph form; serving: "
+                         "per-view FP32 form vs the autotuned single-graph form; serving: "
                          "Poisson-arriving progressive requests")
     ap.add_argument("--views", type=int, default=64)
     ap.add_argument("--rate", type=float, default=20.0)
@@ -196,7 +196,7 @@ def run_reference(args):
 
 def run_batched(args):
     """64 seeded views/scenes: plain per-view FP32 renders vs one autotuned
-    FP16-table render of all views as a single graph launch."""
+    render of all views as a single graph launch."""
     import numpy as np
     import torch
     import paper_2303_15762_gb300 as gr
@@ -235,8 +235,9 @@ def run_batched(args):
     for _ in range(max(1, args.warmup)):
         plain()
     plain_ms = [timed(plain) for _ in range(args.steps)]
-    # batched form: autotuned, FP16 order tables, one graph launch for all views
-    best, trials = autotune.autotune(gr, S, views, dict(seed=2, flags=flags, table_dtype="f16", use_graph=True),
+    # batched form: autotuned (pool, block, threshold, table precision), one
+    # graph launch for all views
+    best, trials = autotune.autotune(gr, S, views, dict(seed=2, flags=flags, table_dtype="f32", use_graph=True),
                                      probe_spp=max(1, views[0]["spp"] // 4))
     F = gr.Frame(views)
 
@@ -265,8 +266,9 @@ def run_batched(args):
             "ms_plain": statistics.mean(plain_ms), "samples_per_step": samples, "n_views": len(views),
             "tris": [len(s["tri_mat"]) for s in scenes], "sides": [v["width"] for v in views],
             "depths": [v["max_depth"] for v in views], "bins": [v["n_bins"] for v in views],
-            "autotuned": {k: best[k] for k in ("pool_size", "block", "regen_threshold_pct")},
-            "autotune_trials": [[t[0]["pool_size"], t[0]["block"], t[0]["regen_threshold_pct"], t[1]] for t in trials],
+            "autotuned": {k: best[k] for k in ("pool_size", "block", "regen_threshold_pct", "table_dtype")},
+            "autotune_trials": [[t[0]["pool_size"], t[0]["block"], t[0]["regen_threshold_pct"], t[0]["table_dtype"],
+                                 t[1]] for t in trials],
             "rel_l2_full_views_vs_oracle": rels, "max_abs_diff_batched_vs_plain": diff,
             "graph_launches_per_render": 1, "iterations": st["iterations"],
             "scene_gen_s": gen_s, "scene_build_s": build_s,
@@ -286,11 +288,11 @@ def run_serving(args):
     def make():
         return [serving.Request(k + 1, *sg.serving_request(rng, k + 1), args.frames) for k in range(args.requests)]
     # warm-up pass (graph builds, allocator) on a few requests
-    srv = serving.ProgressiveServer(gr, render_opts=dict(seed=1, flags=0, table_dtype="f16", use_graph=True))
+    srv = serving.ProgressiveServer(gr, render_opts=dict(seed=1, flags=0, table_dtype="f32", use_graph=True))
     serving.run_poisson(gr, make()[:3], 1000.0, srv)
     srv.close()
     rng = np.random.default_rng(5)
-    srv = serving.ProgressiveServer(gr, render_opts=dict(seed=1, flags=0, table_dtype="f16", use_graph=True))
+    srv = serving.ProgressiveServer(gr, render_opts=dict(seed=1, flags=0, table_dtype="f32", use_graph=True))
     res = serving.run_poisson(gr, make(), args.rate, srv, seed=6)
     srv.close()
     res.update({"workload": "serving", "metric": METRIC, "unit": UNIT, "rate_req_per_s": args.rate,

@@ -1,15 +1,20 @@
 """Autotuner for the wavefront render's launch parameters.
 
-Coordinate descent over the slot-pool size, the block size and the
-regeneration threshold on a reduced-sample probe of the actual workload (the
-same scenes and views, fewer samples per pixel), timed with CUDA events on the
-render stream.  The result is a dict of gr_render options.
+Coordinate descent over the slot-pool size, the block size, the
+regeneration threshold and the order-table precision on a reduced-sample probe
+of the actual workload (the same scenes and views, fewer samples per pixel),
+timed with CUDA events on the render stream.  The result is a dict of
+gr_render options.  Table precision is a tuning choice because a narrower
+table widens the window around a CDF boundary inside which a grating order is
+re-decided in FP64, and FP64 throughput is low on this part: FP16 tables trade
+shared-memory footprint for roughly ten times as many FP64 re-decisions.
 """
 import statistics
 
 POOLS = (1 << 18, 1 << 19, 1 << 20, 1 << 21, 1 << 22)
 BLOCKS = (128, 256)
 THRESHOLDS = (0, 25, 50, 75)
+TABLES = ("f32", "f16")
 
 
 def _time_render(gr, scenes, views, frame, opts, repeats=2):
@@ -30,25 +35,28 @@ def _time_render(gr, scenes, views, frame, opts, repeats=2):
 
 
 def autotune(gr, scenes, views, base_opts, probe_spp=None, pools=POOLS, blocks=BLOCKS, thresholds=THRESHOLDS,
-             log=None):
+             tables=TABLES, log=None):
     """Return (best_opts, trials).  base_opts are fixed options (seed, flags,
-    table dtype, use_graph); probe_spp reduces every view's samples."""
+    use_graph; table_dtype is the starting point of its coordinate);
+    probe_spp reduces every view's samples."""
     probe = [dict(v, spp=probe_spp if probe_spp else v["spp"]) for v in views]
     frame = gr.Frame(probe)
     trials = []
     best = dict(base_opts, pool_size=1 << 20, block=256, regen_threshold_pct=0)
+    best.setdefault("table_dtype", "f32")
 
     def run(cand):
         ms = _time_render(gr, scenes, probe, frame, cand)
         trials.append((dict(pool_size=cand["pool_size"], block=cand["block"],
-                            regen_threshold_pct=cand["regen_threshold_pct"]), ms))
+                            regen_threshold_pct=cand["regen_threshold_pct"], table_dtype=cand["table_dtype"]), ms))
         if log:
-            log("autotune pool=%d block=%d thr=%d: %.2f ms" % (cand["pool_size"], cand["block"],
-                                                              cand["regen_threshold_pct"], ms))
+            log("autotune pool=%d block=%d thr=%d table=%s: %.2f ms" % (
+                cand["pool_size"], cand["block"], cand["regen_threshold_pct"], cand["table_dtype"], ms))
         return ms
 
     best_ms = run(best)
-    for key, values in (("pool_size", pools), ("block", blocks), ("regen_threshold_pct", thresholds)):
+    for key, values in (("pool_size", pools), ("block", blocks), ("regen_threshold_pct", thresholds),
+                        ("table_dtype", tables)):
         for v in values:
             if v == best[key]:
                 continue

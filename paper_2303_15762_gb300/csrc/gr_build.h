@@ -54,6 +54,7 @@ struct RenderParams {
   int flags;
   const TableRow* rows;
   const void* table_vals;
+  const float* table_vals32;  // the same values in FP32 (== table_vals for FP32 tables)
   int table_dtype;
   int table_smem;        // 1 if the order table is staged in shared memory
   int table_rows;

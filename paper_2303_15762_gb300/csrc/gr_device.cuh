@@ -59,11 +59,11 @@ struct DevView {
   float ortho_half;
   float lmin, lmax, beta0;
   long long ticket_base;  // first global ticket of this view
-  long long n_tickets;    // nb * W * H
+  long long n_tickets;    // nbu * W * H
   float* acc_sum;         // [nb][H][W][ns]
   float* acc_comp;
   int table_base;         // first table row of this view ((view, material, bin) rows)
-  int pad;
+  int nbu;                // bins that receive samples: min(spp, nb), from first_sample mod nb on
 };
 
 // Per-(view, material, bin) row of the grating order table: J_j(h k/2)^2 for

@@ -270,11 +270,14 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
           const DevView& V = p.views[view];
           // tickets run pixel-major, wavelength bin fastest: neighbouring
           // slots start the same pixel at neighbouring wavelengths, so a warp's
-          // camera rays (and grating orders) stay coherent.  The ticket's
-          // element is bin * W*H + pixel, whatever the claim order.
+          // camera rays (and grating orders) stay coherent.  Only bins that
+          // receive samples have tickets: sample s goes to bin s mod nb, so
+          // with spp < nb they are the nbu = spp bins from first_sample mod nb
+          // on.  The ticket's element is bin * W*H + pixel, whatever the claim
+          // order.
           const int local = (int)(t - (unsigned long long)V.ticket_base);
-          const int pix = local / V.nb;
-          const int bin = local - pix * V.nb;
+          const int pix = local / V.nbu;
+          const int bin = (V.first_sample + (local - pix * V.nbu)) % V.nb;
           if (bin_samples(V, bin) > 0) {
             P.accS[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             P.accC[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -508,6 +511,53 @@ __device__ float rough_density(float g, float kl2, float r2) {
 }
 
 // ------------------------------------------------------------------ shade
+// Grating order pick from tabulated weights w_|j| = J_j(pi h / lambda)^2
+// (Eq. K_grating): over the propagating orders (|t_mir + j lambda/Lambda g|^2
+// < 1) the first j whose cumulative weight exceeds u * total (total = 1 when
+// the weights are not renormalised), or 0x7fffffff if none does.
+// `ambiguous` is set when u * total lies within rel * total of a cumulative
+// sum, i.e. within the table's rounding of a boundary, or no order is picked
+// under renormalisation: the caller then re-decides at higher precision.
+template <class Val>
+__device__ __forceinline__ int grating_pick_tab(int jm, float3 t_mir, float step, float3 gt, bool renorm, float u,
+                                                float rel, Val val, bool& ambiguous) {
+  float total = 0.0f;
+  for (int j = -jm; j <= jm; ++j) {
+    const float3 tj = t_mir + ((float)j * step) * gt;
+    if (dot(tj, tj) < 1.0f) total += val(j < 0 ? -j : j);
+  }
+  if (!renorm) total = 1.0f;
+  const float target = u * total;
+  float cum = 0.0f, prev = 0.0f;
+  int pick = 0x7fffffff;
+  for (int j = -jm; j <= jm; ++j) {
+    const float3 tj = t_mir + ((float)j * step) * gt;
+    if (dot(tj, tj) < 1.0f) {
+      prev = cum;
+      cum += val(j < 0 ? -j : j);
+      if (cum > target) {
+        pick = j;
+        break;
+      }
+    }
+  }
+  const float eps = rel * fmaxf(total, 1e-30f);
+  ambiguous = (pick != 0x7fffffff && (cum - target < eps || target - prev < eps)) || (pick == 0x7fffffff && renorm);
+  return pick;
+}
+
+// Relative half-width of the window around a CDF boundary inside which a
+// table of this type cannot decide (its rounding of the cumulative sums with
+// margin: FP32 2^-24 per value, FP16 2^-11, BF16 2^-8).
+template <typename TT>
+__device__ __forceinline__ float table_rel_eps();
+template <>
+__device__ __forceinline__ float table_rel_eps<float>() { return 2e-6f; }
+template <>
+__device__ __forceinline__ float table_rel_eps<__half>() { return 2e-3f; }
+template <>
+__device__ __forceinline__ float table_rel_eps<__nv_bfloat16>() { return 2e-2f; }
+
 // FP64 re-decisions, taken only when the FP32 pick lies within the tables'
 // rounding of a CDF boundary; kept out of line so the rare path costs the
 // common one neither code size nor registers.
@@ -727,31 +777,15 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
               const TableRow row = rows[V.table_base + mat * V.nb + bin];
               const int jm = row.jmax;
               const bool renorm = !(p.flags & GR_FLAG_NO_RENORM);
-              float total = 0.0f;
-              for (int j = -jm; j <= jm; ++j) {
-                const float3 tj = t_mir + ((float)j * step) * gt;
-                if (dot(tj, tj) < 1.0f) total += table_load<TT>(tvals, row.offset + (j < 0 ? -j : j));
-              }
-              if (!renorm) total = 1.0f;
-              const float target = u.x * total;
-              float cum = 0.0f, prev = 0.0f;
-              int pick = 0x7fffffff;
-              for (int j = -jm; j <= jm; ++j) {
-                const float3 tj = t_mir + ((float)j * step) * gt;
-                if (dot(tj, tj) < 1.0f) {
-                  prev = cum;
-                  cum += table_load<TT>(tvals, row.offset + (j < 0 ? -j : j));
-                  if (cum > target) {
-                    pick = j;
-                    break;
-                  }
-                }
-              }
-              // FP64 decision near a CDF boundary (tables are approximate)
-              const float eps = (p.table_dtype == GR_TABLE_F32 ? 2e-6f : (p.table_dtype == GR_TABLE_F16 ? 2e-3f : 2e-2f)) *
-                                fmaxf(total, 1e-30f);
-              if ((pick != 0x7fffffff && (cum - target < eps || target - prev < eps)) ||
-                  (pick == 0x7fffffff && renorm)) {
+              // the table's pick; within its rounding of a CDF boundary the
+              // FP32 copy decides, and within FP32's rounding FP64 does
+              bool ambiguous;
+              int pick = grating_pick_tab(jm, t_mir, step, gt, renorm, u.x, table_rel_eps<TT>(),
+                                          [&](int a) { return table_load<TT>(tvals, row.offset + a); }, ambiguous);
+              if (ambiguous && sizeof(TT) != sizeof(float))
+                pick = grating_pick_tab(jm, t_mir, step, gt, renorm, u.x, table_rel_eps<float>(),
+                                        [&](int a) { return __ldg(p.table_vals32 + row.offset + a); }, ambiguous);
+              if (ambiguous) {
                 atomicAdd(&p.ctr->ref_lobe, 1ull);
                 pick = grating_pick_fp64(bin_lambda_d(V, bin), M.height_um, jm, t_mir, step, gt, renorm, u.x);
               }
@@ -929,8 +963,9 @@ struct TableBuildRow {
   int pad[3];
 };
 
+// vals32 (FP32 copy for re-decisions) is null when TT is float.
 template <typename TT>
-__global__ void k_tables(const TableBuildRow* rows, int n_rows, const DevView* views, TT* vals) {
+__global__ void k_tables(const TableBuildRow* rows, int n_rows, const DevView* views, TT* vals, float* vals32) {
   int r = blockIdx.x;
   if (r >= n_rows) return;
   const TableBuildRow R = rows[r];
@@ -946,6 +981,7 @@ __global__ void k_tables(const TableBuildRow* rows, int n_rows, const DevView* v
       vals[R.offset + j] = __float2half_rn(v);
     else
       vals[R.offset + j] = __float2bfloat16_rn(v);
+    if (vals32) vals32[R.offset + j] = v;
   }
 }
 
@@ -1092,7 +1128,8 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     V.lmax = d.lambda_max_um;
     V.beta0 = d.f_beta * d.p_pix_um;
     V.ticket_base = (long long)plan.total_tickets;
-    V.n_tickets = (long long)d.n_bins * d.width * d.height;
+    V.nbu = std::min(d.spp, d.n_bins);
+    V.n_tickets = (long long)V.nbu * d.width * d.height;
     plan.total_tickets += (unsigned long long)V.n_tickets;
     V.acc_sum = acc_sum[v];
     V.acc_comp = acc_comp[v];
@@ -1141,6 +1178,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const size_t o_rows = take(sizeof(TableRow) * std::max<size_t>(plan.rows.size(), 1));
   const size_t o_brows = take(sizeof(TableBuildRow) * std::max<size_t>(plan.build_rows.size(), 1));
   const size_t o_vals = take(tsize * std::max(plan.vals_count, 1));
+  const size_t o_vals32 = o.table_dtype == GR_TABLE_F32 ? o_vals : take(sizeof(float) * std::max(plan.vals_count, 1));
   const size_t o_f4 = take(sizeof(float4) * (size_t)P * 14);
   const size_t o_hit = take(sizeof(float2) * (size_t)P);
   const size_t o_meta = take(sizeof(int4) * (size_t)P);
@@ -1167,6 +1205,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   p.flags = o.flags;
   p.rows = (const TableRow*)(base + o_rows);
   p.table_vals = base + o_vals;
+  p.table_vals32 = (const float*)(base + o_vals32);
   p.table_dtype = o.table_dtype;
   p.table_rows = (int)plan.rows.size();
   p.table_vals_count = plan.vals_count;
@@ -1215,11 +1254,11 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     const TableBuildRow* br = (const TableBuildRow*)(base + o_brows);
     const int nr = (int)plan.build_rows.size();
     if (o.table_dtype == GR_TABLE_F32)
-      k_tables<float><<<nr, 64, 0, st>>>(br, nr, p.views, (float*)(base + o_vals));
+      k_tables<float><<<nr, 64, 0, st>>>(br, nr, p.views, (float*)(base + o_vals), nullptr);
     else if (o.table_dtype == GR_TABLE_F16)
-      k_tables<__half><<<nr, 64, 0, st>>>(br, nr, p.views, (__half*)(base + o_vals));
+      k_tables<__half><<<nr, 64, 0, st>>>(br, nr, p.views, (__half*)(base + o_vals), (float*)(base + o_vals32));
     else
-      k_tables<__nv_bfloat16><<<nr, 64, 0, st>>>(br, nr, p.views, (__nv_bfloat16*)(base + o_vals));
+      k_tables<__nv_bfloat16><<<nr, 64, 0, st>>>(br, nr, p.views, (__nv_bfloat16*)(base + o_vals), (float*)(base + o_vals32));
     f->launches += 1;
   }
   GR_CK(cudaMemsetAsync(p.pool.meta, 0, sizeof(int4) * (size_t)P, st));
@@ -1512,7 +1551,8 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
     V.lmax = d.lambda_max_um;
     V.beta0 = d.f_beta * d.p_pix_um;
     V.ticket_base = (long long)total_tickets;
-    V.n_tickets = (long long)d.n_bins * d.width * d.height;
+    V.nbu = std::min(d.spp, d.n_bins);
+    V.n_tickets = (long long)V.nbu * d.width * d.height;
     total_tickets += (unsigned long long)V.n_tickets;
     V.acc_sum = accum + acc_off;
     V.acc_comp = accum + acc_total + acc_off;
@@ -1557,6 +1597,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   const size_t o_rows = take(sizeof(TableRow) * rows.size());
   const size_t o_brows = take(sizeof(TableBuildRow) * brows.size());
   const size_t o_vals = take(tsize * (size_t)std::max(vals, 1));
+  const size_t o_vals32 = o.table_dtype == GR_TABLE_F32 ? o_vals : take(sizeof(float) * (size_t)std::max(vals, 1));
   const size_t fixed = off;
   const size_t per_slot = sizeof(float4) * 14 + sizeof(float2) + sizeof(int4) + 2 * sizeof(int);
   if (fixed + per_slot * 256 > (size_t)GR_STATIC_SCRATCH_BYTES) {
@@ -1592,6 +1633,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   p.flags = o.flags;
   p.rows = (const TableRow*)(base + o_rows);
   p.table_vals = base + o_vals;
+  p.table_vals32 = (const float*)(base + o_vals32);
   p.table_dtype = o.table_dtype;
   p.table_rows = (int)rows.size();
   p.table_vals_count = vals;
@@ -1642,11 +1684,11 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
     const TableBuildRow* br = (const TableBuildRow*)(base + o_brows);
     const int nr = (int)brows.size();
     if (o.table_dtype == GR_TABLE_F32)
-      k_tables<float><<<nr, 64, 0, st>>>(br, nr, p.views, (float*)(base + o_vals));
+      k_tables<float><<<nr, 64, 0, st>>>(br, nr, p.views, (float*)(base + o_vals), nullptr);
     else if (o.table_dtype == GR_TABLE_F16)
-      k_tables<__half><<<nr, 64, 0, st>>>(br, nr, p.views, (__half*)(base + o_vals));
+      k_tables<__half><<<nr, 64, 0, st>>>(br, nr, p.views, (__half*)(base + o_vals), (float*)(base + o_vals32));
     else
-      k_tables<__nv_bfloat16><<<nr, 64, 0, st>>>(br, nr, p.views, (__nv_bfloat16*)(base + o_vals));
+      k_tables<__nv_bfloat16><<<nr, 64, 0, st>>>(br, nr, p.views, (__nv_bfloat16*)(base + o_vals), (float*)(base + o_vals32));
   }
   GR_SK(cudaGetLastError());
   // --- launch shapes (same rule as gr_render)

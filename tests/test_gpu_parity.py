@@ -28,7 +28,10 @@ def test_grating_workload_full_size(gr, oracle):
 
 @pytest.mark.parametrize("dtype", ["f16", "bf16"])
 def test_grating_workload_low_precision_tables(gr, oracle, dtype):
-    """Order tables stored in FP16 / BF16, FP32 arithmetic."""
+    """Order tables stored in FP16 / BF16, FP32 arithmetic.  A pick inside the
+    narrow table's rounding of a CDF boundary is re-decided from the FP32 copy
+    (and inside FP32's from FP64), so every order choice -- and the image --
+    is the one the FP32 tables give."""
     scene = sg.grating_scene()
     view = sg.grating_view()
     img = gr.render_image(scene, view, seed=1, table_dtype=dtype)
@@ -36,6 +39,19 @@ def test_grating_workload_low_precision_tables(gr, oracle, dtype):
     r = rel_l2(img, ref)
     print(dtype, "rel-L2 =", r)
     assert r <= TOL
+    assert np.array_equal(img, gr.render_image(scene, view, seed=1, table_dtype="f32"))
+    # the procedural scene's mix of gratings and rough conductors: the same
+    # decisions, so the images agree to FP32 rounding (the kernels for each
+    # table type are separate instantiations and may fuse a multiply-add
+    # differently in table-independent Stokes arithmetic; a changed order or
+    # path would move a pixel by a whole sample's share, ~1e-2 here)
+    ps = sg.procedural_scene(seed=7, n_objects=8, target_tris=4000, n_emitters=2)
+    for ns, flags in ((1, gr.FLAG_NEE | gr.FLAG_RR), (4, gr.FLAG_NEE | gr.FLAG_RR)):
+        pv = sg.procedural_view(width=48, height=40, spp=32, n_bins=8, n_stokes=ns, max_depth=4)
+        a = gr.render_image(ps, pv, seed=4, flags=flags, table_dtype=dtype)
+        b = gr.render_image(ps, pv, seed=4, flags=flags, table_dtype="f32").astype(np.float64)
+        assert rel_l2(a, b) <= 1e-6
+        assert np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-30)) <= 1e-4
 
 
 def test_grating_stokes_conductor(gr, oracle):
