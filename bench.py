@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "gen-ray path Msamples/s at <=1e-3 rel-L2 vs FP64 oracle; p50/p99 frame ms"
 UNIT = "Msamples/s"
-FP32_PEAK_TFLOPS = 2 * 152 * 128 * 2.070e9 / 1e12  # FMA = 2 FLOP, 152 SMs x 128 lanes at 2070 MHz
+FP32_PEAK_TFLOPS = 2 * 152 * 128 * 2.070e9 / 1e12  # nominal: FMA = 2 FLOP, 152 SMs x 128 lanes at 2070 MHz
 # Algorithmic FP32 FLOPs (FMA = 2) of the traversal units, counted from the
 # operations the closest-hit query needs: a node visit tests two child boxes
 # (6 slab FMAs + 11 min/max + 3 for the far-distance widening, compare and
@@ -71,12 +71,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-crop", type=int, default=128, help="side of the oracle's centre crop")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", choices=["procedural", "batched", "serving"], default="procedural",
+    ap.add_argument("--workload", choices=["procedural", "batched", "serving", "precision"], default="procedural",
                     help="procedural: the headline single-view workload; batched: 64 views/scenes, plain "
                          "per-view FP32 form vs the autotuned single-graph form; serving: "
-                         "Poisson-arriving progressive requests")
+                         "Poisson-arriving progressive requests; precision: FP32/FP16/BF16 order tables, "
+                         "image and per-quantity errors vs the FP64 oracle")
     ap.add_argument("--views", type=int, default=64)
     ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--rates", default="5,50,100", help="serving: further arrival rates to sweep (req/s)")
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--frames", type=int, default=64)
     return ap.parse_args()
@@ -291,14 +293,97 @@ def run_serving(args):
     srv = serving.ProgressiveServer(gr, render_opts=dict(seed=1, flags=0, table_dtype="f32", use_graph=True))
     serving.run_poisson(gr, make()[:3], 1000.0, srv)
     srv.close()
-    rng = np.random.default_rng(5)
-    srv = serving.ProgressiveServer(gr, render_opts=dict(seed=1, flags=0, table_dtype="f32", use_graph=True))
-    res = serving.run_poisson(gr, make(), args.rate, srv, seed=6)
-    srv.close()
-    res.update({"workload": "serving", "metric": METRIC, "unit": UNIT, "rate_req_per_s": args.rate,
-                "frames_per_request": args.frames, "resolutions": "256^2, 512^2, 1280x720, 1920x1080",
-                "budget_bytes": srv.budget})
+    # the headline rate, then the sweep (the same request stream at each rate)
+    rates = [args.rate] + [float(r) for r in args.rates.split(",") if r and float(r) != args.rate]
+    runs = {}
+    for rate in rates:
+        rng = np.random.default_rng(5)
+        srv = serving.ProgressiveServer(gr, render_opts=dict(seed=1, flags=0, table_dtype="f32", use_graph=True))
+        runs[rate] = serving.run_poisson(gr, make(), rate, srv, seed=6)
+        srv.close()
+    res = dict(runs[args.rate])
+    keys = ("msamples_per_s", "p50_frame_ms", "p99_frame_ms", "p50_first_frame_ms", "p99_first_frame_ms",
+            "device_frames", "wall_s")
+    res.update({"workload": "serving", "metric": METRIC, "unit": UNIT, "value": res["msamples_per_s"],
+                "rate_req_per_s": args.rate, "frames_per_request": args.frames,
+                "resolutions": "256^2, 512^2, 1280x720, 1920x1080", "budget_bytes": srv.budget,
+                "rate_sweep": [dict(rate_req_per_s=r, **{k: runs[r][k] for k in keys}) for r in sorted(runs)]})
     print(json.dumps(res))
+
+
+def run_precision(args):
+    """Planar-grating workload with FP32 / FP16 / BF16 order tables: image
+    rel-L2 vs the FP64 oracle and vs the FP32-table image, and per-quantity
+    errors vs FP64 (stored order weights a_j; beta^2 and rho along
+    three-segment chains) through the library's inspection calls."""
+    import math
+    import numpy as np
+    import torch
+    import paper_2303_15762_gb300 as gr
+    from paper_2303_15762_gb300 import scenegen as sg
+    from oracle import oracle as orc
+    gr.load()
+    scene, view = sg.grating_scene(), sg.grating_view()
+    ref = orc.Scene(scene).render(view, 1, 0, n_threads=os.cpu_count() or 1)
+    samples = view["width"] * view["height"] * view["spp"]
+    S = gr.Scene(scene)
+    F = gr.Frame([view])
+    stream = torch.cuda.current_stream()
+    out = {}
+    img32 = None
+    for dt in ("f32", "f16", "bf16"):
+        times = []
+        for r in range(args.warmup + args.steps):
+            F.reset()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gr.render([S], [view], F, seed=1, table_dtype=dt)
+            e1.record(stream)
+            e1.synchronize()
+            if r >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+        img = F.readback(0).astype(np.float64)
+        if img32 is None:
+            img32 = img
+        # order weights of the workload's 16 bins: relative error where the
+        # type is normal, absolute error where it is not (FP16 below 2^-14)
+        tiny = {"f32": 1.2e-38, "f16": 6.1e-5, "bf16": 1.2e-38}[dt]
+        worst_rel = worst_abs = 0.0
+        for b in range(view["n_bins"]):
+            lam = 0.4 + 0.3 * b / (view["n_bins"] - 1)
+            jmax = int(2 * 1.6 / lam) + 2
+            got = gr.debug_order_table(0.2, lam, jmax, dt).astype(np.float64)
+            x = math.pi * float(np.float32(0.2)) / lam
+            a = np.array([orc.bessel_j(j, x) ** 2 for j in range(jmax + 1)])
+            nrm = a >= tiny
+            if nrm.any():
+                worst_rel = max(worst_rel, float(np.max(np.abs(got - a)[nrm] / a[nrm])))
+            if (~nrm).any():
+                worst_abs = max(worst_abs, float(np.max(np.abs(got - a)[~nrm])))
+        out[dt] = {"rel_l2_vs_oracle": float(np.linalg.norm(img - ref) / np.linalg.norm(ref)),
+                   "rel_l2_vs_f32_tables": float(np.linalg.norm(img - img32) / np.linalg.norm(img32)),
+                   "max_rel_err_a_j_normal_range": worst_rel, "max_abs_err_a_j_below_normal": worst_abs,
+                   "ms_per_render": statistics.mean(times),
+                   "msamples_per_s": samples / (statistics.mean(times) * 1e-3) / 1e6}
+    # footprint: three segments of 0.05-5 m from a camera footprint (beta0 = 1 um)
+    rng = np.random.default_rng(11)
+    n = 2000
+    seg = rng.uniform(0.05, 5.0, (n, 3)).astype(np.float32)
+    kw = (2 * math.pi / rng.uniform(0.4, 0.7, n)).astype(np.float32)
+    st = np.stack([np.ones(n, np.float32), np.zeros(n, np.float32)], axis=1)
+    rf = [(1.0, 0.0)] * n
+    for k in range(3):
+        st = gr.debug_footprint(np.stack([st[:, 0], st[:, 1], seg[:, k], kw], axis=1))
+        rf = [orc.propagate(b, r, float(seg[i, k]) * 1e6 / float(kw[i])) for i, (b, r) in enumerate(rf)]
+    rf = np.array(rf)
+    line = {"workload": "precision", "metric": METRIC, "unit": UNIT,
+            "config": "planar grating 64x64, 64 spp, 16 bins 400-700 nm, 1 interaction, S0",
+            "tables": out,
+            "footprint_fp32_vs_fp64_3_segments": {
+                "max_rel_err_beta2": float(np.max(np.abs(st[:, 0] - rf[:, 0]) / rf[:, 0])),
+                "max_rel_err_rho": float(np.max(np.abs(st[:, 1] - rf[:, 1]) / np.abs(rf[:, 1])))}}
+    print(json.dumps(line))
 
 
 def main():
@@ -311,6 +396,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args)
+        return
+    if args.workload == "precision":
+        run_precision(args)
         return
     world, rank, local = dist_setup()
     import numpy as np
@@ -337,6 +425,9 @@ def main():
     for _ in range(max(3, args.warmup)):
         step(False)
     torch.cuda.synchronize()
+    # FP32 FMA throughput of this GPU (the traversal kernels' roofline
+    # denominator), measured after warm-up and outside the timed region
+    peak_tflops, peak_ms = gr.measure_fp32_peak()
     launches0 = F.stats()["kernel_launches"]
     if world > 1:
         torch.distributed.barrier()
@@ -381,8 +472,10 @@ def main():
         trav_ms = (kms[1] + kms[3]) / args.steps
         achieved = flops / (trav_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": KERNELS[dom] + "+k_shadow" if dom == 1 else KERNELS[dom],
-                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops,
+                "peak_source": "measured: FP32 FMA-chain microbenchmark, gr_measure_fp32_peak (best of 3, %.2f ms); "
+                               "nominal 152 SM x 128 lanes x 2 FLOP x 2070 MHz = %.1f" % (peak_ms, FP32_PEAK_TFLOPS),
                 "traffic": None, "per_launch_ms": per_launch_ms}
         tpr = NCU_TRAFFIC_PER_RAY.get((KERNELS[dom], source_hash()))
         if tpr is not None:
@@ -427,9 +520,32 @@ def main():
             if i > 0:
                 times.append(time.perf_counter() - t0)
         e2e_ms = 1e3 * statistics.mean(times)
+        # the same calls once more with a synchronisation between phases, so
+        # that scene build and readback are timed on their own
+        ph = {"scene_upload_build_ms": [], "frame_alloc_render_ms": [], "readback_ms": []}
+        for i in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s2 = gr.Scene(pinned)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            f2 = gr.Frame([view])
+            gr.render([s2], [view], f2, seed=2, flags=flags, table_dtype=args.table, pool_size=args.pool)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            nat._check(_lib.gr_readback(f2.handle, 0, host_img.ctypes.data_as(nat.ctypes.c_void_p),
+                                        host_img.nbytes, 0, nat.current_stream()))
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            f2.close()
+            s2.close()
+            ph["scene_upload_build_ms"].append(1e3 * (t1 - t0))
+            ph["frame_alloc_render_ms"].append(1e3 * (t2 - t1))
+            ph["readback_ms"].append(1e3 * (t3 - t2))
         e2e = {"value": world * samples / (e2e_ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
-               "includes": "scene upload + BVH build, frame alloc, render, readback to pinned host"}
+               "includes": "scene upload + BVH build, frame alloc, render, readback to pinned host",
+               "phases": {k: statistics.mean(v) for k, v in ph.items()}}
 
     # ---- CPU oracle baseline on a centre crop, and the accuracy of this run there
     cpu = None

@@ -243,6 +243,24 @@ gr_status gr_scene_bvh(gr_scene* scene, int32_t* n_out, uint64_t* keys, int32_t*
 gr_status gr_debug_rng(uint32_t seed, uint32_t view_index, uint32_t pixel, uint32_t sample, int32_t segment,
                        int32_t call, int32_t n, uint32_t* out_u32, void* cuda_stream);
 
+/* Inspection of one grating order-table row for precision tests: the weights
+ * a_j = J_j(pi h / lambda)^2, j = 0..jmax (Eq. K_grating; h = height_um,
+ * lambda = lambda_um), computed and stored exactly as the render stores them
+ * in table_dtype (GR_TABLE_F32/F16/BF16: Bessel function in FP64, rounded
+ * once to FP32, then to the table type) and decoded back to float, written
+ * to host out [jmax + 1].  jmax <= 4096.  Runs one kernel on the stream and
+ * synchronises it. */
+gr_status gr_debug_order_table(float height_um, double lambda_um, int32_t jmax, int32_t table_dtype, float* out,
+                               void* cuda_stream);
+
+/* Inspection of the footprint update for precision tests: for each of the n
+ * host quadruples in [n][4] = (beta^2 in um^2, rho, segment length t in m,
+ * wavenumber 2 pi / lambda in 1/um) the FP32 update the path applies after a
+ * segment (Eq. K_free_space_propagation, zbar = t / |k| with t in um),
+ * written to host out [n][2] = (beta^2, rho).  Runs one kernel on the stream
+ * and synchronises it. */
+gr_status gr_debug_footprint(int32_t n, const float* in, float* out, void* cuda_stream);
+
 /* ---- Rendering without device allocation (no counterpart in the paper).
  *
  * For callers that must not allocate device memory while rendering: a

@@ -19,7 +19,8 @@ TABLE_DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
 
 EXPORTED = ["gr_scene_create", "gr_scene_destroy", "gr_frame_create", "gr_frame_reset", "gr_frame_release",
             "gr_render", "gr_readback", "gr_frame_stats", "gr_scene_bvh", "gr_debug_rng", "gr_render_static", "gr_render_multi",
-            "gr_last_error", "gr_abi_version"]
+            "gr_last_error", "gr_abi_version", "gr_measure_fp32_peak", "gr_debug_order_table",
+            "gr_debug_footprint"]
 
 
 class GrError(RuntimeError):
@@ -318,3 +319,38 @@ def render_image(scene, view, **opts):
     finally:
         f.close()
         s.close()
+
+
+def measure_fp32_peak():
+    """FP32 FMA throughput of the current device (include/gr_measure.h):
+    returns (TFLOP/s, best launch ms)."""
+    L = lib_handle()
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(L.gr_measure_fp32_peak(current_stream(), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
+
+
+_TABLE_CODES = {"f32": 0, "f16": 1, "bf16": 2}
+
+
+def debug_order_table(height_um, lambda_um, jmax, table_dtype="f32"):
+    """Grating order weights a_j = J_j(pi h / lambda)^2, j = 0..jmax, as the
+    render stores them in `table_dtype`, decoded to float32 (gr_debug_order_table)."""
+    L = lib_handle()
+    fn = L.gr_debug_order_table
+    fn.argtypes = [ctypes.c_float, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    out = np.zeros(int(jmax) + 1, dtype=np.float32)
+    _check(fn(float(height_um), float(lambda_um), int(jmax), _TABLE_CODES[table_dtype], _ptr(out), current_stream()))
+    return out
+
+
+def debug_footprint(quads):
+    """The path's FP32 footprint update (gr_debug_footprint): quads [n][4] =
+    (beta^2 um^2, rho, t m, kw 1/um) -> [n][2] = (beta^2, rho)."""
+    L = lib_handle()
+    fn = L.gr_debug_footprint
+    fn.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    q = np.ascontiguousarray(quads, dtype=np.float32).reshape(-1, 4)
+    out = np.zeros((q.shape[0], 2), dtype=np.float32)
+    _check(fn(q.shape[0], _ptr(q), _ptr(out), current_stream()))
+    return out

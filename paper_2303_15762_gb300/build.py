@@ -11,7 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgr.so")
-SOURCES = ["gr_api.cu", "gr_bvh.cu", "gr_render.cu"]
+SOURCES = ["gr_api.cu", "gr_bvh.cu", "gr_render.cu", "gr_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
               "--expt-relaxed-constexpr"]
@@ -35,7 +35,7 @@ def build(force=False, verbose=False, extra_flags=()):
     """Compile every translation unit (in parallel) and link libgr.so."""
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    headers.append(os.path.join(INCLUDE, "gr.h"))
+    headers += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     cc = nvcc()
     objs, procs = [], []
     for src in SOURCES:

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "gr_build.h"
+#include "gr_measure.h"
 
 namespace gr {
 gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc* vd, int n_views,
@@ -42,6 +43,16 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 extern "C" {
 
 int32_t gr_abi_version(void) { return 1; }
+
+gr_status gr_measure_fp32_peak(void* cuda_stream, double* tflops_out, double* ms_out) {
+  if (!tflops_out || !ms_out) return fail(GR_E_INVALID, "gr_measure_fp32_peak: null argument");
+  double tf = 0.0, ms = 0.0;
+  const cudaError_t e = gr::fma_peak_impl((cudaStream_t)cuda_stream, &tf, &ms);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_measure_fp32_peak");
+  *tflops_out = tf;
+  *ms_out = ms;
+  return GR_OK;
+}
 
 const char* gr_last_error(void) { return g_err.c_str(); }
 
@@ -464,6 +475,23 @@ gr_status gr_debug_rng(uint32_t seed, uint32_t view_index, uint32_t pixel, uint3
   cudaError_t e = gr::debug_rng_impl(seed, view_index, pixel, sample, segment, call, n, out_u32,
                                      (cudaStream_t)cuda_stream);
   if (e != cudaSuccess) return cuda_fail(e, "gr_debug_rng");
+  return GR_OK;
+}
+
+gr_status gr_debug_order_table(float height_um, double lambda_um, int32_t jmax, int32_t table_dtype, float* out,
+                               void* cuda_stream) {
+  if (!out || jmax < 0 || jmax > 4096 || !(lambda_um > 0.0) || !(height_um >= 0.0f) ||
+      (table_dtype != GR_TABLE_F32 && table_dtype != GR_TABLE_F16 && table_dtype != GR_TABLE_BF16))
+    return fail(GR_E_INVALID, "gr_debug_order_table: bad arguments");
+  cudaError_t e = gr::debug_table_impl(height_um, lambda_um, jmax, table_dtype, out, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_debug_order_table");
+  return GR_OK;
+}
+
+gr_status gr_debug_footprint(int32_t n, const float* in, float* out, void* cuda_stream) {
+  if (!in || !out || n <= 0) return fail(GR_E_INVALID, "gr_debug_footprint: bad arguments");
+  cudaError_t e = gr::debug_footprint_impl(n, in, out, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_debug_footprint");
   return GR_OK;
 }
 

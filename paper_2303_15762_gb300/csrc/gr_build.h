@@ -65,6 +65,15 @@ struct RenderParams {
   Counters* ctr;
 };
 
+// FP32 FMA microbenchmark (gr_peak.cu): TFLOP/s and the best launch's ms.
+cudaError_t fma_peak_impl(cudaStream_t st, double* tflops, double* best_ms);
+
+// Inspection helpers (gr_render.cu): one order-table row decoded to float
+// [jmax + 1]; the footprint update of n (beta^2, rho, t, kw) quadruples.
+cudaError_t debug_table_impl(float height_um, double lambda_um, int jmax, int dtype, float* host_out,
+                             cudaStream_t st);
+cudaError_t debug_footprint_impl(int n, const float* host_in, float* host_out, cudaStream_t st);
+
 }  // namespace gr
 
 struct gr_scene {

@@ -427,6 +427,20 @@ __global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_trace(RenderParams
   if (err) atomicOr(&p.ctr->err, err);
 }
 
+// ------------------------------------------------------------------ footprint
+// Free-space update of the footprint after a segment of t metres at
+// wavenumber kw = 2 pi / lambda (1/um), Eq. K_free_space_propagation with
+// zbar = z / |k|, z in um:
+//   beta^2 <- beta^2 + 2 zbar rho + zbar^2 (1 + rho^2) / beta^2
+//   rho    <- rho + zbar (1 + rho^2) / beta^2
+__device__ __forceinline__ void footprint_update(float t_m, float kw, float& beta2, float& rho) {
+  const float zbar = t_m * 1e6f / kw;
+  const float b2 = beta2 + 2.0f * zbar * rho + zbar * zbar * (1.0f + rho * rho) / beta2;
+  const float ro = rho + zbar * (1.0f + rho * rho) / beta2;
+  beta2 = b2;
+  rho = ro;
+}
+
 // ------------------------------------------------------------------ measurement
 // Emitter measurement (Eq. measurement_operator on an emissive triangle set):
 // one footprint point x ~ N(0, beta^2/2) transverse to d, projected along d
@@ -515,17 +529,26 @@ __device__ float rough_density(float g, float kl2, float r2) {
 // (Eq. K_grating): over the propagating orders (|t_mir + j lambda/Lambda g|^2
 // < 1) the first j whose cumulative weight exceeds u * total (total = 1 when
 // the weights are not renormalised), or 0x7fffffff if none does.
-// `ambiguous` is set when u * total lies within rel * total of a cumulative
-// sum, i.e. within the table's rounding of a boundary, or no order is picked
-// under renormalisation: the caller then re-decides at higher precision.
+// `ambiguous` is set when the pick could differ from the one made with the
+// exact weights, or no order is picked under renormalisation; the caller then
+// re-decides at higher precision.  The window: each stored weight carries a
+// relative error <= ut (plus an absolute <= at below the type's normal range),
+// and n FP32 additions, the product u * total and the final subtraction each
+// round by <= 2^-24 relative, so |(cum - target) - exact| <=
+// (2 ut + 2 (n + 2) 2^-24) total + 2 n at; the window is 1.25 times that.
 template <class Val>
 __device__ __forceinline__ int grating_pick_tab(int jm, float3 t_mir, float step, float3 gt, bool renorm, float u,
-                                                float rel, Val val, bool& ambiguous) {
+                                                float ut, float at, Val val, bool& ambiguous) {
   float total = 0.0f;
+  int n = 0;
   for (int j = -jm; j <= jm; ++j) {
     const float3 tj = t_mir + ((float)j * step) * gt;
-    if (dot(tj, tj) < 1.0f) total += val(j < 0 ? -j : j);
+    if (dot(tj, tj) < 1.0f) {
+      total += val(j < 0 ? -j : j);
+      ++n;
+    }
   }
+  const float tot_w = total;
   if (!renorm) total = 1.0f;
   const float target = u * total;
   float cum = 0.0f, prev = 0.0f;
@@ -541,22 +564,28 @@ __device__ __forceinline__ int grating_pick_tab(int jm, float3 t_mir, float step
       }
     }
   }
-  const float eps = rel * fmaxf(total, 1e-30f);
+  const float eps = 1.25f * ((2.0f * ut + 2.0f * (float)(n + 2) * 5.9604645e-8f) * fmaxf(fmaxf(total, tot_w), 1e-30f) +
+                             2.0f * (float)n * at);
   ambiguous = (pick != 0x7fffffff && (cum - target < eps || target - prev < eps)) || (pick == 0x7fffffff && renorm);
   return pick;
 }
 
-// Relative half-width of the window around a CDF boundary inside which a
-// table of this type cannot decide (its rounding of the cumulative sums with
-// margin: FP32 2^-24 per value, FP16 2^-11, BF16 2^-8).
+// Rounding of a stored order weight: relative bound (round to nearest in the
+// type's normal range) and absolute bound below it.
 template <typename TT>
-__device__ __forceinline__ float table_rel_eps();
+struct TableRound;
 template <>
-__device__ __forceinline__ float table_rel_eps<float>() { return 2e-6f; }
+struct TableRound<float> {
+  static constexpr float rel = 5.9604645e-8f, abs = 1e-45f;  // 2^-24, subnormals
+};
 template <>
-__device__ __forceinline__ float table_rel_eps<__half>() { return 2e-3f; }
+struct TableRound<__half> {
+  static constexpr float rel = 4.8828125e-4f, abs = 2.9802322e-8f;  // 2^-11, 2^-25
+};
 template <>
-__device__ __forceinline__ float table_rel_eps<__nv_bfloat16>() { return 2e-2f; }
+struct TableRound<__nv_bfloat16> {
+  static constexpr float rel = 3.90625e-3f, abs = 1e-38f;  // 2^-8, subnormals
+};
 
 // FP64 re-decisions, taken only when the FP32 pick lies within the tables'
 // rounding of a CDF boundary; kept out of line so the rare path costs the
@@ -683,14 +712,7 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
         done = true;
       } else {
         const float t = hh.x;
-        // footprint update, Eq. K_free_space_propagation (z in um)
-        {
-          const float zbar = t * 1e6f / kw;
-          const float b2 = beta2 + 2.0f * zbar * rho + zbar * zbar * (1.0f + rho * rho) / beta2;
-          const float ro = rho + zbar * (1.0f + rho * rho) / beta2;
-          beta2 = b2;
-          rho = ro;
-        }
+        footprint_update(t, kw, beta2, rho);
         const float3 x = o + t * d;
         const int mat = S.tri_mat[hslot];
         const gr_material M = S.mats[mat];
@@ -780,10 +802,11 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
               // the table's pick; within its rounding of a CDF boundary the
               // FP32 copy decides, and within FP32's rounding FP64 does
               bool ambiguous;
-              int pick = grating_pick_tab(jm, t_mir, step, gt, renorm, u.x, table_rel_eps<TT>(),
+              int pick = grating_pick_tab(jm, t_mir, step, gt, renorm, u.x, TableRound<TT>::rel, TableRound<TT>::abs,
                                           [&](int a) { return table_load<TT>(tvals, row.offset + a); }, ambiguous);
               if (ambiguous && sizeof(TT) != sizeof(float))
-                pick = grating_pick_tab(jm, t_mir, step, gt, renorm, u.x, table_rel_eps<float>(),
+                pick = grating_pick_tab(jm, t_mir, step, gt, renorm, u.x, TableRound<float>::rel,
+                                        TableRound<float>::abs,
                                         [&](int a) { return __ldg(p.table_vals32 + row.offset + a); }, ambiguous);
               if (ambiguous) {
                 atomicAdd(&p.ctr->ref_lobe, 1ull);
@@ -915,10 +938,8 @@ __global__ void __launch_bounds__(256, GR_SHADOW_MIN_BLOCKS) k_shadow(RenderPara
     const int smp = bin_first_sample(V, bin) + meta_k(m.z) * V.nb;
     const float lambda = bin_lambda(V, bin);
     const float kw = 2.0f * kPi / lambda;
-    float beta2 = a0.w, rho = a1.w;
-    const float zbar = h.t * 1e6f / kw;
-    const float b2 = beta2 + 2.0f * zbar * rho + zbar * zbar * (1.0f + rho * rho) / beta2;
-    const float ro = rho + zbar * (1.0f + rho * rho) / beta2;
+    float b2 = a0.w, ro = a1.w;
+    footprint_update(h.t, kw, b2, ro);
     const float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallNeeFoot);
     const float val = measure_emitter(S, ei, x + h.t * w, w, b2, ro, kw, lambda, u.x, u.y);
     if (val != 0.0f) {
@@ -963,6 +984,22 @@ struct TableBuildRow {
   int pad[3];
 };
 
+// Order weight a_j = J_j(x)^2 at x = pi h / lambda (Eq. K_grating), the
+// Bessel function in FP64, rounded once to FP32; tables of narrower types
+// round that value to nearest.
+__device__ __forceinline__ float order_weight(int j, double x) {
+  const double J = bessel_j_d(j, x);
+  return (float)(J * J);
+}
+template <typename TT>
+__device__ __forceinline__ TT table_store(float v);
+template <>
+__device__ __forceinline__ float table_store<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __half table_store<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 table_store<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
 // vals32 (FP32 copy for re-decisions) is null when TT is float.
 template <typename TT>
 __global__ void k_tables(const TableBuildRow* rows, int n_rows, const DevView* views, TT* vals, float* vals32) {
@@ -973,14 +1010,8 @@ __global__ void k_tables(const TableBuildRow* rows, int n_rows, const DevView* v
   const double lam = bin_lambda_d(V, R.bin);
   const double x = kPiD * (double)R.height_um / lam;  // h k / 2
   for (int j = threadIdx.x; j <= R.jmax; j += blockDim.x) {
-    double J = bessel_j_d(j, x);
-    float v = (float)(J * J);
-    if constexpr (sizeof(TT) == 4)
-      vals[R.offset + j] = v;
-    else if constexpr (std::is_same<TT, __half>::value)
-      vals[R.offset + j] = __float2half_rn(v);
-    else
-      vals[R.offset + j] = __float2bfloat16_rn(v);
+    const float v = order_weight(j, x);
+    vals[R.offset + j] = table_store<TT>(v);
     if (vals32) vals32[R.offset + j] = v;
   }
 }
@@ -1046,6 +1077,62 @@ cudaError_t debug_rng_impl(uint32_t seed, uint32_t view, uint32_t pixel, uint32_
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, d, sizeof(uint4) * (size_t)n, cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(d, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+// Inspection: one order-table row as the render stores it, decoded to float.
+template <typename TT>
+__global__ void k_debug_table(double x, int jmax, float* out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= jmax; j += gridDim.x * blockDim.x) {
+    const TT v = table_store<TT>(order_weight(j, x));
+    out[j] = table_load<TT>(&v, 0);
+  }
+}
+
+cudaError_t debug_table_impl(float height_um, double lambda_um, int jmax, int dtype, float* host_out,
+                             cudaStream_t st) {
+  float* d = nullptr;
+  cudaError_t e = cudaMallocAsync(&d, sizeof(float) * (size_t)(jmax + 1), st);
+  if (e != cudaSuccess) return e;
+  const double x = kPiD * (double)height_um / lambda_um;  // pi h / lambda, as in k_tables
+  const int grid = (jmax + 256) / 256;
+  if (dtype == GR_TABLE_F32)
+    k_debug_table<float><<<grid, 256, 0, st>>>(x, jmax, d);
+  else if (dtype == GR_TABLE_F16)
+    k_debug_table<__half><<<grid, 256, 0, st>>>(x, jmax, d);
+  else
+    k_debug_table<__nv_bfloat16><<<grid, 256, 0, st>>>(x, jmax, d);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, d, sizeof(float) * (size_t)(jmax + 1), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+// Inspection: the footprint update the path applies after each segment.
+__global__ void k_debug_footprint(int n, const float4* in, float2* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4 q = in[i];  // beta^2 (um^2), rho, t (m), kw (1/um)
+    float beta2 = q.x, rho = q.y;
+    footprint_update(q.z, q.w, beta2, rho);
+    out[i] = make_float2(beta2, rho);
+  }
+}
+
+cudaError_t debug_footprint_impl(int n, const float* host_in, float* host_out, cudaStream_t st) {
+  float4* din = nullptr;
+  float2* dout = nullptr;
+  cudaError_t e = cudaMallocAsync(&din, sizeof(float4) * (size_t)n, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&dout, sizeof(float2) * (size_t)n, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(din, host_in, sizeof(float4) * (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    k_debug_footprint<<<std::min((n + 255) / 256, 4096), 256, 0, st>>>(n, din, dout);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, dout, sizeof(float2) * (size_t)n, cudaMemcpyDeviceToHost, st);
+  if (din) cudaFreeAsync(din, st);
+  if (dout) cudaFreeAsync(dout, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e;
 }
