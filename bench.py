@@ -325,7 +325,10 @@ def run_precision(args):
     from oracle import oracle as orc
     gr.load()
     scene, view = sg.grating_scene(), sg.grating_view()
-    ref = orc.Scene(scene).render(view, 1, 0, n_threads=os.cpu_count() or 1)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ref = orc.Scene(scene).render(view, 1, 0, n_threads=cores)
+    oracle_s = time.perf_counter() - t0
     samples = view["width"] * view["height"] * view["spp"]
     S = gr.Scene(scene)
     F = gr.Frame([view])
@@ -381,6 +384,8 @@ def run_precision(args):
     line = {"workload": "precision", "metric": METRIC, "unit": UNIT,
             "config": "planar grating 64x64, 64 spp, 16 bins 400-700 nm, 1 interaction, S0",
             "tables": out,
+            "cpu_baseline": {"value": samples / oracle_s / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "the full workload (%d samples), %.2f s" % (samples, oracle_s)},
             "footprint_fp32_vs_fp64_3_segments": {
                 "max_rel_err_beta2": float(np.max(np.abs(st[:, 0] - rf[:, 0]) / rf[:, 0])),
                 "max_rel_err_rho": float(np.max(np.abs(st[:, 1] - rf[:, 1]) / np.abs(rf[:, 1])))}}
