@@ -37,12 +37,12 @@ struct Pool {
 struct Counters {
   unsigned long long next_ticket;
   unsigned long long total_tickets;
-  int tq_count;
+  int tq_count;  // trace-queue entries filled from the front (continuing segments)
   int sq_count;
   int last_active;
   int err;
   int trace_next;  // next unclaimed trace-queue entry (claimed in groups of 32)
-  int pad;
+  int tq_back;     // trace-queue entries filled from the end of the array (camera rays)
   unsigned long long samples, segments, shadow, ref_hit, ref_lobe, iters, node_visits, tri_tests;
 };
 

@@ -76,6 +76,12 @@ __device__ __forceinline__ float src_spread2(float lambda, float lc) {
   return s * s;
 }
 
+// Entry e of the trace queue: the first `front` entries sit at the start of
+// the array, the rest at its end in reverse.
+__device__ __forceinline__ int tq_entry(const RenderParams& p, int e, int front) {
+  return e < front ? p.pool.tq[e] : p.pool.tq[p.P - 1 - (e - front)];
+}
+
 __device__ __forceinline__ int find_view(const RenderParams& p, unsigned long long t) {
   int lo = 0, hi = p.n_views - 1;
   while (lo < hi) {
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
   for (int base = blockIdx.x * blockDim.x; base < p.P; base += stride) {
     const int slot = base + threadIdx.x;
     const bool valid = slot < p.P;
-    bool need = false, active = false;
+    bool need = false, active = false, fresh = false;
     int4 m = valid ? P.meta[slot] : make_int4(0, 0, 0, 0);
     const int st = meta_state(m.z);
     if (valid && st == ST_DONE) {
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
         P.accS[slot] = s;
         P.accC[slot] = c;
         start_sample<NS>(p, slot, m.x, m.y, k);
-        active = true;
+        active = fresh = true;
       } else {
         // ticket complete: add its sum into the frame accumulator (Kahan)
         const size_t idx = (size_t)m.y * NS;
@@ -282,15 +288,23 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
             P.accS[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             P.accC[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             start_sample<NS>(p, slot, view, bin * (V.W * V.H) + pix, 0);
-            active = true;
+            active = fresh = true;
             need = false;
           }
         }
       }
     }
-    // compact live slots into the trace queue, one atomic per block
-    const int q = block_reserve<int>(&p.ctr->tq_count, active);
-    if (active) P.tq[q] = slot;
+    // compact live slots into the trace queue, one atomic per block per
+    // part: continuing segments (incoherent, longer traversals) from the front
+    // of the array, camera rays from the back, so that the queue is traced
+    // longest-first and the end of the trace launch waits on short rays
+    const int qf = block_reserve<int>(&p.ctr->tq_count, active && !fresh);
+    const int qb = block_reserve<int>(&p.ctr->tq_back, fresh);
+    if (fresh) {
+      P.tq[p.P - 1 - qb] = slot;
+    } else if (active) {
+      P.tq[qf] = slot;
+    }
   }
   block_count(&p.ctr->samples, finished);
 }
@@ -321,12 +335,13 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
 template <bool WIDE>
 __global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_trace(RenderParams p) {
   const Pool& P = p.pool;
-  const int n = *(volatile int*)&p.ctr->tq_count;
+  const int front = *(volatile int*)&p.ctr->tq_count;
+  const int n = front + *(volatile int*)&p.ctr->tq_back;
   if (blockIdx.x == 0 && threadIdx.x == 0) p.ctr->segments += (unsigned long long)n;
   int err = 0, refined = 0, visits = 0, tests = 0;
   if (WIDE) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-      const int slot = P.tq[i];
+      const int slot = tq_entry(p, i, front);
       const int4 m = P.meta[slot];
       const DevView& V = p.views[m.x];
       const DevScene& S = p.scenes[V.scene_index];
@@ -382,7 +397,7 @@ __global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_trace(RenderParams
           }
         }
         if (!live && take >= 0 && take < n) {
-          const int slot = P.tq[take];
+          const int slot = tq_entry(p, take, front);
           const int4 m = P.meta[slot];
           const DevScene& S = p.scenes[p.views[m.x].scene_index];
           const float4 a = P.od0[slot], b = P.od1[slot];
@@ -651,13 +666,14 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
     tvals = svals;
   }
   const Pool& P = p.pool;
-  const int n = *(volatile int*)&p.ctr->tq_count;
+  const int front = *(volatile int*)&p.ctr->tq_count;
+  const int n = front + *(volatile int*)&p.ctr->tq_back;
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int i = base + threadIdx.x;
     bool want_shadow = false;
     int slot = -1;
     if (i < n) {
-      slot = P.tq[i];
+      slot = tq_entry(p, i, front);
       int4 m = P.meta[slot];
       const DevView& V = p.views[m.x];
       const DevScene& S = p.scenes[V.scene_index];
@@ -971,8 +987,9 @@ __global__ void __launch_bounds__(256, GR_SHADOW_MIN_BLOCKS) k_shadow(RenderPara
   if (err) atomicOr(&p.ctr->err, err);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     p.ctr->shadow += (unsigned long long)n;
-    p.ctr->last_active = p.ctr->tq_count;
+    p.ctr->last_active = p.ctr->tq_count + p.ctr->tq_back;
     p.ctr->tq_count = 0;
+    p.ctr->tq_back = 0;
     p.ctr->trace_next = 0;
   }
 }
