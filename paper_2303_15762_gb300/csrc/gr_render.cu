@@ -319,19 +319,120 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
 #ifndef GR_LEAF_BLOCKED
 #define GR_LEAF_BLOCKED 8
 #endif
-// Trace-queue closest hits.  Binary tree: warps claim the queue in groups of
-// 32 entries from a shared cursor and keep their lanes busy across rays -- a
-// lane whose ray has finished stays idle until GR_TRACE_REFILL lanes are idle
-// (or every lane is), then the idle lanes take the next entries together, so
-// ray set-up runs once per batch rather than once per lane, the warp no longer
-// waits for the slowest ray of a fixed group of 32, and all warps advance
-// through the queue together (neighbouring rays share BVH nodes in L1).
-// Leaf triangles are queued per lane (up to 3; a lane holding 2 stops walking)
-// and tested in warp-wide passes once GR_LEAF_BATCH lanes hold some, or
-// GR_LEAF_BLOCKED lanes are stopped, or no lane can walk: one test then serves
-// many lanes instead of two or three.  The hit equals closest_hit's (the least
-// (t, id) over the triangles whose boxes the ray enters); only the counts of
-// visits and tests differ.  The 4-wide tree keeps one ray per thread per pass.
+// Closest hits for a queue of rays on the binary tree, one warp keeping its 32
+// lanes busy across rays.  Warps claim the queue in groups of 32 entries from
+// `cursor`; a lane whose ray has finished stays idle until GR_TRACE_REFILL
+// lanes are idle (or every lane is), then the idle lanes take the next
+// entries together, so ray set-up runs once per batch rather than once per
+// lane, the warp no longer waits for the slowest ray of a fixed group of 32,
+// and all warps advance through the queue together (neighbouring rays share
+// BVH nodes in L1).  Leaf triangles are queued per lane (up to 3; a lane
+// holding 2 stops walking) and tested in warp-wide passes once GR_LEAF_BATCH
+// lanes hold some, or GR_LEAF_BLOCKED lanes are stopped, or no lane can walk:
+// one test then serves many lanes instead of two or three.  The hit equals
+// closest_hit's (the least (t, id) over the triangles whose boxes the ray
+// enters); only the counts of visits and tests differ.
+//   entry(e) -> slot of queue entry e; ray(slot, o, d, exclude) gives the
+//   ray and returns its scene; done(slot, hit) consumes a finished ray.
+template <class Entry, class Ray, class Done>
+__device__ __forceinline__ void lane_trace(const RenderParams& p, int n, int* cursor, Entry&& entry, Ray&& ray,
+                                           Done&& done, int& refined, int& visits, int& tests, int& err) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  BinTrav s;
+  s.t = 0.0f;
+  s.slot = -1;
+  int stack[kStackDepth];
+  const float4* nodes = nullptr;
+  const float4* tri = nullptr;
+  int out = -1;
+  bool live = false;     // the lane holds a ray
+  bool walking = false;  // ... whose node walk has not ended
+  int np = 0, pl0 = 0, pl1 = 0, pl2 = 0;  // queued leaves (at most 3)
+  int exclude = -1;                        // the ray's s.exclude, kept for the queueing test
+  auto queue_leaf = [&](int leaf) {
+    if (leaf == exclude) return;
+    if (np == 0) pl0 = leaf;
+    else if (np == 1) pl1 = leaf;
+    else pl2 = leaf;
+    ++np;
+  };
+  auto finish = [&]() {
+    Hit h;
+    h.t = s.t;
+    h.slot = s.slot;
+    done(out, h);
+    live = false;
+  };
+  // the warp's claimed group: its last `left` entries (from base + 32 - left) are unread
+  int base = 0, left = 0;
+  bool more = true;  // unclaimed groups may remain
+  for (;;) {
+    const unsigned idle = __ballot_sync(0xffffffffu, !live);
+    if (idle == 0xffffffffu && !more && left == 0) break;
+    const int nidle = __popc(idle);
+    if ((left > 0 || more) && (nidle >= GR_TRACE_REFILL || idle == 0xffffffffu)) {
+      const int rank = __popc(idle & below);
+      int take = rank < left ? base + 32 - left + rank : -1;
+      if (nidle <= left) {
+        left -= nidle;
+      } else {
+        const int from_old = left;
+        left = 0;
+        if (more) {
+          int nb = 0;
+          if (lane == 0) nb = atomicAdd(cursor, 32);
+          nb = __shfl_sync(0xffffffffu, nb, 0);
+          if (nb >= n) {
+            more = false;
+          } else {
+            if (rank >= from_old) take = nb + (rank - from_old);
+            base = nb;
+            left = 32 - (nidle - from_old);
+          }
+        }
+      }
+      if (!live && take >= 0 && take < n) {
+        const int slot = entry(take);
+        int x = -1;
+        float3 o, d;
+        const DevScene& S = ray(slot, o, d, x);
+        nodes = S.nodes;
+        tri = S.tri;
+        out = slot;
+        np = 0;
+        exclude = x;
+        live = walking = !bin_begin(S.n_tris, tri, s, o, d, x, &refined, &tests);
+        if (!live) {
+          live = true;
+          finish();
+        }
+      }
+    }
+    // leaf pass: the queued triangles of many lanes are tested together
+    const bool blocked = live && (np >= 2 || (!walking && np > 0));
+    const unsigned pend = __ballot_sync(0xffffffffu, live && np > 0);
+    const unsigned blk = __ballot_sync(0xffffffffu, blocked);
+    const unsigned can_walk = __ballot_sync(0xffffffffu, live && walking && np < 2);
+    if (pend && (__popc(pend) >= GR_LEAF_BATCH || __popc(blk) >= GR_LEAF_BLOCKED || can_walk == 0)) {
+      if (live && np > 0) {
+        bin_leaf(tri, s, pl0, &refined, &tests);
+        if (np > 1) bin_leaf(tri, s, pl1, &refined, &tests);
+        if (np > 2) bin_leaf(tri, s, pl2, &refined, &tests);
+        np = 0;
+        if (!walking) finish();
+      }
+    }
+    if (live && walking && np < 2) {
+      walking = !bin_step(nodes, s, stack, &visits, &err, queue_leaf);
+      if (!walking && np == 0) finish();
+    }
+  }
+}
+
+// Trace-queue closest hits: the binary tree through lane_trace, the 4-wide
+// tree one ray per thread per pass.  The queue holds continuing segments from
+// the front of its array and camera rays from the back.
 template <bool WIDE>
 __global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_trace(RenderParams p) {
   const Pool& P = p.pool;
@@ -350,91 +451,18 @@ __global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_trace(RenderParams
       P.hit[slot] = make_float2(h.t, __int_as_float(h.slot));
     }
   } else {
-    const int lane = threadIdx.x & 31;
-    const unsigned below = (1u << lane) - 1u;
-    BinTrav s;
-    int stack[kStackDepth];
-    const float4* nodes = nullptr;
-    const float4* tri = nullptr;
-    int out = -1;
-    bool live = false;     // the lane holds a ray
-    bool walking = false;  // ... whose node walk has not ended
-    int np = 0, pl0 = 0, pl1 = 0, pl2 = 0;  // queued leaves (at most 3)
-    int exclude = -1;  // the ray's s.exclude, kept for the queueing test
-    auto queue_leaf = [&](int leaf) {
-      if (leaf == exclude) return;
-      if (np == 0) pl0 = leaf;
-      else if (np == 1) pl1 = leaf;
-      else pl2 = leaf;
-      ++np;
-    };
-    // the warp's claimed group: its last `left` entries (from base + 32 - left) are unread
-    int base = 0, left = 0;
-    bool more = true;  // unclaimed groups may remain
-    for (;;) {
-      const unsigned idle = __ballot_sync(0xffffffffu, !live);
-      if (idle == 0xffffffffu && !more && left == 0) break;
-      const int nidle = __popc(idle);
-      if ((left > 0 || more) && (nidle >= GR_TRACE_REFILL || idle == 0xffffffffu)) {
-        const int rank = __popc(idle & below);
-        int take = rank < left ? base + 32 - left + rank : -1;
-        if (nidle <= left) {
-          left -= nidle;
-        } else {
-          const int from_old = left;
-          left = 0;
-          if (more) {
-            int nb = 0;
-            if (lane == 0) nb = atomicAdd(&p.ctr->trace_next, 32);
-            nb = __shfl_sync(0xffffffffu, nb, 0);
-            if (nb >= n) {
-              more = false;
-            } else {
-              if (rank >= from_old) take = nb + (rank - from_old);
-              base = nb;
-              left = 32 - (nidle - from_old);
-            }
-          }
-        }
-        if (!live && take >= 0 && take < n) {
-          const int slot = tq_entry(p, take, front);
+    lane_trace(
+        p, n, &p.ctr->trace_next, [&](int e) { return tq_entry(p, e, front); },
+        [&](int slot, float3& o, float3& d, int& exclude) -> const DevScene& {
           const int4 m = P.meta[slot];
-          const DevScene& S = p.scenes[p.views[m.x].scene_index];
           const float4 a = P.od0[slot], b = P.od1[slot];
-          nodes = S.nodes;
-          tri = S.tri;
-          out = slot;
-          np = 0;
+          o = xyz(a);
+          d = xyz(b);
           exclude = m.w;
-          live = walking = !bin_begin(S.n_tris, tri, s, xyz(a), xyz(b), m.w, &refined, &tests);
-          if (!live) P.hit[slot] = make_float2(s.t, __int_as_float(s.slot));
-        }
-      }
-      // leaf pass: the queued triangles of many lanes are tested together
-      const bool blocked = live && (np >= 2 || (!walking && np > 0));
-      const unsigned pend = __ballot_sync(0xffffffffu, live && np > 0);
-      const unsigned blk = __ballot_sync(0xffffffffu, blocked);
-      const unsigned can_walk = __ballot_sync(0xffffffffu, live && walking && np < 2);
-      if (pend && (__popc(pend) >= GR_LEAF_BATCH || __popc(blk) >= GR_LEAF_BLOCKED || can_walk == 0)) {
-        if (live && np > 0) {
-          bin_leaf(tri, s, pl0, &refined, &tests);
-          if (np > 1) bin_leaf(tri, s, pl1, &refined, &tests);
-          if (np > 2) bin_leaf(tri, s, pl2, &refined, &tests);
-          np = 0;
-          if (!walking) {
-            P.hit[out] = make_float2(s.t, __int_as_float(s.slot));
-            live = false;
-          }
-        }
-      }
-      if (live && walking && np < 2) {
-        walking = !bin_step(nodes, s, stack, &visits, &err, queue_leaf);
-        if (!walking && np == 0) {
-          P.hit[out] = make_float2(s.t, __int_as_float(s.slot));
-          live = false;
-        }
-      }
-    }
+          return p.scenes[p.views[m.x].scene_index];
+        },
+        [&](int slot, const Hit& h) { P.hit[slot] = make_float2(h.t, __int_as_float(h.slot)); }, refined, visits,
+        tests, err);
   }
   block_count(&p.ctr->ref_hit, refined);
   block_count(&p.ctr->node_visits, visits);
@@ -931,6 +959,60 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
 }
 
 // ------------------------------------------------------------------ shadow
+// Next-event contribution of a finished shadow ray: if it reached the emitter
+// it was aimed at, the emitter is measured after the segment's footprint
+// update and the rough lobe's value is weighted against the emitter sampler
+// by the power heuristic (the NEE request and lobe terms were stored by
+// k_shade), and the result is added to the slot's sample contribution.
+template <int NS>
+__device__ __forceinline__ void shadow_finish(const RenderParams& p, int slot, const Hit& h) {
+  const Pool& P = p.pool;
+  const int4 m = P.meta[slot];
+  const DevView& V = p.views[m.x];
+  const DevScene& S = p.scenes[V.scene_index];
+  const float4 sd = P.shd[slot];
+  const int tag = __float_as_int(sd.w);
+  const int ei = tag & 0xffff, seg = tag >> 16;
+  if (h.slot < 0 || S.tri_mat[h.slot] != S.emitters[ei].mat) return;
+  const float4 a0 = P.od0[slot], a1 = P.od1[slot];
+  const float3 x = xyz(a0), w = xyz(sd);
+  const int WH = V.W * V.H;
+  const int bin = m.y / WH;
+  const int pixel = m.y - bin * WH;
+  const int smp = bin_first_sample(V, bin) + meta_k(m.z) * V.nb;
+  const float lambda = bin_lambda(V, bin);
+  const float kw = 2.0f * kPi / lambda;
+  float b2 = a0.w, ro = a1.w;
+  footprint_update(h.t, kw, b2, ro);
+  const float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallNeeFoot);
+  const float val = measure_emitter(S, ei, x + h.t * w, w, b2, ro, kw, lambda, u.x, u.y);
+  if (val == 0.0f) return;
+  // lobe density toward w and the power-heuristic weight against the
+  // emitter's direction sampler
+  const float4 sm = P.shm[slot];
+  const float f = rough_density(sm.y, sm.z, sm.x) * sm.w;
+  const float3 nE = emitter_normal(S, ei);
+  const float s_ray2 = 1.0f / (2.0f * V.beta0 * V.beta0 * kw * kw);
+  const float kap = 1.0f / (s_ray2 + src_spread2(lambda, S.mats[S.emitters[ei].mat].coh_len_um));
+  const float pn = vmf(w, -nE, kap) / (float)S.n_emitters;
+  if (f > 0.0f && pn > 0.0f) {
+    const float wm = pn * pn / (pn * pn + f * f) * (f / pn) * val;
+    const float4 c = P.shc[slot];
+    float4 pt = P.part[slot];
+    pt.x += c.x * wm;
+    if (NS == 4) {
+      pt.y += c.y * wm;
+      pt.z += c.z * wm;
+      pt.w += c.w * wm;
+    }
+    P.part[slot] = pt;
+  }
+}
+
+// NEE shadow rays: closest hit from the interaction point toward the sampled
+// emitter direction, then shadow_finish, one ray per thread per pass (the
+// shadow queue is a third as long as the trace queue: too short for
+// lane_trace's refill schedule to pay for itself).
 template <int NS, bool WIDE>
 __global__ void __launch_bounds__(256, GR_SHADOW_MIN_BLOCKS) k_shadow(RenderParams p) {
   const Pool& P = p.pool;
@@ -939,47 +1021,11 @@ __global__ void __launch_bounds__(256, GR_SHADOW_MIN_BLOCKS) k_shadow(RenderPara
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int slot = P.sq[i];
     const int4 m = P.meta[slot];
-    const DevView& V = p.views[m.x];
-    const DevScene& S = p.scenes[V.scene_index];
-    const float4 a0 = P.od0[slot], a1 = P.od1[slot], sd = P.shd[slot];
-    const int tag = __float_as_int(sd.w);
-    const int ei = tag & 0xffff, seg = tag >> 16;
-    const float3 x = xyz(a0), w = xyz(sd);
-    Hit h = WIDE ? closest_hit_wide(S, x, w, m.w, &refined, &visits, &tests, &err)
-                 : closest_hit(S, x, w, m.w, &refined, &visits, &tests, &err);
-    if (h.slot < 0 || S.tri_mat[h.slot] != S.emitters[ei].mat) continue;
-    const int WH = V.W * V.H;
-    const int bin = m.y / WH;
-    const int pixel = m.y - bin * WH;
-    const int smp = bin_first_sample(V, bin) + meta_k(m.z) * V.nb;
-    const float lambda = bin_lambda(V, bin);
-    const float kw = 2.0f * kPi / lambda;
-    float b2 = a0.w, ro = a1.w;
-    footprint_update(h.t, kw, b2, ro);
-    const float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallNeeFoot);
-    const float val = measure_emitter(S, ei, x + h.t * w, w, b2, ro, kw, lambda, u.x, u.y);
-    if (val != 0.0f) {
-      // lobe density toward w and the power-heuristic weight against the
-      // emitter's direction sampler
-      const float4 sm = P.shm[slot];
-      const float f = rough_density(sm.y, sm.z, sm.x) * sm.w;
-      const float3 nE = emitter_normal(S, ei);
-      const float s_ray2 = 1.0f / (2.0f * V.beta0 * V.beta0 * kw * kw);
-      const float kap = 1.0f / (s_ray2 + src_spread2(lambda, S.mats[S.emitters[ei].mat].coh_len_um));
-      const float pn = vmf(w, -nE, kap) / (float)S.n_emitters;
-      if (f > 0.0f && pn > 0.0f) {
-        const float wm = pn * pn / (pn * pn + f * f) * (f / pn) * val;
-        const float4 c = P.shc[slot];
-        float4 pt = P.part[slot];
-        pt.x += c.x * wm;
-        if (NS == 4) {
-          pt.y += c.y * wm;
-          pt.z += c.z * wm;
-          pt.w += c.w * wm;
-        }
-        P.part[slot] = pt;
-      }
-    }
+    const DevScene& S = p.scenes[p.views[m.x].scene_index];
+    const float3 o = xyz(P.od0[slot]), d = xyz(P.shd[slot]);
+    const Hit h = WIDE ? closest_hit_wide(S, o, d, m.w, &refined, &visits, &tests, &err)
+                       : closest_hit(S, o, d, m.w, &refined, &visits, &tests, &err);
+    shadow_finish<NS>(p, slot, h);
   }
   block_count(&p.ctr->ref_hit, refined);
   block_count(&p.ctr->node_visits, visits);
