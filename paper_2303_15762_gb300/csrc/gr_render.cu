@@ -33,8 +33,12 @@ enum { ST_IDLE = 0, ST_ACTIVE = 1, ST_DONE = 2 };
 
 // Minimum resident 256-thread blocks per SM requested for the traversal
 // kernels (register budget 65536 / (256 x blocks)).
+// binary-tree trace kernel: 128-thread blocks, 7 per SM (<= 72 registers)
 #ifndef GR_TRACE_MIN_BLOCKS
-#define GR_TRACE_MIN_BLOCKS 3
+#define GR_TRACE_MIN_BLOCKS 7
+#endif
+#ifndef GR_TRACE_BLOCK
+#define GR_TRACE_BLOCK 128
 #endif
 #ifndef GR_SHADOW_MIN_BLOCKS
 #define GR_SHADOW_MIN_BLOCKS 3
@@ -434,7 +438,7 @@ __device__ __forceinline__ void lane_trace(const RenderParams& p, int n, int* cu
 // tree one ray per thread per pass.  The queue holds continuing segments from
 // the front of its array and camera rays from the back.
 template <bool WIDE>
-__global__ void __launch_bounds__(256, GR_TRACE_MIN_BLOCKS) k_trace(RenderParams p) {
+__global__ void __launch_bounds__(WIDE ? 256 : GR_TRACE_BLOCK, WIDE ? 3 : GR_TRACE_MIN_BLOCKS) k_trace(RenderParams p) {
   const Pool& P = p.pool;
   const int front = *(volatile int*)&p.ctr->tq_count;
   const int n = front + *(volatile int*)&p.ctr->tq_back;
@@ -1212,6 +1216,9 @@ int sm_count(int dev) {
 // One wavefront iteration.  With `ev` (profiling) an event is recorded before
 // each kernel and after the last, so each kernel's device time is measured on
 // the stream it runs on.
+// Block size of the binary-tree trace kernel for a render's block size.
+int trace_block(int block) { return block < GR_TRACE_BLOCK ? block : GR_TRACE_BLOCK; }
+
 template <int NS, typename TT>
 cudaError_t launch_iteration(const RenderParams& p, int grid_regen, int grid_trace, int grid_shade, int grid_shadow,
                              int block, size_t smem, cudaStream_t st, cudaEvent_t* ev) {
@@ -1222,7 +1229,7 @@ cudaError_t launch_iteration(const RenderParams& p, int grid_regen, int grid_tra
   if (wide)
     k_trace<true><<<grid_trace, block, 0, st>>>(p);
   else
-    k_trace<false><<<grid_trace, block, 0, st>>>(p);
+    k_trace<false><<<grid_trace, trace_block(block), 0, st>>>(p);
   if (ev) cudaEventRecord(ev[2], st);
   k_shade<NS, TT><<<grid_shade, block, smem, st>>>(p);
   if (ev) cudaEventRecord(ev[3], st);
@@ -1422,9 +1429,9 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const int dev = f->device;
   const int sms = sm_count(dev);
   const int block = o.block > 0 ? o.block : 256;
-  auto grid_for = [&](const void* fn, size_t dyn) {
+  auto grid_for = [&](const void* fn, size_t dyn, int blk = 0) {
     int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, block, dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, blk > 0 ? blk : block, dyn);
     if (per < 1) per = 1;
     return sms * per;
   };
@@ -1443,12 +1450,14 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
                : o.table_dtype == GR_TABLE_F16 ? (const void*)k_shade<4, __half>
                                                : (const void*)k_shade<4, __nv_bfloat16>;
   }
-  g_trace = grid_for((const void*)k_trace<false>, 0);
+  const bool wide_bvh = (o.flags & GR_FLAG_WIDE_BVH) != 0;
+  const int tblk = wide_bvh ? block : trace_block(block);
+  g_trace = wide_bvh ? grid_for((const void*)k_trace<true>, 0) : grid_for((const void*)k_trace<false>, 0, tblk);
   g_shade = grid_for(shade_fn, smem);
   // never more blocks than the pool needs
   const int gmax = (P + block - 1) / block;
   g_regen = std::min(g_regen, gmax);
-  g_trace = std::min(g_trace, gmax);
+  g_trace = std::min(g_trace, (P + tblk - 1) / tblk);
   g_shade = std::min(g_shade, gmax);
   g_shadow = std::min(g_shadow, gmax);
 
@@ -1844,9 +1853,9 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   // --- launch shapes (same rule as gr_render)
   const int sms = sm_count(dev);
   const int block = o.block > 0 ? o.block : 256;
-  auto grid_for = [&](const void* fn, size_t dyn) {
+  auto grid_for = [&](const void* fn, size_t dyn, int blk = 0) {
     int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, block, dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, blk > 0 ? blk : block, dyn);
     return sms * std::max(per, 1);
   };
   const void* shade_fn = NSv == 1 ? (o.table_dtype == GR_TABLE_F32 ? (const void*)k_shade<1, float>
@@ -1857,7 +1866,11 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
                                                                      : (const void*)k_shade<4, __nv_bfloat16>);
   const int gmax = (int)((P + block - 1) / block);
   const int g_regen = std::min(gmax, grid_for(NSv == 1 ? (const void*)k_regen<1> : (const void*)k_regen<4>, 0));
-  const int g_trace = std::min(gmax, grid_for((const void*)k_trace<false>, 0));
+  const bool wide_bvh = (o.flags & GR_FLAG_WIDE_BVH) != 0;
+  const int tblk = wide_bvh ? block : trace_block(block);
+  const int g_trace =
+      std::min((int)((P + tblk - 1) / tblk), wide_bvh ? grid_for((const void*)k_trace<true>, 0)
+                                                       : grid_for((const void*)k_trace<false>, 0, tblk));
   const int g_shade = std::min(gmax, grid_for(shade_fn, smem));
   const int g_shadow = std::min(gmax, grid_for(NSv == 1 ? (const void*)k_shadow<1, false> : (const void*)k_shadow<4, false>, 0));
   // --- iteration loop; the host reads the device counters into a stack copy
