@@ -174,7 +174,7 @@ V3 vmf_sample(V3 mu, double kappa, double u0, double u1) {
 }
 
 // ---------------------------------------------------------------- scene
-enum MatType { MAT_ABSORBER = 0, MAT_GRATING = 1, MAT_ROUGH = 2, MAT_MIRROR = 3, MAT_EMITTER = 4 };
+enum MatType { MAT_ABSORBER = 0, MAT_GRATING = 1, MAT_ROUGH = 2, MAT_MIRROR = 3, MAT_EMITTER = 4, MAT_DIELECTRIC = 5 };
 
 struct Material {
   int type;
@@ -184,6 +184,7 @@ struct Material {
   V3 gdir;
   double sigma_h_um, corr_len_um;
   double Le, coh_len_um;
+  double cauchy_b_um2;  // dielectric: index n(lambda) = n_re + cauchy_b_um2 / lambda^2
 };
 
 struct Light {
@@ -450,6 +451,49 @@ M4 mueller_diag(cplx a, cplx b) {
   return r;
 }
 
+// Smooth dielectric interface (Eq. K_reflection_refraction, with refraction):
+// light meets the interface from the medium of index eta_a at cos_i, the far
+// side has eta_b; n_rel = eta_b / eta_a.  Born & Wolf amplitudes with
+// cos_t = sqrt(1 - (1 - cos_i^2) / n_rel^2):
+//   r_s = (cos_i - n_rel cos_t) / (cos_i + n_rel cos_t)
+//   r_p = (n_rel cos_i - cos_t) / (n_rel cos_i + cos_t)
+//   t_s = 2 cos_i / (cos_i + n_rel cos_t),  t_p = 2 cos_i / (n_rel cos_i + cos_t)
+// and power transmittances T_x = (n_rel cos_t / cos_i) |t_x|^2, so that
+// R_x + T_x = 1.  Past the critical angle cos_t is imaginary, |r_s| = |r_p| = 1
+// and nothing is transmitted.  R, T are the unpolarised averages.
+struct Dielectric {
+  cplx rs, rp;
+  double ts, tp;
+  double cos_t;
+  bool tir;
+  double R, T;
+};
+void fresnel_dielectric(double cos_i, double n_rel, Dielectric* D) {
+  fresnel_conductor(cos_i, n_rel, 0.0, &D->rs, &D->rp);
+  const double sin2_t = (1.0 - cos_i * cos_i) / (n_rel * n_rel);
+  D->tir = sin2_t >= 1.0;
+  if (D->tir) {
+    D->cos_t = 0.0;
+    D->ts = D->tp = 0.0;
+    D->R = 1.0;
+    D->T = 0.0;
+    return;
+  }
+  D->cos_t = std::sqrt(1.0 - sin2_t);
+  D->ts = 2.0 * cos_i / (cos_i + n_rel * D->cos_t);
+  D->tp = 2.0 * cos_i / (n_rel * cos_i + D->cos_t);
+  D->R = 0.5 * (std::norm(D->rs) + std::norm(D->rp));
+  const double f = n_rel * D->cos_t / cos_i;
+  D->T = 0.5 * f * (D->ts * D->ts + D->tp * D->tp);
+}
+
+// Refracted unit direction (Snell's law in vector form) for incidence d on a
+// surface whose normal n faces the incident side (dot(d, n) < 0).
+V3 refract_dir(V3 d, V3 n, double n_rel, double cos_i, double cos_t) {
+  const double e = 1.0 / n_rel;
+  return e * d + (e * cos_i - cos_t) * n;
+}
+
 // Rotation of the Stokes reference frame: frame B's x axis at angle phi from
 // frame A's x axis (counter-clockwise about the common propagation direction).
 M4 stokes_rotation(double phi) {
@@ -483,6 +527,7 @@ struct PathState {
   double rho;
   double k;        // |k0| (1/um)
   double lambda;   // um
+  double eta;      // refractive index of the medium the ray travels in (1 = air)
   double s_ray2;   // invariant angular variance (sigma_k/|k|)^2 (rad^2)
   int prev_prim;
   // throughput: scalar (n_stokes == 1) or Mueller matrix with frame x axis
@@ -690,6 +735,7 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
     P.d = normalize(fw + sx * right + sy * upc);
   }
   P.prev_prim = -1;
+  P.eta = 1.0;
   P.t = 1.0;
   P.T = m4_identity();
   P.xf = normalize(right - dot(right, P.d) * P.d);
@@ -711,8 +757,8 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
       add_vec(result, ns, col, m);
       return;
     }
-    // footprint update over the segment (z in um)
-    propagate(&P.beta2, &P.rho, th * 1e6 / P.k);
+    // footprint update over the segment (z in um; |k| = eta k0 in a medium)
+    propagate(&P.beta2, &P.rho, th * 1e6 / (P.k * P.eta));
     V3 x = P.o + th * P.d;
     const Tri& T = S.tris[prim];
     const Material& M = S.mats[T.mat];
@@ -755,7 +801,34 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
     // s-p frames at the incidence angle of the arriving ray; diffractive lobes
     // are scaled by the same matrix (reading).
     M4 MF = m4_identity();
-    if (M.fresnel == 1) {
+    V3 d_dielectric = d_in;
+    double eta_next = P.eta;
+    if (M.type == MAT_DIELECTRIC) {
+      // the front (counter-clockwise) face looks out into air; reflection or
+      // refraction is chosen with the unpolarised reflectance R, and the
+      // Mueller weight divided by the choice's probability; a refracted
+      // radiance carries (eta_a / eta_b)^2 (camera side over light side)
+      const double eta_m = M.n_re + M.cauchy_b_um2 / (P.lambda * P.lambda);
+      const bool entering = dot(P.d, tri_normal(T)) < 0.0;
+      const double eta_a = entering ? 1.0 : eta_m, eta_b = entering ? eta_m : 1.0;
+      const double n_rel = eta_b / eta_a;
+      Dielectric D;
+      fresnel_dielectric(cos_i, n_rel, &D);
+      rng.draw(seg, CALL_LOBE, u);
+      if (u[0] < D.R) {
+        MF = mueller_diag(D.rs, D.rp);
+        for (int i = 0; i < 4; ++i)
+          for (int j = 0; j < 4; ++j) MF.m[i][j] /= D.R;
+        d_dielectric = d_in + (2.0 * cos_i) * n;
+      } else {
+        MF = mueller_diag(cplx(D.ts, 0.0), cplx(D.tp, 0.0));
+        const double f = (n_rel * D.cos_t / cos_i) * (eta_a / eta_b) * (eta_a / eta_b) / (1.0 - D.R);
+        for (int i = 0; i < 4; ++i)
+          for (int j = 0; j < 4; ++j) MF.m[i][j] *= f;
+        d_dielectric = refract_dir(d_in, n, n_rel, cos_i, D.cos_t);
+        eta_next = eta_b;
+      }
+    } else if (M.fresnel == 1) {
       cplx rs, rp;
       fresnel_conductor(cos_i, M.n_re, M.n_im, &rs, &rp);
       MF = mueller_diag(rs, rp);
@@ -802,6 +875,8 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
       d_out = L.dir[pick];
     } else if (M.type == MAT_MIRROR) {
       d_out = d_in + (2.0 * cos_i) * n;
+    } else if (M.type == MAT_DIELECTRIC) {
+      d_out = d_dielectric;  // chosen above with the same uniform
     } else {  // MAT_ROUGH
       g_r = std::pow(2.0 * P.k * M.sigma_h_um * cos_i, 2);
       double m;
@@ -862,7 +937,7 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
           double pn = vmf(w, neg(ne), kap) / n_emit;
           if (f > 0.0 && pn > 0.0) {
             double b2 = P.beta2, r = P.rho;
-            propagate(&b2, &r, ts * 1e6 / P.k);
+            propagate(&b2, &r, ts * 1e6 / (P.k * P.eta));
             rng.draw(seg, CALL_NEE_FOOT, uf);
             double m = measure_emitter(S, sp, x + ts * w, w, b2, r, P.k, P.lambda, uf[0], uf[1]);
             double wmis = pn * pn / (pn * pn + f * f);
@@ -885,6 +960,7 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
     }
     P.o = x;
     P.d = d_out;
+    P.eta = eta_next;
     P.prev_prim = prim;
     P.prev_delta = delta;
     P.prev_pdf = pdf;
@@ -897,6 +973,40 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
 extern "C" {
 
 int oracle_abi_version() { return 1; }
+
+// Dielectric interface at cos_i with relative index n_rel (test access):
+// out = [Rs, Rp, Ts, Tp, R, T, cos_t, tir].
+void oracle_fresnel_dielectric(double cos_i, double n_rel, double* out) {
+  Dielectric D;
+  fresnel_dielectric(cos_i, n_rel, &D);
+  const double f = D.tir ? 0.0 : n_rel * D.cos_t / cos_i;
+  out[0] = std::norm(D.rs);
+  out[1] = std::norm(D.rp);
+  out[2] = f * D.ts * D.ts;
+  out[3] = f * D.tp * D.tp;
+  out[4] = D.R;
+  out[5] = D.T;
+  out[6] = D.cos_t;
+  out[7] = D.tir ? 1.0 : 0.0;
+}
+
+// Refracted direction for incidence d at a surface with normal n (either
+// orientation) from index eta_a into eta_b (test access); returns 0 under total
+// internal reflection.
+int oracle_refract(const double* d, const double* n, double eta_a, double eta_b, double* out) {
+  V3 dd = v3(d[0], d[1], d[2]), nn = v3(n[0], n[1], n[2]);
+  if (dot(dd, nn) > 0.0) nn = neg(nn);
+  const double cos_i = -dot(dd, nn);
+  Dielectric D;
+  fresnel_dielectric(cos_i, eta_b / eta_a, &D);
+  if (D.tir) return 0;
+  V3 t = refract_dir(dd, nn, eta_b / eta_a, cos_i, D.cos_t);
+  out[0] = t.x;
+  out[1] = t.y;
+  out[2] = t.z;
+  return 1;
+}
+
 
 void oracle_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) { philox4x32_10(ctr, key, out); }
 
@@ -941,6 +1051,7 @@ static Material read_material(const float* m) {
   M.corr_len_um = m[10];
   M.Le = m[11];
   M.coh_len_um = m[12];
+  M.cauchy_b_um2 = m[13];
   return M;
 }
 

@@ -8,9 +8,10 @@ seeded scene generator and marshal them independently.
 
 Input layouts (plain arrays written by the scene generator):
   material row float32[16]: 0 type (0 absorber, 1 grating, 2 rough, 3 mirror,
-      4 emitter), 1 fresnel (0 unit, 1 conductor), 2 n_re, 3 n_im,
-      4 period_um, 5 height_um (peak to peak), 6-8 grating direction,
-      9 sigma_h_um, 10 corr_len_um, 11 Le, 12 coh_len_um, 13-15 unused
+      4 emitter, 5 dielectric), 1 fresnel (0 unit, 1 conductor), 2 n_re,
+      3 n_im, 4 period_um, 5 height_um (peak to peak), 6-8 grating direction,
+      9 sigma_h_um, 10 corr_len_um, 11 Le, 12 coh_len_um, 13 cauchy_b_um2
+      (dielectric index n_re + cauchy_b_um2 / lambda^2), 14-15 unused
   light row float32[8]: 0 type (0 distant, 1 constant environment),
       1-3 direction toward the source, 4 E, 5 coh_len_um, 6-7 unused
 """
@@ -86,6 +87,9 @@ def lib():
     L.oracle_render.restype = L_
     L.oracle_lbvh_build.argtypes = [I, P, P, P, P]
     L.oracle_lbvh_build.restype = I
+    L.oracle_fresnel_dielectric.argtypes = [D, D, P]
+    L.oracle_refract.argtypes = [P, P, D, D, P]
+    L.oracle_refract.restype = I
     _lib = L
     return L
 
@@ -132,6 +136,22 @@ def propagate(beta2, rho, zbar):
     o = np.zeros(2)
     lib().oracle_propagate(float(beta2), float(rho), float(zbar), _p(o))
     return o[0], o[1]
+
+
+def fresnel_dielectric(cos_i, n_rel):
+    """Smooth dielectric interface: dict of Rs, Rp, Ts, Tp (power), R, T
+    (unpolarised), cos_t and tir."""
+    o = np.zeros(8)
+    lib().oracle_fresnel_dielectric(float(cos_i), float(n_rel), _p(o))
+    return dict(Rs=o[0], Rp=o[1], Ts=o[2], Tp=o[3], R=o[4], T=o[5], cos_t=o[6], tir=bool(o[7]))
+
+
+def refract(d, n, eta_a, eta_b):
+    """Refracted unit direction from index eta_a into eta_b, or None under
+    total internal reflection."""
+    o = np.zeros(3)
+    ok = lib().oracle_refract(_p(_d3(d)), _p(_d3(n)), float(eta_a), float(eta_b), _p(o))
+    return o if ok else None
 
 
 def grating_lobes(mat_row, d_in, n, lambda_um, renorm=True, cap=128):

@@ -33,12 +33,12 @@ import math
 
 import numpy as np
 
-MAT_ABSORBER, MAT_GRATING, MAT_ROUGH, MAT_MIRROR, MAT_EMITTER = 0, 1, 2, 3, 4
+MAT_ABSORBER, MAT_GRATING, MAT_ROUGH, MAT_MIRROR, MAT_EMITTER, MAT_DIELECTRIC = 0, 1, 2, 3, 4, 5
 LIGHT_DISTANT, LIGHT_ENV = 0, 1
 
 
 def material(type_, fresnel=0, n_re=1.0, n_im=0.0, period_um=0.0, height_um=0.0,
-             gdir=(1.0, 0.0, 0.0), sigma_h_um=0.0, corr_len_um=1.0, Le=0.0, coh_len_um=0.0):
+             gdir=(1.0, 0.0, 0.0), sigma_h_um=0.0, corr_len_um=1.0, Le=0.0, coh_len_um=0.0, cauchy_b_um2=0.0):
     row = np.zeros(16, dtype=np.float32)
     row[0] = type_
     row[1] = fresnel
@@ -51,6 +51,7 @@ def material(type_, fresnel=0, n_re=1.0, n_im=0.0, period_um=0.0, height_um=0.0,
     row[10] = corr_len_um
     row[11] = Le
     row[12] = coh_len_um
+    row[13] = cauchy_b_um2
     return row
 
 
@@ -93,6 +94,18 @@ def _scene(tris, tri_mat, mats, lights):
                 tri_mat=np.ascontiguousarray(np.asarray(tri_mat, dtype=np.int32)),
                 mats=np.ascontiguousarray(np.asarray(mats, dtype=np.float32).reshape(-1, 16)),
                 lights=np.ascontiguousarray(np.asarray(lights, dtype=np.float32).reshape(-1, 8)))
+
+
+def _box(center, half, rot_y_deg=0.0):
+    """12 triangles of a box, wound counter-clockwise seen from outside (outward
+    normals), rotated about the vertical axis through its centre."""
+    c = np.asarray(center, dtype=np.float64)
+    hx, hy, hz = half
+    X, Y, Z = np.array([hx, 0, 0]), np.array([0, hy, 0]), np.array([0, 0, hz])
+    faces = [_quad(+Z, X, Y), _quad(-Z, Y, X), _quad(+X, Y, Z), _quad(-X, Z, Y), _quad(+Y, Z, X), _quad(-Y, X, Z)]
+    t = math.radians(rot_y_deg)
+    R = np.array([[math.cos(t), 0, math.sin(t)], [0, 1, 0], [-math.sin(t), 0, math.cos(t)]])
+    return np.concatenate(faces, axis=0) @ R.T + c
 
 
 # ---------------------------------------------------------------- grating workload
@@ -240,6 +253,42 @@ def procedural_scene(seed=2, n_objects=64, target_tris=100_000, n_emitters=None,
         tri_mat += [em, em]
     T = np.concatenate([np.asarray(t).reshape(-1, 3, 3) for t in tris], axis=0)
     return _scene(T, tri_mat, mats, np.zeros((0, 8), dtype=np.float32))
+
+
+def dielectric_scene(n_re=1.5, cauchy_b_um2=0.0042, slab_half=(0.15, 0.1, 0.01), tilt_deg=25.0, with_ground=True,
+                     env=0.0, distant=True, emitter=True):
+    """A glass slab (index n_re + cauchy_b_um2 / lambda^2, closed box with
+    outward faces) tilted about the vertical axis, above a rough conductor
+    ground, lit by a distant source, an emissive quad and optionally a
+    constant environment."""
+    tris, tri_mat, mats, lights = [], [], [], []
+    mats.append(material(MAT_DIELECTRIC, n_re=n_re, cauchy_b_um2=cauchy_b_um2))
+    box = _box((0.0, 0.12, 0.0), slab_half, tilt_deg)
+    tris.append(box)
+    tri_mat += [0] * len(box)
+    if with_ground:
+        mats.append(material(MAT_ROUGH, fresnel=1, n_re=0.3, n_im=3.5, sigma_h_um=0.15, corr_len_um=4.0))
+        g = _quad((0, 0, 0), (0, 0, 0.5), (0.5, 0, 0))  # normal +y
+        tris.append(g)
+        tri_mat += [len(mats) - 1] * 2
+    if emitter:
+        mats.append(material(MAT_EMITTER, Le=1.0, coh_len_um=20.0))
+        q = _quad((0.05, 0.45, 0.1), (0.08, 0, 0), (0, 0, 0.08))  # normal -y: faces down
+        tris.append(q)
+        tri_mat += [len(mats) - 1] * 2
+    if distant:
+        lights.append(light(LIGHT_DISTANT, (0.35, 0.9, 0.25), 1.0, 0.0))
+    if env > 0.0:
+        lights.append(light(LIGHT_ENV, (0, 0, 1), env, 0.0))
+    return _scene(np.concatenate([np.asarray(t).reshape(-1, 3, 3) for t in tris]), tri_mat, mats,
+                  np.asarray(lights, dtype=np.float32).reshape(-1, 8))
+
+
+def dielectric_view(width=48, height=40, spp=32, n_bins=8, n_stokes=4, max_depth=8, first_sample=0):
+    """Camera looking through the tilted slab at the ground."""
+    return view(eye=(0.0, 0.22, 0.6), look_at=(0.0, 0.08, 0.0), up=(0, 1, 0), vfov_deg=40.0, width=width,
+                height=height, n_bins=n_bins, n_stokes=n_stokes, max_depth=max_depth, spp=spp,
+                first_sample=first_sample)
 
 
 def procedural_view(width=512, height=512, spp=256, n_bins=32, n_stokes=4, max_depth=3,
