@@ -72,11 +72,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-crop", type=int, default=128, help="side of the oracle's centre crop")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", choices=["procedural", "batched", "serving", "precision"], default="procedural",
+    ap.add_argument("--workload", choices=["procedural", "batched", "serving", "precision", "dielectric"],
+                    default="procedural",
                     help="procedural: the headline single-view workload; batched: 64 views/scenes, plain "
                          "per-view FP32 form vs the autotuned single-graph form; serving: "
                          "Poisson-arriving progressive requests; precision: FP32/FP16/BF16 order tables, "
-                         "image and per-quantity errors vs the FP64 oracle")
+                         "image and per-quantity errors vs the FP64 oracle; dielectric: the procedural "
+                         "workload with refracting glass slabs")
     ap.add_argument("--views", type=int, default=64)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--rates", default="5,50,100", help="serving: further arrival rates to sweep (req/s)")
@@ -112,13 +114,16 @@ def job_throughput(samples_per_rank, t_max_ms, world):
 def workload(args, rank):
     from paper_2303_15762_gb300 import scenegen as sg
     scene = sg.procedural_scene(seed=2)
+    if args.workload == "dielectric":
+        scene = sg.add_glass(scene)
     view = sg.procedural_view(width=args.size, height=args.size, spp=args.spp, view_index=rank)
     return scene, view
 
 
 def workload_name(args, scene):
-    return ("procedural scene, %d tris, %dx%d, %d spp, 32 bins 400-700 nm, 4 Stokes, depth<=3, NEE+MIS"
-            % (len(scene["tri_mat"]), args.size, args.size, args.spp))
+    glass = " with 8 dispersive glass slabs (n = 1.5 + 0.0042/lambda^2)" if args.workload == "dielectric" else ""
+    return ("procedural scene%s, %d tris, %dx%d, %d spp, 32 bins 400-700 nm, 4 Stokes, depth<=3, NEE+MIS"
+            % (glass, len(scene["tri_mat"]), args.size, args.size, args.spp))
 
 
 class ClockSampler:

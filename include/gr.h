@@ -58,7 +58,8 @@ enum {
   GR_MAT_GRATING = 1,  /* sinusoidal grating, Eq. K_grating */
   GR_MAT_ROUGH = 2,    /* Gaussian-statistics rough surface, Eq. K_surface_HS */
   GR_MAT_MIRROR = 3,   /* smooth reflector, Eq. K_reflection_refraction */
-  GR_MAT_EMITTER = 4   /* emissive geometry light source (Sec. 7.2) */
+  GR_MAT_EMITTER = 4,  /* emissive geometry light source (Sec. 7.2) */
+  GR_MAT_DIELECTRIC = 5 /* smooth refracting interface, Eq. K_reflection_refraction */
 };
 
 /* One material, 64 bytes.  fresnel: 0 = unit reflectance (Mueller identity),
@@ -71,7 +72,13 @@ enum {
  * Emitter: Le (exitance), coh_len_um (coherence length; angular spread
  * lambda / coh_len per axis, Eq. coherence_diffusivity; 0 = coherent).  An
  * emitter is the planar set of triangles carrying the same emitter material;
- * only its front face (counter-clockwise winding) emits. */
+ * only its front face (counter-clockwise winding) emits.
+ * Dielectric: refractive index n(lambda) = n_re + cauchy_b_um2 / lambda^2
+ * (lambda in um); the front face (counter-clockwise winding) looks out into
+ * air (index 1), so a dielectric body is a closed mesh wound outward; media do
+ * not nest.  Reflection or refraction is chosen by the Fresnel reflectance
+ * (Mueller weights in s-p frames, total internal reflection past the critical
+ * angle); inside, the footprint propagates with |k| = n k0. */
 typedef struct {
   int32_t type;
   int32_t fresnel;
@@ -80,7 +87,8 @@ typedef struct {
   float gdir[3];
   float sigma_h_um, corr_len_um;
   float Le, coh_len_um;
-  float reserved[3];
+  float cauchy_b_um2;
+  float reserved[2];
 } gr_material;
 
 /* Light sources measured on escape (Sec. 7.2): distant source of irradiance E

@@ -33,7 +33,8 @@ class gr_material(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int32), ("fresnel", ctypes.c_int32), ("n_re", ctypes.c_float),
                 ("n_im", ctypes.c_float), ("period_um", ctypes.c_float), ("height_um", ctypes.c_float),
                 ("gdir", ctypes.c_float * 3), ("sigma_h_um", ctypes.c_float), ("corr_len_um", ctypes.c_float),
-                ("Le", ctypes.c_float), ("coh_len_um", ctypes.c_float), ("reserved", ctypes.c_float * 3)]
+                ("Le", ctypes.c_float), ("coh_len_um", ctypes.c_float), ("cauchy_b_um2", ctypes.c_float),
+                ("reserved", ctypes.c_float * 2)]
 
 
 class gr_light(ctypes.Structure):
@@ -158,6 +159,7 @@ def _pack_materials(rows):
         m.n_re, m.n_im, m.period_um, m.height_um = float(r[2]), float(r[3]), float(r[4]), float(r[5])
         m.gdir[:] = [float(x) for x in r[6:9]]
         m.sigma_h_um, m.corr_len_um, m.Le, m.coh_len_um = float(r[9]), float(r[10]), float(r[11]), float(r[12])
+        m.cauchy_b_um2 = float(r[13])
     return arr, len(rows)
 
 

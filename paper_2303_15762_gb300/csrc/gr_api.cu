@@ -66,12 +66,14 @@ gr_status gr_scene_create(const gr_scene_desc* desc, void* cuda_stream, gr_scene
   if (n > (1 << 28)) return fail(GR_E_INVALID, "gr_scene_create: too many triangles");
   for (int i = 0; i < desc->n_mats; ++i) {
     const gr_material& M = desc->mats[i];
-    if (M.type < GR_MAT_ABSORBER || M.type > GR_MAT_EMITTER || M.fresnel < 0 || M.fresnel > 1)
+    if (M.type < GR_MAT_ABSORBER || M.type > GR_MAT_DIELECTRIC || M.fresnel < 0 || M.fresnel > 1)
       return fail(GR_E_INVALID, "gr_scene_create: bad material " + std::to_string(i));
     if (M.type == GR_MAT_GRATING && !(M.period_um > 0.0f))
       return fail(GR_E_INVALID, "gr_scene_create: grating period must be > 0");
     if (M.type == GR_MAT_ROUGH && !(M.corr_len_um > 0.0f))
       return fail(GR_E_INVALID, "gr_scene_create: correlation length must be > 0");
+    if (M.type == GR_MAT_DIELECTRIC && !(M.n_re > 0.0f && M.cauchy_b_um2 >= 0.0f))
+      return fail(GR_E_INVALID, "gr_scene_create: dielectric index must be > 0 (n_re > 0, cauchy_b_um2 >= 0)");
   }
   for (int i = 0; i < desc->n_lights; ++i) {
     const gr_light& L = desc->lights[i];

@@ -576,6 +576,41 @@ __device__ __forceinline__ FresnelM fresnel_conductor(float cos_i, float n_re, f
   return m;
 }
 
+// Smooth dielectric interface (Eq. K_reflection_refraction with refraction),
+// met at cos_i from the medium of index eta_a, relative index n_rel =
+// eta_b / eta_a.  Reflection is chosen when u < R, the unpolarised
+// reflectance (R = 1 past the critical angle), else refraction.  Returns the
+// Mueller entries (as fresnel_conductor) of the chosen lobe divided by its
+// probability; a refraction also carries the radiance factor (eta_a/eta_b)^2
+// and the power factor n_rel cos_t / cos_i of the Born & Wolf amplitudes
+// t_s = 2 cos_i / (cos_i + n_rel cos_t), t_p = 2 cos_i / (n_rel cos_i + cos_t).
+__device__ __forceinline__ FresnelM dielectric_pick(float cos_i, float n_rel, float u, bool& refract, float& cos_t) {
+  const float sin2_t = (1.0f - cos_i * cos_i) / (n_rel * n_rel);
+  FresnelM F = fresnel_conductor(cos_i, n_rel, 0.0f);
+  const bool tir = sin2_t >= 1.0f;
+  const float R = tir ? 1.0f : F.a;
+  refract = !(u < R);
+  cos_t = 0.0f;
+  if (!refract) {
+    const float inv = 1.0f / R;
+    F.a *= inv;
+    F.b *= inv;
+    F.cr *= inv;
+    F.ci *= inv;
+    return F;
+  }
+  cos_t = sqrtf(1.0f - sin2_t);
+  const float ts = 2.0f * cos_i / (cos_i + n_rel * cos_t);
+  const float tp = 2.0f * cos_i / (n_rel * cos_i + cos_t);
+  const float ratio = 1.0f / n_rel;  // eta_a / eta_b
+  const float f = (n_rel * cos_t / cos_i) * (ratio * ratio) / (1.0f - R);
+  F.a = 0.5f * (ts * ts + tp * tp) * f;
+  F.b = 0.5f * (ts * ts - tp * tp) * f;
+  F.cr = ts * tp * f;
+  F.ci = 0.0f;
+  return F;
+}
+
 // s vector of the plane of incidence for propagation k at normal n; falls back
 // to `fb` (orthogonalised against k) near normal incidence.
 __device__ __forceinline__ float3 s_vector(float3 n, float3 k, float3 fb) {

@@ -145,9 +145,10 @@ __device__ __forceinline__ void start_sample(const RenderParams& p, int slot, in
     P.tp[2][slot] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
     P.tp[3][slot] = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
     float3 xf = normalize(V.right - dot(V.right, d) * d);
-    P.xf[slot] = make_float4(xf.x, xf.y, xf.z, 0.0f);
+    P.xf[slot] = make_float4(xf.x, xf.y, xf.z, 1.0f);
   }
-  if (NS == 1) P.xf[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  // xf.w: refractive index of the medium the ray travels in (1 = air)
+  if (NS == 1) P.xf[slot] = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
   P.part[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   P.meta[slot] = make_int4(view, local, meta_pack(k, 0, ST_ACTIVE, 1), -1);
 }
@@ -760,7 +761,8 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
         done = true;
       } else {
         const float t = hh.x;
-        footprint_update(t, kw, beta2, rho);
+        const float eta = xfv.w;  // |k| = eta k0 in the current medium
+        footprint_update(t, kw * eta, beta2, rho);
         const float3 x = o + t * d;
         const int mat = S.tri_mat[hslot];
         const gr_material M = S.mats[mat];
@@ -798,10 +800,22 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
             const float4 v0 = __ldg(&S.tri[3 * hslot]), v1 = __ldg(&S.tri[3 * hslot + 1]),
                          v2 = __ldg(&S.tri[3 * hslot + 2]);
             float3 nrm = normalize(cross(xyz(v1) - xyz(v0), xyz(v2) - xyz(v0)));
-            if (dot(nrm, d) > 0.0f) nrm = -nrm;
+            // the front (counter-clockwise) face looks outward (into air for a dielectric)
+            const bool entering = !(dot(nrm, d) > 0.0f);
+            if (!entering) nrm = -nrm;
             const float cos_i = -dot(d, nrm);
+            const float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallLobe);
             FresnelM F{1.0f, 0.0f, 1.0f, 0.0f};
-            if (M.fresnel == 1) F = fresnel_conductor(cos_i, M.n_re, M.n_im);
+            bool refracted = false;
+            float cos_t = 0.0f, n_rel = 1.0f, eta_next = eta;
+            if (M.type == GR_MAT_DIELECTRIC) {
+              const float eta_m = M.n_re + M.cauchy_b_um2 / (lambda * lambda);
+              n_rel = entering ? eta_m : 1.0f / eta_m;
+              F = dielectric_pick(cos_i, n_rel, u.x, refracted, cos_t);
+              if (refracted) eta_next = entering ? eta_m : 1.0f;
+            } else if (M.fresnel == 1) {
+              F = fresnel_conductor(cos_i, M.n_re, M.n_im);
+            }
             float cn[4];
             float3 s_o = f3(0.f, 0.f, 0.f);
             if (NS == 1) {
@@ -827,7 +841,6 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
               }
             }
             // --- sample the scattered distribution
-            const float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallLobe);
             const float3 t_mir = d - dot(d, nrm) * nrm;
             float3 d_out = d;
             int delta = 1;
@@ -868,6 +881,10 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
               }
             } else if (M.type == GR_MAT_MIRROR) {
               d_out = d + (2.0f * cos_i) * nrm;
+            } else if (M.type == GR_MAT_DIELECTRIC) {
+              // chosen with u.x above; refraction by Snell's law in vector form
+              const float e = 1.0f / n_rel;
+              d_out = refracted ? e * d + (e * cos_i - cos_t) * nrm : d + (2.0f * cos_i) * nrm;
             } else {  // rough
               g_r = 2.0f * kw * M.sigma_h_um * cos_i;
               g_r *= g_r;
@@ -943,8 +960,9 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
               } else {
                 for (int r = 0; r < 4; ++r) P.tp[r][slot] = make_float4(T[r][0], T[r][1], T[r][2], T[r][3]);
                 const float3 xn = s_vector(nrm, -d_out, s_o);
-                P.xf[slot] = make_float4(xn.x, xn.y, xn.z, 0.0f);
+                P.xf[slot] = make_float4(xn.x, xn.y, xn.z, eta_next);
               }
+              if (NS == 1 && refracted) P.xf[slot] = make_float4(0.0f, 0.0f, 0.0f, eta_next);
               if (!delta) P.mis[slot] = mis_rec;
               P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg + 1, ST_ACTIVE, delta), hslot);
             } else {
@@ -987,7 +1005,7 @@ __device__ __forceinline__ void shadow_finish(const RenderParams& p, int slot, c
   const float lambda = bin_lambda(V, bin);
   const float kw = 2.0f * kPi / lambda;
   float b2 = a0.w, ro = a1.w;
-  footprint_update(h.t, kw, b2, ro);
+  footprint_update(h.t, kw * P.xf[slot].w, b2, ro);  // |k| = eta k0 in the ray's medium
   const float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallNeeFoot);
   const float val = measure_emitter(S, ei, x + h.t * w, w, b2, ro, kw, lambda, u.x, u.y);
   if (val == 0.0f) return;

@@ -284,6 +284,23 @@ def dielectric_scene(n_re=1.5, cauchy_b_um2=0.0042, slab_half=(0.15, 0.1, 0.01),
                   np.asarray(lights, dtype=np.float32).reshape(-1, 8))
 
 
+def add_glass(scene, n_glass=8, seed=12, n_re=1.5, cauchy_b_um2=0.0042, extent_m=2.0):
+    """The scene with n_glass closed glass slabs (dielectric, outward faces,
+    random size, height and rotation about the vertical) added among its
+    objects; the original triangles, materials and lights are unchanged."""
+    rng = np.random.default_rng(seed)
+    mats = np.concatenate([scene["mats"], material(MAT_DIELECTRIC, n_re=n_re, cauchy_b_um2=cauchy_b_um2)[None]])
+    gm = len(mats) - 1
+    boxes = []
+    for _ in range(n_glass):
+        half = (rng.uniform(0.08, 0.25), rng.uniform(0.1, 0.3), rng.uniform(0.01, 0.05))
+        c = (rng.uniform(-0.7, 0.7) * extent_m, half[1] + rng.uniform(0.0, 0.2), rng.uniform(-0.7, 0.7) * extent_m)
+        boxes.append(_box(c, half, rng.uniform(0, 180)))
+    verts = np.concatenate([scene["verts"], np.concatenate(boxes).astype(np.float32)])
+    tri_mat = np.concatenate([scene["tri_mat"], np.full(12 * n_glass, gm, dtype=np.int32)])
+    return _scene(verts, tri_mat, mats, scene["lights"])
+
+
 def dielectric_view(width=48, height=40, spp=32, n_bins=8, n_stokes=4, max_depth=8, first_sample=0):
     """Camera looking through the tilted slab at the ground."""
     return view(eye=(0.0, 0.22, 0.6), look_at=(0.0, 0.08, 0.0), up=(0, 1, 0), vfov_deg=40.0, width=width,

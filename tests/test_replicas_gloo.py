@@ -25,7 +25,7 @@ def _rank_main(rank, world, port, q):
     import bench
 
     class A:
-        size, spp = 64, 16
+        size, spp, workload = 64, 16, "procedural"
     scene, view = bench.workload(A, rank)
     ms = 100.0 + 50.0 * rank  # rank 1 is the slow replica
     t_max = bench.reduce_max(ms, world)
@@ -60,5 +60,5 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "2")
 
     class A:
-        size, spp, steps, warmup, gpus = 64, 16, 1, 1, 2
+        size, spp, steps, warmup, gpus, workload = 64, 16, 1, 1, 2, "procedural"
     assert bench.run_reference(A) is None
