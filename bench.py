@@ -72,13 +72,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-crop", type=int, default=128, help="side of the oracle's centre crop")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", choices=["procedural", "batched", "serving", "precision", "dielectric"],
+    ap.add_argument("--workload", choices=["procedural", "batched", "serving", "precision", "dielectric",
+                                           "doubleslit"],
                     default="procedural",
                     help="procedural: the headline single-view workload; batched: 64 views/scenes, plain "
                          "per-view FP32 form vs the autotuned single-graph form; serving: "
                          "Poisson-arriving progressive requests; precision: FP32/FP16/BF16 order tables, "
                          "image and per-quantity errors vs the FP64 oracle; dielectric: the procedural "
-                         "workload with refracting glass slabs")
+                         "workload with refracting glass slabs; doubleslit: footprint-resolved generalized "
+                         "rays through two slits at scale")
     ap.add_argument("--views", type=int, default=64)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--rates", default="5,50,100", help="serving: further arrival rates to sweep (req/s)")
@@ -397,6 +399,51 @@ def run_precision(args):
     print(json.dumps(line))
 
 
+def run_doubleslit(args):
+    """Double slit at scale (Sec. 5.1-5.2 with the footprint-resolved
+    propagation of Sec. 6): 4001 detector elements across +-2000 wavelengths,
+    d = 400, b = 40, z = 10^4, every element integrated over its ~8300
+    directions, each overlapped with 800 aperture samples.  Unit: generalized
+    rays (element x direction) per second; the oracle's FP64 computation of
+    the same sums on a bounded sample of elements is the CPU baseline."""
+    import numpy as np
+    import paper_2303_15762_gb300 as gr
+    from paper_2303_15762_gb300 import scenegen as sg
+    from oracle import doubleslit as ds
+    gr.load()
+    s = sg.double_slit_setup(d=400.0, x0=np.linspace(-2000.0, 2000.0, 4001))
+    th = lambda x0: int(np.ceil((np.arctan((x0 + s["reach"]) / s["z"]) - np.arctan((x0 - s["reach"]) / s["z"]))
+                                / s["dtheta"]))
+    rays = sum(th(x) for x in s["x0"])
+    args_ = (s["x0"], s["x_ap"], s["w_ap"], s["beta"], s["z"], s["k"], s["reach"], s["dtheta"], s["rho_cut"])
+    for _ in range(args.warmup):
+        gr.aperture_backward_2d(*args_)
+    times, walls = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        out, ms = gr.aperture_backward_2d(*args_)
+        walls.append(time.perf_counter() - t0)
+        times.append(ms)
+    ms = statistics.mean(times)
+    # FP64 oracle on 5 elements, scaled per ray
+    sub = s["x0"][::1000]
+    t0 = time.perf_counter()
+    ref = ds.backward_generalized_rays(sub, 400.0, s["beta"], rho_cut=s["rho_cut"])
+    cpu_s = time.perf_counter() - t0
+    cpu_rays = sum(th(x) for x in sub)
+    err = float(np.max(np.abs(out[::1000] - ref)) / np.max(ref))
+    line = {"workload": "doubleslit", "metric": "generalized rays (element x direction) per second, each overlapped "
+            "with the aperture samples", "unit": "Mrays/s", "value": rays / (ms * 1e-3) / 1e6,
+            "ms_per_step": ms, "wall_ms_per_call": 1e3 * statistics.mean(walls), "steps": args.steps,
+            "warmup": args.warmup, "config": {"elements": len(s["x0"]), "rays": rays, "aperture_samples": len(s["x_ap"]),
+                                             "d": 400, "b": 40, "z": 1e4, "beta": s["beta"], "rho_cut": s["rho_cut"]},
+            "overlaps_per_s": rays * len(s["x_ap"]) / (ms * 1e-3),
+            "max_err_vs_oracle_over_peak": err,
+            "cpu_baseline": {"value": cpu_rays / cpu_s / 1e6, "unit": "Mrays/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d of the elements (%d rays), numpy FP64, %.1f s" % (len(sub), cpu_rays, cpu_s)}}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -410,6 +457,9 @@ def main():
         return
     if args.workload == "precision":
         run_precision(args)
+        return
+    if args.workload == "doubleslit":
+        run_doubleslit(args)
         return
     world, rank, local = dist_setup()
     import numpy as np

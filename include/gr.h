@@ -269,6 +269,35 @@ gr_status gr_debug_order_table(float height_um, double lambda_um, int32_t jmax, 
  * and synchronises it. */
 gr_status gr_debug_footprint(int32_t n, const float* in, float* out, void* cuda_stream);
 
+/* Footprint-resolved generalized rays through a 1D aperture in a 2D world:
+ * the paper's double-slit validation (Sec. 5.1-5.2) with the accurate,
+ * footprint-resolved propagation of Sec. 6, at scale.  All lengths in one
+ * unit (that of the wavelength); k = 2 pi / lambda.
+ *   x0[n_det]        detector element centres on the screen; each element is a
+ *                    coherent state of width beta (Eq. wdf_coherent_states)
+ *   x_ap, w_ap[n_ap] samples of the aperture plane at distance z from the
+ *                    screen: positions and field weights (quadrature weight x
+ *                    real field amplitude; the aperture is lit at normal
+ *                    incidence), n_ap <= 16384
+ *   reach, dtheta    each element's directions theta run from
+ *                    atan((x0 - reach)/z) in steps of dtheta up to
+ *                    atan((x0 + reach)/z) (exclusive); reach must cover the
+ *                    aperture plus the states' width there
+ *   rho_cut          truncation radius in units of the propagated width beta'
+ *                    (Sec. 6 uses 2.5; a large value disables truncation)
+ * Each direction is a generalized ray propagated back over z / cos(theta) in
+ * closed form (Eq. K_free_space_propagation from rho = 0: beta'^2 = beta^2 +
+ * zbar^2/beta^2, rho' = zbar/beta^2, zbar = z / (k cos(theta))) and overlapped
+ * with the aperture field; out[n_det] (host) receives
+ * sum_theta |<U_ap, psi_theta>|^2 k cos(theta) dtheta / (2 pi).  Per-direction
+ * terms are formed in FP64, the aperture sums in FP32, the per-element sum in
+ * FP64 in a fixed order.  *kernel_ms (may be NULL) receives the kernel's device
+ * time.  Host buffers; the call synchronises the stream.  GR_E_INVALID for bad
+ * sizes or non-positive lengths. */
+gr_status gr_aperture_backward_2d(int32_t n_det, const double* x0, int32_t n_ap, const double* x_ap,
+                                  const double* w_ap, double beta, double z, double k, double reach, double dtheta,
+                                  double rho_cut, double* out, float* kernel_ms, void* cuda_stream);
+
 /* ---- Rendering without device allocation (no counterpart in the paper).
  *
  * For callers that must not allocate device memory while rendering: a

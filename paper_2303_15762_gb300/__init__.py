@@ -10,7 +10,8 @@ from . import scenegen  # noqa: F401
 
 _NATIVE_NAMES = ("Scene", "Frame", "render", "render_image", "make_opts", "GrError", "lib_handle",
                  "FLAG_NEE", "FLAG_RR", "FLAG_NO_RENORM", "FLAG_WIDE_BVH", "pack_views", "current_stream", "debug_rng",
-                 "render_multi", "measure_fp32_peak", "debug_order_table", "debug_footprint")
+                 "render_multi", "measure_fp32_peak", "debug_order_table", "debug_footprint",
+                 "aperture_backward_2d")
 
 
 def load():

@@ -20,7 +20,7 @@ TABLE_DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
 EXPORTED = ["gr_scene_create", "gr_scene_destroy", "gr_frame_create", "gr_frame_reset", "gr_frame_release",
             "gr_render", "gr_readback", "gr_frame_stats", "gr_scene_bvh", "gr_debug_rng", "gr_render_static", "gr_render_multi",
             "gr_last_error", "gr_abi_version", "gr_measure_fp32_peak", "gr_debug_order_table",
-            "gr_debug_footprint"]
+            "gr_debug_footprint", "gr_aperture_backward_2d"]
 
 
 class GrError(RuntimeError):
@@ -356,3 +356,22 @@ def debug_footprint(quads):
     out = np.zeros((q.shape[0], 2), dtype=np.float32)
     _check(fn(q.shape[0], _ptr(q), _ptr(out), current_stream()))
     return out
+
+
+def aperture_backward_2d(x0, x_ap, w_ap, beta, z, k, reach, dtheta, rho_cut=2.5):
+    """Footprint-resolved generalized rays through a 1D aperture
+    (gr_aperture_backward_2d): returns (intensity per detector element,
+    kernel ms)."""
+    L = lib_handle()
+    fn = L.gr_aperture_backward_2d
+    D = ctypes.c_double
+    fn.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, D, D, D, D, D,
+                   D, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    xa = np.ascontiguousarray(x_ap, dtype=np.float64)
+    wa = np.ascontiguousarray(w_ap, dtype=np.float64)
+    out = np.zeros(len(x0), dtype=np.float64)
+    ms = ctypes.c_float()
+    _check(fn(len(x0), _ptr(x0), len(xa), _ptr(xa), _ptr(wa), beta, z, k, reach, dtheta, rho_cut, _ptr(out),
+              ctypes.byref(ms), current_stream()))
+    return out, ms.value

@@ -11,7 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgr.so")
-SOURCES = ["gr_api.cu", "gr_bvh.cu", "gr_render.cu", "gr_peak.cu"]
+SOURCES = ["gr_api.cu", "gr_bvh.cu", "gr_render.cu", "gr_peak.cu", "gr_aperture.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
               "--expt-relaxed-constexpr"]

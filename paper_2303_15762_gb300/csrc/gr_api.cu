@@ -497,4 +497,20 @@ gr_status gr_debug_footprint(int32_t n, const float* in, float* out, void* cuda_
   return GR_OK;
 }
 
+gr_status gr_aperture_backward_2d(int32_t n_det, const double* x0, int32_t n_ap, const double* x_ap,
+                                  const double* w_ap, double beta, double z, double k, double reach, double dtheta,
+                                  double rho_cut, double* out, float* kernel_ms, void* cuda_stream) {
+  if (!x0 || !x_ap || !w_ap || !out || n_det <= 0 || n_ap <= 0 || n_ap > 16384 || !(beta > 0.0) || !(z > 0.0) ||
+      !(k > 0.0) || !(reach > 0.0) || !(dtheta > 0.0) || !(rho_cut > 0.0))
+    return fail(GR_E_INVALID, "gr_aperture_backward_2d: bad arguments");
+  // bound the direction grid: an element spans at most 2 atan(reach / z), in
+  // at most 2^26 directions
+  const double span = 2.0 * std::atan(reach / z);
+  if (span / dtheta > (double)(1 << 26)) return fail(GR_E_INVALID, "gr_aperture_backward_2d: direction grid too fine");
+  cudaError_t e = gr::aperture_backward_impl(n_det, x0, n_ap, x_ap, w_ap, beta, z, k, reach, dtheta, rho_cut, out,
+                                             (cudaStream_t)cuda_stream, kernel_ms);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_aperture_backward_2d");
+  return GR_OK;
+}
+
 }  // extern "C"

@@ -74,6 +74,11 @@ cudaError_t debug_table_impl(float height_um, double lambda_um, int jmax, int dt
                              cudaStream_t st);
 cudaError_t debug_footprint_impl(int n, const float* host_in, float* host_out, cudaStream_t st);
 
+// Footprint-resolved generalized rays through a 1D aperture (gr_aperture.cu).
+cudaError_t aperture_backward_impl(int n_det, const double* x0_host, int n_ap, const double* xa_host,
+                                   const double* wa_host, double beta, double z, double k, double reach,
+                                   double dtheta, double rho_cut, double* out_host, cudaStream_t st, float* ms);
+
 }  // namespace gr
 
 struct gr_scene {

@@ -315,6 +315,28 @@ def procedural_view(width=512, height=512, spp=256, n_bins=32, n_stokes=4, max_d
                 spp=spp, first_sample=first_sample, view_index=view_index, scene_index=scene_index)
 
 
+# ---------------------------------------------------------------- double slit (2D world)
+def double_slit_setup(d=400.0, b=40.0, z=1e4, wavelength=1.0, sigma_at_slits=100.0, n_per_slit=400,
+                      x0=None, rho_cut=2.5, dkappa=2e-4):
+    """Inputs of the double-slit experiment of Sec. 5.1-5.2 in units of the
+    wavelength: two slits of width b at +-d/2, screen at z, detector states of
+    the pixel-scale width beta whose footprint at the slits has std
+    sigma_at_slits (the smaller root of beta^2 + zbar^2/beta^2 = 2 sigma^2),
+    Gauss-Legendre samples of the unit aperture field, detector centres, and
+    the direction grid (reach around the slits, step dkappa / k)."""
+    k = 2 * math.pi / wavelength
+    zb = z / k
+    s2 = 2 * sigma_at_slits ** 2
+    beta = math.sqrt((s2 - math.sqrt(s2 * s2 - 4 * zb * zb)) / 2)
+    g, w = np.polynomial.legendre.leggauss(n_per_slit)
+    xa = np.concatenate([c + 0.5 * b * g for c in (-d / 2, d / 2)])
+    wa = np.concatenate([0.5 * b * w, 0.5 * b * w])
+    if x0 is None:
+        x0 = np.arange(-600, 601, 100.0)
+    return dict(x0=np.asarray(x0, dtype=np.float64), x_ap=xa, w_ap=wa, beta=beta, z=z, k=k,
+                reach=d / 2 + b + 8 * 150.0, dtheta=dkappa / k, rho_cut=rho_cut, d=d, b=b)
+
+
 # ---------------------------------------------------------------- batched workload
 def batch_views(seed=4, n_views=64, spp=16, tris_range=(5_000, 200_000), side_range=(128, 1024)):
     """64 views, each with its own seeded procedural scene; returns (scenes, views)."""
