@@ -23,6 +23,30 @@ namespace {
 
 constexpr int kApertureThreads = 256;
 
+// 2 pi split as hi + lo with hi the nearest float (Cody & Waite's additive
+// range reduction): x - n (2 pi) is formed as (x - n hi) - n lo with one
+// rounding per step, accurate to a few 1e-7 rad for |x| up to ~1e4.
+constexpr float kTwoPiHi = 6.28318548202514648f;
+constexpr float kTwoPiLo = -1.7484555314695172e-7f;
+constexpr float kInvTwoPi = 0.159154943091895336f;
+
+#ifndef GR_APERTURE_FAST_TRIG
+#define GR_APERTURE_FAST_TRIG 1
+#endif
+
+// (cos x, sin x) for the overlap phases: reduced to [-pi, pi], then the
+// hardware approximation (absolute error ~1e-6 there), below the ~6e-5 rad to
+// which the FP32 phase itself is known.
+__device__ __forceinline__ void phase_cis(float x, float* s, float* c) {
+#if GR_APERTURE_FAST_TRIG
+  const float n = rintf(x * kInvTwoPi);
+  const float r = fmaf(-n, kTwoPiLo, fmaf(-n, kTwoPiHi, x));
+  __sincosf(r, s, c);
+#else
+  sincosf(x, s, c);
+#endif
+}
+
 __global__ void __launch_bounds__(kApertureThreads) k_aperture_backward(int n_det, const double* __restrict__ x0s,
                                                                         int n_ap, const float2* __restrict__ ap,
                                                                         double beta, double z, double k, double reach,
@@ -56,9 +80,13 @@ __global__ void __launch_bounds__(kApertureThreads) k_aperture_backward(int n_de
         const float u = dx * cf;
         if (fabsf(u) > cut) continue;
         const float u2 = u * u * inv2b2;
+#if GR_APERTURE_FAST_TRIG
+        const float g = q.y * __expf(-u2);
+#else
         const float g = q.y * expf(-u2);
+#endif
         float s, co;
-        sincosf(kap * dx - rhof * u2, &s, &co);
+        phase_cis(kap * dx - rhof * u2, &s, &co);
         re += g * co;
         im += g * s;
       }
