@@ -107,15 +107,43 @@ gr_status gr_scene_create(const gr_scene_desc* desc, void* cuda_stream, gr_scene
   std::vector<float4> etris;
   for (size_t g = 0; g < groups.size(); ++g) {
     gr::DevEmitter E;
+    std::memset(&E, 0, sizeof E);
     E.mat = desc->tri_mat[groups[g][0]];
     E.first = (int)(etris.size() / 3);
     E.count = (int)groups[g].size();
-    E.pad = 0;
+    for (int a = 0; a < 3; ++a) {
+      E.lo[a] = 3.4e38f;
+      E.hi[a] = -3.4e38f;
+    }
     for (int t : groups[g])
       for (int k = 0; k < 3; ++k) {
         const float* v = desc->verts + 9 * t + 3 * k;
         etris.push_back(make_float4(v[0], v[1], v[2], 0.0f));
+        for (int a = 0; a < 3; ++a) {
+          E.lo[a] = std::min(E.lo[a], v[a]);
+          E.hi[a] = std::max(E.hi[a], v[a]);
+        }
       }
+    // planar when every vertex lies within 1e-6 of the extent from the first
+    // triangle's plane (the next-event precheck relies on it)
+    {
+      const float* v0 = desc->verts + 9 * groups[g][0];
+      const double e1[3] = {(double)v0[3] - v0[0], (double)v0[4] - v0[1], (double)v0[5] - v0[2]};
+      const double e2[3] = {(double)v0[6] - v0[0], (double)v0[7] - v0[1], (double)v0[8] - v0[2]};
+      double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+      const double ln = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+      double ext = 0.0;
+      for (int a = 0; a < 3; ++a) ext = std::max(ext, (double)E.hi[a] - E.lo[a]);
+      bool planar = ln > 0.0;
+      for (int t : groups[g])
+        for (int k = 0; k < 3 && planar; ++k) {
+          const float* v = desc->verts + 9 * t + 3 * k;
+          const double dist = ((v[0] - (double)v0[0]) * n[0] + (v[1] - (double)v0[1]) * n[1] +
+                               (v[2] - (double)v0[2]) * n[2]) / ln;
+          planar = std::fabs(dist) <= 1e-6 * ext;
+        }
+      E.planar = planar ? 1 : 0;
+    }
     emit.push_back(E);
   }
 

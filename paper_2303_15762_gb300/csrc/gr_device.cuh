@@ -28,10 +28,13 @@ enum Call { kCallJitter = 0, kCallEmitFoot = 1, kCallLobe = 2, kCallNeeDir = 3, 
 
 // ------------------------------------------------------------------ device scene
 struct DevEmitter {
-  int mat;    // emitter material id
-  int first;  // first triangle in emitter_tris
-  int count;  // number of triangles
-  int pad;
+  int mat;       // emitter material id
+  int first;     // first triangle in emitter_tris
+  int count;     // number of triangles
+  int planar;    // 1 if every triangle lies in the first one's plane
+  float lo[3];   // bounding box of the emitter's triangles
+  float hi[3];
+  int pad[2];
 };
 
 struct DevScene {
