@@ -174,7 +174,7 @@ typedef struct {
 typedef struct {
   int64_t samples;        /* path samples completed */
   int64_t segments;       /* ray segments traced (camera + continuation) */
-  int64_t shadow_rays;    /* NEE shadow-ray requests (rays that cannot reach their emitter are not traced) */
+  int64_t shadow_rays;    /* NEE shadow rays traced (directions that cannot reach their emitter are not requested) */
   int64_t refine64_hits;  /* ray-triangle tests decided in FP64 */
   int64_t refine64_lobes; /* grating / Poisson choices decided in FP64 */
   int64_t iterations;     /* wavefront iterations */

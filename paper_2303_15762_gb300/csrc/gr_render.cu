@@ -572,6 +572,28 @@ __device__ float rough_density(float g, float kl2, float r2) {
   return sum;
 }
 
+// Conservative precheck of a next-event ray toward emitter ei: false only if
+// the ray's closest hit cannot be a front-face point of that (planar) emitter
+// -- its plane is behind the ray or met from the back (where the emitter does
+// not emit), or the ray meets the plane outside the emitter's bounding box
+// widened by 1e-4 (1 + t) m, far above the FP32 error of the plane point.
+// Near-grazing rays (|cos| < 1e-3) and non-planar emitters always pass.  A
+// false result means a zero contribution, so the ray is not traced.
+__device__ __forceinline__ bool emitter_reachable(const DevScene& S, int ei, float3 x, float3 w) {
+  const DevEmitter E = S.emitters[ei];
+  if (!E.planar) return true;
+  const float3 ne = emitter_normal(S, ei);
+  const float den = dot(w, ne);
+  if (den >= 0.0f) return false;  // back face or parallel: measured as zero
+  if (den > -1e-3f) return true;
+  const float te = dot(xyz(S.emitter_tris[3 * E.first]) - x, ne) / den;
+  if (!(te > 0.0f)) return false;
+  const float3 q = x + te * w;
+  const float m = 1e-4f * (1.0f + te);
+  return q.x >= E.lo[0] - m && q.x <= E.hi[0] + m && q.y >= E.lo[1] - m && q.y <= E.hi[1] + m &&
+         q.z >= E.lo[2] - m && q.z <= E.hi[2] + m;
+}
+
 // ------------------------------------------------------------------ shade
 // Grating order pick from tabulated weights w_|j| = J_j(pi h / lambda)^2
 // (Eq. K_grating): over the propagating orders (|t_mir + j lambda/Lambda g|^2
@@ -939,7 +961,7 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
               const float kap = 1.0f / (s_ray2 + src_spread2(lambda, EM.coh_len_um));
               const float3 w = vmf_sample(-nE, kap, un.y, un.z);
               const float cos_o = dot(w, nrm);
-              if (cos_o > 0.0f && g_r > 0.0f) {
+              if (cos_o > 0.0f && g_r > 0.0f && emitter_reachable(S, ei, x, w)) {
                 // the lobe density, the MIS weight and the measurement are
                 // evaluated by k_shadow once the shadow ray reaches the emitter
                 const float3 dtn = (w - dot(w, nrm) * nrm) - t_mir;
@@ -1031,28 +1053,6 @@ __device__ __forceinline__ void shadow_finish(const RenderParams& p, int slot, c
   }
 }
 
-// Conservative precheck of a next-event ray toward emitter ei: false only if
-// the ray's closest hit cannot be a front-face point of that (planar) emitter
-// -- its plane is behind the ray or met from the back (where the emitter does
-// not emit), or the ray meets the plane outside the emitter's bounding box
-// widened by 1e-4 (1 + t) m, far above the FP32 error of the plane point.
-// Near-grazing rays (|cos| < 1e-3) and non-planar emitters always pass.  A
-// false result means a zero contribution, so the ray is not traced.
-__device__ __forceinline__ bool emitter_reachable(const DevScene& S, int ei, float3 x, float3 w) {
-  const DevEmitter E = S.emitters[ei];
-  if (!E.planar) return true;
-  const float3 ne = emitter_normal(S, ei);
-  const float den = dot(w, ne);
-  if (den >= 0.0f) return false;  // back face or parallel: measured as zero
-  if (den > -1e-3f) return true;
-  const float te = dot(xyz(S.emitter_tris[3 * E.first]) - x, ne) / den;
-  if (!(te > 0.0f)) return false;
-  const float3 q = x + te * w;
-  const float m = 1e-4f * (1.0f + te);
-  return q.x >= E.lo[0] - m && q.x <= E.hi[0] + m && q.y >= E.lo[1] - m && q.y <= E.hi[1] + m &&
-         q.z >= E.lo[2] - m && q.z <= E.hi[2] + m;
-}
-
 // NEE shadow rays: closest hit from the interaction point toward the sampled
 // emitter direction, then shadow_finish, one ray per thread per pass (the
 // shadow queue is a third as long as the trace queue: too short for
@@ -1066,9 +1066,7 @@ __global__ void __launch_bounds__(256, GR_SHADOW_MIN_BLOCKS) k_shadow(RenderPara
     const int slot = P.sq[i];
     const int4 m = P.meta[slot];
     const DevScene& S = p.scenes[p.views[m.x].scene_index];
-    const float4 sd = P.shd[slot];
-    const float3 o = xyz(P.od0[slot]), d = xyz(sd);
-    if (!emitter_reachable(S, __float_as_int(sd.w) & 0xffff, o, d)) continue;
+    const float3 o = xyz(P.od0[slot]), d = xyz(P.shd[slot]);  // requested only if emitter_reachable
     const Hit h = WIDE ? closest_hit_wide(S, o, d, m.w, &refined, &visits, &tests, &err)
                        : closest_hit(S, o, d, m.w, &refined, &visits, &tests, &err);
     shadow_finish<NS>(p, slot, h);
