@@ -137,19 +137,9 @@ __device__ __forceinline__ void start_sample(const RenderParams& p, int slot, in
   const Pool& P = p.pool;
   P.od0[slot] = make_float4(o.x, o.y, o.z, V.beta0 * V.beta0);
   P.od1[slot] = make_float4(d.x, d.y, d.z, 0.0f);
-  if (NS == 1) {
-    P.tp[0][slot] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
-  } else {
-    P.tp[0][slot] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
-    P.tp[1][slot] = make_float4(0.0f, 1.0f, 0.0f, 0.0f);
-    P.tp[2][slot] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
-    P.tp[3][slot] = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
-    float3 xf = normalize(V.right - dot(V.right, d) * d);
-    P.xf[slot] = make_float4(xf.x, xf.y, xf.z, 1.0f);
-  }
-  // xf.w: refractive index of the medium the ray travels in (1 = air)
-  if (NS == 1) P.xf[slot] = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
-  P.part[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  // the throughput (identity), the Stokes frame, the medium (air) and the
+  // contribution (zero) of a camera segment are implied by segment 0: k_shade
+  // forms them instead of reading them
   P.meta[slot] = make_int4(view, local, meta_pack(k, 0, ST_ACTIVE, 1), -1);
 }
 
@@ -745,19 +735,33 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
       const float kw = 2.0f * kPi / lambda;
       const float s_ray2 = 1.0f / (2.0f * V.beta0 * V.beta0 * kw * kw);
       float T[4][4];
-      if (NS == 1) {
-        T[0][0] = P.tp[0][slot].x;
+      float4 xfv = make_float4(0.0f, 0.0f, 0.0f, 1.0f), pt;
+      if (seg == 0) {
+        // camera segment (nothing stored by start_sample): identity Mueller
+        // matrix, no contribution yet, Stokes frame x axis = the camera's right
+        // vector made orthogonal to d, medium air
+        for (int r = 0; r < 4; ++r)
+          for (int c = 0; c < 4; ++c) T[r][c] = r == c ? 1.0f : 0.0f;
+        const float3 xf0 = NS == 1 ? f3(0.0f, 0.0f, 0.0f) : normalize(V.right - dot(V.right, d) * d);
+        xfv = make_float4(xf0.x, xf0.y, xf0.z, 1.0f);
+        pt = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       } else {
-        for (int r = 0; r < 4; ++r) {
-          float4 v = P.tp[r][slot];
-          T[r][0] = v.x;
-          T[r][1] = v.y;
-          T[r][2] = v.z;
-          T[r][3] = v.w;
+        if (NS == 1) {
+          const float4 t0 = P.tp[0][slot];
+          T[0][0] = t0.x;
+          xfv.w = t0.y;  // the medium's index rides in the unused word of the scalar throughput
+        } else {
+          for (int r = 0; r < 4; ++r) {
+            float4 v = P.tp[r][slot];
+            T[r][0] = v.x;
+            T[r][1] = v.y;
+            T[r][2] = v.z;
+            T[r][3] = v.w;
+          }
         }
+        if (NS == 4) xfv = P.xf[slot];
+        pt = P.part[slot];
       }
-      float4 xfv = P.xf[slot];
-      float4 pt = P.part[slot];
       const int hslot = __float_as_int(hh.y);
       bool done = false;
       auto add_col = [&](float val) {
@@ -978,13 +982,12 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
             if (alive) {
               P.od1[slot] = make_float4(d_out.x, d_out.y, d_out.z, rho);
               if (NS == 1) {
-                P.tp[0][slot] = make_float4(T[0][0], 0.0f, 0.0f, 0.0f);
+                P.tp[0][slot] = make_float4(T[0][0], eta_next, 0.0f, 0.0f);
               } else {
                 for (int r = 0; r < 4; ++r) P.tp[r][slot] = make_float4(T[r][0], T[r][1], T[r][2], T[r][3]);
                 const float3 xn = s_vector(nrm, -d_out, s_o);
                 P.xf[slot] = make_float4(xn.x, xn.y, xn.z, eta_next);
               }
-              if (NS == 1 && refracted) P.xf[slot] = make_float4(0.0f, 0.0f, 0.0f, eta_next);
               if (!delta) P.mis[slot] = mis_rec;
               P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg + 1, ST_ACTIVE, delta), hslot);
             } else {
@@ -1027,7 +1030,10 @@ __device__ __forceinline__ void shadow_finish(const RenderParams& p, int slot, c
   const float lambda = bin_lambda(V, bin);
   const float kw = 2.0f * kPi / lambda;
   float b2 = a0.w, ro = a1.w;
-  footprint_update(h.t, kw * P.xf[slot].w, b2, ro);  // |k| = eta k0 in the ray's medium
+  // |k| = eta k0 in the ray's medium: air on the camera segment, else the
+  // index carried with the path's throughput (scalar) or Stokes frame
+  const float eta = seg == 0 ? 1.0f : (NS == 1 ? P.tp[0][slot].y : P.xf[slot].w);
+  footprint_update(h.t, kw * eta, b2, ro);
   const float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallNeeFoot);
   const float val = measure_emitter(S, ei, x + h.t * w, w, b2, ro, kw, lambda, u.x, u.y);
   if (val == 0.0f) return;
