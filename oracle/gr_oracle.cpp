@@ -384,6 +384,14 @@ double bin_lambda(const View& V, int b) {
   return V.lmin_um + (double)b * (V.lmax_um - V.lmin_um) / (double)(V.n_bins - 1);
 }
 
+// Number of the view's samples s in [first_sample, first_sample + spp) whose
+// bin s mod n_bins is b.
+long bin_count(const View& V, int b) {
+  long n = 0;
+  for (long s = V.first_sample; s < V.first_sample + V.spp; ++s) n += (s % V.n_bins) == b;
+  return n;
+}
+
 // ---------------------------------------------------------------- free-space propagation
 // Eq. K_free_space_propagation with zbar = z/|k0| (z in um):
 //   beta_o^2 = beta^2 + 2 zbar rho + zbar^2 (1 + rho^2) / beta^2
@@ -545,7 +553,7 @@ struct Ctx {
   int flags;
   Rng rng;
 };
-const int FLAG_NEE = 1, FLAG_RR = 2, FLAG_NO_RENORM = 4;
+const int FLAG_NEE = 1, FLAG_RR = 2, FLAG_NO_RENORM = 4, FLAG_HERO = 16;
 
 // Angular spread of a source of coherence length lc (Eq. coherence_diffusivity
 // read per axis with Theta = lc^2): s_src = lambda / lc; lc = 0 means spatially
@@ -702,7 +710,7 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
   const Scene& S = *C.S;
   const View& V = *C.V;
   const int ns = V.n_stokes;
-  for (int i = 0; i < 4; ++i) result[i] = 0.0;
+  for (int i = 0; i < 16; ++i) result[i] = 0.0;
   Rng rng = C.rng;
   rng.pixel = (uint32_t)(py * V.W + px);
   rng.sample = (uint32_t)sample;
@@ -743,6 +751,40 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
   P.prev_pdf = 0.0;
   const int n_emit = (int)S.emitters.size();
 
+  // Hero-wavelength spectral MIS (Sec. 7.2, after Wilkie et al. 2014): the
+  // path's bin is the hero of the class of G = 4 bins {c, c+Q, c+2Q, c+3Q}
+  // (Q = n_bins / 4) and drives every sampling decision.  q[g] is the
+  // probability density of the path sampled so far at class bin g's
+  // wavelength divided by its density at the hero's; it stays 1 through
+  // wavelength-independent decisions and drops to 0 at a dispersive delta
+  // (a grating order j != 0, a dispersive dielectric), where no other
+  // wavelength could have made the same path.  An escape is measured at every
+  // class wavelength and bin g receives T M_g cf_g q_g / sum_j cf_j q_j (the
+  // balance heuristic over the class's wavelengths, cf_j = share of the
+  // class's samples whose hero is bin j); contributions of emitters (hits and
+  // next-event estimation) stay with the hero, as without the flag.
+  // result[4 g + k] is class bin g's Stokes component k.
+  const bool hero = (C.flags & FLAG_HERO) != 0;
+  const int G = hero ? 4 : 1, Qb = V.n_bins / G;
+  const int gh = hero ? bin / Qb : 0;
+  const int c0 = bin - gh * Qb;
+  double lam_g[4], q[4], cf[4];
+  {
+    long ncls = 0, nb_g[4];
+    for (int g = 0; g < G; ++g) {
+      lam_g[g] = bin_lambda(V, c0 + g * Qb);
+      q[g] = 1.0;
+      nb_g[g] = hero ? bin_count(V, c0 + g * Qb) : 1;
+      ncls += nb_g[g];
+    }
+    for (int g = 0; g < G; ++g) cf[g] = (double)nb_g[g] / (double)ncls;
+  }
+  auto drop_companions = [&]() {
+    for (int g = 0; g < G; ++g)
+      if (g != gh) q[g] = 0.0;
+  };
+  double* res_h = result + 4 * gh;
+
   for (int seg = 0;; ++seg) {
     // --- propagation: closest hit along d (point-hit assumption, Sec. 7.2)
     double th;
@@ -752,9 +794,22 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
     throughput_column(P, ns, col);
     if (!hit) {
       // --- measurement of distant sources on escape
-      double m = 0.0;
-      for (const Light& L : S.lights) m += measure_distant(L, P.d, P.lambda, P.s_ray2);
-      add_vec(result, ns, col, m);
+      if (!hero) {
+        double m = 0.0;
+        for (const Light& L : S.lights) m += measure_distant(L, P.d, P.lambda, P.s_ray2);
+        add_vec(result, ns, col, m);
+        return;
+      }
+      double den = 0.0;
+      for (int g = 0; g < G; ++g) den += cf[g] * q[g];
+      for (int g = 0; g < G; ++g) {
+        if (cf[g] * q[g] == 0.0) continue;
+        const double kg = 2.0 * PI / lam_g[g];
+        const double s2g = 1.0 / (2.0 * beta0 * beta0 * kg * kg);  // the invariant spread at lambda_g
+        double m = 0.0;
+        for (const Light& L : S.lights) m += measure_distant(L, P.d, lam_g[g], s2g);
+        add_vec(result + 4 * g, ns, col, m * cf[g] * q[g] / den);
+      }
       return;
     }
     // footprint update over the segment (z in um; |k| = eta k0 in a medium)
@@ -773,7 +828,7 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
         double pb = P.prev_pdf;
         w = pb * pb / (pb * pb + pn * pn);
       }
-      add_vec(result, ns, col, m * w);
+      add_vec(res_h, ns, col, m * w);
       return;
     }
     if (M.type == MAT_ABSORBER) return;
@@ -855,6 +910,8 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
     double pdf = 0.0;
     bool alive = true;
     double g_r = 0.0;
+    double m_rough = -1.0;
+    V3 delta_rough = v3(0.0, 0.0, 0.0);
     V3 t_mir = d_in - dot(d_in, n) * n;
     if (M.type == MAT_GRATING) {
       Lobes L;
@@ -873,6 +930,24 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
       }
       if (pick < 0) return;  // only possible without renormalisation
       d_out = L.dir[pick];
+      if (hero) {
+        if (L.order[pick] != 0) {
+          drop_companions();  // the order's direction depends on lambda
+        } else {
+          // specular order: same direction at every wavelength, probability
+          // a_0 / total there
+          const double ph = L.w[pick] / L.total;
+          for (int g = 0; g < G; ++g) {
+            if (g == gh || q[g] == 0.0) continue;
+            Lobes Lg;
+            grating_lobes(M, d_in, n, lam_g[g], !(C.flags & FLAG_NO_RENORM), &Lg);
+            double p0 = 0.0;
+            for (int i = 0; i < Lg.n; ++i)
+              if (Lg.order[i] == 0) p0 = Lg.w[i] / Lg.total;
+            q[g] *= p0 / ph;
+          }
+        }
+      }
     } else if (M.type == MAT_MIRROR) {
       d_out = d_in + (2.0 * cos_i) * n;
     } else if (M.type == MAT_DIELECTRIC) {
@@ -893,6 +968,7 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
         }
         m = mi;
       }
+      m_rough = m;
       if (m == 0.0) {
         d_out = d_in + (2.0 * cos_i) * n;
       } else {
@@ -904,6 +980,7 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
         V3 e1, e2;
         onb(n, &e1, &e2);
         V3 delta_t = (sig * z0) * e1 + (sig * z1) * e2;
+        delta_rough = delta_t;
         V3 t_out = t_mir + delta_t;
         double tt = dot(t_out, t_out);
         if (tt >= 1.0) {
@@ -914,6 +991,21 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
         }
       }
     }
+
+    // --- the class wavelengths' densities of the direction just sampled
+    if (hero && alive && M.type == MAT_ROUGH) {
+      for (int g = 0; g < G; ++g) {
+        if (g == gh || q[g] == 0.0) continue;
+        const double kg = 2.0 * PI / lam_g[g];
+        const double gg = std::pow(2.0 * kg * M.sigma_h_um * cos_i, 2);
+        if (m_rough == 0.0)  // specular term: probability e^{-g} (none in the continuous limit)
+          q[g] *= gg > G_CONT ? 0.0 : std::exp(g_r - gg);
+        else  // diffuse terms: density at the sampled offset (the cos factor is common)
+          q[g] *= rough_diffuse_density(gg, kg, M.corr_len_um, delta_rough) /
+                  rough_diffuse_density(g_r, P.k, M.corr_len_um, delta_rough);
+      }
+    }
+    if (hero && M.type == MAT_DIELECTRIC && M.cauchy_b_um2 != 0.0) drop_companions();
 
     // --- next-event estimation toward an emissive triangle (rough lobes only:
     // grating orders and mirror reflection are delta lobes)
@@ -941,7 +1033,7 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
             rng.draw(seg, CALL_NEE_FOOT, uf);
             double m = measure_emitter(S, sp, x + ts * w, w, b2, r, P.k, P.lambda, uf[0], uf[1]);
             double wmis = pn * pn / (pn * pn + f * f);
-            add_vec(result, ns, c_nee, m * f / pn * wmis);
+            add_vec(res_h, ns, c_nee, m * f / pn * wmis);
           }
         }
       }
@@ -1177,9 +1269,10 @@ static View read_view(const double* p) {
   return V;
 }
 
-// One path sample's contribution (n_stokes values) for tests.
+// One path sample's contribution for tests: out16[4 g + k], class bin g (only
+// g = 0 without hero MIS), Stokes component k.
 void oracle_trace_sample(void* s, const double* view, uint32_t seed, int flags, int px, int py, long sample,
-                         double* out4) {
+                         double* out16) {
   Scene* S = (Scene*)s;
   View V = read_view(view);
   Ctx C;
@@ -1188,18 +1281,24 @@ void oracle_trace_sample(void* s, const double* view, uint32_t seed, int flags, 
   C.flags = flags;
   C.rng.key[0] = seed;
   C.rng.key[1] = V.view_index;
-  trace_sample(C, px, py, sample, out4);
+  trace_sample(C, px, py, sample, out16);
 }
 
 // Render the pixels of the crop [x0,x1) x [y0,y1): for every pixel and bin, the
 // mean over the samples s in [first_sample, first_sample + spp) with
 // s mod n_bins == bin, summed in sample order with compensated (Neumaier)
-// summation.  out_mean: [crop_h][crop_w][n_bins][n_stokes]; out_var (optional):
+// summation.  With FLAG_HERO (n_bins a multiple of 4) every sample also adds
+// its weighted contributions to the other bins of its class, and a bin's
+// sum is still divided by the number of samples whose hero it is (the
+// weights make that the class average); out_var then holds the second moment
+// of the added values about that mean, not a per-sample variance.  Returns -1
+// for FLAG_HERO with n_bins not a multiple of 4.  out_mean: [crop_h][crop_w][n_bins][n_stokes]; out_var (optional):
 // the per-sample variance of the same values.  Returns the number of samples.
 long oracle_render(void* s, const double* view, uint32_t seed, int flags, int x0, int y0, int x1, int y1,
                    int n_threads, double* out_mean, double* out_var) {
   Scene* S = (Scene*)s;
   View V = read_view(view);
+  if ((flags & FLAG_HERO) && V.n_bins % 4 != 0) return -1;  // hero classes need 4 | n_bins
   Ctx C;
   C.S = S;
   C.V = &V;
@@ -1223,20 +1322,26 @@ long oracle_render(void* s, const double* view, uint32_t seed, int flags, int x0
         std::fill(cnt.begin(), cnt.end(), 0L);
         for (long si = 0; si < V.spp; ++si) {
           long smp = V.first_sample + si;
-          double c[4];
+          double c[16];
           trace_sample(C, px, py, smp, c);
           int b = (int)(smp % nb);
           cnt[b]++;
-          for (int k = 0; k < ns; ++k) {
-            // Neumaier compensated summation
-            double a = sum[b * 4 + k], v = c[k];
-            double t = a + v;
-            if (std::fabs(a) >= std::fabs(v))
-              comp[b * 4 + k] += (a - t) + v;
-            else
-              comp[b * 4 + k] += (v - t) + a;
-            sum[b * 4 + k] = t;
-            sq[b * 4 + k] += v * v;
+          // without hero MIS the sample adds to its bin; with it, to each bin
+          // of its class (c[4 g + k] for class bin g)
+          const int G = (flags & FLAG_HERO) ? 4 : 1, Qb = nb / G, c0 = b % Qb;
+          for (int g = 0; g < G; ++g) {
+            const int bb = G == 1 ? b : c0 + g * Qb;
+            for (int k = 0; k < ns; ++k) {
+              // Neumaier compensated summation
+              double a = sum[bb * 4 + k], v = c[4 * g + k];
+              double t = a + v;
+              if (std::fabs(a) >= std::fabs(v))
+                comp[bb * 4 + k] += (a - t) + v;
+              else
+                comp[bb * 4 + k] += (v - t) + a;
+              sum[bb * 4 + k] = t;
+              sq[bb * 4 + k] += v * v;
+            }
           }
         }
         size_t base = ((size_t)r * cw + (px - x0)) * nb * ns;

@@ -29,6 +29,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 FLAG_NEE = 1
 FLAG_RR = 2
 FLAG_NO_RENORM = 4
+FLAG_HERO = 16
 
 _lib = None
 
@@ -250,10 +251,13 @@ class Scene:
 
     def trace_sample(self, view, seed, flags, px, py, sample):
         v = view_vector(view)
-        o = np.zeros(4)
+        o = np.zeros(16)
         lib().oracle_trace_sample(self._h, _p(v), int(seed) & 0xFFFFFFFF, int(flags), int(px), int(py),
                                   int(sample), _p(o))
-        return o[: int(view["n_stokes"])].copy()
+        ns = int(view["n_stokes"])
+        if flags & FLAG_HERO:  # [class bin][Stokes]
+            return o.reshape(4, 4)[:, :ns].copy()
+        return o[:ns].copy()
 
     def render(self, view, seed, flags, crop=None, n_threads=None, want_var=False):
         """Mean image [h][w][n_bins][n_stokes] over the crop (x0, y0, x1, y1)."""
@@ -265,6 +269,8 @@ class Scene:
         if n_threads is None:
             n_threads = os.cpu_count() or 1
         v = view_vector(view)
-        lib().oracle_render(self._h, _p(v), int(seed) & 0xFFFFFFFF, int(flags), x0, y0, x1, y1,
-                            int(n_threads), _p(mean), _p(var) if want_var else None)
+        n = lib().oracle_render(self._h, _p(v), int(seed) & 0xFFFFFFFF, int(flags), x0, y0, x1, y1,
+                                int(n_threads), _p(mean), _p(var) if want_var else None)
+        if n < 0:
+            raise ValueError("hero-wavelength MIS needs n_bins to be a multiple of 4")
         return (mean, var) if want_var else mean
