@@ -144,10 +144,19 @@ typedef struct {
  * propagating orders); GR_FLAG_WIDE_BVH traverses the 4-wide BVH with 8-bit
  * quantised child boxes instead of the default binary FP32 BVH (both give the
  * same closest hits; the wide tree halves node visits but needs more
- * registers per thread).  table_dtype: storage of the grating order tables
+ * registers per thread); GR_FLAG_HERO hero-wavelength spectral MIS (Sec. 7.2):
+ * with n_bins a multiple of 4, a path's bin is the hero of the class of bins
+ * {c, c+Q, c+2Q, c+3Q} (Q = n_bins/4) and drives every sampling decision; an
+ * escape to distant sources is measured at all four wavelengths, weighted by
+ * the balance heuristic over the class wavelengths' path densities (zero for
+ * a wavelength after a dispersive delta: a grating order j != 0 or a
+ * dispersive dielectric), while emitter hits and next-event contributions
+ * stay with the hero; each bin is still divided by the number of samples
+ * whose hero it is (GR_E_INVALID if n_bins % 4 != 0; not available in
+ * gr_render_static).  table_dtype: storage of the grating order tables
  * (GR_TABLE_F32 / F16 / BF16); arithmetic is FP32 either way.  pool_size:
  * wavefront slots (0 = default); block: threads per block (0 = default). */
-enum { GR_FLAG_NEE = 1, GR_FLAG_RR = 2, GR_FLAG_NO_RENORM = 4, GR_FLAG_WIDE_BVH = 8 };
+enum { GR_FLAG_NEE = 1, GR_FLAG_RR = 2, GR_FLAG_NO_RENORM = 4, GR_FLAG_WIDE_BVH = 8, GR_FLAG_HERO = 16 };
 enum { GR_TABLE_F32 = 0, GR_TABLE_F16 = 1, GR_TABLE_BF16 = 2 };
 typedef struct {
   uint32_t seed;

@@ -66,7 +66,9 @@ struct DevView {
   float* acc_sum;         // [nb][H][W][ns]
   float* acc_comp;
   int table_base;         // first table row of this view ((view, material, bin) rows)
-  int nbu;                // bins that receive samples: min(spp, nb), from first_sample mod nb on
+  int nbu;                // sample classes that receive samples: min(spp, Q), from first_sample mod Q on
+  int Q;                  // class modulus: a ticket owns the samples s with s mod Q == its class
+                          // (Q = nb: one bin per ticket; Q = nb/4 with hero-wavelength MIS)
 };
 
 // Per-(view, material, bin) row of the grating order table: J_j(h k/2)^2 for

@@ -55,16 +55,23 @@ __device__ __forceinline__ int meta_pack(int k, int seg, int st, int delta) {
   return k | (seg << 16) | (st << 24) | (delta << 26);
 }
 
-__device__ __forceinline__ int bin_first_sample(const DevView& V, int bin) {
-  int r = (bin - V.first_sample) % V.nb;
-  if (r < 0) r += V.nb;
+__device__ __forceinline__ int meta_escaped(int z) { return (z >> 27) & 1; }
+
+// First sample s >= first_sample with s mod Q == c, and the number of the
+// view's samples in that residue class.  A ticket owns one class: with Q = nb
+// a class is one wavelength bin; with hero-wavelength MIS (Q = nb/4) the
+// class's samples are heroes of the bins c, c+Q, c+2Q, c+3Q in turn.
+__device__ __forceinline__ int class_first_sample(const DevView& V, int c, int Q) {
+  int r = (c - V.first_sample) % Q;
+  if (r < 0) r += Q;
   return V.first_sample + r;
 }
-__device__ __forceinline__ int bin_samples(const DevView& V, int bin) {
-  int s0 = bin_first_sample(V, bin);
+__device__ __forceinline__ int class_samples(const DevView& V, int c, int Q) {
+  int s0 = class_first_sample(V, c, Q);
   int end = V.first_sample + V.spp;
-  return s0 < end ? (end - 1 - s0) / V.nb + 1 : 0;
+  return s0 < end ? (end - 1 - s0) / Q + 1 : 0;
 }
+__device__ __forceinline__ int bin_samples(const DevView& V, int bin) { return class_samples(V, bin, V.nb); }
 __device__ __forceinline__ float bin_lambda(const DevView& V, int b) {
   if (V.nb <= 1) return V.lmin;
   return V.lmin + (float)b * (V.lmax - V.lmin) / (float)(V.nb - 1);
@@ -118,10 +125,10 @@ template <int NS>
 __device__ __forceinline__ void start_sample(const RenderParams& p, int slot, int view, int local, int k) {
   const DevView& V = p.views[view];
   const int WH = V.W * V.H;
-  const int bin = local / WH;
-  const int pixel = local - bin * WH;
+  const int cls = local / WH;
+  const int pixel = local - cls * WH;
   const int py = pixel / V.W, px = pixel - py * V.W;
-  const int s = bin_first_sample(V, bin) + k * V.nb;
+  const int s = class_first_sample(V, cls, V.Q) + k * V.Q;
   float4 u = rng4(p.seed, (uint32_t)V.view_index, (uint32_t)pixel, (uint32_t)s, 0, kCallJitter);
   float fx = ((float)px + u.x) / (float)V.W, fy = ((float)py + u.y) / (float)V.H;
   float3 o, d;
@@ -199,7 +206,50 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
 }
 
 // ------------------------------------------------------------------ regen
+// Hero-wavelength MIS: fold the finished sample into the ticket's four member
+// sums (member g = bin c + g Q): its own contribution (escape share, emitter
+// hits, next-event terms) into the hero's member, its escape shares of the
+// other class wavelengths into theirs.  On the ticket's last sample every
+// member's total goes to its bin's frame accumulator.  Returns true if the
+// ticket has more samples.
 template <int NS>
+__device__ __forceinline__ bool fold_class(const RenderParams& p, int slot, const int4& m) {
+  const Pool& P = p.pool;
+  const DevView& V = p.views[m.x];
+  const int WH = V.W * V.H;
+  const int cls = m.y / WH;
+  const int k = meta_k(m.z);
+  const int gh = ((class_first_sample(V, cls, V.Q) + k * V.Q) % V.nb) / V.Q;
+  const bool more = k + 1 < class_samples(V, cls, V.Q);
+  const bool esc = meta_escaped(m.z);
+  const size_t Ps = (size_t)p.P;
+  for (int g = 0; g < 4; ++g) {
+    const float4 v = g == gh ? P.part[slot] : (esc ? P.hpart[g * Ps + slot] : make_float4(0.f, 0.f, 0.f, 0.f));
+    float4 sm = P.haccS[g * Ps + slot], c = P.haccC[g * Ps + slot];
+    kahan_add(sm.x, c.x, v.x);
+    if (NS == 4) {
+      kahan_add(sm.y, c.y, v.y);
+      kahan_add(sm.z, c.z, v.z);
+      kahan_add(sm.w, c.w, v.w);
+    }
+    if (more) {
+      P.haccS[g * Ps + slot] = sm;
+      P.haccC[g * Ps + slot] = c;
+    } else {
+      const size_t idx = ((size_t)m.y + (size_t)g * V.Q * WH) * NS;
+      const float tot[4] = {sm.x - c.x, sm.y - c.y, sm.z - c.z, sm.w - c.w};
+      for (int q = 0; q < NS; ++q) {
+        float a = V.acc_sum[idx + q], e = V.acc_comp[idx + q];
+        kahan_add(a, e, tot[q]);
+        V.acc_sum[idx + q] = a;
+        V.acc_comp[idx + q] = e;
+      }
+    }
+  }
+  return more;
+}
+
+template <int NS, bool HERO>
 __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
   const Pool& P = p.pool;
   const int stride = gridDim.x * blockDim.x;
@@ -219,7 +269,15 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
     bool need = false, active = false, fresh = false;
     int4 m = valid ? P.meta[slot] : make_int4(0, 0, 0, 0);
     const int st = meta_state(m.z);
-    if (valid && st == ST_DONE) {
+    if (valid && st == ST_DONE && HERO) {
+      ++finished;
+      if (fold_class<NS>(p, slot, m)) {
+        start_sample<NS>(p, slot, m.x, m.y, meta_k(m.z) + 1);
+        active = fresh = true;
+      } else {
+        need = true;
+      }
+    } else if (valid && st == ST_DONE) {
       ++finished;
       const DevView& V = p.views[m.x];
       float4 s = P.accS[slot], c = P.accC[slot], v = P.part[slot];
@@ -269,20 +327,27 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
         } else {
           int view = find_view(p, t);
           const DevView& V = p.views[view];
-          // tickets run pixel-major, wavelength bin fastest: neighbouring
+          // tickets run pixel-major, sample class fastest: neighbouring
           // slots start the same pixel at neighbouring wavelengths, so a warp's
-          // camera rays (and grating orders) stay coherent.  Only bins that
-          // receive samples have tickets: sample s goes to bin s mod nb, so
-          // with spp < nb they are the nbu = spp bins from first_sample mod nb
-          // on.  The ticket's element is bin * W*H + pixel, whatever the claim
-          // order.
+          // camera rays (and grating orders) stay coherent.  Only classes that
+          // receive samples have tickets: sample s goes to class s mod Q, so
+          // with spp < Q they are the nbu = spp classes from first_sample mod Q
+          // on.  The ticket's element is class * W*H + pixel, whatever the
+          // claim order (with Q = nb the class is the bin).
           const int local = (int)(t - (unsigned long long)V.ticket_base);
           const int pix = local / V.nbu;
-          const int bin = (V.first_sample + (local - pix * V.nbu)) % V.nb;
-          if (bin_samples(V, bin) > 0) {
-            P.accS[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            P.accC[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            start_sample<NS>(p, slot, view, bin * (V.W * V.H) + pix, 0);
+          const int cls = (V.first_sample + (local - pix * V.nbu)) % V.Q;
+          if (class_samples(V, cls, V.Q) > 0) {
+            if (HERO) {
+              for (int g = 0; g < 4; ++g) {
+                P.haccS[(size_t)g * p.P + slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                P.haccC[(size_t)g * p.P + slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+              }
+            } else {
+              P.accS[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+              P.accC[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+            start_sample<NS>(p, slot, view, cls * (V.W * V.H) + pix, 0);
             active = fresh = true;
             need = false;
           }
@@ -696,8 +761,33 @@ __device__ __noinline__ int poisson_pick_fp64(double lam_d, float sigma_h_um, fl
   return mi;
 }
 
-template <int NS, typename TT>
-__global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams p) {
+// Probability of grating order 0 at one wavelength (Eq. K_grating): its
+// weight J_0^2 over the total of the propagating orders (|t_mir + j step g|^2
+// < 1), or the raw weight without renormalisation; from the FP32 copy of the
+// order table.  Used for the density ratios of hero-wavelength MIS, where a
+// probability (not a decision) is needed.
+__device__ __forceinline__ float order0_prob(const TableRow& row, float3 t_mir, float step, float3 gt, bool renorm,
+                                            const float* __restrict__ vals32) {
+  const float a0 = __ldg(vals32 + row.offset);
+  if (!renorm) return a0;
+  float total = 0.0f;
+  for (int j = -row.jmax; j <= row.jmax; ++j) {
+    const float3 tj = t_mir + ((float)j * step) * gt;
+    if (dot(tj, tj) < 1.0f) total += __ldg(vals32 + row.offset + (j < 0 ? -j : j));
+  }
+  return total > 0.0f ? a0 / total : 0.0f;
+}
+
+// HERO: hero-wavelength spectral MIS (Sec. 7.2).  The path's bin is the hero
+// of its class {c, c+Q, c+2Q, c+3Q} and makes every decision; hq[g] holds the
+// path's density at class wavelength g divided by its density at the hero's
+// (1 through wavelength-independent decisions, the ratio of order-0 or rough
+// lobe densities, 0 after a dispersive delta).  An escape is measured at each
+// class wavelength with weight cf_g hq_g / sum_j cf_j hq_j (balance heuristic;
+// cf_j = the class's share of samples whose hero is bin j); emitter hits and
+// next-event terms stay with the hero.
+template <int NS, typename TT, bool HERO>
+__global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(RenderParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const TableRow* rows = p.rows;
   const TT* tvals = (const TT*)p.table_vals;
@@ -728,9 +818,12 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
       float beta2 = a0.w, rho = a1.w;
       const int kk = meta_k(m.z), seg = meta_seg(m.z), prev_delta = meta_delta(m.z);
       const int WH = V.W * V.H;
-      const int bin = m.y / WH;
-      const int pixel = m.y - bin * WH;
-      const int smp = bin_first_sample(V, bin) + kk * V.nb;
+      const int cls = m.y / WH;  // the ticket's sample class (its bin without HERO)
+      const int pixel = m.y - cls * WH;
+      const int Qv = HERO ? V.Q : V.nb;
+      const int smp = class_first_sample(V, cls, Qv) + kk * Qv;
+      const int bin = HERO ? smp % V.nb : cls;
+      const int gh = HERO ? (bin - cls) / Qv : 0;  // the hero's member of the class
       const float lambda = bin_lambda(V, bin);
       const float kw = 2.0f * kPi / lambda;
       const float s_ray2 = 1.0f / (2.0f * V.beta0 * V.beta0 * kw * kw);
@@ -762,6 +855,20 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
         if (NS == 4) xfv = P.xf[slot];
         pt = P.part[slot];
       }
+      float hq[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+      if (HERO && seg > 0) {
+        const float4 q4 = P.hq[slot];
+        hq[0] = q4.x;
+        hq[1] = q4.y;
+        hq[2] = q4.z;
+        hq[3] = q4.w;
+      }
+      auto drop_companions = [&]() {
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+          if (g != gh) hq[g] = 0.0f;
+      };
+      int escaped = 0;
       const int hslot = __float_as_int(hh.y);
       bool done = false;
       auto add_col = [&](float val) {
@@ -772,7 +879,44 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
           pt.w += T[3][0] * val;
         }
       };
-      if (hslot < 0) {
+      if (hslot < 0 && HERO) {
+        // escape measured at every class wavelength, balance-heuristic weights
+        float cf[4], den = 0.0f;
+        const float ncls = (float)class_samples(V, cls, Qv);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          cf[g] = (float)bin_samples(V, cls + g * Qv) / ncls;
+          den += cf[g] * hq[g];
+        }
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const float wq = cf[g] * hq[g];
+          float val = 0.0f;
+          if (wq > 0.0f) {
+            const float lg = bin_lambda(V, cls + g * Qv);
+            const float kg = 2.0f * kPi / lg;
+            const float s2g = 1.0f / (2.0f * V.beta0 * V.beta0 * kg * kg);
+            float mg = 0.0f;
+            for (int l = 0; l < S.n_lights; ++l) {
+              const gr_light L = S.lights[l];
+              if (L.type == GR_LIGHT_ENV) {
+                mg += L.E;
+              } else {
+                const float kap = 1.0f / (s2g + src_spread2(lg, L.coh_len_um));
+                mg += L.E * vmf(d, f3(L.dir[0], L.dir[1], L.dir[2]), kap);
+              }
+            }
+            val = mg * (wq / den);
+          }
+          if (g == gh)
+            add_col(val);
+          else
+            P.hpart[(size_t)g * p.P + slot] = make_float4(T[0][0] * val, NS == 4 ? T[1][0] * val : 0.0f,
+                                                          NS == 4 ? T[2][0] * val : 0.0f, NS == 4 ? T[3][0] * val : 0.0f);
+        }
+        escaped = 1;
+        done = true;
+      } else if (hslot < 0) {
         float msum = 0.0f;
         for (int l = 0; l < S.n_lights; ++l) {
           const gr_light L = S.lights[l];
@@ -904,6 +1048,22 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
               } else {
                 const float3 tj = t_mir + ((float)pick * step) * gt;
                 d_out = tj + sqrtf(fmaxf(0.0f, 1.0f - dot(tj, tj))) * nrm;
+                if (HERO) {
+                  if (pick != 0) {
+                    drop_companions();  // the order's direction depends on the wavelength
+                  } else {
+                    // order 0 leaves in the same direction at every wavelength
+                    const float ph = order0_prob(row, t_mir, step, gt, renorm, p.table_vals32);
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                      if (g == gh || hq[g] == 0.0f) continue;
+                      const int bg = cls + g * Qv;
+                      const float p0 = order0_prob(rows[V.table_base + mat * V.nb + bg], t_mir,
+                                                   bin_lambda(V, bg) / M.period_um, gt, renorm, p.table_vals32);
+                      hq[g] = ph > 0.0f ? hq[g] * (p0 / ph) : 0.0f;
+                    }
+                  }
+                }
               }
             } else if (M.type == GR_MAT_MIRROR) {
               d_out = d + (2.0f * cos_i) * nrm;
@@ -953,7 +1113,27 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
                   mis_rec = make_float4(dot(dt, dt), g_r, kl * kl, cz);
                 }
               }
+              if (HERO && alive) {
+                // the class wavelengths' densities of the lobe term just sampled:
+                // specular e^-g, or the m >= 1 density at the sampled offset
+                // (the cosine factor is common to all wavelengths)
+                const float dh = mreal == 0.0f ? 0.0f : rough_density(g_r, mis_rec.z, mis_rec.x);
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                  if (g == gh || hq[g] == 0.0f) continue;
+                  const float kg = 2.0f * kPi / bin_lambda(V, cls + g * Qv);
+                  float gg = 2.0f * kg * M.sigma_h_um * cos_i;
+                  gg *= gg;
+                  if (mreal == 0.0f) {
+                    hq[g] *= gg > kGCont ? 0.0f : expf(g_r - gg);
+                  } else {
+                    const float klg = kg * M.corr_len_um;
+                    hq[g] = dh > 0.0f ? hq[g] * (rough_density(gg, klg * klg, mis_rec.x) / dh) : 0.0f;
+                  }
+                }
+              }
             }
+            if (HERO && M.type == GR_MAT_DIELECTRIC && M.cauchy_b_um2 != 0.0f) drop_companions();
             // --- next-event estimation toward an emitter (rough lobes only)
             if (M.type == GR_MAT_ROUGH && (p.flags & GR_FLAG_NEE) && S.n_emitters > 0) {
               const float4 un = rng4(p.seed, V.view_index, pixel, smp, seg, kCallNeeDir);
@@ -989,6 +1169,7 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
                 P.xf[slot] = make_float4(xn.x, xn.y, xn.z, eta_next);
               }
               if (!delta) P.mis[slot] = mis_rec;
+              if (HERO) P.hq[slot] = make_float4(hq[0], hq[1], hq[2], hq[3]);
               P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg + 1, ST_ACTIVE, delta), hslot);
             } else {
               P.od1[slot] = make_float4(d.x, d.y, d.z, rho);
@@ -998,7 +1179,7 @@ __global__ void __launch_bounds__(256, GR_SHADE_MIN_BLOCKS) k_shade(RenderParams
         }
       }
       P.part[slot] = pt;
-      if (done) P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg, ST_DONE, 0), m.w);
+      if (done) P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg, ST_DONE, 0) | (escaped << 27), m.w);
     }
     const int q = block_reserve<int>(&p.ctr->sq_count, want_shadow);
     if (want_shadow) P.sq[q] = slot;
@@ -1024,9 +1205,10 @@ __device__ __forceinline__ void shadow_finish(const RenderParams& p, int slot, c
   const float4 a0 = P.od0[slot], a1 = P.od1[slot];
   const float3 x = xyz(a0), w = xyz(sd);
   const int WH = V.W * V.H;
-  const int bin = m.y / WH;
-  const int pixel = m.y - bin * WH;
-  const int smp = bin_first_sample(V, bin) + meta_k(m.z) * V.nb;
+  const int cls = m.y / WH;
+  const int pixel = m.y - cls * WH;
+  const int smp = class_first_sample(V, cls, V.Q) + meta_k(m.z) * V.Q;
+  const int bin = V.Q == V.nb ? cls : smp % V.nb;  // the hero's bin under hero-wavelength MIS
   const float lambda = bin_lambda(V, bin);
   const float kw = 2.0f * kPi / lambda;
   float b2 = a0.w, ro = a1.w;
@@ -1269,15 +1451,22 @@ template <int NS, typename TT>
 cudaError_t launch_iteration(const RenderParams& p, int grid_regen, int grid_trace, int grid_shade, int grid_shadow,
                              int block, size_t smem, cudaStream_t st, cudaEvent_t* ev) {
   const bool wide = (p.flags & GR_FLAG_WIDE_BVH) != 0;
+  const bool hero = (p.flags & GR_FLAG_HERO) != 0;
   if (ev) cudaEventRecord(ev[0], st);
-  k_regen<NS><<<grid_regen, block, 0, st>>>(p);
+  if (hero)
+    k_regen<NS, true><<<grid_regen, block, 0, st>>>(p);
+  else
+    k_regen<NS, false><<<grid_regen, block, 0, st>>>(p);
   if (ev) cudaEventRecord(ev[1], st);
   if (wide)
     k_trace<true><<<grid_trace, block, 0, st>>>(p);
   else
     k_trace<false><<<grid_trace, trace_block(block), 0, st>>>(p);
   if (ev) cudaEventRecord(ev[2], st);
-  k_shade<NS, TT><<<grid_shade, block, smem, st>>>(p);
+  if (hero)
+    k_shade<NS, TT, true><<<grid_shade, block, smem, st>>>(p);
+  else
+    k_shade<NS, TT, false><<<grid_shade, block, smem, st>>>(p);
   if (ev) cudaEventRecord(ev[3], st);
   if (wide)
     k_shadow<NS, true><<<grid_shadow, block, 0, st>>>(p);
@@ -1288,6 +1477,22 @@ cudaError_t launch_iteration(const RenderParams& p, int grid_regen, int grid_tra
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// The shade and regen kernels a render launches (for occupancy queries).
+const void* shade_kernel(int ns, int dtype, bool hero) {
+  if (ns == 1) {
+    if (dtype == GR_TABLE_F32) return hero ? (const void*)k_shade<1, float, true> : (const void*)k_shade<1, float, false>;
+    if (dtype == GR_TABLE_F16) return hero ? (const void*)k_shade<1, __half, true> : (const void*)k_shade<1, __half, false>;
+    return hero ? (const void*)k_shade<1, __nv_bfloat16, true> : (const void*)k_shade<1, __nv_bfloat16, false>;
+  }
+  if (dtype == GR_TABLE_F32) return hero ? (const void*)k_shade<4, float, true> : (const void*)k_shade<4, float, false>;
+  if (dtype == GR_TABLE_F16) return hero ? (const void*)k_shade<4, __half, true> : (const void*)k_shade<4, __half, false>;
+  return hero ? (const void*)k_shade<4, __nv_bfloat16, true> : (const void*)k_shade<4, __nv_bfloat16, false>;
+}
+const void* regen_kernel(int ns, bool hero) {
+  if (ns == 1) return hero ? (const void*)k_regen<1, true> : (const void*)k_regen<1, false>;
+  return hero ? (const void*)k_regen<4, true> : (const void*)k_regen<4, false>;
+}
 
 }  // namespace
 
@@ -1331,7 +1536,8 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     V.lmax = d.lambda_max_um;
     V.beta0 = d.f_beta * d.p_pix_um;
     V.ticket_base = (long long)plan.total_tickets;
-    V.nbu = std::min(d.spp, d.n_bins);
+    V.Q = (o.flags & GR_FLAG_HERO) ? d.n_bins / 4 : d.n_bins;
+    V.nbu = std::min(d.spp, V.Q);
     V.n_tickets = (long long)V.nbu * d.width * d.height;
     plan.total_tickets += (unsigned long long)V.n_tickets;
     V.acc_sum = acc_sum[v];
@@ -1387,6 +1593,8 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const size_t o_meta = take(sizeof(int4) * (size_t)P);
   const size_t o_tq = take(sizeof(int) * (size_t)P);
   const size_t o_sq = take(sizeof(int) * (size_t)P);
+  const bool hero = (o.flags & GR_FLAG_HERO) != 0;
+  const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 13) : 0;  // hq, hpart[4], haccS[4], haccC[4]
   const size_t total = off;
   if (f->scratch_bytes < total) {
     if (f->scratch) cudaFreeAsync(f->scratch, st);
@@ -1428,6 +1636,13 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   p.pool.meta = (int4*)(base + o_meta);
   p.pool.tq = (int*)(base + o_tq);
   p.pool.sq = (int*)(base + o_sq);
+  if (hero) {
+    float4* h4 = (float4*)(base + o_hero);
+    p.pool.hq = h4;
+    p.pool.hpart = h4 + (size_t)P;
+    p.pool.haccS = h4 + (size_t)P * 5;
+    p.pool.haccC = h4 + (size_t)P * 9;
+  }
   p.P = P;
   p.regen_thr = o.regen_threshold_pct;
   p.ctr = f->ctr;
@@ -1482,20 +1697,9 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     return sms * per;
   };
   int g_regen, g_trace, g_shade, g_shadow;
-  const void* shade_fn;
-  if (NSv == 1) {
-    g_regen = grid_for((const void*)k_regen<1>, 0);
-    g_shadow = grid_for((const void*)k_shadow<1, false>, 0);
-    shade_fn = o.table_dtype == GR_TABLE_F32 ? (const void*)k_shade<1, float>
-               : o.table_dtype == GR_TABLE_F16 ? (const void*)k_shade<1, __half>
-                                               : (const void*)k_shade<1, __nv_bfloat16>;
-  } else {
-    g_regen = grid_for((const void*)k_regen<4>, 0);
-    g_shadow = grid_for((const void*)k_shadow<4, false>, 0);
-    shade_fn = o.table_dtype == GR_TABLE_F32 ? (const void*)k_shade<4, float>
-               : o.table_dtype == GR_TABLE_F16 ? (const void*)k_shade<4, __half>
-                                               : (const void*)k_shade<4, __nv_bfloat16>;
-  }
+  const void* shade_fn = shade_kernel(NSv, o.table_dtype, hero);
+  g_regen = grid_for(regen_kernel(NSv, hero), 0);
+  g_shadow = grid_for(NSv == 1 ? (const void*)k_shadow<1, false> : (const void*)k_shadow<4, false>, 0);
   const bool wide_bvh = (o.flags & GR_FLAG_WIDE_BVH) != 0;
   const int tblk = wide_bvh ? block : trace_block(block);
   g_trace = wide_bvh ? grid_for((const void*)k_trace<true>, 0) : grid_for((const void*)k_trace<false>, 0, tblk);
@@ -1549,7 +1753,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   {
     long long n_max = 1, d_max = 0;
     for (int v = 0; v < n_views; ++v) {
-      n_max = std::max<long long>(n_max, (long long)vd[v].spp / vd[v].n_bins + 1);
+      n_max = std::max<long long>(n_max, (long long)vd[v].spp / plan.views[v].Q + 1);
       d_max = std::max<long long>(d_max, vd[v].max_depth);
     }
     long long rounds = (long long)((plan.total_tickets + P - 1) / P) + 1;
@@ -1756,6 +1960,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
     V.lmax = d.lambda_max_um;
     V.beta0 = d.f_beta * d.p_pix_um;
     V.ticket_base = (long long)total_tickets;
+    V.Q = d.n_bins;  // no hero-wavelength MIS here
     V.nbu = std::min(d.spp, d.n_bins);
     V.n_tickets = (long long)V.nbu * d.width * d.height;
     total_tickets += (unsigned long long)V.n_tickets;
@@ -1904,14 +2109,9 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, blk > 0 ? blk : block, dyn);
     return sms * std::max(per, 1);
   };
-  const void* shade_fn = NSv == 1 ? (o.table_dtype == GR_TABLE_F32 ? (const void*)k_shade<1, float>
-                                     : o.table_dtype == GR_TABLE_F16 ? (const void*)k_shade<1, __half>
-                                                                     : (const void*)k_shade<1, __nv_bfloat16>)
-                                  : (o.table_dtype == GR_TABLE_F32 ? (const void*)k_shade<4, float>
-                                     : o.table_dtype == GR_TABLE_F16 ? (const void*)k_shade<4, __half>
-                                                                     : (const void*)k_shade<4, __nv_bfloat16>);
+  const void* shade_fn = shade_kernel(NSv, o.table_dtype, false);
   const int gmax = (int)((P + block - 1) / block);
-  const int g_regen = std::min(gmax, grid_for(NSv == 1 ? (const void*)k_regen<1> : (const void*)k_regen<4>, 0));
+  const int g_regen = std::min(gmax, grid_for(regen_kernel(NSv, false), 0));
   const bool wide_bvh = (o.flags & GR_FLAG_WIDE_BVH) != 0;
   const int tblk = wide_bvh ? block : trace_block(block);
   const int g_trace =

@@ -1,0 +1,134 @@
+"""Hero-wavelength spectral MIS on the GPU (Sec. 7.2) against the FP64 oracle
+with the same flag, on the same seeded inputs: every path's hero bin makes the
+decisions, escapes are shared with the class's other three wavelengths by the
+balance heuristic, and dispersive deltas (grating orders j != 0, dispersive
+glass) leave the path to its hero.  Tolerance: relative L2 <= 1e-3, as for
+the plain estimator."""
+import numpy as np
+import pytest
+
+from paper_2303_15762_gb300 import scenegen as sg
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-3
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _rough_grating_scene(env=0.3):
+    """Rough conductor ground and a grating tile under a distant source near
+    the mirror direction of the camera, plus a constant environment."""
+    mats = [sg.material(sg.MAT_ROUGH, fresnel=1, n_re=0.3, n_im=3.5, sigma_h_um=0.12, corr_len_um=3.0),
+            sg.material(sg.MAT_GRATING, fresnel=1, n_re=0.3, n_im=3.5, period_um=1.8, height_um=0.2,
+                        gdir=(1, 0, 0))]
+    tris = np.concatenate([sg._quad((0, 0, 0), (0, 0, 0.5), (0.5, 0, 0)),
+                           sg._quad((0.05, 0.02, -0.05), (0, 0, 0.06), (0.06, 0, 0))])
+    lights = [sg.light(sg.LIGHT_DISTANT, (0.05, 0.5, -0.86), 1.0, 20.0), sg.light(sg.LIGHT_ENV, (0, 0, 1), env, 0.0)]
+    return sg._scene(tris, [0, 0, 1, 1], mats, np.asarray(lights, dtype=np.float32))
+
+
+def _view(**kw):
+    base = dict(eye=(0.0, 0.25, 0.45), look_at=(0.0, 0.0, 0.0), up=(0, 1, 0), vfov_deg=40.0, width=24, height=20,
+                n_bins=8, n_stokes=1, max_depth=4, spp=64)
+    base.update(kw)
+    return sg.view(**base)
+
+
+@pytest.mark.parametrize("ns", [1, 4])
+@pytest.mark.parametrize("nee", [False, True])
+def test_rough_grating_matches_oracle(gr, oracle, ns, nee):
+    scene = _rough_grating_scene()
+    v = _view(n_stokes=ns)
+    g_flags = gr.FLAG_HERO | (gr.FLAG_NEE if nee else 0)
+    o_flags = oracle.FLAG_HERO | (oracle.FLAG_NEE if nee else 0)
+    img = gr.render_image(scene, v, seed=3, flags=g_flags)
+    ref = oracle.Scene(scene).render(v, 3, o_flags)
+    r = rel_l2(img, ref)
+    print("hero rough+grating ns=%d nee=%d rel-L2 = %.3g" % (ns, nee, r))
+    assert r <= TOL
+    # the weights move contributions between the bins of a class: the image
+    # differs from the plain estimator's
+    plain = gr.render_image(scene, v, seed=3, flags=g_flags & ~gr.FLAG_HERO)
+    assert rel_l2(img, plain.astype(np.float64)) > 1e-3
+
+
+def test_procedural_stokes_nee_rr_matches_oracle(gr, oracle):
+    """Gratings, rough conductors and emitters (the procedural workload's mix)
+    with full Stokes, next-event estimation and Russian roulette."""
+    scene = sg.procedural_scene(seed=7, n_objects=8, target_tris=4000, n_emitters=2)
+    v = sg.procedural_view(width=48, height=40, spp=32, n_bins=16, n_stokes=4, max_depth=4)
+    img = gr.render_image(scene, v, seed=4, flags=gr.FLAG_HERO | gr.FLAG_NEE | gr.FLAG_RR)
+    ref = oracle.Scene(scene).render(v, 4, oracle.FLAG_HERO | oracle.FLAG_NEE | oracle.FLAG_RR)
+    r = rel_l2(img, ref)
+    print("hero procedural rel-L2 =", r)
+    assert r <= TOL
+
+
+@pytest.mark.parametrize("cauchy_b", [0.0, 0.0042])
+def test_glass_slab_matches_oracle(gr, oracle, cauchy_b):
+    """A tilted glass slab over a rough ground: without dispersion refraction
+    keeps the class wavelengths; with it every path through the glass is left
+    to its hero."""
+    scene = sg.dielectric_scene(cauchy_b_um2=cauchy_b)
+    v = sg.dielectric_view(width=32, height=24, spp=32, n_bins=8, n_stokes=4, max_depth=8)
+    img = gr.render_image(scene, v, seed=5, flags=gr.FLAG_HERO | gr.FLAG_NEE)
+    ref = oracle.Scene(scene).render(v, 5, oracle.FLAG_HERO | oracle.FLAG_NEE)
+    r = rel_l2(img, ref)
+    print("hero glass b=%g rel-L2 = %.3g" % (cauchy_b, r))
+    assert r <= TOL
+
+
+def test_ragged_windows_match_oracle(gr, oracle):
+    """Odd image sizes, a sample offset, fewer samples than bins (bins of a
+    class without samples) and spp not a multiple of the bin count."""
+    scene = _rough_grating_scene()
+    cases = [dict(width=37, height=23, n_bins=8, spp=13, first_sample=3),
+             dict(width=9, height=4, n_bins=16, spp=5),
+             dict(width=5, height=3, n_bins=4, spp=2, first_sample=1),
+             dict(width=16, height=8, n_bins=4, spp=9, max_depth=0)]
+    for c in cases:
+        v = _view(**c)
+        img = gr.render_image(scene, v, seed=6, flags=gr.FLAG_HERO)
+        ref = oracle.Scene(scene).render(v, 6, oracle.FLAG_HERO)
+        r = rel_l2(img, ref)
+        print(c, "rel-L2 =", r)
+        assert r <= TOL, c
+
+
+def test_mirror_furnace_every_bin_one(gr):
+    """No wavelength-dependent decision: the class weights of every path sum
+    to one, so each bin is 1 to FP32 rounding."""
+    scene = sg._scene(sg._quad((0, 0, 0), (0, 0, 0.2), (0.2, 0, 0)), [0, 0], [sg.material(sg.MAT_MIRROR)],
+                      [sg.light(sg.LIGHT_ENV, (0, 0, 1), 1.0, 0.0)])
+    img = gr.render_image(scene, _view(spp=40), seed=3, flags=gr.FLAG_HERO)
+    assert np.max(np.abs(img - 1.0)) < 1e-5
+
+
+def test_deterministic_graph_and_batched(gr):
+    """Bit-identical reruns, one-graph renders and batched views (each
+    pixel's class tickets are summed in sample order whatever the schedule)."""
+    scene = _rough_grating_scene()
+    v = _view(spp=24)
+    a = gr.render_image(scene, v, seed=8, flags=gr.FLAG_HERO | gr.FLAG_NEE)
+    assert np.array_equal(a, gr.render_image(scene, v, seed=8, flags=gr.FLAG_HERO | gr.FLAG_NEE))
+    assert np.array_equal(a, gr.render_image(scene, v, seed=8, flags=gr.FLAG_HERO | gr.FLAG_NEE, use_graph=True))
+    S = [gr.Scene(scene)]
+    views = [dict(v, view_index=0), dict(_view(width=11, height=7, spp=16, n_bins=12), view_index=1)]
+    f = gr.Frame(views)
+    gr.render(S, views, f, seed=8, flags=gr.FLAG_HERO | gr.FLAG_NEE)
+    for i, vi in enumerate(views):
+        single = gr.Frame([vi])
+        gr.render(S, [vi], single, seed=8, flags=gr.FLAG_HERO | gr.FLAG_NEE)
+        assert np.array_equal(f.readback(i), single.readback(0)), i
+
+
+def test_bins_not_multiple_of_four_rejected(gr):
+    scene = _rough_grating_scene()
+    v = _view(n_bins=6, spp=8)
+    s = gr.Scene(scene)
+    f = gr.Frame([v])
+    with pytest.raises(gr.GrError) as e:
+        gr.render([s], [v], f, flags=gr.FLAG_HERO)
+    assert e.value.status == 1
