@@ -758,11 +758,19 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
   // wavelength divided by its density at the hero's; it stays 1 through
   // wavelength-independent decisions and drops to 0 at a dispersive delta
   // (a grating order j != 0, a dispersive dielectric), where no other
-  // wavelength could have made the same path.  An escape is measured at every
-  // class wavelength and bin g receives T M_g cf_g q_g / sum_j cf_j q_j (the
-  // balance heuristic over the class's wavelengths, cf_j = share of the
-  // class's samples whose hero is bin j); contributions of emitters (hits and
-  // next-event estimation) stay with the hero, as without the flag.
+  // wavelength could have made the same path.  Every connection to a light is
+  // measured at each class wavelength (with that wavelength's footprint,
+  // carried along the path in fb2/frho) and weighted by multiple importance
+  // sampling over the techniques that could have made the path, with
+  // cf_j = share of the class's samples whose hero is bin j:
+  //  - an escape, or an emitter hit whose last direction only the lobe could
+  //    have sampled: balance heuristic over the class wavelengths,
+  //    T M_g cf_g q_g / sum_j cf_j q_j;
+  //  - an emitter hit after a diffuse rough vertex, and next-event estimation,
+  //    with NEE on: power heuristic over the eight (wavelength j, technique t
+  //    = lobe or emitter sampling) pairs with full path densities
+  //    cf_j P_j p_{j,t}; with one hero per class it is the plain estimator's
+  //    power heuristic between lobe and emitter sampling.
   // result[4 g + k] is class bin g's Stokes component k.
   const bool hero = (C.flags & FLAG_HERO) != 0;
   const int G = hero ? 4 : 1, Qb = V.n_bins / G;
@@ -783,7 +791,21 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
     for (int g = 0; g < G; ++g)
       if (g != gh) q[g] = 0.0;
   };
-  double* res_h = result + 4 * gh;
+  // qpre: q before the latest interaction (the density ratio of the path up
+  // to the vertex whose outgoing direction is being weighted); fb2/frho: the
+  // footprint (beta^2, rho) the path has at class wavelength g
+  double qpre[4], fb2[4], frho[4], kcls[4];
+  for (int g = 0; g < G; ++g) {
+    qpre[g] = 1.0;
+    fb2[g] = P.beta2;
+    frho[g] = P.rho;
+    kcls[g] = 2.0 * PI / lam_g[g];
+  }
+  // the vMF density of emitter sampling toward w at class wavelength g
+  auto nee_density = [&](int g, V3 w, V3 ne, double coh_len_um) {
+    const double s2g = 1.0 / (2.0 * beta0 * beta0 * kcls[g] * kcls[g]);
+    return vmf(w, neg(ne), 1.0 / (s2g + source_spread2(lam_g[g], coh_len_um))) / n_emit;
+  };
 
   for (int seg = 0;; ++seg) {
     // --- propagation: closest hit along d (point-hit assumption, Sec. 7.2)
@@ -814,9 +836,35 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
     }
     // footprint update over the segment (z in um; |k| = eta k0 in a medium)
     propagate(&P.beta2, &P.rho, th * 1e6 / (P.k * P.eta));
+    if (hero)
+      for (int g = 0; g < G; ++g) propagate(&fb2[g], &frho[g], th * 1e6 / (kcls[g] * P.eta));
     V3 x = P.o + th * P.d;
     const Tri& T = S.tris[prim];
     const Material& M = S.mats[T.mat];
+    if (M.type == MAT_EMITTER && hero) {
+      rng.draw(seg, CALL_EMIT_FOOT, u);
+      const V3 ne = tri_normal(T);
+      const bool two = (C.flags & FLAG_NEE) && !P.prev_delta && n_emit > 0;
+      const double pb = P.prev_pdf;  // the hero's lobe density of the last direction
+      // with two techniques, cf_j qpre_j p_{j,lobe} = cf_j q_j pb (q = qpre times
+      // the lobe density ratio of the last vertex)
+      double den = 0.0;
+      for (int j = 0; j < G; ++j) {
+        if (two) {
+          const double a = cf[j] * q[j] * pb, b = cf[j] * qpre[j] * nee_density(j, P.d, ne, M.coh_len_um);
+          den += a * a + b * b;
+        } else {
+          den += cf[j] * q[j];
+        }
+      }
+      for (int g = 0; g < G; ++g) {
+        if (cf[g] * q[g] == 0.0 || den == 0.0) continue;
+        const double m = measure_emitter(S, prim, x, P.d, fb2[g], frho[g], kcls[g], lam_g[g], u[0], u[1]);
+        const double w = two ? cf[g] * cf[gh] * q[g] * pb * pb / den : cf[g] * q[g] / den;
+        add_vec(result + 4 * g, ns, col, m * w);
+      }
+      return;
+    }
     if (M.type == MAT_EMITTER) {
       rng.draw(seg, CALL_EMIT_FOOT, u);
       double m = measure_emitter(S, prim, x, P.d, P.beta2, P.rho, P.k, P.lambda, u[0], u[1]);
@@ -828,7 +876,7 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
         double pb = P.prev_pdf;
         w = pb * pb / (pb * pb + pn * pn);
       }
-      add_vec(res_h, ns, col, m * w);
+      add_vec(result, ns, col, m * w);
       return;
     }
     if (M.type == MAT_ABSORBER) return;
@@ -851,6 +899,7 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
     if (dot(n, P.d) > 0.0) n = neg(n);
     double cos_i = -dot(P.d, n);
     V3 d_in = P.d;
+    for (int g = 0; g < G; ++g) qpre[g] = q[g];
 
     // Fresnel weight (Eq. K_reflection_refraction), as a Mueller matrix in the
     // s-p frames at the incidence angle of the arriving ray; diffractive lobes
@@ -1027,13 +1076,33 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
           V3 delta_t = (w - dot(w, n) * n) - t_mir;
           double f = (g_r > 0.0 ? rough_diffuse_density(g_r, P.k, M.corr_len_um, delta_t) : 0.0) * cos_o;
           double pn = vmf(w, neg(ne), kap) / n_emit;
-          if (f > 0.0 && pn > 0.0) {
+          if (hero && pn > 0.0) {
+            // joint power heuristic over (class wavelength, technique); the
+            // lobe density toward w at wavelength j (the cos factor included)
+            double pbw[4], den = 0.0;
+            for (int j = 0; j < G; ++j) {
+              pbw[j] = 0.0;
+              if (cf[j] * qpre[j] == 0.0) continue;
+              const double gj = std::pow(2.0 * kcls[j] * M.sigma_h_um * cos_i, 2);
+              pbw[j] = (gj > 0.0 ? rough_diffuse_density(gj, kcls[j], M.corr_len_um, delta_t) : 0.0) * cos_o;
+              const double a = cf[j] * qpre[j] * pbw[j], b = cf[j] * qpre[j] * nee_density(j, w, ne, EM.coh_len_um);
+              den += a * a + b * b;
+            }
+            rng.draw(seg, CALL_NEE_FOOT, uf);
+            for (int g = 0; g < G; ++g) {
+              if (pbw[g] == 0.0 || den == 0.0) continue;
+              double b2 = fb2[g], r = frho[g];
+              propagate(&b2, &r, ts * 1e6 / (kcls[g] * P.eta));
+              double m = measure_emitter(S, sp, x + ts * w, w, b2, r, kcls[g], lam_g[g], uf[0], uf[1]);
+              add_vec(result + 4 * g, ns, c_nee, m * cf[g] * cf[gh] * qpre[g] * pn * pbw[g] / den);
+            }
+          } else if (f > 0.0 && pn > 0.0) {
             double b2 = P.beta2, r = P.rho;
             propagate(&b2, &r, ts * 1e6 / (P.k * P.eta));
             rng.draw(seg, CALL_NEE_FOOT, uf);
             double m = measure_emitter(S, sp, x + ts * w, w, b2, r, P.k, P.lambda, uf[0], uf[1]);
             double wmis = pn * pn / (pn * pn + f * f);
-            add_vec(res_h, ns, c_nee, m * f / pn * wmis);
+            add_vec(result, ns, c_nee, m * f / pn * wmis);
           }
         }
       }
