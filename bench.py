@@ -73,14 +73,15 @@ def parse():
     ap.add_argument("--cpu-crop", type=int, default=128, help="side of the oracle's centre crop")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", choices=["procedural", "batched", "serving", "precision", "dielectric",
-                                           "doubleslit"],
+                                           "doubleslit", "hero"],
                     default="procedural",
                     help="procedural: the headline single-view workload; batched: 64 views/scenes, plain "
                          "per-view FP32 form vs the autotuned single-graph form; serving: "
                          "Poisson-arriving progressive requests; precision: FP32/FP16/BF16 order tables, "
                          "image and per-quantity errors vs the FP64 oracle; dielectric: the procedural "
                          "workload with refracting glass slabs; doubleslit: footprint-resolved generalized "
-                         "rays through two slits at scale")
+                         "rays through two slits at scale; hero: the procedural workload with "
+                         "hero-wavelength spectral MIS vs without (throughput, variance, efficiency)")
     ap.add_argument("--views", type=int, default=64)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--rates", default="5,50,100", help="serving: further arrival rates to sweep (req/s)")
@@ -444,6 +445,95 @@ def run_doubleslit(args):
     print(json.dumps(line))
 
 
+def run_hero(args):
+    """Hero-wavelength spectral MIS (Sec. 7.2) on the headline procedural
+    workload: throughput with and without the flag, with per-kernel device
+    time; rel-L2 of the hero image against the oracle's hero estimator on a
+    centre crop; and the variance of both estimators across independent
+    seeds at equal samples per pixel, so that efficiency = (variance x time
+    per sample) of the plain estimator over that of the hero estimator (> 1:
+    hero MIS reaches a given noise sooner)."""
+    import numpy as np
+    import torch
+    import paper_2303_15762_gb300 as gr
+    from paper_2303_15762_gb300 import scenegen as sg
+    gr.load()
+    scene, view = workload(args, 0)
+    samples = view["width"] * view["height"] * view["spp"]
+    S = gr.Scene(scene)
+    F = gr.Frame([view])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    modes = {"plain": gr.FLAG_NEE, "hero": gr.FLAG_NEE | gr.FLAG_HERO}
+
+    def step(flags, profile=False):
+        F.reset()
+        gr.render([S], [view], F, seed=2, flags=flags, table_dtype=args.table, pool_size=args.pool, profile=profile)
+
+    ms, kernel_ms, clk = {}, {}, None
+    for name, flags in modes.items():
+        for _ in range(max(3, args.warmup)):
+            step(flags)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0) if name == "hero" else None
+        times, kms = [], [0.0] * 4
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(flags, profile=True)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            st = F.stats()
+            for k in range(4):
+                kms[k] += st["kernel_ms"][k] / args.steps
+        if clocks is not None:
+            clk = clocks.stop()
+        ms[name] = statistics.mean(times)
+        kernel_ms[name] = {KERNELS[k]: kms[k] for k in range(4)}
+    img = F.readback(0)  # the last hero render
+    st = F.stats()
+    rel = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as orc
+        c = min(args.cpu_crop, args.size)
+        x0 = args.size // 2 - c // 2
+        ref = orc.Scene(scene).render(view, 2, orc.FLAG_NEE | orc.FLAG_HERO, crop=(x0, x0, x0 + c, x0 + c))
+        rel = float(np.linalg.norm(img[x0:x0 + c, x0:x0 + c].astype(np.float64) - ref) /
+                    max(np.linalg.norm(ref), 1e-300))
+    # variance across seeds at equal samples (a smaller view of the same camera)
+    vv = sg.procedural_view(width=128, height=128, spp=32)
+    Fv = gr.Frame([vv])
+    var = {}
+    n_seeds = 8
+    for name, flags in modes.items():
+        imgs = []
+        for sd in range(n_seeds):
+            Fv.reset()
+            gr.render([S], [vv], Fv, seed=100 + sd, flags=flags)
+            imgs.append(Fv.readback(0).astype(np.float64))
+        a = np.stack(imgs)
+        v = np.var(a, axis=0, ddof=1)
+        var[name] = {"total": float(v[..., 0].sum()), "mean_intensity": float(a[..., 0].mean())}
+    vratio = var["plain"]["total"] / max(var["hero"]["total"], 1e-300)
+    line = {"workload": "hero", "metric": METRIC, "unit": UNIT, "value": samples / (ms["hero"] * 1e-3) / 1e6,
+            "plain_value": samples / (ms["plain"] * 1e-3) / 1e6, "ms_hero": ms["hero"], "ms_plain": ms["plain"],
+            "kernel_ms_per_step": kernel_ms, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(args, scene) + ", hero-wavelength MIS over classes of 4 bins",
+                       "l2": "flushed before every timed step (256 MB write)"},
+            "rel_l2_vs_oracle_hero": rel,
+            "variance_ratio_plain_over_hero": vratio,
+            "efficiency_plain_over_hero": vratio * ms["plain"] / ms["hero"],
+            "variance": {"view": "128x128, 32 spp, 32 bins, intensity (Stokes I), %d seeds per estimator" % n_seeds,
+                         **var},
+            "clocks": clk, "stats": {"iterations": st["iterations"], "segments": st["segments"],
+                                     "shadow_rays": st["shadow_rays"]}}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -460,6 +550,9 @@ def main():
         return
     if args.workload == "doubleslit":
         run_doubleslit(args)
+        return
+    if args.workload == "hero":
+        run_hero(args)
         return
     world, rank, local = dist_setup()
     import numpy as np

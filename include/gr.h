@@ -146,13 +146,15 @@ typedef struct {
  * same closest hits; the wide tree halves node visits but needs more
  * registers per thread); GR_FLAG_HERO hero-wavelength spectral MIS (Sec. 7.2):
  * with n_bins a multiple of 4, a path's bin is the hero of the class of bins
- * {c, c+Q, c+2Q, c+3Q} (Q = n_bins/4) and drives every sampling decision; an
- * escape to distant sources is measured at all four wavelengths, weighted by
- * the balance heuristic over the class wavelengths' path densities (zero for
- * a wavelength after a dispersive delta: a grating order j != 0 or a
- * dispersive dielectric), while emitter hits and next-event contributions
- * stay with the hero; each bin is still divided by the number of samples
- * whose hero it is (GR_E_INVALID if n_bins % 4 != 0; not available in
+ * {c, c+Q, c+2Q, c+3Q} (Q = n_bins/4) and drives every sampling decision;
+ * every connection to a light (escape, emitter hit, next-event estimate) is
+ * measured at all four wavelengths, each with its own footprint, and weighted
+ * by multiple importance sampling over the class wavelengths' path densities
+ * (zero for a wavelength after a dispersive delta: a grating order j != 0 or
+ * a dispersive dielectric) -- the balance heuristic where only lobe sampling
+ * could make the path, the power heuristic over (wavelength, lobe or emitter
+ * sampling) where next-event estimation could too; each bin is still divided
+ * by the number of samples whose hero it is (GR_E_INVALID if n_bins % 4 != 0; not available in
  * gr_render_static).  table_dtype: storage of the grating order tables
  * (GR_TABLE_F32 / F16 / BF16); arithmetic is FP32 either way.  pool_size:
  * wavefront slots (0 = default); block: threads per block (0 = default). */

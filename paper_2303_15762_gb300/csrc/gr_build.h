@@ -29,14 +29,16 @@ struct Pool {
   float4* shm;   // NEE lobe terms: squared offset, g, (k l)^2, cos
   float4* mis;   // lobe terms of the vertex that sampled the current direction
   float2* hit;   // t, leaf slot
-  int4* meta;    // view, local ticket, (sample k | seg << 16 | state << 24 | delta << 26 | escaped << 27),
-                 // previous leaf slot
+  int4* meta;    // view, local ticket, (sample k | seg << 16 | state << 24 | delta << 26), previous leaf slot
   int* tq;       // trace queue
   int* sq;       // shadow queue
   // hero-wavelength MIS only (null otherwise); planes [g * P + slot] for the
   // class member g (bin c + g Q)
   float4* hq;    // path density ratios q_g of the class wavelengths to the hero's
-  float4* hpart; // [4] the current sample's escape contribution to member g (g != hero)
+  float4* hqp;   // the same ratios before the latest interaction
+  float4* hfb;   // beta^2 of the path's footprint at each class wavelength
+  float4* hfr;   // rho of the path's footprint at each class wavelength
+  float4* hpart; // [4] the current sample's contributions to member g (g != hero)
   float4* haccS; // [4] ticket sums of member g (Kahan)
   float4* haccC; // [4] ticket compensations of member g
 };

@@ -55,8 +55,6 @@ __device__ __forceinline__ int meta_pack(int k, int seg, int st, int delta) {
   return k | (seg << 16) | (st << 24) | (delta << 26);
 }
 
-__device__ __forceinline__ int meta_escaped(int z) { return (z >> 27) & 1; }
-
 // First sample s >= first_sample with s mod Q == c, and the number of the
 // view's samples in that residue class.  A ticket owns one class: with Q = nb
 // a class is one wavelength bin; with hero-wavelength MIS (Q = nb/4) the
@@ -72,6 +70,12 @@ __device__ __forceinline__ int class_samples(const DevView& V, int c, int Q) {
   return s0 < end ? (end - 1 - s0) / Q + 1 : 0;
 }
 __device__ __forceinline__ int bin_samples(const DevView& V, int bin) { return class_samples(V, bin, V.nb); }
+// cf[g]: the share of class c's samples (modulus Q) whose hero is bin c + g Q.
+__device__ __forceinline__ void class_shares(const DevView& V, int c, int Q, float cf[4]) {
+  const float n = (float)class_samples(V, c, Q);
+#pragma unroll
+  for (int g = 0; g < 4; ++g) cf[g] = (float)bin_samples(V, c + g * Q) / n;
+}
 __device__ __forceinline__ float bin_lambda(const DevView& V, int b) {
   if (V.nb <= 1) return V.lmin;
   return V.lmin + (float)b * (V.lmax - V.lmin) / (float)(V.nb - 1);
@@ -121,7 +125,7 @@ __device__ __forceinline__ float table_load<__nv_bfloat16>(const __nv_bfloat16* 
 }
 
 // ------------------------------------------------------------------ sourcing
-template <int NS>
+template <int NS, bool HERO>
 __device__ __forceinline__ void start_sample(const RenderParams& p, int slot, int view, int local, int k) {
   const DevView& V = p.views[view];
   const int WH = V.W * V.H;
@@ -148,6 +152,8 @@ __device__ __forceinline__ void start_sample(const RenderParams& p, int slot, in
   // contribution (zero) of a camera segment are implied by segment 0: k_shade
   // forms them instead of reading them
   P.meta[slot] = make_int4(view, local, meta_pack(k, 0, ST_ACTIVE, 1), -1);
+  if (HERO)  // the sample's contributions to the other bins of its class
+    for (int g = 0; g < 4; ++g) P.hpart[(size_t)g * p.P + slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
 // Sum a per-thread count over the warp and add it with one atomic.
@@ -207,9 +213,9 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
 
 // ------------------------------------------------------------------ regen
 // Hero-wavelength MIS: fold the finished sample into the ticket's four member
-// sums (member g = bin c + g Q): its own contribution (escape share, emitter
-// hits, next-event terms) into the hero's member, its escape shares of the
-// other class wavelengths into theirs.  On the ticket's last sample every
+// sums (member g = bin c + g Q): its own contribution into the hero's member,
+// its shares at the other class wavelengths (escapes, emitter hits,
+// next-event estimates) into theirs.  On the ticket's last sample every
 // member's total goes to its bin's frame accumulator.  Returns true if the
 // ticket has more samples.
 template <int NS>
@@ -221,10 +227,9 @@ __device__ __forceinline__ bool fold_class(const RenderParams& p, int slot, cons
   const int k = meta_k(m.z);
   const int gh = ((class_first_sample(V, cls, V.Q) + k * V.Q) % V.nb) / V.Q;
   const bool more = k + 1 < class_samples(V, cls, V.Q);
-  const bool esc = meta_escaped(m.z);
   const size_t Ps = (size_t)p.P;
   for (int g = 0; g < 4; ++g) {
-    const float4 v = g == gh ? P.part[slot] : (esc ? P.hpart[g * Ps + slot] : make_float4(0.f, 0.f, 0.f, 0.f));
+    const float4 v = g == gh ? P.part[slot] : P.hpart[g * Ps + slot];
     float4 sm = P.haccS[g * Ps + slot], c = P.haccC[g * Ps + slot];
     kahan_add(sm.x, c.x, v.x);
     if (NS == 4) {
@@ -272,7 +277,7 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
     if (valid && st == ST_DONE && HERO) {
       ++finished;
       if (fold_class<NS>(p, slot, m)) {
-        start_sample<NS>(p, slot, m.x, m.y, meta_k(m.z) + 1);
+        start_sample<NS, true>(p, slot, m.x, m.y, meta_k(m.z) + 1);
         active = fresh = true;
       } else {
         need = true;
@@ -293,7 +298,7 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
       if (k < bin_samples(V, bin)) {
         P.accS[slot] = s;
         P.accC[slot] = c;
-        start_sample<NS>(p, slot, m.x, m.y, k);
+        start_sample<NS, false>(p, slot, m.x, m.y, k);
         active = fresh = true;
       } else {
         // ticket complete: add its sum into the frame accumulator (Kahan)
@@ -347,7 +352,7 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
               P.accS[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
               P.accC[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
-            start_sample<NS>(p, slot, view, cls * (V.W * V.H) + pix, 0);
+            start_sample<NS, HERO>(p, slot, view, cls * (V.W * V.H) + pix, 0);
             active = fresh = true;
             need = false;
           }
@@ -627,6 +632,45 @@ __device__ float rough_density(float g, float kl2, float r2) {
   return sum;
 }
 
+// The same density at the four wavelengths of a hero class (roughness g_j,
+// kl2_j = (|k_j| l)^2) at one squared offset r2, in one pass over the term
+// count m: term m is e^-g g^m / m! * kl2 / (4 pi m) * exp(-r2 kl2 / (4 m)),
+// one reciprocal per m shared by the four wavelengths and no division.  The
+// sum stops once m has passed every g_j and every Poisson weight is below
+// 1e-13 (or at rough_density's bound).  want[j] false gives 0.
+__device__ void rough_density_class(const float g[4], const float kl2[4], const bool want[4], float r2, float out[4]) {
+  float pm[4], c[4], a[4];
+  bool pois[4];
+  float gmax = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    out[j] = 0.0f;
+    pois[j] = want[j] && g[j] > 0.0f && g[j] <= kGCont;
+    if (want[j] && g[j] > kGCont) {
+      const float var = 2.0f * g[j] / kl2[j];
+      out[j] = __expf(-0.5f * r2 / var) / (2.0f * kPi * var);
+    }
+    pm[j] = pois[j] ? __expf(-g[j]) : 0.0f;
+    c[j] = 0.25f * r2 * kl2[j];
+    a[j] = kl2[j] * (0.25f / kPi);
+    if (pois[j]) gmax = fmaxf(gmax, g[j]);
+  }
+  if (gmax == 0.0f) return;
+  const int mmax = (int)(gmax + 12.0f * sqrtf(gmax) + 20.0f);
+  for (int m = 1; m <= mmax; ++m) {
+    const float inv = __frcp_rn((float)m);
+    float big = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!pois[j]) continue;
+      pm[j] *= g[j] * inv;
+      out[j] += pm[j] * (a[j] * inv) * __expf(-c[j] * inv);
+      big = fmaxf(big, pm[j]);
+    }
+    if ((float)m > gmax && big < 1e-13f) break;
+  }
+}
+
 // Conservative precheck of a next-event ray toward emitter ei: false only if
 // the ray's closest hit cannot be a front-face point of that (planar) emitter
 // -- its plane is behind the ray or met from the back (where the emitter does
@@ -782,10 +826,14 @@ __device__ __forceinline__ float order0_prob(const TableRow& row, float3 t_mir, 
 // of its class {c, c+Q, c+2Q, c+3Q} and makes every decision; hq[g] holds the
 // path's density at class wavelength g divided by its density at the hero's
 // (1 through wavelength-independent decisions, the ratio of order-0 or rough
-// lobe densities, 0 after a dispersive delta).  An escape is measured at each
-// class wavelength with weight cf_g hq_g / sum_j cf_j hq_j (balance heuristic;
-// cf_j = the class's share of samples whose hero is bin j); emitter hits and
-// next-event terms stay with the hero.
+// lobe densities, 0 after a dispersive delta); fb/fr carry the footprint at
+// each class wavelength.  Every connection to a light is measured at each
+// class wavelength: escapes (and emitter hits after a delta vertex) with the
+// balance heuristic cf_g hq_g / sum_j cf_j hq_j (cf_j = the class's share of
+// samples whose hero is bin j); emitter hits after a diffuse vertex and
+// next-event estimates, with NEE on, with the power heuristic over the
+// (wavelength, lobe or emitter sampling) pairs, which with one hero per class
+// is the plain lobe/emitter power heuristic.
 template <int NS, typename TT, bool HERO>
 __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(RenderParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -863,12 +911,24 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
         hq[2] = q4.z;
         hq[3] = q4.w;
       }
+      // the path's footprint at each class wavelength (camera footprint on
+      // the first segment)
+      float fb[4], fr[4];
+      if (HERO) {
+        if (seg > 0) {
+          const float4 b4 = P.hfb[slot], r4 = P.hfr[slot];
+          fb[0] = b4.x, fb[1] = b4.y, fb[2] = b4.z, fb[3] = b4.w;
+          fr[0] = r4.x, fr[1] = r4.y, fr[2] = r4.z, fr[3] = r4.w;
+        } else {
+#pragma unroll
+          for (int g = 0; g < 4; ++g) fb[g] = beta2, fr[g] = rho;
+        }
+      }
       auto drop_companions = [&]() {
 #pragma unroll
         for (int g = 0; g < 4; ++g)
           if (g != gh) hq[g] = 0.0f;
       };
-      int escaped = 0;
       const int hslot = __float_as_int(hh.y);
       bool done = false;
       auto add_col = [&](float val) {
@@ -879,15 +939,29 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
           pt.w += T[3][0] * val;
         }
       };
+      // a contribution to class member g: the hero's into the sample's own
+      // sum, the others' into their planes
+      auto add_member = [&](int g, float val) {
+        if (g == gh) {
+          add_col(val);
+          return;
+        }
+        float4* hp = P.hpart + (size_t)g * p.P + slot;
+        float4 c = *hp;
+        c.x += T[0][0] * val;
+        if (NS == 4) {
+          c.y += T[1][0] * val;
+          c.z += T[2][0] * val;
+          c.w += T[3][0] * val;
+        }
+        *hp = c;
+      };
       if (hslot < 0 && HERO) {
         // escape measured at every class wavelength, balance-heuristic weights
         float cf[4], den = 0.0f;
-        const float ncls = (float)class_samples(V, cls, Qv);
+        class_shares(V, cls, Qv, cf);
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          cf[g] = (float)bin_samples(V, cls + g * Qv) / ncls;
-          den += cf[g] * hq[g];
-        }
+        for (int g = 0; g < 4; ++g) den += cf[g] * hq[g];
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
           const float wq = cf[g] * hq[g];
@@ -908,13 +982,8 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
             }
             val = mg * (wq / den);
           }
-          if (g == gh)
-            add_col(val);
-          else
-            P.hpart[(size_t)g * p.P + slot] = make_float4(T[0][0] * val, NS == 4 ? T[1][0] * val : 0.0f,
-                                                          NS == 4 ? T[2][0] * val : 0.0f, NS == 4 ? T[3][0] * val : 0.0f);
+          add_member(g, val);
         }
-        escaped = 1;
         done = true;
       } else if (hslot < 0) {
         float msum = 0.0f;
@@ -933,10 +1002,51 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
         const float t = hh.x;
         const float eta = xfv.w;  // |k| = eta k0 in the current medium
         footprint_update(t, kw * eta, beta2, rho);
+        if (HERO) {
+#pragma unroll
+          for (int g = 0; g < 4; ++g) footprint_update(t, 2.0f * kPi / bin_lambda(V, cls + g * Qv) * eta, fb[g], fr[g]);
+        }
         const float3 x = o + t * d;
         const int mat = S.tri_mat[hslot];
         const gr_material M = S.mats[mat];
-        if (M.type == GR_MAT_EMITTER) {
+        if (M.type == GR_MAT_EMITTER && HERO) {
+          // the hit measured at every class wavelength with its footprint; with
+          // NEE after a diffuse vertex, power heuristic over the (wavelength,
+          // technique) pairs: cf_j qpre_j p_{j,lobe} = cf_j q_j pb, cf_j qpre_j
+          // p_{j,emitter}; else balance over the wavelengths
+          const int ei = S.emitter_of_mat[mat];
+          const float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallEmitFoot);
+          const bool two = (p.flags & GR_FLAG_NEE) && !prev_delta && S.n_emitters > 0;
+          float cf[4], qp[4] = {1.0f, 1.0f, 1.0f, 1.0f}, pb = 0.0f, den = 0.0f;
+          class_shares(V, cls, Qv, cf);
+          const float3 ne = emitter_normal(S, ei);
+          if (two) {
+            const float4 mi = P.mis[slot];  // (r2, g, kl2, cos) of the rough vertex that sampled d
+            pb = rough_density(mi.y, mi.z, mi.x) * mi.w;
+            const float4 q4 = P.hqp[slot];
+            qp[0] = q4.x, qp[1] = q4.y, qp[2] = q4.z, qp[3] = q4.w;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (two) {
+              const float lj = bin_lambda(V, cls + j * Qv), kj = 2.0f * kPi / lj;
+              const float kap = 1.0f / (1.0f / (2.0f * V.beta0 * V.beta0 * kj * kj) + src_spread2(lj, M.coh_len_um));
+              const float a = cf[j] * hq[j] * pb, b = cf[j] * qp[j] * vmf(-d, ne, kap) / (float)S.n_emitters;
+              den += a * a + b * b;
+            } else {
+              den += cf[j] * hq[j];
+            }
+          }
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            if (!(cf[g] * hq[g] > 0.0f) || !(den > 0.0f)) continue;
+            const float lg = bin_lambda(V, cls + g * Qv);
+            const float mg = measure_emitter(S, ei, x, d, fb[g], fr[g], 2.0f * kPi / lg, lg, u.x, u.y);
+            const float w = two ? cf[g] * cf[gh] * hq[g] * pb * pb / den : cf[g] * hq[g] / den;
+            add_member(g, mg * w);
+          }
+          done = true;
+        } else if (M.type == GR_MAT_EMITTER) {
           const int ei = S.emitter_of_mat[mat];
           float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallEmitFoot);
           float val = measure_emitter(S, ei, x, d, beta2, rho, kw, lambda, u.x, u.y);
@@ -967,6 +1077,14 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
           }
           if (!done) {
             // --- interaction with the reversed wavevector
+            if (HERO) {
+              // the density ratios before this vertex's decision and the
+              // footprints at the vertex, for its next-event estimate and for
+              // an emitter hit by the direction it samples
+              P.hqp[slot] = make_float4(hq[0], hq[1], hq[2], hq[3]);
+              P.hfb[slot] = make_float4(fb[0], fb[1], fb[2], fb[3]);
+              P.hfr[slot] = make_float4(fr[0], fr[1], fr[2], fr[3]);
+            }
             const float4 v0 = __ldg(&S.tri[3 * hslot]), v1 = __ldg(&S.tri[3 * hslot + 1]),
                          v2 = __ldg(&S.tri[3 * hslot + 2]);
             float3 nrm = normalize(cross(xyz(v1) - xyz(v0), xyz(v2) - xyz(v0)));
@@ -1117,19 +1235,25 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
                 // the class wavelengths' densities of the lobe term just sampled:
                 // specular e^-g, or the m >= 1 density at the sampled offset
                 // (the cosine factor is common to all wavelengths)
-                const float dh = mreal == 0.0f ? 0.0f : rough_density(g_r, mis_rec.z, mis_rec.x);
+                // (g and (k l)^2 scale with k^2 across the class)
+                float gq[4], klq[4], dens[4];
+                bool want[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  const float kj = 2.0f * kPi / bin_lambda(V, cls + j * Qv);
+                  const float sc = (kj / kw) * (kj / kw);
+                  gq[j] = g_r * sc;
+                  klq[j] = mis_rec.z * sc;
+                  want[j] = mreal != 0.0f && (j == gh || hq[j] != 0.0f);
+                }
+                if (mreal != 0.0f) rough_density_class(gq, klq, want, mis_rec.x, dens);
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
                   if (g == gh || hq[g] == 0.0f) continue;
-                  const float kg = 2.0f * kPi / bin_lambda(V, cls + g * Qv);
-                  float gg = 2.0f * kg * M.sigma_h_um * cos_i;
-                  gg *= gg;
-                  if (mreal == 0.0f) {
-                    hq[g] *= gg > kGCont ? 0.0f : expf(g_r - gg);
-                  } else {
-                    const float klg = kg * M.corr_len_um;
-                    hq[g] = dh > 0.0f ? hq[g] * (rough_density(gg, klg * klg, mis_rec.x) / dh) : 0.0f;
-                  }
+                  if (mreal == 0.0f)
+                    hq[g] *= gq[g] > kGCont ? 0.0f : expf(g_r - gq[g]);
+                  else
+                    hq[g] = dens[gh] > 0.0f ? hq[g] * (dens[g] / dens[gh]) : 0.0f;
                 }
               }
             }
@@ -1179,7 +1303,7 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
         }
       }
       P.part[slot] = pt;
-      if (done) P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg, ST_DONE, 0) | (escaped << 27), m.w);
+      if (done) P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg, ST_DONE, 0), m.w);
     }
     const int q = block_reserve<int>(&p.ctr->sq_count, want_shadow);
     if (want_shadow) P.sq[q] = slot;
@@ -1241,11 +1365,92 @@ __device__ __forceinline__ void shadow_finish(const RenderParams& p, int slot, c
   }
 }
 
+// The same with hero-wavelength MIS: the estimate is measured at every class
+// wavelength (footprints of the vertex, stored by k_shade) and weighted by
+// the power heuristic over the (wavelength j, technique) pairs, with full
+// path densities cf_j qpre_j p_{j,lobe}(w) and cf_j qpre_j p_{j,emitter}(w);
+// a class wavelength's lobe density scales the hero's g and (k l)^2 by
+// (k_j / k)^2.
+template <int NS>
+__device__ __forceinline__ void shadow_finish_hero(const RenderParams& p, int slot, const Hit& h) {
+  const Pool& P = p.pool;
+  const int4 m = P.meta[slot];
+  const DevView& V = p.views[m.x];
+  const DevScene& S = p.scenes[V.scene_index];
+  const float4 sd = P.shd[slot];
+  const int tag = __float_as_int(sd.w);
+  const int ei = tag & 0xffff, seg = tag >> 16;
+  if (h.slot < 0 || S.tri_mat[h.slot] != S.emitters[ei].mat) return;
+  const float3 x = xyz(P.od0[slot]), w = xyz(sd);
+  const int WH = V.W * V.H;
+  const int cls = m.y / WH;
+  const int pixel = m.y - cls * WH;
+  const int Qv = V.Q;
+  const int smp = class_first_sample(V, cls, Qv) + meta_k(m.z) * Qv;
+  const int bin = smp % V.nb;
+  const int gh = (bin - cls) / Qv;
+  const float kw = 2.0f * kPi / bin_lambda(V, bin);
+  const float eta = seg == 0 ? 1.0f : (NS == 1 ? P.tp[0][slot].y : P.xf[slot].w);
+  const float3 nE = emitter_normal(S, ei);
+  const float lc = S.mats[S.emitters[ei].mat].coh_len_um;
+  const float inv_ne = 1.0f / (float)S.n_emitters;
+  const float4 sm = P.shm[slot];  // squared offset, g, (k l)^2, cos of the hero's lobe toward w
+  const float4 q4 = P.hqp[slot];
+  const float qp[4] = {q4.x, q4.y, q4.z, q4.w};
+  float cf[4], pbw[4], gq[4], klq[4], pn_h = 0.0f, den = 0.0f;
+  bool want[4];
+  class_shares(V, cls, Qv, cf);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float kj = 2.0f * kPi / bin_lambda(V, cls + j * Qv);
+    const float sc = (kj / kw) * (kj / kw);
+    gq[j] = sm.y * sc;
+    klq[j] = sm.z * sc;
+    want[j] = cf[j] * qp[j] > 0.0f;
+  }
+  rough_density_class(gq, klq, want, sm.x, pbw);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    pbw[j] *= sm.w;
+    const float cq = cf[j] * qp[j];
+    if (!(cq > 0.0f)) continue;
+    const float lj = bin_lambda(V, cls + j * Qv), kj = 2.0f * kPi / lj;
+    const float kap = 1.0f / (1.0f / (2.0f * V.beta0 * V.beta0 * kj * kj) + src_spread2(lj, lc));
+    const float pn = vmf(w, -nE, kap) * inv_ne;
+    if (j == gh) pn_h = pn;
+    den += cq * cq * (pbw[j] * pbw[j] + pn * pn);
+  }
+  if (!(pn_h > 0.0f) || !(den > 0.0f)) return;
+  const float4 b4 = P.hfb[slot], r4 = P.hfr[slot];
+  const float fb[4] = {b4.x, b4.y, b4.z, b4.w}, fr[4] = {r4.x, r4.y, r4.z, r4.w};
+  const float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallNeeFoot);
+  const float4 c = P.shc[slot];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    if (!(pbw[g] > 0.0f)) continue;
+    const float lg = bin_lambda(V, cls + g * Qv), kg = 2.0f * kPi / lg;
+    float b2 = fb[g], ro = fr[g];
+    footprint_update(h.t, kg * eta, b2, ro);
+    const float mg = measure_emitter(S, ei, x + h.t * w, w, b2, ro, kg, lg, u.x, u.y);
+    const float val = mg * cf[g] * cf[gh] * qp[g] * pn_h * pbw[g] / den;
+    if (val == 0.0f) continue;
+    float4* dst = g == gh ? P.part + slot : P.hpart + (size_t)g * p.P + slot;
+    float4 pt = *dst;
+    pt.x += c.x * val;
+    if (NS == 4) {
+      pt.y += c.y * val;
+      pt.z += c.z * val;
+      pt.w += c.w * val;
+    }
+    *dst = pt;
+  }
+}
+
 // NEE shadow rays: closest hit from the interaction point toward the sampled
 // emitter direction, then shadow_finish, one ray per thread per pass (the
 // shadow queue is a third as long as the trace queue: too short for
 // lane_trace's refill schedule to pay for itself).
-template <int NS, bool WIDE>
+template <int NS, bool WIDE, bool HERO>
 __global__ void __launch_bounds__(256, GR_SHADOW_MIN_BLOCKS) k_shadow(RenderParams p) {
   const Pool& P = p.pool;
   const int n = *(volatile int*)&p.ctr->sq_count;
@@ -1257,7 +1462,10 @@ __global__ void __launch_bounds__(256, GR_SHADOW_MIN_BLOCKS) k_shadow(RenderPara
     const float3 o = xyz(P.od0[slot]), d = xyz(P.shd[slot]);  // requested only if emitter_reachable
     const Hit h = WIDE ? closest_hit_wide(S, o, d, m.w, &refined, &visits, &tests, &err)
                        : closest_hit(S, o, d, m.w, &refined, &visits, &tests, &err);
-    shadow_finish<NS>(p, slot, h);
+    if (HERO)
+      shadow_finish_hero<NS>(p, slot, h);
+    else
+      shadow_finish<NS>(p, slot, h);
   }
   block_count(&p.ctr->ref_hit, refined);
   block_count(&p.ctr->node_visits, visits);
@@ -1468,10 +1676,14 @@ cudaError_t launch_iteration(const RenderParams& p, int grid_regen, int grid_tra
   else
     k_shade<NS, TT, false><<<grid_shade, block, smem, st>>>(p);
   if (ev) cudaEventRecord(ev[3], st);
-  if (wide)
-    k_shadow<NS, true><<<grid_shadow, block, 0, st>>>(p);
+  if (wide && hero)
+    k_shadow<NS, true, true><<<grid_shadow, block, 0, st>>>(p);
+  else if (wide)
+    k_shadow<NS, true, false><<<grid_shadow, block, 0, st>>>(p);
+  else if (hero)
+    k_shadow<NS, false, true><<<grid_shadow, block, 0, st>>>(p);
   else
-    k_shadow<NS, false><<<grid_shadow, block, 0, st>>>(p);
+    k_shadow<NS, false, false><<<grid_shadow, block, 0, st>>>(p);
   if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError();
 }
@@ -1594,7 +1806,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const size_t o_tq = take(sizeof(int) * (size_t)P);
   const size_t o_sq = take(sizeof(int) * (size_t)P);
   const bool hero = (o.flags & GR_FLAG_HERO) != 0;
-  const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 13) : 0;  // hq, hpart[4], haccS[4], haccC[4]
+  const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 16) : 0;  // hq, hqp, hfb, hfr, hpart/haccS/haccC[4]
   const size_t total = off;
   if (f->scratch_bytes < total) {
     if (f->scratch) cudaFreeAsync(f->scratch, st);
@@ -1639,9 +1851,12 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   if (hero) {
     float4* h4 = (float4*)(base + o_hero);
     p.pool.hq = h4;
-    p.pool.hpart = h4 + (size_t)P;
-    p.pool.haccS = h4 + (size_t)P * 5;
-    p.pool.haccC = h4 + (size_t)P * 9;
+    p.pool.hqp = h4 + (size_t)P;
+    p.pool.hfb = h4 + (size_t)P * 2;
+    p.pool.hfr = h4 + (size_t)P * 3;
+    p.pool.hpart = h4 + (size_t)P * 4;
+    p.pool.haccS = h4 + (size_t)P * 8;
+    p.pool.haccC = h4 + (size_t)P * 12;
   }
   p.P = P;
   p.regen_thr = o.regen_threshold_pct;
@@ -1699,7 +1914,9 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   int g_regen, g_trace, g_shade, g_shadow;
   const void* shade_fn = shade_kernel(NSv, o.table_dtype, hero);
   g_regen = grid_for(regen_kernel(NSv, hero), 0);
-  g_shadow = grid_for(NSv == 1 ? (const void*)k_shadow<1, false> : (const void*)k_shadow<4, false>, 0);
+  g_shadow = grid_for(NSv == 1 ? (hero ? (const void*)k_shadow<1, false, true> : (const void*)k_shadow<1, false, false>)
+                                : (hero ? (const void*)k_shadow<4, false, true> : (const void*)k_shadow<4, false, false>),
+                      0);
   const bool wide_bvh = (o.flags & GR_FLAG_WIDE_BVH) != 0;
   const int tblk = wide_bvh ? block : trace_block(block);
   g_trace = wide_bvh ? grid_for((const void*)k_trace<true>, 0) : grid_for((const void*)k_trace<false>, 0, tblk);
@@ -2118,7 +2335,8 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
       std::min((int)((P + tblk - 1) / tblk), wide_bvh ? grid_for((const void*)k_trace<true>, 0)
                                                        : grid_for((const void*)k_trace<false>, 0, tblk));
   const int g_shade = std::min(gmax, grid_for(shade_fn, smem));
-  const int g_shadow = std::min(gmax, grid_for(NSv == 1 ? (const void*)k_shadow<1, false> : (const void*)k_shadow<4, false>, 0));
+  const int g_shadow =
+      std::min(gmax, grid_for(NSv == 1 ? (const void*)k_shadow<1, false, false> : (const void*)k_shadow<4, false, false>, 0));
   // --- iteration loop; the host reads the device counters into a stack copy
   // after every batch (no events, no pinned buffer)
   long long n_max = 1, d_max = 0;
