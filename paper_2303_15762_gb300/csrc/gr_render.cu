@@ -70,6 +70,14 @@ __device__ __forceinline__ int class_samples(const DevView& V, int c, int Q) {
   return s0 < end ? (end - 1 - s0) / Q + 1 : 0;
 }
 __device__ __forceinline__ int bin_samples(const DevView& V, int bin) { return class_samples(V, bin, V.nb); }
+// Wavelength of bin b from the bin step (lmax - lmin) / (nb - 1), computed
+// once per path: the class wavelengths of hero-wavelength MIS cost one
+// multiply-add each instead of a division.
+__device__ __forceinline__ float bin_step(const DevView& V) {
+  return V.nb <= 1 ? 0.0f : (V.lmax - V.lmin) / (float)(V.nb - 1);
+}
+__device__ __forceinline__ float step_lambda(const DevView& V, float step, int b) { return V.lmin + (float)b * step; }
+constexpr float kInv2Pi = 0.15915494309189535f;
 // cf[g]: the share of class c's samples (modulus Q) whose hero is bin c + g Q.
 __device__ __forceinline__ void class_shares(const DevView& V, int c, int Q, float cf[4]) {
   const float n = (float)class_samples(V, c, Q);
@@ -548,6 +556,15 @@ __device__ __forceinline__ void footprint_update(float t_m, float kw, float& bet
   beta2 = b2;
   rho = ro;
 }
+// The same update given 1/|k| (um), with one reciprocal instead of divisions
+// (the class wavelengths of hero-wavelength MIS).
+__device__ __forceinline__ void footprint_update_ik(float t_m, float ik, float& beta2, float& rho) {
+  const float zbar = t_m * 1e6f * ik;
+  const float f = zbar * (1.0f + rho * rho) * __frcp_rn(beta2);
+  const float b2 = beta2 + 2.0f * zbar * rho + zbar * f;
+  rho = rho + f;
+  beta2 = b2;
+}
 
 // ------------------------------------------------------------------ measurement
 // Emitter measurement (Eq. measurement_operator on an emissive triangle set):
@@ -873,6 +890,7 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
       const int bin = HERO ? smp % V.nb : cls;
       const int gh = HERO ? (bin - cls) / Qv : 0;  // the hero's member of the class
       const float lambda = bin_lambda(V, bin);
+      const float cstep = HERO ? bin_step(V) : 0.0f;
       const float kw = 2.0f * kPi / lambda;
       const float s_ray2 = 1.0f / (2.0f * V.beta0 * V.beta0 * kw * kw);
       float T[4][4];
@@ -967,8 +985,8 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
           const float wq = cf[g] * hq[g];
           float val = 0.0f;
           if (wq > 0.0f) {
-            const float lg = bin_lambda(V, cls + g * Qv);
-            const float kg = 2.0f * kPi / lg;
+            const float lg = step_lambda(V, cstep, cls + g * Qv);
+            const float kg = 2.0f * kPi * __frcp_rn(lg);
             const float s2g = 1.0f / (2.0f * V.beta0 * V.beta0 * kg * kg);
             float mg = 0.0f;
             for (int l = 0; l < S.n_lights; ++l) {
@@ -1004,7 +1022,8 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
         footprint_update(t, kw * eta, beta2, rho);
         if (HERO) {
 #pragma unroll
-          for (int g = 0; g < 4; ++g) footprint_update(t, 2.0f * kPi / bin_lambda(V, cls + g * Qv) * eta, fb[g], fr[g]);
+          for (int g = 0; g < 4; ++g)
+            footprint_update_ik(t, step_lambda(V, cstep, cls + g * Qv) * kInv2Pi * __frcp_rn(eta), fb[g], fr[g]);
         }
         const float3 x = o + t * d;
         const int mat = S.tri_mat[hslot];
@@ -1029,7 +1048,7 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             if (two) {
-              const float lj = bin_lambda(V, cls + j * Qv), kj = 2.0f * kPi / lj;
+              const float lj = step_lambda(V, cstep, cls + j * Qv), kj = 2.0f * kPi * __frcp_rn(lj);
               const float kap = 1.0f / (1.0f / (2.0f * V.beta0 * V.beta0 * kj * kj) + src_spread2(lj, M.coh_len_um));
               const float a = cf[j] * hq[j] * pb, b = cf[j] * qp[j] * vmf(-d, ne, kap) / (float)S.n_emitters;
               den += a * a + b * b;
@@ -1040,8 +1059,8 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
 #pragma unroll
           for (int g = 0; g < 4; ++g) {
             if (!(cf[g] * hq[g] > 0.0f) || !(den > 0.0f)) continue;
-            const float lg = bin_lambda(V, cls + g * Qv);
-            const float mg = measure_emitter(S, ei, x, d, fb[g], fr[g], 2.0f * kPi / lg, lg, u.x, u.y);
+            const float lg = step_lambda(V, cstep, cls + g * Qv);
+            const float mg = measure_emitter(S, ei, x, d, fb[g], fr[g], 2.0f * kPi * __frcp_rn(lg), lg, u.x, u.y);
             const float w = two ? cf[g] * cf[gh] * hq[g] * pb * pb / den : cf[g] * hq[g] / den;
             add_member(g, mg * w);
           }
@@ -1240,8 +1259,8 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
                 bool want[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                  const float kj = 2.0f * kPi / bin_lambda(V, cls + j * Qv);
-                  const float sc = (kj / kw) * (kj / kw);
+                  const float r = j == gh ? 1.0f : lambda * __frcp_rn(step_lambda(V, cstep, cls + j * Qv));
+                  const float sc = r * r;  // (k_j / k)^2
                   gq[j] = g_r * sc;
                   klq[j] = mis_rec.z * sc;
                   want[j] = mreal != 0.0f && (j == gh || hq[j] != 0.0f);
@@ -1389,7 +1408,8 @@ __device__ __forceinline__ void shadow_finish_hero(const RenderParams& p, int sl
   const int smp = class_first_sample(V, cls, Qv) + meta_k(m.z) * Qv;
   const int bin = smp % V.nb;
   const int gh = (bin - cls) / Qv;
-  const float kw = 2.0f * kPi / bin_lambda(V, bin);
+  const float lambda = bin_lambda(V, bin);
+  const float cstep = bin_step(V);
   const float eta = seg == 0 ? 1.0f : (NS == 1 ? P.tp[0][slot].y : P.xf[slot].w);
   const float3 nE = emitter_normal(S, ei);
   const float lc = S.mats[S.emitters[ei].mat].coh_len_um;
@@ -1402,8 +1422,8 @@ __device__ __forceinline__ void shadow_finish_hero(const RenderParams& p, int sl
   class_shares(V, cls, Qv, cf);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const float kj = 2.0f * kPi / bin_lambda(V, cls + j * Qv);
-    const float sc = (kj / kw) * (kj / kw);
+    const float r = j == gh ? 1.0f : lambda * __frcp_rn(step_lambda(V, cstep, cls + j * Qv));
+    const float sc = r * r;  // (k_j / k)^2
     gq[j] = sm.y * sc;
     klq[j] = sm.z * sc;
     want[j] = cf[j] * qp[j] > 0.0f;
@@ -1414,7 +1434,7 @@ __device__ __forceinline__ void shadow_finish_hero(const RenderParams& p, int sl
     pbw[j] *= sm.w;
     const float cq = cf[j] * qp[j];
     if (!(cq > 0.0f)) continue;
-    const float lj = bin_lambda(V, cls + j * Qv), kj = 2.0f * kPi / lj;
+    const float lj = step_lambda(V, cstep, cls + j * Qv), kj = 2.0f * kPi * __frcp_rn(lj);
     const float kap = 1.0f / (1.0f / (2.0f * V.beta0 * V.beta0 * kj * kj) + src_spread2(lj, lc));
     const float pn = vmf(w, -nE, kap) * inv_ne;
     if (j == gh) pn_h = pn;
@@ -1428,9 +1448,9 @@ __device__ __forceinline__ void shadow_finish_hero(const RenderParams& p, int sl
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     if (!(pbw[g] > 0.0f)) continue;
-    const float lg = bin_lambda(V, cls + g * Qv), kg = 2.0f * kPi / lg;
+    const float lg = step_lambda(V, cstep, cls + g * Qv), kg = 2.0f * kPi * __frcp_rn(lg);
     float b2 = fb[g], ro = fr[g];
-    footprint_update(h.t, kg * eta, b2, ro);
+    footprint_update_ik(h.t, lg * kInv2Pi * __frcp_rn(eta), b2, ro);
     const float mg = measure_emitter(S, ei, x + h.t * w, w, b2, ro, kg, lg, u.x, u.y);
     const float val = mg * cf[g] * cf[gh] * qp[g] * pn_h * pbw[g] / den;
     if (val == 0.0f) continue;
