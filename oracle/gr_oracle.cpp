@@ -545,6 +545,9 @@ struct PathState {
   // MIS bookkeeping for the vertex that produced the current segment
   bool prev_delta;  // true after the camera, a specular lobe, a grating order or a mirror
   double prev_pdf;  // solid-angle density of the current direction at that vertex
+  // anisotropic footprint (FLAG_ANISO): K = A^{-1} (um^2) of the transverse
+  // field exp(-x^T A x / 2), x in the frame (xf, d x xf); entries K11, K12, K22
+  cplx K[3];
 };
 
 struct Ctx {
@@ -553,7 +556,7 @@ struct Ctx {
   int flags;
   Rng rng;
 };
-const int FLAG_NEE = 1, FLAG_RR = 2, FLAG_NO_RENORM = 4, FLAG_HERO = 16;
+const int FLAG_NEE = 1, FLAG_RR = 2, FLAG_NO_RENORM = 4, FLAG_HERO = 16, FLAG_ANISO = 32;
 
 // Angular spread of a source of coherence length lc (Eq. coherence_diffusivity
 // read per axis with Theta = lc^2): s_src = lambda / lc; lc = 0 means spatially
@@ -572,6 +575,26 @@ double measure_distant(const Light& L, V3 d, double lambda, double s_ray2) {
   if (L.type == 1) return L.E;  // constant environment
   double kappa = 1.0 / (s_ray2 + source_spread2(lambda, L.coh_len_um));
   return L.E * vmf(d, L.dir, kappa);
+}
+
+// Coverage of the footprint point p (m), projected along d onto the plane of
+// emitter triangle prim: inside any triangle of the emitter (barycentric test,
+// edges inclusive); the emitter's triangles are coplanar.
+bool emitter_covers(const Scene& S, int prim, V3 p, V3 d) {
+  const Tri& T = S.tris[prim];
+  V3 ne = tri_normal(T);
+  double tp = dot(T.v0 - p, ne) / dot(d, ne);
+  V3 q = p + tp * d;
+  for (int ti : S.emitters[S.emitter_of_mat[T.mat]]) {
+    const Tri& E = S.tris[ti];
+    V3 a = E.v1 - E.v0, b = E.v2 - E.v0, c = q - E.v0;
+    double daa = dot(a, a), dab = dot(a, b), dbb = dot(b, b), dca = dot(c, a), dcb = dot(c, b);
+    double den = daa * dbb - dab * dab;
+    double bu = (dbb * dca - dab * dcb) / den;
+    double bv = (daa * dcb - dab * dca) / den;
+    if (bu >= 0.0 && bv >= 0.0 && bu + bv <= 1.0) return true;
+  }
+  return false;
 }
 
 // Measurement operator for an emissive triangle hit by the ray (Eq.
@@ -594,30 +617,172 @@ double measure_emitter(const Scene& S, int prim, V3 hit, V3 d, double beta2, dou
   V3 e1, e2;
   onb(d, &e1, &e2);
   V3 x_um = (sigma * z0) * e1 + (sigma * z1) * e2;
-  V3 p = hit + 1e-6 * x_um;
-  double tp = dot(T.v0 - p, ne) / dot(d, ne);
-  V3 q = p + tp * d;
-  // coverage: q inside any triangle of the emitter (barycentric test, edges
-  // inclusive); the emitter's triangles are coplanar
-  bool covered = false;
-  for (int ti : S.emitters[S.emitter_of_mat[T.mat]]) {
-    const Tri& E = S.tris[ti];
-    V3 a = E.v1 - E.v0, b = E.v2 - E.v0, c = q - E.v0;
-    double daa = dot(a, a), dab = dot(a, b), dbb = dot(b, b), dca = dot(c, a), dcb = dot(c, b);
-    double den = daa * dbb - dab * dab;
-    double bu = (dbb * dca - dab * dcb) / den;
-    double bv = (daa * dcb - dab * dca) / den;
-    if (bu >= 0.0 && bv >= 0.0 && bu + bv <= 1.0) {
-      covered = true;
-      break;
-    }
-  }
-  if (!covered) return 0.0;
+  if (!emitter_covers(S, prim, hit + 1e-6 * x_um, d)) return 0.0;
   V3 mu = (rho / (beta2 * k)) * x_um;
   V3 dl = normalize(d + mu);
   double sc2 = 1.0 / (2.0 * beta2 * k * k);
   double kappa = 1.0 / (sc2 + source_spread2(lambda, M.coh_len_um));
   return M.Le * vmf(neg(dl), ne, kappa);
+}
+
+// ---------------------------------------------------------------- anisotropic footprints
+// Anisotropic generalized rays (beta and rho as matrices; Sec. 3.1 and the
+// definition of the generalized ray, Eq. def_gen_ray, leave the general form
+// to a supplemental that is not available; this is our derivation).  The
+// transverse field of a generalized ray is exp(-x^T A x / 2) with A complex
+// symmetric and Re A positive definite; the scalar ray is A = (1 - i rho) /
+// beta^2.  The state kept is K = A^{-1}:
+//  - free-space propagation (the paraxial transfer function exp(-i zbar
+//    |k_t|^2 / 2), zbar = z/|k|) gives K <- K + i zbar I, which for the
+//    scalar ray is Eq. K_free_space_propagation;
+//  - the wavevector marginal is Gaussian with covariance Re(K)^{-1} / 2, the
+//    spatial marginal has covariance Re(A)^{-1} / 2, and given position x the
+//    wavevector has mean -Im(A) x and covariance Re(A) / 2 (the Wigner
+//    function of the Gaussian field);
+//  - an interaction with a surface matches the field on the surface: with
+//    P_in, P_out the projections of a tangent basis onto the incident and
+//    outgoing transverse frames, K_out = W K W^T, W = P_out P_in^{-1} (the
+//    anamorphic map; orthogonal for mirror reflection).
+struct CS2 {
+  cplx a, b, c;  // [[a, b], [b, c]]
+};
+
+CS2 cs2_inverse(const CS2& K) {
+  const cplx det = K.a * K.c - K.b * K.b;
+  return CS2{K.c / det, -K.b / det, K.a / det};
+}
+
+// W K W^T for a real 2x2 W
+CS2 cs2_congruence(const double W[2][2], const CS2& K) {
+  CS2 r;
+  r.a = W[0][0] * W[0][0] * K.a + 2.0 * W[0][0] * W[0][1] * K.b + W[0][1] * W[0][1] * K.c;
+  r.b = W[0][0] * W[1][0] * K.a + (W[0][0] * W[1][1] + W[0][1] * W[1][0]) * K.b + W[0][1] * W[1][1] * K.c;
+  r.c = W[1][0] * W[1][0] * K.a + 2.0 * W[1][0] * W[1][1] * K.b + W[1][1] * W[1][1] * K.c;
+  return r;
+}
+
+void inv2(const double M[2][2], double R[2][2]) {
+  const double det = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+  R[0][0] = M[1][1] / det;
+  R[0][1] = -M[0][1] / det;
+  R[1][0] = -M[1][0] / det;
+  R[1][1] = M[0][0] / det;
+}
+
+// K after an interaction at a surface of normal n: incident direction d_in
+// with frame x axis f_in, outgoing direction d_out with frame x axis f_out
+// (frames (f, d x f)).
+CS2 aniso_interaction(const CS2& K, V3 f_in, V3 d_in, V3 f_out, V3 d_out, V3 n) {
+  V3 s1, s2;
+  onb(n, &s1, &s2);
+  const V3 u[2] = {f_in, cross(d_in, f_in)}, v[2] = {f_out, cross(d_out, f_out)};
+  double Pin[2][2], Pout[2][2], Iin[2][2], W[2][2];
+  for (int i = 0; i < 2; ++i) {
+    Pin[i][0] = dot(u[i], s1);
+    Pin[i][1] = dot(u[i], s2);
+    Pout[i][0] = dot(v[i], s1);
+    Pout[i][1] = dot(v[i], s2);
+  }
+  inv2(Pin, Iin);
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) W[i][j] = Pout[i][0] * Iin[0][j] + Pout[i][1] * Iin[1][j];
+  return cs2_congruence(W, K);
+}
+
+void aniso_propagate(CS2* K, double zbar) {
+  K->a += cplx(0.0, zbar);
+  K->c += cplx(0.0, zbar);
+}
+
+// An angular Gaussian lobe about mu with (2D) precision matrix Ci in the
+// frame (f1, f2) transverse to the lobe, written so that an isotropic Ci =
+// kappa I gives the vMF of Eq. measurement_operator exactly: with kbar =
+// tr(Ci) / 2 and dv = w - mu, exponent kbar |dv|^2 / 2 plus the traceless
+// part (Ci - kbar I) on the transverse components of dv; normalised with the
+// vMF constant of kappa_eff = sqrt(det Ci).
+double aniso_lobe(V3 w, V3 mu, V3 f1, V3 f2, const double Ci[2][2]) {
+  const double ke = std::sqrt(std::max(0.0, Ci[0][0] * Ci[1][1] - Ci[0][1] * Ci[1][0]));
+  if (ke < 1e-8) return 1.0 / (4.0 * PI);
+  const double kbar = 0.5 * (Ci[0][0] + Ci[1][1]);
+  const V3 dv = w - mu;
+  const double t1 = dot(dv, f1), t2 = dot(dv, f2);
+  const double q = 0.5 * (kbar * dot(dv, dv) + (Ci[0][0] - kbar) * t1 * t1 + 2.0 * Ci[0][1] * t1 * t2 +
+                          (Ci[1][1] - kbar) * t2 * t2);
+  return ke / (2.0 * PI * (-std::expm1(-2.0 * ke))) * std::exp(-q);
+}
+
+// Distant source measured by an anisotropic ray: the wavevector marginal
+// (covariance Re(K)^{-1} / 2 in k units, / |k|^2 in direction units) plus
+// the source's spread.
+double measure_distant_aniso(const Light& L, V3 d, double lambda, double k, const CS2& K, V3 xf) {
+  if (L.type == 1) return L.E;
+  const double ReK[2][2] = {{K.a.real(), K.b.real()}, {K.b.real(), K.c.real()}};
+  double C[2][2], Ci[2][2];
+  inv2(ReK, C);
+  const double s2 = source_spread2(lambda, L.coh_len_um);
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) C[i][j] = 0.5 * C[i][j] / (k * k) + (i == j ? s2 : 0.0);
+  inv2(C, Ci);
+  return L.E * aniso_lobe(d, L.dir, xf, cross(d, xf), Ci);
+}
+
+// Emitter measured by an anisotropic ray: the footprint point is drawn from
+// the spatial marginal (Cholesky factor in the frame onb(d), so that an
+// isotropic footprint draws the same point as measure_emitter), its direction
+// shifted by -Im(A) x / |k|, with residual angular covariance Re(A) / (2 |k|^2)
+// plus the source's spread.
+struct AnisoFoot {
+  V3 e1, e2;         // frame onb(d)
+  double x1, x2;     // footprint point (um) in that frame
+  double m1, m2;     // direction shift there
+  double Ar[2][2];   // Re A in that frame
+};
+
+// The footprint point for the standard normal pair (z0, z1) and its
+// conditional direction shift.
+AnisoFoot aniso_footprint(V3 d, const CS2& K, V3 xf, double k, double z0, double z1) {
+  AnisoFoot F;
+  onb(d, &F.e1, &F.e2);
+  const V3 u2 = cross(d, xf);
+  const double R[2][2] = {{dot(F.e1, xf), dot(F.e1, u2)}, {dot(F.e2, xf), dot(F.e2, u2)}};
+  const CS2 A = cs2_inverse(cs2_congruence(R, K));
+  const double Ai[2][2] = {{A.a.imag(), A.b.imag()}, {A.b.imag(), A.c.imag()}};
+  F.Ar[0][0] = A.a.real();
+  F.Ar[0][1] = F.Ar[1][0] = A.b.real();
+  F.Ar[1][1] = A.c.real();
+  double Sg[2][2];
+  inv2(F.Ar, Sg);
+  const double l11 = std::sqrt(0.5 * Sg[0][0]), l21 = 0.5 * Sg[1][0] / l11;
+  const double l22 = std::sqrt(std::max(0.0, 0.5 * Sg[1][1] - l21 * l21));
+  F.x1 = l11 * z0;
+  F.x2 = l21 * z0 + l22 * z1;
+  F.m1 = -(Ai[0][0] * F.x1 + Ai[0][1] * F.x2) / k;
+  F.m2 = -(Ai[1][0] * F.x1 + Ai[1][1] * F.x2) / k;
+  return F;
+}
+
+// The emitter lobe seen from the footprint point F (covered), source spread
+// s2 about the emitter normal ne, unit exitance.
+double aniso_emitter_lobe(const AnisoFoot& F, V3 d, double k, double s2, V3 ne) {
+  const V3 dl = normalize(d + F.m1 * F.e1 + F.m2 * F.e2);
+  double C[2][2], Ci[2][2];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) C[i][j] = 0.5 * F.Ar[i][j] / (k * k) + (i == j ? s2 : 0.0);
+  inv2(C, Ci);
+  return aniso_lobe(neg(dl), ne, F.e1, F.e2, Ci);
+}
+
+double measure_emitter_aniso(const Scene& S, int prim, V3 hit, V3 d, const CS2& K, V3 xf, double k, double lambda,
+                             double ua, double ub) {
+  const Tri& T = S.tris[prim];
+  const Material& M = S.mats[T.mat];
+  V3 ne = tri_normal(T);
+  if (dot(d, ne) >= 0.0) return 0.0;
+  double z0, z1;
+  box_muller(ua, ub, &z0, &z1);
+  const AnisoFoot F = aniso_footprint(d, K, xf, k, z0, z1);
+  if (!emitter_covers(S, prim, hit + 1e-6 * (F.x1 * F.e1 + F.x2 * F.e2), d)) return 0.0;
+  return M.Le * aniso_emitter_lobe(F, d, k, source_spread2(lambda, M.coh_len_um), ne);
 }
 
 // ---------------------------------------------------------------- interactions
@@ -750,6 +915,10 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
   P.prev_delta = true;
   P.prev_pdf = 0.0;
   const int n_emit = (int)S.emitters.size();
+  // anisotropic footprint (FLAG_ANISO): the camera state is isotropic,
+  // K = beta0^2 I (rho = 0)
+  const bool aniso = (C.flags & FLAG_ANISO) != 0;
+  CS2 K{cplx(P.beta2, 0.0), cplx(0.0, 0.0), cplx(P.beta2, 0.0)};
 
   // Hero-wavelength spectral MIS (Sec. 7.2, after Wilkie et al. 2014): the
   // path's bin is the hero of the class of G = 4 bins {c, c+Q, c+2Q, c+3Q}
@@ -818,7 +987,8 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
       // --- measurement of distant sources on escape
       if (!hero) {
         double m = 0.0;
-        for (const Light& L : S.lights) m += measure_distant(L, P.d, P.lambda, P.s_ray2);
+        for (const Light& L : S.lights)
+          m += aniso ? measure_distant_aniso(L, P.d, P.lambda, P.k, K, P.xf) : measure_distant(L, P.d, P.lambda, P.s_ray2);
         add_vec(result, ns, col, m);
         return;
       }
@@ -836,6 +1006,7 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
     }
     // footprint update over the segment (z in um; |k| = eta k0 in a medium)
     propagate(&P.beta2, &P.rho, th * 1e6 / (P.k * P.eta));
+    if (aniso) aniso_propagate(&K, th * 1e6 / (P.k * P.eta));
     if (hero)
       for (int g = 0; g < G; ++g) propagate(&fb2[g], &frho[g], th * 1e6 / (kcls[g] * P.eta));
     V3 x = P.o + th * P.d;
@@ -867,7 +1038,8 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
     }
     if (M.type == MAT_EMITTER) {
       rng.draw(seg, CALL_EMIT_FOOT, u);
-      double m = measure_emitter(S, prim, x, P.d, P.beta2, P.rho, P.k, P.lambda, u[0], u[1]);
+      double m = aniso ? measure_emitter_aniso(S, prim, x, P.d, K, P.xf, P.k, P.lambda, u[0], u[1])
+                       : measure_emitter(S, prim, x, P.d, P.beta2, P.rho, P.k, P.lambda, u[0], u[1]);
       double w = 1.0;
       if ((C.flags & FLAG_NEE) && !P.prev_delta && n_emit > 0) {
         V3 ne = tri_normal(T);
@@ -1096,6 +1268,15 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
               double m = measure_emitter(S, sp, x + ts * w, w, b2, r, kcls[g], lam_g[g], uf[0], uf[1]);
               add_vec(result + 4 * g, ns, c_nee, m * cf[g] * cf[gh] * qpre[g] * pn * pbw[g] / den);
             }
+          } else if (f > 0.0 && pn > 0.0 && aniso) {
+            // the vertex's footprint mapped to the emitter direction's frame
+            const V3 xf_w = s_vector(n, neg(w), s_o);
+            CS2 Kw = aniso_interaction(K, P.xf, d_in, xf_w, w, n);
+            aniso_propagate(&Kw, ts * 1e6 / (P.k * P.eta));
+            rng.draw(seg, CALL_NEE_FOOT, uf);
+            double m = measure_emitter_aniso(S, sp, x + ts * w, w, Kw, xf_w, P.k, P.lambda, uf[0], uf[1]);
+            double wmis = pn * pn / (pn * pn + f * f);
+            add_vec(result, ns, c_nee, m * f / pn * wmis);
           } else if (f > 0.0 && pn > 0.0) {
             double b2 = P.beta2, r = P.rho;
             propagate(&b2, &r, ts * 1e6 / (P.k * P.eta));
@@ -1112,6 +1293,12 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
     // --- continue the path with the sampled generalized ray: position and
     // (beta, rho) unchanged by the interaction (Eq. K_reflection_refraction;
     // rho growth at the grating ignored, Eq. K_grating).
+    if (aniso) {
+      // the footprint mapped onto the outgoing direction's transverse frame
+      const V3 xf_out = s_vector(n, neg(d_out), s_o);
+      K = aniso_interaction(K, P.xf, d_in, xf_out, d_out, n);
+      P.xf = xf_out;
+    }
     if (ns == 1) {
       P.t = t_new;
     } else {
@@ -1340,6 +1527,40 @@ static View read_view(const double* p) {
 
 // One path sample's contribution for tests: out16[4 g + k], class bin g (only
 // g = 0 without hero MIS), Stokes component k.
+// Anisotropic footprint maps for tests; K as 6 doubles (Re, Im) of K11, K12,
+// K22.  Free-space propagation by zbar (um), and the interaction map for the
+// frames (f_in, d_in) -> (f_out, d_out) at a surface of normal n.
+void oracle_aniso_propagate(const double* k6, double zbar, double* out6) {
+  CS2 K{cplx(k6[0], k6[1]), cplx(k6[2], k6[3]), cplx(k6[4], k6[5])};
+  aniso_propagate(&K, zbar);
+  const cplx r[3] = {K.a, K.b, K.c};
+  for (int i = 0; i < 3; ++i) out6[2 * i] = r[i].real(), out6[2 * i + 1] = r[i].imag();
+}
+void oracle_aniso_interaction(const double* k6, const double* f_in, const double* d_in, const double* f_out,
+                              const double* d_out, const double* n, double* out6) {
+  CS2 K{cplx(k6[0], k6[1]), cplx(k6[2], k6[3]), cplx(k6[4], k6[5])};
+  auto V = [](const double* a) { return v3(a[0], a[1], a[2]); };
+  CS2 R = aniso_interaction(K, V(f_in), V(d_in), V(f_out), V(d_out), V(n));
+  const cplx r[3] = {R.a, R.b, R.c};
+  for (int i = 0; i < 3; ++i) out6[2 * i] = r[i].real(), out6[2 * i + 1] = r[i].imag();
+}
+
+// The footprint point, its direction shift and the emitter lobe (unit
+// exitance, point covered) for the standard normal pair (z0, z1); out6 =
+// x1, x2 (um, frame onb(d)), m1, m2, lobe value, 0.
+void oracle_aniso_emitter(const double* k6, const double* xf, const double* d, double k, double s2, const double* ne,
+                          double z0, double z1, double* out6) {
+  CS2 K{cplx(k6[0], k6[1]), cplx(k6[2], k6[3]), cplx(k6[4], k6[5])};
+  const V3 dd = v3(d[0], d[1], d[2]);
+  const AnisoFoot F = aniso_footprint(dd, K, v3(xf[0], xf[1], xf[2]), k, z0, z1);
+  out6[0] = F.x1;
+  out6[1] = F.x2;
+  out6[2] = F.m1;
+  out6[3] = F.m2;
+  out6[4] = aniso_emitter_lobe(F, dd, k, s2, v3(ne[0], ne[1], ne[2]));
+  out6[5] = 0.0;
+}
+
 void oracle_trace_sample(void* s, const double* view, uint32_t seed, int flags, int px, int py, long sample,
                          double* out16) {
   Scene* S = (Scene*)s;
@@ -1368,6 +1589,7 @@ long oracle_render(void* s, const double* view, uint32_t seed, int flags, int x0
   Scene* S = (Scene*)s;
   View V = read_view(view);
   if ((flags & FLAG_HERO) && V.n_bins % 4 != 0) return -1;  // hero classes need 4 | n_bins
+  if ((flags & FLAG_HERO) && (flags & FLAG_ANISO)) return -2;  // not combined
   Ctx C;
   C.S = S;
   C.V = &V;

@@ -30,6 +30,7 @@ FLAG_NEE = 1
 FLAG_RR = 2
 FLAG_NO_RENORM = 4
 FLAG_HERO = 16
+FLAG_ANISO = 32
 
 _lib = None
 
@@ -91,6 +92,9 @@ def lib():
     L.oracle_fresnel_dielectric.argtypes = [D, D, P]
     L.oracle_refract.argtypes = [P, P, D, D, P]
     L.oracle_refract.restype = I
+    L.oracle_aniso_propagate.argtypes = [P, D, P]
+    L.oracle_aniso_interaction.argtypes = [P, P, P, P, P, P, P]
+    L.oracle_aniso_emitter.argtypes = [P, P, P, D, D, P, D, D, P]
     _lib = L
     return L
 
@@ -137,6 +141,43 @@ def propagate(beta2, rho, zbar):
     o = np.zeros(2)
     lib().oracle_propagate(float(beta2), float(rho), float(zbar), _p(o))
     return o[0], o[1]
+
+
+def _k6(K):
+    K = np.asarray(K, dtype=np.complex128)
+    return np.ascontiguousarray([K[0, 0].real, K[0, 0].imag, K[0, 1].real, K[0, 1].imag, K[1, 1].real, K[1, 1].imag])
+
+
+def _kmat(o):
+    a, b, c = o[0] + 1j * o[1], o[2] + 1j * o[3], o[4] + 1j * o[5]
+    return np.array([[a, b], [b, c]])
+
+
+def aniso_propagate(K, zbar):
+    """Anisotropic footprint K = A^-1 (complex symmetric 2x2, um^2) after free
+    propagation by zbar = z / |k| (um)."""
+    o = np.zeros(6)
+    lib().oracle_aniso_propagate(_p(_k6(K)), float(zbar), _p(o))
+    return _kmat(o)
+
+
+def aniso_interaction(K, f_in, d_in, f_out, d_out, n):
+    """K mapped from the incident frame (f_in, d_in x f_in) to the outgoing
+    frame (f_out, d_out x f_out) through a surface of normal n."""
+    o = np.zeros(6)
+    lib().oracle_aniso_interaction(_p(_k6(K)), _p(_d3(f_in)), _p(_d3(d_in)), _p(_d3(f_out)), _p(_d3(d_out)),
+                                   _p(_d3(n)), _p(o))
+    return _kmat(o)
+
+
+def aniso_emitter(K, xf, d, k, s2, ne, z0, z1):
+    """Footprint point (x1, x2 in um, frame onb(d)), its direction shift (m1,
+    m2) and the emitter lobe value (unit exitance, point covered) for the
+    standard normal pair (z0, z1)."""
+    o = np.zeros(6)
+    lib().oracle_aniso_emitter(_p(_k6(K)), _p(_d3(xf)), _p(_d3(d)), float(k), float(s2), _p(_d3(ne)), float(z0),
+                               float(z1), _p(o))
+    return o[:2].copy(), o[2:4].copy(), float(o[4])
 
 
 def fresnel_dielectric(cos_i, n_rel):
@@ -271,6 +312,8 @@ class Scene:
         v = view_vector(view)
         n = lib().oracle_render(self._h, _p(v), int(seed) & 0xFFFFFFFF, int(flags), x0, y0, x1, y1,
                                 int(n_threads), _p(mean), _p(var) if want_var else None)
-        if n < 0:
+        if n == -1:
             raise ValueError("hero-wavelength MIS needs n_bins to be a multiple of 4")
+        if n == -2:
+            raise ValueError("hero-wavelength MIS and anisotropic footprints are not combined")
         return (mean, var) if want_var else mean
