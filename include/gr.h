@@ -155,10 +155,17 @@ typedef struct {
  * could make the path, the power heuristic over (wavelength, lobe or emitter
  * sampling) where next-event estimation could too; each bin is still divided
  * by the number of samples whose hero it is (GR_E_INVALID if n_bins % 4 != 0; not available in
- * gr_render_static).  table_dtype: storage of the grating order tables
+ * gr_render_static); GR_FLAG_ANISO anisotropic footprints (Sec. 3.1: beta and rho as
+ * matrices): each ray carries the complex 2x2 K = A^-1 of its transverse field
+ * exp(-x^T A x / 2), propagates it exactly (K + i z/|k| I), maps it through every
+ * interaction by the surface's anamorphic projection (orthogonal for mirrors; the
+ * grating and Snell anamorphic factors for orders and refraction) and measures sources
+ * with its anisotropic wavevector and footprint Gaussians; a path that meets only
+ * mirror reflections renders as without the flag (not combined with GR_FLAG_HERO;
+ * not available in gr_render_static).  table_dtype: storage of the grating order tables
  * (GR_TABLE_F32 / F16 / BF16); arithmetic is FP32 either way.  pool_size:
  * wavefront slots (0 = default); block: threads per block (0 = default). */
-enum { GR_FLAG_NEE = 1, GR_FLAG_RR = 2, GR_FLAG_NO_RENORM = 4, GR_FLAG_WIDE_BVH = 8, GR_FLAG_HERO = 16 };
+enum { GR_FLAG_NEE = 1, GR_FLAG_RR = 2, GR_FLAG_NO_RENORM = 4, GR_FLAG_WIDE_BVH = 8, GR_FLAG_HERO = 16, GR_FLAG_ANISO = 32 };
 enum { GR_TABLE_F32 = 0, GR_TABLE_F16 = 1, GR_TABLE_BF16 = 2 };
 typedef struct {
   uint32_t seed;

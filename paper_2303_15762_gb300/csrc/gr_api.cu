@@ -353,6 +353,8 @@ gr_status check_render_args(const char* who, gr_scene* const* scenes, int32_t n_
       return fail(GR_E_INVALID, w + ": bad sample range in view " + std::to_string(v));
     if ((long long)d.spp / d.n_bins + 1 >= 65536)
       return fail(GR_E_INVALID, w + ": more than 65535 samples per pixel and bin in one call");
+    if ((opts->flags & GR_FLAG_HERO) && (opts->flags & GR_FLAG_ANISO))
+      return fail(GR_E_INVALID, w + ": GR_FLAG_HERO and GR_FLAG_ANISO are not combined");
     if (opts->flags & GR_FLAG_HERO) {
       if (d.n_bins % 4 != 0)
         return fail(GR_E_INVALID, w + ": hero-wavelength MIS needs n_bins to be a multiple of 4 (view " +
@@ -475,8 +477,9 @@ gr_status gr_render_static(gr_scene* const* scenes, int32_t n_scenes, const gr_v
     return fail(GR_E_INVALID, "gr_render_static: null or empty argument");
   if (opts->use_graph || opts->profile)
     return fail(GR_E_INVALID, "gr_render_static: use_graph and profile are not available without allocation");
-  if (opts->flags & GR_FLAG_HERO)
-    return fail(GR_E_INVALID, "gr_render_static: hero-wavelength MIS is not available without allocation");
+  if (opts->flags & (GR_FLAG_HERO | GR_FLAG_ANISO))
+    return fail(GR_E_INVALID,
+                "gr_render_static: hero-wavelength MIS and anisotropic footprints are not available without allocation");
   for (int i = 0; i < n_scenes; ++i)
     if (!scenes[i]) return fail(GR_E_INVALID, "gr_render_static: null scene " + std::to_string(i));
   if (opts->table_dtype < GR_TABLE_F32 || opts->table_dtype > GR_TABLE_BF16)

@@ -41,6 +41,14 @@ struct Pool {
   float4* hpart; // [4] the current sample's contributions to member g (g != hero)
   float4* haccS; // [4] ticket sums of member g (Kahan)
   float4* haccC; // [4] ticket compensations of member g
+  // anisotropic footprints only (null otherwise): K = Kr + i Ki in the ray's
+  // frame (xf), as (Kr11, Kr12, Kr22, Ki11), (Ki12, Ki22, -, -); the same for
+  // a next-event request in the frame nkf of its direction
+  float4* ak0;
+  float4* ak1;
+  float4* nk0;
+  float4* nk1;
+  float4* nkf;
 };
 
 struct Counters {

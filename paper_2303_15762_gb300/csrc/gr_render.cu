@@ -573,6 +573,28 @@ __device__ __forceinline__ void footprint_update_ik(float t_m, float ik, float& 
 // shifted by rho x / (beta^2 |k|) with residual angular variance
 // 1/(2 beta^2 |k|^2); the source emits a Gaussian lobe of spread lambda/lc
 // about its normal.  The lobe's quadratic form is evaluated in FP64.
+// Coverage of the footprint point pt (m), projected along d onto the plane
+// (normal ne, through v0) of emitter E: inside any of its triangles
+// (barycentric test, edges inclusive).
+__device__ __forceinline__ bool emitter_covers(const DevScene& S, const DevEmitter& E, float3 pt, float3 d, float3 ne,
+                                               float3 v0p) {
+  const float tp = dot(v0p - pt, ne) / dot(d, ne);
+  const float3 q = pt + tp * d;
+  bool covered = false;
+  for (int i = 0; i < E.count && !covered; ++i) {
+    const float3 v0 = xyz(S.emitter_tris[3 * (E.first + i)]);
+    const float3 a = xyz(S.emitter_tris[3 * (E.first + i) + 1]) - v0;
+    const float3 b = xyz(S.emitter_tris[3 * (E.first + i) + 2]) - v0;
+    const float3 c = q - v0;
+    const float daa = dot(a, a), dab = dot(a, b), dbb = dot(b, b), dca = dot(c, a), dcb = dot(c, b);
+    const float den = daa * dbb - dab * dab;
+    const float bu = (dbb * dca - dab * dcb) / den;
+    const float bv = (daa * dcb - dab * dca) / den;
+    covered = bu >= 0.0f && bv >= 0.0f && bu + bv <= 1.0f;
+  }
+  return covered;
+}
+
 __device__ float measure_emitter(const DevScene& S, int ei, float3 hit, float3 d, float beta2, float rho, float k,
                                  float lambda, float u0, float u1) {
   const DevEmitter E = S.emitters[ei];
@@ -588,22 +610,7 @@ __device__ float measure_emitter(const DevScene& S, int ei, float3 hit, float3 d
   float3 e1, e2;
   onb(d, e1, e2);
   const float3 x_um = (sigma * z0) * e1 + (sigma * z1) * e2;
-  const float3 pt = hit + 1e-6f * x_um;
-  const float tp = dot(xyz(t0) - pt, ne) / dot(d, ne);
-  const float3 q = pt + tp * d;
-  bool covered = false;
-  for (int i = 0; i < E.count && !covered; ++i) {
-    const float3 v0 = xyz(S.emitter_tris[3 * (E.first + i)]);
-    const float3 a = xyz(S.emitter_tris[3 * (E.first + i) + 1]) - v0;
-    const float3 b = xyz(S.emitter_tris[3 * (E.first + i) + 2]) - v0;
-    const float3 c = q - v0;
-    const float daa = dot(a, a), dab = dot(a, b), dbb = dot(b, b), dca = dot(c, a), dcb = dot(c, b);
-    const float den = daa * dbb - dab * dab;
-    const float bu = (dbb * dca - dab * dcb) / den;
-    const float bv = (daa * dcb - dab * dca) / den;
-    covered = bu >= 0.0f && bv >= 0.0f && bu + bv <= 1.0f;
-  }
-  if (!covered) return 0.0f;
+  if (!emitter_covers(S, E, hit + 1e-6f * x_um, d, ne, xyz(t0))) return 0.0f;
   const float3 mu = (rho / (beta2 * k)) * x_um;
   // FP64 quadratic form of the measured lobe
   const d3 dl = dnormalize(dadd(D3(d), D3(mu)));
@@ -620,6 +627,124 @@ __device__ float measure_emitter(const DevScene& S, int ei, float3 hit, float3 d
   const float kf = (float)kappa;
   const float pref = kf < 1e-8f ? 0.25f / kPi : kf / (2.0f * kPi * (-expm1f(-2.0f * kf)));
   return M.Le * pref * expf(-(float)q2);
+}
+
+// ------------------------------------------------------------------ anisotropic footprints
+// Anisotropic generalized rays (GR_FLAG_ANISO; beta and rho as matrices,
+// Sec. 3.1 and Eq. def_gen_ray, with the general form derived from the
+// Gaussian field): the transverse field exp(-x^T A x / 2) is kept as K = A^-1
+// = Kr + i Ki (um^2) in the ray's frame (f, d x f).  Free propagation adds
+// i zbar I; an interaction maps K by the surface's anamorphic map W = P_out
+// P_in^-1 (P: a tangent basis projected onto the transverse frames).  With
+// S = (Kr + Ki Kr^-1 Ki) / 2 the spatial covariance, a footprint point x has
+// direction shift Kr^-1 Ki S^-1 x / (2|k|) and residual angular covariance
+// S^-1 / (4|k|^2); the wavevector marginal is Kr^-1 / 2.  Only Kr, which
+// propagation leaves unchanged, is inverted, so FP32 does not cancel.
+struct AK {
+  float r11, r12, r22, i11, i12, i22;
+};
+__device__ __forceinline__ void sym_inv(float a, float b, float c, float& ia, float& ib, float& ic) {
+  const float id = 1.0f / (a * c - b * b);
+  ia = c * id;
+  ib = -b * id;
+  ic = a * id;
+}
+// W K W^T (real W)
+__device__ __forceinline__ AK ak_congruence(const float W[2][2], const AK& K) {
+  AK r;
+  r.r11 = W[0][0] * W[0][0] * K.r11 + 2.0f * W[0][0] * W[0][1] * K.r12 + W[0][1] * W[0][1] * K.r22;
+  r.r12 = W[0][0] * W[1][0] * K.r11 + (W[0][0] * W[1][1] + W[0][1] * W[1][0]) * K.r12 + W[0][1] * W[1][1] * K.r22;
+  r.r22 = W[1][0] * W[1][0] * K.r11 + 2.0f * W[1][0] * W[1][1] * K.r12 + W[1][1] * W[1][1] * K.r22;
+  r.i11 = W[0][0] * W[0][0] * K.i11 + 2.0f * W[0][0] * W[0][1] * K.i12 + W[0][1] * W[0][1] * K.i22;
+  r.i12 = W[0][0] * W[1][0] * K.i11 + (W[0][0] * W[1][1] + W[0][1] * W[1][0]) * K.i12 + W[0][1] * W[1][1] * K.i22;
+  r.i22 = W[1][0] * W[1][0] * K.i11 + 2.0f * W[1][0] * W[1][1] * K.i12 + W[1][1] * W[1][1] * K.i22;
+  return r;
+}
+// K across an interaction at normal n: (f_in, d_in) -> (f_out, d_out)
+__device__ AK ak_interaction(const AK& K, float3 f_in, float3 d_in, float3 f_out, float3 d_out, float3 n) {
+  float3 s1, s2;
+  onb(n, s1, s2);
+  const float3 u2 = cross(d_in, f_in), v2 = cross(d_out, f_out);
+  const float p00 = dot(f_in, s1), p01 = dot(f_in, s2), p10 = dot(u2, s1), p11 = dot(u2, s2);
+  const float q00 = dot(f_out, s1), q01 = dot(f_out, s2), q10 = dot(v2, s1), q11 = dot(v2, s2);
+  const float id = 1.0f / (p00 * p11 - p01 * p10);
+  const float i00 = p11 * id, i01 = -p01 * id, i10 = -p10 * id, i11 = p00 * id;
+  const float W[2][2] = {{q00 * i00 + q01 * i10, q00 * i01 + q01 * i11}, {q10 * i00 + q11 * i10, q10 * i01 + q11 * i11}};
+  return ak_congruence(W, K);
+}
+// An angular lobe of 2D precision (c11, c12, c22) in the frame (f1, f2),
+// written so that an isotropic precision kappa I is the vMF exactly: kbar
+// |dv|^2 / 2 (kbar = the mean of the eigenvalues) plus the traceless part on
+// the transverse components, normalised with the vMF constant of
+// kappa_eff = sqrt(det); |dv|^2 is taken in FP64 by the caller where the
+// lobe can be narrow.
+__device__ __forceinline__ float aniso_lobe_q(double dv2, float t1, float t2, float c11, float c12, float c22) {
+  const float kbar = 0.5f * (c11 + c22);
+  return 0.5f * (float)((double)kbar * dv2) + 0.5f * ((c11 - kbar) * t1 * t1 + 2.0f * c12 * t1 * t2 + (c22 - kbar) * t2 * t2);
+}
+__device__ __forceinline__ float aniso_lobe_pref(float c11, float c12, float c22) {
+  const float ke = sqrtf(fmaxf(0.0f, c11 * c22 - c12 * c12));
+  return ke < 1e-8f ? 0.25f / kPi : ke / (2.0f * kPi * (-expm1f(-2.0f * ke)));
+}
+// Distant source seen by an anisotropic ray: wavevector marginal Kr^-1 / 2
+// (over |k|^2) plus the source's spread.
+__device__ float measure_distant_aniso(const gr_light& L, float3 d, float lambda, float k, const AK& K, float3 xf) {
+  if (L.type == GR_LIGHT_ENV) return L.E;
+  float a, b, c;
+  sym_inv(K.r11, K.r12, K.r22, a, b, c);
+  const float s2 = src_spread2(lambda, L.coh_len_um), ik2 = 0.5f / (k * k);
+  float c11, c12, c22;
+  sym_inv(a * ik2 + s2, b * ik2, c * ik2 + s2, c11, c12, c22);
+  const float3 dv = d - f3(L.dir[0], L.dir[1], L.dir[2]);
+  const float q = aniso_lobe_q((double)dot(dv, dv), dot(dv, xf), dot(dv, cross(d, xf)), c11, c12, c22);
+  return L.E * aniso_lobe_pref(c11, c12, c22) * expf(-q);
+}
+
+// Emitter seen by an anisotropic ray: the footprint point from the spatial
+// covariance S (Cholesky factor in the frame onb(d)), its direction shift and
+// residual lobe, the lobe's isotropic part in FP64 as in measure_emitter.
+__device__ float measure_emitter_aniso(const DevScene& S, int ei, float3 hit, float3 d, const AK& K, float3 xf,
+                                       float k, float lambda, float u0, float u1) {
+  const DevEmitter E = S.emitters[ei];
+  const gr_material& M = S.mats[E.mat];
+  const float4 t0 = S.emitter_tris[3 * E.first], t1 = S.emitter_tris[3 * E.first + 1],
+               t2 = S.emitter_tris[3 * E.first + 2];
+  const d3 ned = dnormalize(dcross(dsub(D3(xyz(t1)), D3(xyz(t0))), dsub(D3(xyz(t2)), D3(xyz(t0)))));
+  const float3 ne = f3((float)ned.x, (float)ned.y, (float)ned.z);
+  if (dot(d, ne) >= 0.0f) return 0.0f;
+  float z0, z1;
+  box_muller(u0, u1, z0, z1);
+  float3 e1, e2;
+  onb(d, e1, e2);
+  const float3 u2 = cross(d, xf);
+  const float R[2][2] = {{dot(e1, xf), dot(e1, u2)}, {dot(e2, xf), dot(e2, u2)}};
+  const AK Ke = ak_congruence(R, K);
+  // S = (Kr + Ki Kr^-1 Ki) / 2
+  float a, b, c;
+  sym_inv(Ke.r11, Ke.r12, Ke.r22, a, b, c);
+  const float m11 = Ke.i11 * a + Ke.i12 * b, m12 = Ke.i11 * b + Ke.i12 * c;  // Ki Kr^-1
+  const float m21 = Ke.i12 * a + Ke.i22 * b, m22 = Ke.i12 * b + Ke.i22 * c;
+  const float s11 = 0.5f * (Ke.r11 + m11 * Ke.i11 + m12 * Ke.i12);
+  const float s12 = 0.5f * (Ke.r12 + m11 * Ke.i12 + m12 * Ke.i22);
+  const float s22 = 0.5f * (Ke.r22 + m21 * Ke.i12 + m22 * Ke.i22);
+  const float l11 = sqrtf(s11), l21 = s12 / l11, l22 = sqrtf(fmaxf(0.0f, s22 - l21 * l21));
+  const float x1 = l11 * z0, x2 = l21 * z0 + l22 * z1;  // um
+  if (!emitter_covers(S, E, hit + 1e-6f * (x1 * e1 + x2 * e2), d, ne, xyz(t0))) return 0.0f;
+  // shift Kr^-1 Ki S^-1 x / (2k); residual covariance S^-1 / (4k^2) + spread
+  float j11, j12, j22;
+  sym_inv(s11, s12, s22, j11, j12, j22);
+  const float y1 = j11 * x1 + j12 * x2, y2 = j12 * x1 + j22 * x2;
+  const float v1 = Ke.i11 * y1 + Ke.i12 * y2, v2 = Ke.i12 * y1 + Ke.i22 * y2;
+  const float hk = 0.5f / k;
+  const float mu1 = hk * (a * v1 + b * v2), mu2 = hk * (b * v1 + c * v2);
+  const float s2 = src_spread2(lambda, M.coh_len_um), q4 = 0.25f / (k * k);
+  float c11, c12, c22;
+  sym_inv(j11 * q4 + s2, j12 * q4, j22 * q4 + s2, c11, c12, c22);
+  const d3 dl = dnormalize(dadd(D3(d), D3(mu1 * e1 + mu2 * e2)));
+  const d3 diff = d3{-dl.x - ned.x, -dl.y - ned.y, -dl.z - ned.z};
+  const float3 df = f3((float)diff.x, (float)diff.y, (float)diff.z);
+  const float q = aniso_lobe_q(ddot(diff, diff), dot(df, e1), dot(df, e2), c11, c12, c22);
+  return M.Le * aniso_lobe_pref(c11, c12, c22) * expf(-q);
 }
 
 __device__ __forceinline__ float3 emitter_normal(const DevScene& S, int ei) {
@@ -851,8 +976,11 @@ __device__ __forceinline__ float order0_prob(const TableRow& row, float3 t_mir, 
 // next-event estimates, with NEE on, with the power heuristic over the
 // (wavelength, lobe or emitter sampling) pairs, which with one hero per class
 // is the plain lobe/emitter power heuristic.
-template <int NS, typename TT, bool HERO>
-__global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(RenderParams p) {
+// MODE 0: plain; 1: hero-wavelength MIS (HERO); 2: anisotropic footprints
+// (ANISO, K carried per slot).
+template <int NS, typename TT, int MODE>
+__global__ void __launch_bounds__(256, MODE != 0 ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(RenderParams p) {
+  constexpr bool HERO = MODE == 1, ANISO = MODE == 2;
   extern __shared__ __align__(16) unsigned char smem[];
   const TableRow* rows = p.rows;
   const TT* tvals = (const TT*)p.table_vals;
@@ -901,7 +1029,7 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
         // vector made orthogonal to d, medium air
         for (int r = 0; r < 4; ++r)
           for (int c = 0; c < 4; ++c) T[r][c] = r == c ? 1.0f : 0.0f;
-        const float3 xf0 = NS == 1 ? f3(0.0f, 0.0f, 0.0f) : normalize(V.right - dot(V.right, d) * d);
+        const float3 xf0 = NS == 1 && !ANISO ? f3(0.0f, 0.0f, 0.0f) : normalize(V.right - dot(V.right, d) * d);
         xfv = make_float4(xf0.x, xf0.y, xf0.z, 1.0f);
         pt = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       } else {
@@ -919,7 +1047,17 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
           }
         }
         if (NS == 4) xfv = P.xf[slot];
+        if (NS == 1 && ANISO) {  // the footprint's frame
+          const float4 f = P.xf[slot];
+          xfv = make_float4(f.x, f.y, f.z, xfv.w);
+        }
         pt = P.part[slot];
+      }
+      // anisotropic footprint: isotropic beta0^2 I on the camera segment
+      AK K{beta2, 0.0f, beta2, 0.0f, 0.0f, 0.0f};
+      if (ANISO && seg > 0) {
+        const float4 k0 = P.ak0[slot], k1 = P.ak1[slot];
+        K = AK{k0.x, k0.y, k0.z, k0.w, k1.x, k1.y};
       }
       float hq[4] = {1.0f, 1.0f, 1.0f, 1.0f};
       if (HERO && seg > 0) {
@@ -1003,6 +1141,11 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
           add_member(g, val);
         }
         done = true;
+      } else if (hslot < 0 && ANISO) {
+        float msum = 0.0f;
+        for (int l = 0; l < S.n_lights; ++l) msum += measure_distant_aniso(S.lights[l], d, lambda, kw, K, xyz(xfv));
+        add_col(msum);
+        done = true;
       } else if (hslot < 0) {
         float msum = 0.0f;
         for (int l = 0; l < S.n_lights; ++l) {
@@ -1020,6 +1163,11 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
         const float t = hh.x;
         const float eta = xfv.w;  // |k| = eta k0 in the current medium
         footprint_update(t, kw * eta, beta2, rho);
+        if (ANISO) {
+          const float zb = t * 1e6f / (kw * eta);
+          K.i11 += zb;
+          K.i22 += zb;
+        }
         if (HERO) {
 #pragma unroll
           for (int g = 0; g < 4; ++g)
@@ -1068,7 +1216,8 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
         } else if (M.type == GR_MAT_EMITTER) {
           const int ei = S.emitter_of_mat[mat];
           float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallEmitFoot);
-          float val = measure_emitter(S, ei, x, d, beta2, rho, kw, lambda, u.x, u.y);
+          float val = ANISO ? measure_emitter_aniso(S, ei, x, d, K, xyz(xfv), kw, lambda, u.x, u.y)
+                            : measure_emitter(S, ei, x, d, beta2, rho, kw, lambda, u.x, u.y);
           float w = 1.0f;
           if ((p.flags & GR_FLAG_NEE) && !prev_delta && S.n_emitters > 0 && val > 0.0f) {
             const float3 ne = emitter_normal(S, ei);
@@ -1128,6 +1277,7 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
             if (NS == 1) {
               T[0][0] *= F.a;
               cn[0] = T[0][0];
+              if (ANISO) s_o = s_vector(nrm, -d, xyz(xfv));
             } else {
               const float3 k_o = -d;
               const float3 xf = xyz(xfv);
@@ -1296,6 +1446,14 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
                 P.shd[slot] = make_float4(w.x, w.y, w.z, __int_as_float(ei | (seg << 16)));
                 P.shc[slot] = make_float4(cn[0], NS == 4 ? cn[1] : 0.0f, NS == 4 ? cn[2] : 0.0f, NS == 4 ? cn[3] : 0.0f);
                 P.shm[slot] = make_float4(dot(dtn, dtn), g_r, kl * kl, cos_o);
+                if (ANISO) {
+                  // the vertex's footprint in the frame of the emitter direction
+                  const float3 xw = s_vector(nrm, -w, s_o);
+                  const AK Kw = ak_interaction(K, xyz(xfv), d, xw, w, nrm);
+                  P.nk0[slot] = make_float4(Kw.r11, Kw.r12, Kw.r22, Kw.i11);
+                  P.nk1[slot] = make_float4(Kw.i12, Kw.i22, 0.0f, 0.0f);
+                  P.nkf[slot] = make_float4(xw.x, xw.y, xw.z, 0.0f);
+                }
                 want_shadow = true;
               }
             }
@@ -1313,6 +1471,14 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
               }
               if (!delta) P.mis[slot] = mis_rec;
               if (HERO) P.hq[slot] = make_float4(hq[0], hq[1], hq[2], hq[3]);
+              if (ANISO) {
+                // the footprint mapped onto the outgoing direction's frame
+                const float3 xn = s_vector(nrm, -d_out, s_o);
+                const AK Ko = ak_interaction(K, xyz(xfv), d, xn, d_out, nrm);
+                P.ak0[slot] = make_float4(Ko.r11, Ko.r12, Ko.r22, Ko.i11);
+                P.ak1[slot] = make_float4(Ko.i12, Ko.i22, 0.0f, 0.0f);
+                if (NS == 1) P.xf[slot] = make_float4(xn.x, xn.y, xn.z, 0.0f);
+              }
               P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg + 1, ST_ACTIVE, delta), hslot);
             } else {
               P.od1[slot] = make_float4(d.x, d.y, d.z, rho);
@@ -1335,7 +1501,7 @@ __global__ void __launch_bounds__(256, HERO ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(R
 // update and the rough lobe's value is weighted against the emitter sampler
 // by the power heuristic (the NEE request and lobe terms were stored by
 // k_shade), and the result is added to the slot's sample contribution.
-template <int NS>
+template <int NS, bool ANISO>
 __device__ __forceinline__ void shadow_finish(const RenderParams& p, int slot, const Hit& h) {
   const Pool& P = p.pool;
   const int4 m = P.meta[slot];
@@ -1358,9 +1524,20 @@ __device__ __forceinline__ void shadow_finish(const RenderParams& p, int slot, c
   // |k| = eta k0 in the ray's medium: air on the camera segment, else the
   // index carried with the path's throughput (scalar) or Stokes frame
   const float eta = seg == 0 ? 1.0f : (NS == 1 ? P.tp[0][slot].y : P.xf[slot].w);
-  footprint_update(h.t, kw * eta, b2, ro);
   const float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallNeeFoot);
-  const float val = measure_emitter(S, ei, x + h.t * w, w, b2, ro, kw, lambda, u.x, u.y);
+  float val;
+  if (ANISO) {
+    // the footprint stored by k_shade in the frame of w, propagated
+    const float4 k0 = P.nk0[slot], k1 = P.nk1[slot], xw = P.nkf[slot];
+    AK Kw{k0.x, k0.y, k0.z, k0.w, k1.x, k1.y};
+    const float zb = h.t * 1e6f / (kw * eta);
+    Kw.i11 += zb;
+    Kw.i22 += zb;
+    val = measure_emitter_aniso(S, ei, x + h.t * w, w, Kw, xyz(xw), kw, lambda, u.x, u.y);
+  } else {
+    footprint_update(h.t, kw * eta, b2, ro);
+    val = measure_emitter(S, ei, x + h.t * w, w, b2, ro, kw, lambda, u.x, u.y);
+  }
   if (val == 0.0f) return;
   // lobe density toward w and the power-heuristic weight against the
   // emitter's direction sampler
@@ -1470,7 +1647,7 @@ __device__ __forceinline__ void shadow_finish_hero(const RenderParams& p, int sl
 // emitter direction, then shadow_finish, one ray per thread per pass (the
 // shadow queue is a third as long as the trace queue: too short for
 // lane_trace's refill schedule to pay for itself).
-template <int NS, bool WIDE, bool HERO>
+template <int NS, bool WIDE, int MODE>
 __global__ void __launch_bounds__(256, GR_SHADOW_MIN_BLOCKS) k_shadow(RenderParams p) {
   const Pool& P = p.pool;
   const int n = *(volatile int*)&p.ctr->sq_count;
@@ -1482,10 +1659,10 @@ __global__ void __launch_bounds__(256, GR_SHADOW_MIN_BLOCKS) k_shadow(RenderPara
     const float3 o = xyz(P.od0[slot]), d = xyz(P.shd[slot]);  // requested only if emitter_reachable
     const Hit h = WIDE ? closest_hit_wide(S, o, d, m.w, &refined, &visits, &tests, &err)
                        : closest_hit(S, o, d, m.w, &refined, &visits, &tests, &err);
-    if (HERO)
+    if (MODE == 1)
       shadow_finish_hero<NS>(p, slot, h);
     else
-      shadow_finish<NS>(p, slot, h);
+      shadow_finish<NS, MODE == 2>(p, slot, h);
   }
   block_count(&p.ctr->ref_hit, refined);
   block_count(&p.ctr->node_visits, visits);
@@ -1679,7 +1856,7 @@ template <int NS, typename TT>
 cudaError_t launch_iteration(const RenderParams& p, int grid_regen, int grid_trace, int grid_shade, int grid_shadow,
                              int block, size_t smem, cudaStream_t st, cudaEvent_t* ev) {
   const bool wide = (p.flags & GR_FLAG_WIDE_BVH) != 0;
-  const bool hero = (p.flags & GR_FLAG_HERO) != 0;
+  const bool hero = (p.flags & GR_FLAG_HERO) != 0, aniso = (p.flags & GR_FLAG_ANISO) != 0;
   if (ev) cudaEventRecord(ev[0], st);
   if (hero)
     k_regen<NS, true><<<grid_regen, block, 0, st>>>(p);
@@ -1692,34 +1869,54 @@ cudaError_t launch_iteration(const RenderParams& p, int grid_regen, int grid_tra
     k_trace<false><<<grid_trace, trace_block(block), 0, st>>>(p);
   if (ev) cudaEventRecord(ev[2], st);
   if (hero)
-    k_shade<NS, TT, true><<<grid_shade, block, smem, st>>>(p);
+    k_shade<NS, TT, 1><<<grid_shade, block, smem, st>>>(p);
+  else if (aniso)
+    k_shade<NS, TT, 2><<<grid_shade, block, smem, st>>>(p);
   else
-    k_shade<NS, TT, false><<<grid_shade, block, smem, st>>>(p);
+    k_shade<NS, TT, 0><<<grid_shade, block, smem, st>>>(p);
   if (ev) cudaEventRecord(ev[3], st);
-  if (wide && hero)
-    k_shadow<NS, true, true><<<grid_shadow, block, 0, st>>>(p);
+  const int mode = hero ? 1 : aniso ? 2 : 0;
+  if (wide && mode == 1)
+    k_shadow<NS, true, 1><<<grid_shadow, block, 0, st>>>(p);
+  else if (wide && mode == 2)
+    k_shadow<NS, true, 2><<<grid_shadow, block, 0, st>>>(p);
   else if (wide)
-    k_shadow<NS, true, false><<<grid_shadow, block, 0, st>>>(p);
-  else if (hero)
-    k_shadow<NS, false, true><<<grid_shadow, block, 0, st>>>(p);
+    k_shadow<NS, true, 0><<<grid_shadow, block, 0, st>>>(p);
+  else if (mode == 1)
+    k_shadow<NS, false, 1><<<grid_shadow, block, 0, st>>>(p);
+  else if (mode == 2)
+    k_shadow<NS, false, 2><<<grid_shadow, block, 0, st>>>(p);
   else
-    k_shadow<NS, false, false><<<grid_shadow, block, 0, st>>>(p);
+    k_shadow<NS, false, 0><<<grid_shadow, block, 0, st>>>(p);
   if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError();
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// The shade and regen kernels a render launches (for occupancy queries).
-const void* shade_kernel(int ns, int dtype, bool hero) {
+// The shade, regen and shadow kernels a render launches (for occupancy
+// queries); mode 0 plain, 1 hero-wavelength MIS, 2 anisotropic footprints.
+template <int NS, typename TT>
+const void* shade_kernel_t(int mode) {
+  return mode == 1 ? (const void*)k_shade<NS, TT, 1> : mode == 2 ? (const void*)k_shade<NS, TT, 2>
+                                                                 : (const void*)k_shade<NS, TT, 0>;
+}
+const void* shade_kernel(int ns, int dtype, int mode) {
   if (ns == 1) {
-    if (dtype == GR_TABLE_F32) return hero ? (const void*)k_shade<1, float, true> : (const void*)k_shade<1, float, false>;
-    if (dtype == GR_TABLE_F16) return hero ? (const void*)k_shade<1, __half, true> : (const void*)k_shade<1, __half, false>;
-    return hero ? (const void*)k_shade<1, __nv_bfloat16, true> : (const void*)k_shade<1, __nv_bfloat16, false>;
+    if (dtype == GR_TABLE_F32) return shade_kernel_t<1, float>(mode);
+    if (dtype == GR_TABLE_F16) return shade_kernel_t<1, __half>(mode);
+    return shade_kernel_t<1, __nv_bfloat16>(mode);
   }
-  if (dtype == GR_TABLE_F32) return hero ? (const void*)k_shade<4, float, true> : (const void*)k_shade<4, float, false>;
-  if (dtype == GR_TABLE_F16) return hero ? (const void*)k_shade<4, __half, true> : (const void*)k_shade<4, __half, false>;
-  return hero ? (const void*)k_shade<4, __nv_bfloat16, true> : (const void*)k_shade<4, __nv_bfloat16, false>;
+  if (dtype == GR_TABLE_F32) return shade_kernel_t<4, float>(mode);
+  if (dtype == GR_TABLE_F16) return shade_kernel_t<4, __half>(mode);
+  return shade_kernel_t<4, __nv_bfloat16>(mode);
+}
+const void* shadow_kernel(int ns, int mode) {
+  if (ns == 1)
+    return mode == 1 ? (const void*)k_shadow<1, false, 1> : mode == 2 ? (const void*)k_shadow<1, false, 2>
+                                                                      : (const void*)k_shadow<1, false, 0>;
+  return mode == 1 ? (const void*)k_shadow<4, false, 1> : mode == 2 ? (const void*)k_shadow<4, false, 2>
+                                                                    : (const void*)k_shadow<4, false, 0>;
 }
 const void* regen_kernel(int ns, bool hero) {
   if (ns == 1) return hero ? (const void*)k_regen<1, true> : (const void*)k_regen<1, false>;
@@ -1825,8 +2022,10 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const size_t o_meta = take(sizeof(int4) * (size_t)P);
   const size_t o_tq = take(sizeof(int) * (size_t)P);
   const size_t o_sq = take(sizeof(int) * (size_t)P);
-  const bool hero = (o.flags & GR_FLAG_HERO) != 0;
+  const bool hero = (o.flags & GR_FLAG_HERO) != 0, aniso = (o.flags & GR_FLAG_ANISO) != 0;
+  const int mode = hero ? 1 : aniso ? 2 : 0;
   const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 16) : 0;  // hq, hqp, hfb, hfr, hpart/haccS/haccC[4]
+  const size_t o_aniso = aniso ? take(sizeof(float4) * (size_t)P * 5) : 0;  // ak0, ak1, nk0, nk1, nkf
   const size_t total = off;
   if (f->scratch_bytes < total) {
     if (f->scratch) cudaFreeAsync(f->scratch, st);
@@ -1877,6 +2076,14 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     p.pool.hpart = h4 + (size_t)P * 4;
     p.pool.haccS = h4 + (size_t)P * 8;
     p.pool.haccC = h4 + (size_t)P * 12;
+  }
+  if (aniso) {
+    float4* a4 = (float4*)(base + o_aniso);
+    p.pool.ak0 = a4;
+    p.pool.ak1 = a4 + (size_t)P;
+    p.pool.nk0 = a4 + (size_t)P * 2;
+    p.pool.nk1 = a4 + (size_t)P * 3;
+    p.pool.nkf = a4 + (size_t)P * 4;
   }
   p.P = P;
   p.regen_thr = o.regen_threshold_pct;
@@ -1932,11 +2139,9 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     return sms * per;
   };
   int g_regen, g_trace, g_shade, g_shadow;
-  const void* shade_fn = shade_kernel(NSv, o.table_dtype, hero);
+  const void* shade_fn = shade_kernel(NSv, o.table_dtype, mode);
   g_regen = grid_for(regen_kernel(NSv, hero), 0);
-  g_shadow = grid_for(NSv == 1 ? (hero ? (const void*)k_shadow<1, false, true> : (const void*)k_shadow<1, false, false>)
-                                : (hero ? (const void*)k_shadow<4, false, true> : (const void*)k_shadow<4, false, false>),
-                      0);
+  g_shadow = grid_for(shadow_kernel(NSv, mode), 0);
   const bool wide_bvh = (o.flags & GR_FLAG_WIDE_BVH) != 0;
   const int tblk = wide_bvh ? block : trace_block(block);
   g_trace = wide_bvh ? grid_for((const void*)k_trace<true>, 0) : grid_for((const void*)k_trace<false>, 0, tblk);
@@ -2346,7 +2551,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, blk > 0 ? blk : block, dyn);
     return sms * std::max(per, 1);
   };
-  const void* shade_fn = shade_kernel(NSv, o.table_dtype, false);
+  const void* shade_fn = shade_kernel(NSv, o.table_dtype, 0);
   const int gmax = (int)((P + block - 1) / block);
   const int g_regen = std::min(gmax, grid_for(regen_kernel(NSv, false), 0));
   const bool wide_bvh = (o.flags & GR_FLAG_WIDE_BVH) != 0;
@@ -2356,7 +2561,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
                                                        : grid_for((const void*)k_trace<false>, 0, tblk));
   const int g_shade = std::min(gmax, grid_for(shade_fn, smem));
   const int g_shadow =
-      std::min(gmax, grid_for(NSv == 1 ? (const void*)k_shadow<1, false, false> : (const void*)k_shadow<4, false, false>, 0));
+      std::min(gmax, grid_for(shadow_kernel(NSv, 0), 0));
   // --- iteration loop; the host reads the device counters into a stack copy
   // after every batch (no events, no pinned buffer)
   long long n_max = 1, d_max = 0;
