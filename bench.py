@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--cpu-crop", type=int, default=128, help="side of the oracle's centre crop")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", choices=["procedural", "batched", "serving", "precision", "dielectric",
-                                           "doubleslit", "hero"],
+                                           "doubleslit", "hero", "aniso"],
                     default="procedural",
                     help="procedural: the headline single-view workload; batched: 64 views/scenes, plain "
                          "per-view FP32 form vs the autotuned single-graph form; serving: "
@@ -81,7 +81,8 @@ def parse():
                          "image and per-quantity errors vs the FP64 oracle; dielectric: the procedural "
                          "workload with refracting glass slabs; doubleslit: footprint-resolved generalized "
                          "rays through two slits at scale; hero: the procedural workload with "
-                         "hero-wavelength spectral MIS vs without (throughput, variance, efficiency)")
+                         "hero-wavelength spectral MIS vs without (throughput, variance, efficiency); "
+                         "aniso: the procedural workload with anisotropic footprints vs the scalar model")
     ap.add_argument("--views", type=int, default=64)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--rates", default="5,50,100", help="serving: further arrival rates to sweep (req/s)")
@@ -445,37 +446,25 @@ def run_doubleslit(args):
     print(json.dumps(line))
 
 
-def run_hero(args):
-    """Hero-wavelength spectral MIS (Sec. 7.2) on the headline procedural
-    workload: throughput with and without the flag, with per-kernel device
-    time; rel-L2 of the hero image against the oracle's hero estimator on a
-    centre crop; and the variance of both estimators across independent
-    seeds at equal samples per pixel, so that efficiency = (variance x time
-    per sample) of the plain estimator over that of the hero estimator (> 1:
-    hero MIS reaches a given noise sooner)."""
-    import numpy as np
+def time_modes(args, S, F, view, modes, clock_mode):
+    """Device time per step (CUDA events, L2 flushed) and per-kernel time of
+    each named flag set; nvidia-smi clocks are sampled during `clock_mode`.
+    Returns ms, kernel ms per step, clocks and each mode's last image."""
     import torch
     import paper_2303_15762_gb300 as gr
-    from paper_2303_15762_gb300 import scenegen as sg
-    gr.load()
-    scene, view = workload(args, 0)
-    samples = view["width"] * view["height"] * view["spp"]
-    S = gr.Scene(scene)
-    F = gr.Frame([view])
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
-    modes = {"plain": gr.FLAG_NEE, "hero": gr.FLAG_NEE | gr.FLAG_HERO}
 
     def step(flags, profile=False):
         F.reset()
         gr.render([S], [view], F, seed=2, flags=flags, table_dtype=args.table, pool_size=args.pool, profile=profile)
 
-    ms, kernel_ms, clk = {}, {}, None
+    ms, kernel_ms, clk, imgs = {}, {}, None, {}
     for name, flags in modes.items():
         for _ in range(max(3, args.warmup)):
             step(flags)
         torch.cuda.synchronize()
-        clocks = ClockSampler(0) if name == "hero" else None
+        clocks = ClockSampler(0) if name == clock_mode else None
         times, kms = [], [0.0] * 4
         for _ in range(args.steps):
             flush.zero_()
@@ -493,6 +482,65 @@ def run_hero(args):
             clk = clocks.stop()
         ms[name] = statistics.mean(times)
         kernel_ms[name] = {KERNELS[k]: kms[k] for k in range(4)}
+        imgs[name] = F.readback(0)
+    return ms, kernel_ms, clk, imgs
+
+
+def run_aniso(args):
+    """Anisotropic footprints (beta and rho as 2x2 matrices, Sec. 3.1) on the
+    headline procedural workload: throughput with and without the flag,
+    per-kernel device time, rel-L2 against the oracle's anisotropic model on
+    a centre crop, and how far the anisotropic image moves from the scalar
+    model's."""
+    import numpy as np
+    import paper_2303_15762_gb300 as gr
+    gr.load()
+    scene, view = workload(args, 0)
+    samples = view["width"] * view["height"] * view["spp"]
+    S = gr.Scene(scene)
+    F = gr.Frame([view])
+    modes = {"scalar": gr.FLAG_NEE, "aniso": gr.FLAG_NEE | gr.FLAG_ANISO}
+    ms, kernel_ms, clk, imgs = time_modes(args, S, F, view, modes, "aniso")
+    st = F.stats()
+    a, b = imgs["aniso"].astype(np.float64), imgs["scalar"].astype(np.float64)
+    rel = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as orc
+        c = min(args.cpu_crop, args.size)
+        x0 = args.size // 2 - c // 2
+        ref = orc.Scene(scene).render(view, 2, orc.FLAG_NEE | orc.FLAG_ANISO, crop=(x0, x0, x0 + c, x0 + c))
+        rel = float(np.linalg.norm(a[x0:x0 + c, x0:x0 + c] - ref) / max(np.linalg.norm(ref), 1e-300))
+    line = {"workload": "aniso", "metric": METRIC, "unit": UNIT, "value": samples / (ms["aniso"] * 1e-3) / 1e6,
+            "scalar_value": samples / (ms["scalar"] * 1e-3) / 1e6, "ms_aniso": ms["aniso"], "ms_scalar": ms["scalar"],
+            "kernel_ms_per_step": kernel_ms, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(args, scene) + ", anisotropic footprints",
+                       "l2": "flushed before every timed step (256 MB write)"},
+            "rel_l2_vs_oracle_aniso": rel,
+            "rel_change_vs_scalar_model": float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)),
+            "clocks": clk, "stats": {"iterations": st["iterations"], "segments": st["segments"],
+                                     "shadow_rays": st["shadow_rays"]}}
+    print(json.dumps(line))
+
+
+def run_hero(args):
+    """Hero-wavelength spectral MIS (Sec. 7.2) on the headline procedural
+    workload: throughput with and without the flag, with per-kernel device
+    time; rel-L2 of the hero image against the oracle's hero estimator on a
+    centre crop; and the variance of both estimators across independent
+    seeds at equal samples per pixel, so that efficiency = (variance x time
+    per sample) of the plain estimator over that of the hero estimator (> 1:
+    hero MIS reaches a given noise sooner)."""
+    import numpy as np
+    import paper_2303_15762_gb300 as gr
+    from paper_2303_15762_gb300 import scenegen as sg
+    gr.load()
+    scene, view = workload(args, 0)
+    samples = view["width"] * view["height"] * view["spp"]
+    S = gr.Scene(scene)
+    F = gr.Frame([view])
+    modes = {"plain": gr.FLAG_NEE, "hero": gr.FLAG_NEE | gr.FLAG_HERO}
+    ms, kernel_ms, clk, _ = time_modes(args, S, F, view, modes, "hero")
     img = F.readback(0)  # the last hero render
     st = F.stats()
     rel = None
@@ -553,6 +601,9 @@ def main():
         return
     if args.workload == "hero":
         run_hero(args)
+        return
+    if args.workload == "aniso":
+        run_aniso(args)
         return
     world, rank, local = dist_setup()
     import numpy as np
