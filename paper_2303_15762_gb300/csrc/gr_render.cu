@@ -293,17 +293,22 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
     } else if (valid && st == ST_DONE) {
       ++finished;
       const DevView& V = p.views[m.x];
-      float4 s = P.accS[slot], c = P.accC[slot], v = P.part[slot];
+      const int WH = V.W * V.H;
+      const int bin = m.y / WH;
+      const int k = meta_k(m.z) + 1;
+      const int n_smp = bin_samples(V, bin);
+      // a one-sample ticket's sum is its sample: no slot accumulator is kept
+      // (the same bits as a Kahan sum of one term)
+      float4 s = n_smp == 1 ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : P.accS[slot];
+      float4 c = n_smp == 1 ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : P.accC[slot];
+      const float4 v = P.part[slot];
       kahan_add(s.x, c.x, v.x);
       if (NS == 4) {
         kahan_add(s.y, c.y, v.y);
         kahan_add(s.z, c.z, v.z);
         kahan_add(s.w, c.w, v.w);
       }
-      const int WH = V.W * V.H;
-      const int bin = m.y / WH;
-      const int k = meta_k(m.z) + 1;
-      if (k < bin_samples(V, bin)) {
+      if (k < n_smp) {
         P.accS[slot] = s;
         P.accC[slot] = c;
         start_sample<NS, false>(p, slot, m.x, m.y, k);
@@ -356,7 +361,7 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
                 P.haccS[(size_t)g * p.P + slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 P.haccC[(size_t)g * p.P + slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
               }
-            } else {
+            } else if (class_samples(V, cls, V.Q) > 1) {
               P.accS[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
               P.accC[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
@@ -384,7 +389,7 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
 
 // ------------------------------------------------------------------ trace
 #ifndef GR_TRACE_REFILL
-#define GR_TRACE_REFILL 8
+#define GR_TRACE_REFILL 12
 #endif
 #ifndef GR_LEAF_BATCH
 #define GR_LEAF_BATCH 16
@@ -1937,9 +1942,20 @@ struct RenderPlan {
 // Called by gr_render after argument validation.
 // acc_sum[v] / acc_comp[v]: view v's accumulator planes; f supplies the
 // scratch, counters and graph cache of the call.
-gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc* vd, int n_views,
+gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc* vd_in, int n_views,
                       const gr_render_opts& o, gr_frame* f, const std::vector<float*>& acc_sum,
                       const std::vector<float*>& acc_comp, cudaStream_t st, std::string& err) {
+  // Tickets are numbered over the views in order of decreasing path depth, so
+  // that the paths still running once every ticket is claimed (the render's
+  // tail) belong to the shallowest views.  Results do not depend on the
+  // order: each view keeps its RNG key and its accumulators.
+  std::vector<int> order(n_views);
+  for (int v = 0; v < n_views; ++v) order[v] = v;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return vd_in[a].max_depth > vd_in[b].max_depth; });
+  std::vector<gr_view_desc> vds(n_views);
+  for (int v = 0; v < n_views; ++v) vds[v] = vd_in[order[v]];
+  const gr_view_desc* vd = vds.data();
   const int NSv = vd[0].n_stokes;
   RenderPlan plan;
   plan.scenes.resize(n_scenes);
@@ -1969,8 +1985,8 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     V.nbu = std::min(d.spp, V.Q);
     V.n_tickets = (long long)V.nbu * d.width * d.height;
     plan.total_tickets += (unsigned long long)V.n_tickets;
-    V.acc_sum = acc_sum[v];
-    V.acc_comp = acc_comp[v];
+    V.acc_sum = acc_sum[order[v]];
+    V.acc_comp = acc_comp[order[v]];
     // grating order table rows for every (material, bin) of this view
     const gr_scene* sc = scenes[d.scene_index];
     V.table_base = (int)plan.rows.size();
