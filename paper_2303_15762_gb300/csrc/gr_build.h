@@ -32,6 +32,7 @@ struct Pool {
   int4* meta;    // view, local ticket, (sample k | seg << 16 | state << 24 | delta << 26), previous leaf slot
   int* tq;       // trace queue
   int* sq;       // shadow queue
+  unsigned char* st8;  // slot state (idle / active / done): the one field k_regen scans for every slot
   // hero-wavelength MIS only (null otherwise); planes [g * P + slot] for the
   // class member g (bin c + g Q)
   float4* hq;    // path density ratios q_g of the class wavelengths to the hero's

@@ -46,6 +46,10 @@ enum { ST_IDLE = 0, ST_ACTIVE = 1, ST_DONE = 2 };
 #ifndef GR_SHADE_MIN_BLOCKS
 #define GR_SHADE_MIN_BLOCKS 3
 #endif
+// scalar (n_stokes = 1) shading holds fewer values per thread
+#ifndef GR_SHADE_MIN_BLOCKS_NS1
+#define GR_SHADE_MIN_BLOCKS_NS1 4
+#endif
 
 __device__ __forceinline__ int meta_k(int z) { return z & 0xffff; }
 __device__ __forceinline__ int meta_seg(int z) { return (z >> 16) & 0xff; }
@@ -105,17 +109,25 @@ __device__ __forceinline__ int tq_entry(const RenderParams& p, int e, int front)
   return e < front ? p.pool.tq[e] : p.pool.tq[p.P - 1 - (e - front)];
 }
 
-__device__ __forceinline__ int find_view(const RenderParams& p, unsigned long long t) {
+// The view that owns ticket t: binary search over the views' first tickets,
+// read from `bases` (a shared-memory copy) when given, else from the views.
+__device__ __forceinline__ int find_view(const RenderParams& p, unsigned long long t,
+                                         const long long* bases = nullptr) {
   int lo = 0, hi = p.n_views - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    if ((unsigned long long)p.views[mid].ticket_base <= t)
+    const long long b = bases ? bases[mid] : p.views[mid].ticket_base;
+    if ((unsigned long long)b <= t)
       lo = mid;
     else
       hi = mid - 1;
   }
   return lo;
 }
+// views whose first tickets k_regen stages in shared memory (4 KB)
+#ifndef GR_REGEN_SMEM_VIEWS
+#define GR_REGEN_SMEM_VIEWS 512
+#endif
 
 template <typename TT>
 __device__ __forceinline__ float table_load(const TT* v, int i);
@@ -160,6 +172,7 @@ __device__ __forceinline__ void start_sample(const RenderParams& p, int slot, in
   // contribution (zero) of a camera segment are implied by segment 0: k_shade
   // forms them instead of reading them
   P.meta[slot] = make_int4(view, local, meta_pack(k, 0, ST_ACTIVE, 1), -1);
+  P.st8[slot] = ST_ACTIVE;
   if (HERO)  // the sample's contributions to the other bins of its class
     for (int g = 0; g < 4; ++g) P.hpart[(size_t)g * p.P + slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
@@ -276,12 +289,20 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
   const int active_prev = *(volatile int*)&p.ctr->last_active;
   const bool may_claim = p.regen_thr <= 0 || active_prev == 0 ||
                          (long long)(p.P - active_prev) * 100 >= (long long)p.regen_thr * p.P;
+  // the views' first tickets, for the claims' view search (batches of views)
+  __shared__ long long s_base[GR_REGEN_SMEM_VIEWS];
+  const bool staged = p.n_views > 1 && p.n_views <= GR_REGEN_SMEM_VIEWS;
+  if (staged) {
+    for (int i = threadIdx.x; i < p.n_views; i += blockDim.x) s_base[i] = p.views[i].ticket_base;
+    __syncthreads();
+  }
   for (int base = blockIdx.x * blockDim.x; base < p.P; base += stride) {
     const int slot = base + threadIdx.x;
     const bool valid = slot < p.P;
     bool need = false, active = false, fresh = false;
-    int4 m = valid ? P.meta[slot] : make_int4(0, 0, 0, 0);
-    const int st = meta_state(m.z);
+    // one byte of state per slot; the meta record only for finished samples
+    const int st = valid ? P.st8[slot] : ST_IDLE;
+    const int4 m = valid && st == ST_DONE ? P.meta[slot] : make_int4(0, 0, 0, 0);
     if (valid && st == ST_DONE && HERO) {
       ++finished;
       if (fold_class<NS>(p, slot, m)) {
@@ -332,7 +353,7 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
     }
     if (need && !may_claim) {
       need = false;
-      P.meta[slot] = make_int4(0, 0, meta_pack(0, 0, ST_IDLE, 0), -1);
+      if (st != ST_IDLE) P.st8[slot] = ST_IDLE;
     }
     // claim tickets, one atomic per block (tickets without samples in this
     // render are skipped by claiming again)
@@ -341,9 +362,9 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
       if (need) {
         if (t >= p.ctr->total_tickets) {
           need = false;
-          P.meta[slot] = make_int4(0, 0, meta_pack(0, 0, ST_IDLE, 0), -1);
+          if (st != ST_IDLE) P.st8[slot] = ST_IDLE;
         } else {
-          int view = find_view(p, t);
+          int view = find_view(p, t, staged ? s_base : nullptr);
           const DevView& V = p.views[view];
           // tickets run pixel-major, sample class fastest: neighbouring
           // slots start the same pixel at neighbouring wavelengths, so a warp's
@@ -394,6 +415,12 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
 #ifndef GR_LEAF_BATCH
 #define GR_LEAF_BATCH 16
 #endif
+// queue entries a warp claims with one atomic: 32, or 64 for launches of
+// more than GR_TRACE_BIG_QUEUE rays, where the atomics on the shared cursor
+// add up and the end-of-launch imbalance of larger groups does not
+#ifndef GR_TRACE_BIG_QUEUE
+#define GR_TRACE_BIG_QUEUE (1 << 22)
+#endif
 #ifndef GR_LEAF_BLOCKED
 #define GR_LEAF_BLOCKED 8
 #endif
@@ -442,7 +469,8 @@ __device__ __forceinline__ void lane_trace(const RenderParams& p, int n, int* cu
     done(out, h);
     live = false;
   };
-  // the warp's claimed group: its last `left` entries (from base + 32 - left) are unread
+  // the warp's claimed group: its last `left` entries (from base + group - left) are unread
+  const int group = n > GR_TRACE_BIG_QUEUE ? 64 : 32;
   int base = 0, left = 0;
   bool more = true;  // unclaimed groups may remain
   for (;;) {
@@ -451,7 +479,7 @@ __device__ __forceinline__ void lane_trace(const RenderParams& p, int n, int* cu
     const int nidle = __popc(idle);
     if ((left > 0 || more) && (nidle >= GR_TRACE_REFILL || idle == 0xffffffffu)) {
       const int rank = __popc(idle & below);
-      int take = rank < left ? base + 32 - left + rank : -1;
+      int take = rank < left ? base + group - left + rank : -1;
       if (nidle <= left) {
         left -= nidle;
       } else {
@@ -459,14 +487,14 @@ __device__ __forceinline__ void lane_trace(const RenderParams& p, int n, int* cu
         left = 0;
         if (more) {
           int nb = 0;
-          if (lane == 0) nb = atomicAdd(cursor, 32);
+          if (lane == 0) nb = atomicAdd(cursor, group);
           nb = __shfl_sync(0xffffffffu, nb, 0);
           if (nb >= n) {
             more = false;
           } else {
             if (rank >= from_old) take = nb + (rank - from_old);
             base = nb;
-            left = 32 - (nidle - from_old);
+            left = group - (nidle - from_old);
           }
         }
       }
@@ -984,7 +1012,8 @@ __device__ __forceinline__ float order0_prob(const TableRow& row, float3 t_mir, 
 // MODE 0: plain; 1: hero-wavelength MIS (HERO); 2: anisotropic footprints
 // (ANISO, K carried per slot).
 template <int NS, typename TT, int MODE>
-__global__ void __launch_bounds__(256, MODE != 0 ? 2 : GR_SHADE_MIN_BLOCKS) k_shade(RenderParams p) {
+__global__ void __launch_bounds__(256, MODE != 0 ? 2 : (NS == 1 ? GR_SHADE_MIN_BLOCKS_NS1 : GR_SHADE_MIN_BLOCKS))
+    k_shade(RenderParams p) {
   constexpr bool HERO = MODE == 1, ANISO = MODE == 2;
   extern __shared__ __align__(16) unsigned char smem[];
   const TableRow* rows = p.rows;
@@ -1488,12 +1517,16 @@ __global__ void __launch_bounds__(256, MODE != 0 ? 2 : GR_SHADE_MIN_BLOCKS) k_sh
             } else {
               P.od1[slot] = make_float4(d.x, d.y, d.z, rho);
               P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg, ST_DONE, 0), hslot);
+              P.st8[slot] = ST_DONE;
             }
           }
         }
       }
       P.part[slot] = pt;
-      if (done) P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg, ST_DONE, 0), m.w);
+      if (done) {
+        P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg, ST_DONE, 0), m.w);
+        P.st8[slot] = ST_DONE;
+      }
     }
     const int q = block_reserve<int>(&p.ctr->sq_count, want_shadow);
     if (want_shadow) P.sq[q] = slot;
@@ -2038,6 +2071,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const size_t o_meta = take(sizeof(int4) * (size_t)P);
   const size_t o_tq = take(sizeof(int) * (size_t)P);
   const size_t o_sq = take(sizeof(int) * (size_t)P);
+  const size_t o_st8 = take((size_t)P);
   const bool hero = (o.flags & GR_FLAG_HERO) != 0, aniso = (o.flags & GR_FLAG_ANISO) != 0;
   const int mode = hero ? 1 : aniso ? 2 : 0;
   const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 16) : 0;  // hq, hqp, hfb, hfr, hpart/haccS/haccC[4]
@@ -2083,6 +2117,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   p.pool.meta = (int4*)(base + o_meta);
   p.pool.tq = (int*)(base + o_tq);
   p.pool.sq = (int*)(base + o_sq);
+  p.pool.st8 = base + o_st8;
   if (hero) {
     float4* h4 = (float4*)(base + o_hero);
     p.pool.hq = h4;
@@ -2138,6 +2173,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     f->launches += 1;
   }
   GR_CK(cudaMemsetAsync(p.pool.meta, 0, sizeof(int4) * (size_t)P, st));
+  GR_CK(cudaMemsetAsync(p.pool.st8, ST_IDLE, (size_t)P, st));
   Counters c0;
   std::memset(&c0, 0, sizeof c0);
   c0.total_tickets = plan.total_tickets;
@@ -2467,13 +2503,13 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   const size_t o_vals = take(tsize * (size_t)std::max(vals, 1));
   const size_t o_vals32 = o.table_dtype == GR_TABLE_F32 ? o_vals : take(sizeof(float) * (size_t)std::max(vals, 1));
   const size_t fixed = off;
-  const size_t per_slot = sizeof(float4) * 14 + sizeof(float2) + sizeof(int4) + 2 * sizeof(int);
+  const size_t per_slot = sizeof(float4) * 14 + sizeof(float2) + sizeof(int4) + 2 * sizeof(int) + 1;
   if (fixed + per_slot * 256 > (size_t)GR_STATIC_SCRATCH_BYTES) {
     err = "views and order tables need " + std::to_string(fixed) + " bytes; the static scratch holds " +
           std::to_string((size_t)GR_STATIC_SCRATCH_BYTES);
     return GR_E_INVALID;
   }
-  const long long p_max = (long long)(((size_t)GR_STATIC_SCRATCH_BYTES - fixed - 6 * 256) / per_slot) / 256 * 256;
+  const long long p_max = (long long)(((size_t)GR_STATIC_SCRATCH_BYTES - fixed - 7 * 256) / per_slot) / 256 * 256;
   if (o.pool_size > p_max) {
     err = "pool_size " + std::to_string(o.pool_size) + " exceeds the static scratch capacity of " +
           std::to_string(p_max) + " slots";
@@ -2488,6 +2524,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   const size_t o_meta = take(sizeof(int4) * (size_t)P);
   const size_t o_tq = take(sizeof(int) * (size_t)P);
   const size_t o_sq = take(sizeof(int) * (size_t)P);
+  const size_t o_st8 = take((size_t)P);
   if (off > (size_t)GR_STATIC_SCRATCH_BYTES) {
     err = "static scratch layout overflow";
     return GR_E_INVALID;
@@ -2521,6 +2558,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   p.pool.meta = (int4*)(base + o_meta);
   p.pool.tq = (int*)(base + o_tq);
   p.pool.sq = (int*)(base + o_sq);
+  p.pool.st8 = base + o_st8;
   p.P = (int)P;
   p.regen_thr = o.regen_threshold_pct;
   p.ctr = (Counters*)(base + o_ctr);
@@ -2542,6 +2580,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   c0.total_tickets = total_tickets;
   GR_SK(cudaMemcpyAsync(base + o_ctr, &c0, sizeof c0, cudaMemcpyHostToDevice, st));
   GR_SK(cudaMemsetAsync(p.pool.meta, 0, sizeof(int4) * (size_t)P, st));
+  GR_SK(cudaMemsetAsync(p.pool.st8, ST_IDLE, (size_t)P, st));
   GR_SK(cudaMemcpyAsync(base + o_views, views.data(), sizeof(DevView) * n_views, cudaMemcpyHostToDevice, st));
   GR_SK(cudaMemcpyAsync(base + o_vdesc, vd, sizeof(gr_view_desc) * n_views, cudaMemcpyHostToDevice, st));
   GR_SK(cudaMemcpyAsync(base + o_scenes, sc.data(), sizeof(DevScene) * n_scenes, cudaMemcpyHostToDevice, st));
