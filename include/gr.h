@@ -341,7 +341,7 @@ gr_status gr_aperture_backward_2d(int32_t n_det, const double* x0, int32_t n_ap,
  *
  * Scratch limits: the views' descriptors and grating order tables, plus the
  * slot pool, must fit in GR_STATIC_SCRATCH_BYTES; opts.pool_size (0 = as many
- * slots as fit, about 270k) above that capacity is rejected with GR_E_INVALID
+ * slots as fit, about 260k) above that capacity is rejected with GR_E_INVALID
  * and a message naming the limit.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture.  Every call reuses the same
