@@ -43,10 +43,12 @@ enum { ST_IDLE = 0, ST_ACTIVE = 1, ST_DONE = 2 };
 #ifndef GR_SHADOW_MIN_BLOCKS
 #define GR_SHADOW_MIN_BLOCKS 3
 #endif
+// shading: 4 blocks/SM (64 registers) for both Stokes counts.  The spills
+// this costs the 4-Stokes kernel are cheaper than the latency left exposed
+// with a quarter fewer resident warps (measured on both forms).
 #ifndef GR_SHADE_MIN_BLOCKS
-#define GR_SHADE_MIN_BLOCKS 3
+#define GR_SHADE_MIN_BLOCKS 4
 #endif
-// scalar (n_stokes = 1) shading holds fewer values per thread
 #ifndef GR_SHADE_MIN_BLOCKS_NS1
 #define GR_SHADE_MIN_BLOCKS_NS1 4
 #endif
