@@ -45,16 +45,25 @@ KERNELS = ["k_regen", "k_trace", "k_shade", "k_shadow"]
 # dram__bytes_read.sum + dram__bytes_write.sum of the second k_trace launch of
 # the 256x256 x 64 spp case (64.47 + 1.62 MB), divided by the rays it traced
 # (the full pool: 2^20 slots, all live in the second iteration); traffic grows
-# with the rays a launch processes.  Valid only for the kernel sources whose
-# hash is recorded with it (else reported null).
-NCU_TRAFFIC_PER_RAY = {("k_trace", "9d2bd29d4b3ca751"): (64.472064e6 + 1.620736e6) / 1048576}
+# with the rays a launch processes.  Valid only for the traversal sources
+# whose hash (source_hash) is recorded with it (else reported null).
+NCU_TRAFFIC_PER_RAY = {("k_trace", "dc70178eb9f341ac"): (64.472064e6 + 1.620736e6) / 1048576}
 
 
 def source_hash():
+    """Hash of what k_trace's DRAM bytes per ray depend on: the device header
+    (traversal, BVH layout), the slot-pool layout and the trace section of the
+    render source (the queue schedule and the kernel)."""
+    csrc = os.path.join(ROOT, "paper_2303_15762_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ["gr_device.cuh", "gr_render.cu", "gr_build.h"]:
-        with open(os.path.join(ROOT, "paper_2303_15762_gb300", "csrc", f), "rb") as fh:
+    for f in ["gr_device.cuh", "gr_build.h"]:
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(csrc, "gr_render.cu"), "rb") as fh:
+        text = fh.read()
+    start = text.index(b"// ------------------------------------------------------------------ trace")
+    end = text.index(b"// ------------------------------------------------------------------ footprint")
+    h.update(text[start:end])
     return h.hexdigest()[:16]
 
 

@@ -55,7 +55,6 @@ enum { ST_IDLE = 0, ST_ACTIVE = 1, ST_DONE = 2 };
 
 __device__ __forceinline__ int meta_k(int z) { return z & 0xffff; }
 __device__ __forceinline__ int meta_seg(int z) { return (z >> 16) & 0xff; }
-__device__ __forceinline__ int meta_state(int z) { return (z >> 24) & 3; }
 __device__ __forceinline__ int meta_delta(int z) { return (z >> 26) & 1; }
 __device__ __forceinline__ int meta_pack(int k, int seg, int st, int delta) {
   return k | (seg << 16) | (st << 24) | (delta << 26);
