@@ -52,6 +52,10 @@ enum { ST_IDLE = 0, ST_ACTIVE = 1, ST_DONE = 2 };
 #ifndef GR_SHADE_MIN_BLOCKS_NS1
 #define GR_SHADE_MIN_BLOCKS_NS1 4
 #endif
+// the hero-wavelength and anisotropic instantiations
+#ifndef GR_SHADE_MIN_BLOCKS_EXT
+#define GR_SHADE_MIN_BLOCKS_EXT 4
+#endif
 
 __device__ __forceinline__ int meta_k(int z) { return z & 0xffff; }
 __device__ __forceinline__ int meta_seg(int z) { return (z >> 16) & 0xff; }
@@ -1013,7 +1017,8 @@ __device__ __forceinline__ float order0_prob(const TableRow& row, float3 t_mir, 
 // MODE 0: plain; 1: hero-wavelength MIS (HERO); 2: anisotropic footprints
 // (ANISO, K carried per slot).
 template <int NS, typename TT, int MODE>
-__global__ void __launch_bounds__(256, MODE != 0 ? 2 : (NS == 1 ? GR_SHADE_MIN_BLOCKS_NS1 : GR_SHADE_MIN_BLOCKS))
+__global__ void __launch_bounds__(256, MODE != 0 ? GR_SHADE_MIN_BLOCKS_EXT
+                                                 : (NS == 1 ? GR_SHADE_MIN_BLOCKS_NS1 : GR_SHADE_MIN_BLOCKS))
     k_shade(RenderParams p) {
   constexpr bool HERO = MODE == 1, ANISO = MODE == 2;
   extern __shared__ __align__(16) unsigned char smem[];
