@@ -3,7 +3,7 @@
 // Propagation of a generalized ray under the interactive simplification of the
 // paper (Sec. 7.2) is ray tracing, which needs a spatial subdivision of the
 // scene (Sec. 1 motivates locality by exactly this).  The paper does not
-// describe its structure; this build uses
+// describe its structure; the tree here is built by
 //   centroid bounds -> 30-bit Morton codes -> 64-bit keys (morton << 32 | id)
 //   -> bitonic sort -> agglomerative clustering along the Morton order
 //   (PLOC: Meister & Bittner, "Parallel Locally-Ordered Clustering for
