@@ -43,11 +43,11 @@ FLOP_PER_WNODE = 109
 KERNELS = ["k_regen", "k_trace", "k_shade", "k_shadow"]
 # DRAM traffic of the dominant kernel per unit (ray) from one ncu capture:
 # dram__bytes_read.sum + dram__bytes_write.sum of the second k_trace launch of
-# the 256x256 x 64 spp case (64.47 + 1.62 MB), divided by the rays it traced
+# the 256x256 x 64 spp case (64.48 + 1.65 MB), divided by the rays it traced
 # (the full pool: 2^20 slots, all live in the second iteration); traffic grows
 # with the rays a launch processes.  Valid only for the traversal sources
 # whose hash (source_hash) is recorded with it (else reported null).
-NCU_TRAFFIC_PER_RAY = {("k_trace", "dc70178eb9f341ac"): (64.472064e6 + 1.620736e6) / 1048576}
+NCU_TRAFFIC_PER_RAY = {("k_trace", "e3d10e75e5bd98aa"): (64.481792e6 + 1.645568e6) / 1048576}
 
 
 def source_hash():

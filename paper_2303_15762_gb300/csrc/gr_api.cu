@@ -143,6 +143,11 @@ gr_status gr_scene_create(const gr_scene_desc* desc, void* cuda_stream, gr_scene
           planar = std::fabs(dist) <= 1e-6 * ext;
         }
       E.planar = planar ? 1 : 0;
+      // the unit normal, once per scene (FP64, and rounded to FP32)
+      for (int a = 0; a < 3; ++a) {
+        E.nd[a] = n[a] / ln;
+        E.n[a] = (float)E.nd[a];
+      }
     }
     emit.push_back(E);
   }

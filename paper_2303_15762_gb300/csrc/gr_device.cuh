@@ -34,7 +34,9 @@ struct DevEmitter {
   int planar;    // 1 if every triangle lies in the first one's plane
   float lo[3];   // bounding box of the emitter's triangles
   float hi[3];
-  int pad[2];
+  float n[3];    // unit normal of the first triangle (front face), FP32
+  int pad;
+  double nd[3];  // the same normal in FP64 (for the measurement lobe's quadratic form)
 };
 
 struct DevScene {

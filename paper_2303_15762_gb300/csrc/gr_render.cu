@@ -637,10 +637,9 @@ __device__ float measure_emitter(const DevScene& S, int ei, float3 hit, float3 d
                                  float lambda, float u0, float u1) {
   const DevEmitter E = S.emitters[ei];
   const gr_material& M = S.mats[E.mat];
-  const float4 t0 = S.emitter_tris[3 * E.first], t1 = S.emitter_tris[3 * E.first + 1],
-               t2 = S.emitter_tris[3 * E.first + 2];
-  d3 ned = dnormalize(dcross(dsub(D3(xyz(t1)), D3(xyz(t0))), dsub(D3(xyz(t2)), D3(xyz(t0)))));
-  float3 ne = f3((float)ned.x, (float)ned.y, (float)ned.z);
+  const float4 t0 = S.emitter_tris[3 * E.first];
+  const d3 ned = d3{E.nd[0], E.nd[1], E.nd[2]};  // normal computed once per scene
+  const float3 ne = f3(E.n[0], E.n[1], E.n[2]);
   if (dot(d, ne) >= 0.0f) return 0.0f;
   float z0, z1;
   box_muller(u0, u1, z0, z1);
@@ -745,10 +744,9 @@ __device__ float measure_emitter_aniso(const DevScene& S, int ei, float3 hit, fl
                                        float k, float lambda, float u0, float u1) {
   const DevEmitter E = S.emitters[ei];
   const gr_material& M = S.mats[E.mat];
-  const float4 t0 = S.emitter_tris[3 * E.first], t1 = S.emitter_tris[3 * E.first + 1],
-               t2 = S.emitter_tris[3 * E.first + 2];
-  const d3 ned = dnormalize(dcross(dsub(D3(xyz(t1)), D3(xyz(t0))), dsub(D3(xyz(t2)), D3(xyz(t0)))));
-  const float3 ne = f3((float)ned.x, (float)ned.y, (float)ned.z);
+  const float4 t0 = S.emitter_tris[3 * E.first];
+  const d3 ned = d3{E.nd[0], E.nd[1], E.nd[2]};
+  const float3 ne = f3(E.n[0], E.n[1], E.n[2]);
   if (dot(d, ne) >= 0.0f) return 0.0f;
   float z0, z1;
   box_muller(u0, u1, z0, z1);
@@ -785,12 +783,11 @@ __device__ float measure_emitter_aniso(const DevScene& S, int ei, float3 hit, fl
   return M.Le * aniso_lobe_pref(c11, c12, c22) * expf(-q);
 }
 
+// An emitter's unit normal (front face), computed in FP64 when the scene is
+// created and stored rounded to FP32.
 __device__ __forceinline__ float3 emitter_normal(const DevScene& S, int ei) {
-  const DevEmitter E = S.emitters[ei];
-  const float4 t0 = S.emitter_tris[3 * E.first], t1 = S.emitter_tris[3 * E.first + 1],
-               t2 = S.emitter_tris[3 * E.first + 2];
-  d3 n = dnormalize(dcross(dsub(D3(xyz(t1)), D3(xyz(t0))), dsub(D3(xyz(t2)), D3(xyz(t0)))));
-  return f3((float)n.x, (float)n.y, (float)n.z);
+  const DevEmitter& E = S.emitters[ei];
+  return f3(E.n[0], E.n[1], E.n[2]);
 }
 
 // Density of the m >= 1 part of the rough lobe in tangential direction
