@@ -246,3 +246,29 @@ def test_far_field_shift_is_geometric(oracle):
         x, m, _ = oracle.aniso_emitter(K, xf, d, k, 0.0, -d, z0, z1)
         g = x / (zbar * k)
         assert np.linalg.norm(m - g) <= 1e-5 * np.linalg.norm(g)
+
+
+def test_footprint_point_covariance_is_the_spatial_marginal(oracle):
+    """The footprint point's covariance (Gauss-Hermite moments over the
+    standard normal pair) equals Re(A)^-1 / 2 with A = K^-1, K rotated into
+    the frame onb(d), computed here with numpy: a wrong Cholesky factor,
+    frame rotation or transposition fails it."""
+    d, xf = _frame([0.3, -0.4, -0.8])
+    k = 2 * np.pi / 0.55
+    K = np.array([[25.0 + 90.0j, -6.0 + 40.0j], [-6.0 + 40.0j, 9.0 + 120.0j]])
+    e1, e2 = oracle.onb(d)
+    u2 = np.cross(d, xf)
+    R = np.array([[e1 @ xf, e1 @ u2], [e2 @ xf, e2 @ u2]])
+    A = np.linalg.inv(R @ K @ R.T)
+    sigma = 0.5 * np.linalg.inv(A.real)
+    z, w = np.polynomial.hermite_e.hermegauss(12)
+    w = w / w.sum()
+    cov = np.zeros((2, 2))
+    mean = np.zeros(2)
+    for i in range(len(z)):
+        for j in range(len(z)):
+            x, _, _ = oracle.aniso_emitter(K, xf, d, k, 0.0, -d, z[i], z[j])
+            cov += w[i] * w[j] * np.outer(x, x)
+            mean += w[i] * w[j] * x
+    assert np.max(np.abs(mean)) < 1e-12 * np.sqrt(np.max(np.abs(sigma)))
+    assert np.max(np.abs(cov - sigma)) < 1e-10 * np.max(np.abs(sigma))
