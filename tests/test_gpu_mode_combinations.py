@@ -47,3 +47,29 @@ def test_russian_roulette_matches_oracle(gr, oracle, mode, ns):
     print(mode, "ns", ns, "RR depth 7 rel-L2 =", r)
     assert np.linalg.norm(ref) > 0
     assert r <= TOL
+
+
+@pytest.mark.parametrize("mode", ["hero", "aniso"])
+def test_render_multi_and_progressive(gr, mode):
+    """Continuous batching (views accumulating into separate frames in one
+    launch) gives each view's image bit for bit, and two sample windows of
+    equal, bin-aligned length give one render's image to Kahan rounding (the
+    hero class shares are the same in each window)."""
+    scene = _scene()
+    m = (gr.FLAG_HERO if mode == "hero" else gr.FLAG_ANISO) | gr.FLAG_NEE
+    views = [dict(sg.procedural_view(width=40, height=32, spp=16, n_bins=8, n_stokes=4, max_depth=4), view_index=0),
+             dict(sg.procedural_view(width=24, height=24, spp=32, n_bins=16, n_stokes=4, max_depth=3), view_index=1)]
+    S = [gr.Scene(scene)]
+    frames = [gr.Frame([v]) for v in views]
+    gr.render_multi(S, [dict(v, scene_index=0) for v in views], frames, [0, 0], seed=3, flags=m)
+    for i, v in enumerate(views):
+        single = gr.Frame([v])
+        gr.render(S, [dict(v, scene_index=0)], single, seed=3, flags=m)
+        assert np.array_equal(frames[i].readback(0), single.readback(0)), i
+    v = dict(views[0], scene_index=0)
+    one = gr.Frame([v])
+    gr.render(S, [v], one, seed=3, flags=m)
+    two = gr.Frame([v])
+    gr.render(S, [dict(v, spp=8)], two, seed=3, flags=m)
+    gr.render(S, [dict(v, spp=8, first_sample=8)], two, seed=3, flags=m)
+    assert rel_l2(two.readback(0), one.readback(0).astype(np.float64)) < 1e-6
