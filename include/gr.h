@@ -205,32 +205,69 @@ typedef struct {
   int64_t kernel_count[4];
 } gr_stats;
 
-/* Upload a scene and build its BVH on the device: 30-bit Morton order, then
- * agglomerative clustering along that order (PLOC, window +-8, least merged
- * surface area); topology and FP32 bounds are deterministic.  The binary tree
- * is also collapsed into a 4-wide BVH with 8-bit quantised, conservatively
- * rounded child boxes.  desc arrays are host memory
- * and are copied; the library owns the device copy until gr_scene_destroy.
+/* Upload a scene: the interaction operators of Sec. 6 (per-triangle
+ * materials: grating Eq. K_grating, rough surface Eq. K_surface_HS, smooth
+ * reflection and refraction Eq. K_reflection_refraction) and the sourcing
+ * distributions the measurement operator integrates (Eq. measurement_operator:
+ * distant sources and emissive triangle sets, Sec. 7.2).  The geometry is
+ * traced as rays (Sec. 7.2: footprints are small against geometric detail), so
+ * a BVH is built on the device: 30-bit Morton order, then agglomerative
+ * clustering along that order (PLOC, window +-8, least merged surface area);
+ * topology and FP32 bounds are deterministic.  The binary tree is also
+ * collapsed into a 4-wide BVH with 8-bit quantised, conservatively rounded
+ * child boxes.  desc arrays are host memory, read during the call only; the
+ * library owns the device copy until gr_scene_destroy.  The scene belongs to
+ * the device current at creation and may only be rendered there.
  * Errors: GR_E_INVALID (null/negative sizes, material index out of range,
  * unknown material or light type), GR_E_OOM, GR_E_CUDA. */
 gr_status gr_scene_create(const gr_scene_desc* desc, void* cuda_stream, gr_scene** out);
 gr_status gr_scene_destroy(gr_scene* scene);
 
-/* Frame = device accumulators for n_views views: for each view, float32 sum
- * and Kahan compensation per [bin][y][x][stokes], plus per-bin sample counts
- * (host side).  Library-owned device memory, zero-initialised on stream.
+/* Frame = the detector elements' accumulators for n_views views.  A view is
+ * a detector (Sec. 3.2, Eq. wdf_coherent_states: each pixel a set of coherent
+ * states), and its output is the intensity per detector element (Algorithm 1:
+ * the mean over the element's samples), resolved per spectral bin and Stokes
+ * component.  For each view the frame holds a float32 sum and a Kahan
+ * compensation per [bin][y][x][stokes], plus per-bin sample counts (host
+ * side).  gr_frame_create allocates them on the device (library-owned,
+ * zero-initialised on stream).  The frame belongs to the current device.
  * Errors: GR_E_INVALID, GR_E_OOM, GR_E_CUDA. */
 gr_status gr_frame_create(const gr_view_desc* views, int32_t n_views, void* cuda_stream, gr_frame** out);
+
+/* A frame over caller-owned accumulators (e.g. a torch tensor).
+ * accum_device: device memory of the current device holding 2 * T float32,
+ * T = the sum over views of width * height * n_bins * n_stokes: the per-view
+ * sums laid out view after view as [bin][y][x][stokes], then their Kahan
+ * compensations in the same order (the layout gr_render_static uses).  The
+ * buffer is borrowed until gr_frame_release; it is not cleared, renders add
+ * into it, and gr_readback's means assume it held zeros at wrap time (the
+ * frame's sample counts start at zero).  gr_frame_reset zeroes it.  The mean of
+ * an element is (sum - compensation) / count.  accum_device == NULL is
+ * gr_frame_create (library-owned accumulators).  Host or other-device pointers
+ * are rejected with GR_E_INVALID (the buffer's size cannot be checked: it
+ * must hold 2 * T floats).  Errors: GR_E_INVALID, GR_E_OOM, GR_E_CUDA. */
+gr_status gr_frame_wrap(const gr_view_desc* views, int32_t n_views, float* accum_device, void* cuda_stream,
+                        gr_frame** out);
+/* Zero the frame's accumulators (on stream) and its sample counts. */
 gr_status gr_frame_reset(gr_frame* frame, void* cuda_stream);
+/* Free the frame (library-owned accumulators included; a wrapped buffer stays
+ * the caller's).  Synchronises the device. */
 gr_status gr_frame_release(gr_frame* frame);
 
 /* Enqueue the samples [first_sample, first_sample + spp) of every view on the
  * stream, adding them into frame (which must have been created for views of
- * the same shapes).  scenes[view.scene_index] supplies each view's scene.
- * Accumulation is per pixel and bin in sample order (deterministic).
- * Errors: GR_E_INVALID (shape mismatch, bad scene index, bad options),
- * GR_E_OOM, GR_E_CUDA, GR_E_TIMEOUT (iteration bound exceeded; the frame's
- * accumulators are then incomplete). */
+ * the same shapes).  Each sample is one path of Algorithm 1: a generalized
+ * ray sourced from the pixel (Eq. MC_sourcing; Sec. 7.2: uniform position on
+ * the pixel, rho = 0, beta = f_beta * p_pix_um, one wavelength bin), traced
+ * through scenes[view.scene_index] with the footprint update of
+ * Eq. K_free_space_propagation, interacting by sampling one child ray per
+ * vertex (Eq. MC_light_transport_Q1) and measured against the sources
+ * (Eq. measurement_operator).  Accumulation is per pixel and bin in sample
+ * order (deterministic).  Scenes and frame must belong to the current device.
+ * Errors: GR_E_INVALID (shape mismatch, bad scene index, bad options, scene or
+ * frame of another device), GR_E_OOM, GR_E_CUDA, GR_E_TIMEOUT (iteration
+ * bound exceeded; the frame's accumulators are then incomplete: reset the
+ * frame before rendering into it again). */
 gr_status gr_render(gr_scene* const* scenes, int32_t n_scenes, const gr_view_desc* views, int32_t n_views,
                     const gr_render_opts* opts, gr_frame* frame, void* cuda_stream);
 
@@ -244,10 +281,12 @@ gr_status gr_render_multi(gr_scene* const* scenes, int32_t n_scenes, const gr_vi
                           const gr_render_opts* opts, gr_frame* const* frames, const int32_t* frame_view,
                           void* cuda_stream);
 
-/* Copy view `view`'s mean image, float32 [height][width][n_bins][n_stokes]
- * (sum / count per bin, 0 where a bin has no samples), to dst (device memory
- * if dst_is_device, else host memory; host copies complete before return).
- * dst_bytes must be at least the image size.  Errors: GR_E_INVALID, GR_E_CUDA. */
+/* Copy view `view`'s intensity per detector element (Algorithm 1: the sum of
+ * the element's sample contributions over their count), float32
+ * [height][width][n_bins][n_stokes] (sum / count per bin, 0 where a bin has no
+ * samples), to dst (device memory if dst_is_device, else host memory; host
+ * copies complete before return).  dst_bytes must be at least the image size.
+ * Errors: GR_E_INVALID, GR_E_CUDA. */
 gr_status gr_readback(gr_frame* frame, int32_t view, float* dst, size_t dst_bytes, int32_t dst_is_device,
                       void* cuda_stream);
 
@@ -341,13 +380,15 @@ gr_status gr_aperture_backward_2d(int32_t n_det, const double* x0, int32_t n_ap,
  *
  * Scratch limits: the views' descriptors and grating order tables, plus the
  * slot pool, must fit in GR_STATIC_SCRATCH_BYTES; opts.pool_size (0 = as many
- * slots as fit, about 260k) above that capacity is rejected with GR_E_INVALID
- * and a message naming the limit.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call reuses the same
- * array and resets what must start at zero; calls that overlap on the GPU
- * (other streams or threads) race on it and must be serialised by the caller.
- * Errors: as gr_render. */
+ * slots as fit, about 260k) above that capacity, or descriptors that leave
+ * fewer than 256 slots, are rejected with GR_E_INVALID and a message naming
+ * the limit.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress, which allocates nothing) with the calling thread's
+ * device current.  Every call reuses the same array and resets what must
+ * start at zero; calls that overlap on the GPU (other streams or threads) race
+ * on it and must be serialised by the caller.  Scenes must belong to the
+ * current device and accum must be device memory of it (GR_E_INVALID
+ * otherwise).  Errors: as gr_render. */
 #define GR_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
 gr_status gr_render_static(gr_scene* const* scenes, int32_t n_scenes, const gr_view_desc* views, int32_t n_views,
                            const gr_render_opts* opts, float* accum, void* cuda_stream);

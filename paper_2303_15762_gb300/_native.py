@@ -17,7 +17,7 @@ GR_OK, GR_E_INVALID, GR_E_OOM, GR_E_CUDA, GR_E_TIMEOUT, GR_E_BUSY = range(6)
 FLAG_NEE, FLAG_RR, FLAG_NO_RENORM, FLAG_WIDE_BVH, FLAG_HERO, FLAG_ANISO = 1, 2, 4, 8, 16, 32
 TABLE_DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
 
-EXPORTED = ["gr_scene_create", "gr_scene_destroy", "gr_frame_create", "gr_frame_reset", "gr_frame_release",
+EXPORTED = ["gr_scene_create", "gr_scene_destroy", "gr_frame_create", "gr_frame_wrap", "gr_frame_reset", "gr_frame_release",
             "gr_render", "gr_readback", "gr_frame_stats", "gr_scene_bvh", "gr_debug_rng", "gr_render_static", "gr_render_multi",
             "gr_last_error", "gr_abi_version", "gr_measure_fp32_peak", "gr_debug_order_table",
             "gr_debug_footprint", "gr_aperture_backward_2d"]
@@ -94,6 +94,7 @@ def lib_handle(require_gpu=True):
     L.gr_scene_create.argtypes = [P, P, P]
     L.gr_scene_destroy.argtypes = [P]
     L.gr_frame_create.argtypes = [P, I32, P, P]
+    L.gr_frame_wrap.argtypes = [P, I32, P, P, P]
     L.gr_frame_reset.argtypes = [P, P]
     L.gr_frame_release.argtypes = [P]
     L.gr_render.argtypes = [P, I32, P, I32, P, P, P]
@@ -216,15 +217,36 @@ class Scene:
             pass
 
 
-class Frame:
-    """Resident per-view accumulators (sum + Kahan compensation)."""
+def accum_floats(views):
+    """Floats of a frame's accumulators: 2 * sum of W * H * n_bins * n_stokes."""
+    return 2 * sum(int(v["width"]) * int(v["height"]) * int(v["n_bins"]) * int(v["n_stokes"]) for v in views)
 
-    def __init__(self, views, stream=None):
+
+class Frame:
+    """Resident per-view accumulators (sum + Kahan compensation).
+
+    accum: None for library-owned accumulators (gr_frame_create), or a
+    contiguous float32 CUDA tensor of accum_floats(views) elements that the
+    library adds into (gr_frame_wrap; sums view after view as [bin][y][x]
+    [stokes], then compensations).  The tensor is kept referenced while the
+    frame lives."""
+
+    def __init__(self, views, stream=None, accum=None):
         L = lib_handle()
         self.views = [dict(v) for v in views]
         self._h = ctypes.c_void_p()
         arr = pack_views(self.views)
-        _check(L.gr_frame_create(arr, len(self.views), stream or current_stream(), ctypes.byref(self._h)))
+        self.accum = accum
+        if accum is None:
+            _check(L.gr_frame_create(arr, len(self.views), stream or current_stream(), ctypes.byref(self._h)))
+        else:
+            import torch
+            if not (accum.is_cuda and accum.dtype == torch.float32 and accum.is_contiguous()
+                    and accum.numel() >= accum_floats(self.views)):
+                raise ValueError("accum must be a contiguous float32 CUDA tensor of at least %d elements"
+                                 % accum_floats(self.views))
+            _check(L.gr_frame_wrap(arr, len(self.views), ctypes.c_void_p(accum.data_ptr()),
+                                   stream or current_stream(), ctypes.byref(self._h)))
 
     @property
     def handle(self):

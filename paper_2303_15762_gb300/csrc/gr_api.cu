@@ -38,6 +38,94 @@ gr_status cuda_fail(cudaError_t e, const char* what) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Every scene of a render must live on the calling thread's current device
+// (its BVH and triangles are read by kernels launched there).
+gr_status check_scene_devices(const std::string& who, gr_scene* const* scenes, int n_scenes, int dev) {
+  for (int i = 0; i < n_scenes; ++i)
+    if (scenes[i]->device != dev)
+      return fail(GR_E_INVALID, who + ": scene " + std::to_string(i) + " was created on device " +
+                                    std::to_string(scenes[i]->device) + ", the current device is " +
+                                    std::to_string(dev));
+  return GR_OK;
+}
+
+// A caller-owned accumulator buffer must be device (or managed) memory that
+// the current device owns; a host pointer would fault in the kernels.
+gr_status check_device_buffer(const std::string& who, const void* p, int dev) {
+  cudaPointerAttributes a;
+  const cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GR_E_INVALID, who + ": accumulator pointer is not known to CUDA (" + cudaGetErrorString(e) + ")");
+  }
+  if (!((a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev))
+    return fail(GR_E_INVALID, who + ": accumulators must be device memory of the current device " +
+                                  std::to_string(dev));
+  return GR_OK;
+}
+
+int current_device() {
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess) return -1;
+  return d;
+}
+
+// Frame over caller-owned accumulators (acc != nullptr, not zeroed: the
+// caller's buffer is added into) or library-owned ones (zeroed on stream).
+gr_status frame_make(const char* who, const gr_view_desc* views, int32_t n_views, float* acc, cudaStream_t st,
+                     gr_frame** out) {
+  const std::string w(who);
+  if (!views || !out || n_views <= 0) return fail(GR_E_INVALID, w + ": bad arguments");
+  size_t total = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const gr_view_desc& d = views[v];
+    if (d.width <= 0 || d.height <= 0 || d.n_bins <= 0 || d.n_bins > 4096 || (d.n_stokes != 1 && d.n_stokes != 4))
+      return fail(GR_E_INVALID, w + ": bad view shape " + std::to_string(v));
+    if ((long long)d.width * d.height * d.n_bins >= (1LL << 31))
+      return fail(GR_E_INVALID, w + ": view too large " + std::to_string(v));
+    total += (size_t)d.width * d.height * d.n_bins * d.n_stokes;
+  }
+  const int dev = current_device();
+  if (dev < 0) return fail(GR_E_CUDA, w + ": no current CUDA device");
+  if (acc) {
+    const gr_status s = check_device_buffer(w, acc, dev);
+    if (s != GR_OK) return s;
+  }
+  gr_frame* F = new (std::nothrow) gr_frame();
+  if (!F) return fail(GR_E_OOM, w + ": host allocation");
+  F->device = dev;
+  F->n_views = n_views;
+  size_t off = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const gr_view_desc& d = views[v];
+    F->shapes.push_back(gr_view_shape{d.width, d.height, d.n_bins, d.n_stokes});
+    F->offsets.push_back(off);
+    off += (size_t)d.width * d.height * d.n_bins * d.n_stokes;
+    F->counts.emplace_back(d.n_bins, 0LL);
+  }
+  F->acc_floats = total;
+  F->owns_acc = acc == nullptr;
+  cudaError_t e = cudaSuccess;
+  if (acc) {
+    F->acc = acc;
+  } else {
+    e = cudaMallocAsync(&F->acc, sizeof(float) * total * 2, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(F->acc, 0, sizeof(float) * total * 2, st);
+  }
+  if (e == cudaSuccess) e = cudaMallocAsync(&F->ctr, sizeof(gr::Counters), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(F->ctr, 0, sizeof(gr::Counters), st);
+  if (e == cudaSuccess) e = cudaHostAlloc(&F->ctr_host, sizeof(gr::Counters) * 2, cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    if (F->acc && F->owns_acc) cudaFreeAsync(F->acc, st);
+    if (F->ctr) cudaFreeAsync(F->ctr, st);
+    delete F;
+    return cuda_fail(e, w.c_str());
+  }
+  std::memset(F->ctr_host, 0, sizeof(gr::Counters) * 2);
+  *out = F;
+  return GR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -262,43 +350,12 @@ gr_status gr_scene_bvh(gr_scene* scene, int32_t* n_out, uint64_t* keys, int32_t*
 }
 
 gr_status gr_frame_create(const gr_view_desc* views, int32_t n_views, void* cuda_stream, gr_frame** out) {
-  if (!views || !out || n_views <= 0) return fail(GR_E_INVALID, "gr_frame_create: bad arguments");
-  cudaStream_t st = (cudaStream_t)cuda_stream;
-  gr_frame* F = new (std::nothrow) gr_frame();
-  if (!F) return fail(GR_E_OOM, "gr_frame_create: host allocation");
-  cudaGetDevice(&F->device);
-  F->n_views = n_views;
-  size_t total = 0;
-  for (int v = 0; v < n_views; ++v) {
-    const gr_view_desc& d = views[v];
-    if (d.width <= 0 || d.height <= 0 || d.n_bins <= 0 || d.n_bins > 4096 || (d.n_stokes != 1 && d.n_stokes != 4)) {
-      delete F;
-      return fail(GR_E_INVALID, "gr_frame_create: bad view shape " + std::to_string(v));
-    }
-    if ((long long)d.width * d.height * d.n_bins >= (1LL << 31)) {
-      delete F;
-      return fail(GR_E_INVALID, "gr_frame_create: view too large " + std::to_string(v));
-    }
-    F->shapes.push_back(gr_view_shape{d.width, d.height, d.n_bins, d.n_stokes});
-    F->offsets.push_back(total);
-    total += (size_t)d.width * d.height * d.n_bins * d.n_stokes;
-    F->counts.emplace_back(d.n_bins, 0LL);
-  }
-  F->acc_floats = total;
-  cudaError_t e = cudaMallocAsync(&F->acc, sizeof(float) * total * 2, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(F->acc, 0, sizeof(float) * total * 2, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&F->ctr, sizeof(gr::Counters), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(F->ctr, 0, sizeof(gr::Counters), st);
-  if (e == cudaSuccess) e = cudaHostAlloc(&F->ctr_host, sizeof(gr::Counters) * 2, cudaHostAllocDefault);
-  if (e != cudaSuccess) {
-    if (F->acc) cudaFreeAsync(F->acc, st);
-    if (F->ctr) cudaFreeAsync(F->ctr, st);
-    delete F;
-    return cuda_fail(e, "gr_frame_create");
-  }
-  std::memset(F->ctr_host, 0, sizeof(gr::Counters) * 2);
-  *out = F;
-  return GR_OK;
+  return frame_make("gr_frame_create", views, n_views, nullptr, (cudaStream_t)cuda_stream, out);
+}
+
+gr_status gr_frame_wrap(const gr_view_desc* views, int32_t n_views, float* accum_device, void* cuda_stream,
+                        gr_frame** out) {
+  return frame_make("gr_frame_wrap", views, n_views, accum_device, (cudaStream_t)cuda_stream, out);
 }
 
 gr_status gr_frame_reset(gr_frame* f, void* cuda_stream) {
@@ -312,7 +369,7 @@ gr_status gr_frame_reset(gr_frame* f, void* cuda_stream) {
 gr_status gr_frame_release(gr_frame* f) {
   if (!f) return fail(GR_E_INVALID, "gr_frame_release: null frame");
   cudaDeviceSynchronize();
-  if (f->acc) cudaFree(f->acc);
+  if (f->acc && f->owns_acc) cudaFree(f->acc);
   if (f->scratch) cudaFree(f->scratch);
   if (f->ctr) cudaFree(f->ctr);
   if (f->ctr_host) cudaFreeHost(f->ctr_host);
@@ -381,6 +438,22 @@ gr_status check_render_args(const char* who, gr_scene* const* scenes, int32_t n_
   return GR_OK;
 }
 
+// Scenes and frames of one render must all belong to the current device.
+gr_status check_call_devices(const char* who, gr_scene* const* scenes, int32_t n_scenes, gr_frame* const* frames,
+                             int32_t n_frames) {
+  const std::string w(who);
+  const int dev = current_device();
+  if (dev < 0) return fail(GR_E_CUDA, w + ": no current CUDA device");
+  gr_status s = check_scene_devices(w, scenes, n_scenes, dev);
+  if (s != GR_OK) return s;
+  for (int i = 0; i < n_frames; ++i)
+    if (frames[i]->device != dev)
+      return fail(GR_E_INVALID, w + ": frame of view " + std::to_string(i) + " was created on device " +
+                                    std::to_string(frames[i]->device) + ", the current device is " +
+                                    std::to_string(dev));
+  return GR_OK;
+}
+
 void add_counts(gr_frame* fr, int fv, const gr_view_desc& d) {
   for (int b = 0; b < d.n_bins; ++b) {
     long long r = ((long long)b - d.first_sample) % d.n_bins;
@@ -399,6 +472,8 @@ gr_status gr_render(gr_scene* const* scenes, int32_t n_scenes, const gr_view_des
   std::vector<gr_frame*> frames(std::max(n_views, 1), frame);
   gr_status s = check_render_args("gr_render", scenes, n_scenes, views, n_views, opts, frames.data(), nullptr);
   if (s != GR_OK) return s;
+  s = check_call_devices("gr_render", scenes, n_scenes, frames.data(), n_views);
+  if (s != GR_OK) return s;
   std::vector<float*> as(n_views), ac(n_views);
   for (int v = 0; v < n_views; ++v) {
     as[v] = frame->acc + frame->offsets[v];
@@ -416,6 +491,8 @@ gr_status gr_render_multi(gr_scene* const* scenes, int32_t n_scenes, const gr_vi
                           void* cuda_stream) {
   if (!frame_view) return fail(GR_E_INVALID, "gr_render_multi: null frame_view");
   gr_status s = check_render_args("gr_render_multi", scenes, n_scenes, views, n_views, opts, frames, frame_view);
+  if (s != GR_OK) return s;
+  s = check_call_devices("gr_render_multi", scenes, n_scenes, frames, n_views);
   if (s != GR_OK) return s;
   std::vector<float*> as(n_views), ac(n_views);
   for (int v = 0; v < n_views; ++v) {
@@ -491,6 +568,8 @@ gr_status gr_render_static(gr_scene* const* scenes, int32_t n_scenes, const gr_v
     return fail(GR_E_INVALID, "gr_render_static: bad table dtype");
   if (opts->pool_size < 0 || opts->block < 0 || (opts->block && (opts->block % 32 || opts->block > 256)))
     return fail(GR_E_INVALID, "gr_render_static: bad pool size or block (block must be a multiple of 32, <= 256)");
+  if (opts->regen_threshold_pct < 0 || opts->regen_threshold_pct > 100)
+    return fail(GR_E_INVALID, "gr_render_static: regen_threshold_pct out of [0, 100]");
   const int ns = views[0].n_stokes;
   for (int v = 0; v < n_views; ++v) {
     const gr_view_desc& d = views[v];
@@ -509,8 +588,14 @@ gr_status gr_render_static(gr_scene* const* scenes, int32_t n_scenes, const gr_v
     if (!(d.vfov_deg > 0.0f && d.vfov_deg < 180.0f) && !d.ortho)
       return fail(GR_E_INVALID, "gr_render_static: bad field of view in view " + std::to_string(v));
   }
+  const int dev = current_device();
+  if (dev < 0) return fail(GR_E_CUDA, "gr_render_static: no current CUDA device");
+  gr_status s = check_scene_devices("gr_render_static", scenes, n_scenes, dev);
+  if (s != GR_OK) return s;
+  s = check_device_buffer("gr_render_static", accum, dev);
+  if (s != GR_OK) return s;
   std::string err;
-  gr_status s = gr::render_static_impl(scenes, n_scenes, views, n_views, *opts, accum, (cudaStream_t)cuda_stream, err);
+  s = gr::render_static_impl(scenes, n_scenes, views, n_views, *opts, accum, (cudaStream_t)cuda_stream, err);
   if (s != GR_OK) return fail(s, "gr_render_static: " + err);
   return GR_OK;
 }

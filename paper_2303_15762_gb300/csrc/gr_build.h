@@ -117,6 +117,7 @@ struct gr_frame {
   std::vector<gr_view_shape> shapes;
   std::vector<size_t> offsets;           // float offset of each view's sum plane
   float* acc = nullptr;                  // sums then compensations
+  bool owns_acc = true;                  // false: caller-owned device buffer (gr_frame_wrap)
   size_t acc_floats = 0;                 // floats per plane set (sum part)
   std::vector<std::vector<long long>> counts;  // [view][bin] samples accumulated
   // scratch kept between renders

@@ -2401,31 +2401,25 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
 // two host threads) race on it; calls must be ordered.
 static __device__ __align__(256) unsigned char g_static_scratch[GR_STATIC_SCRATCH_BYTES];
 
-namespace {
-constexpr int kMaxDevices = 64;
-void* g_static_addr[kMaxDevices] = {};  // device address of g_static_scratch, per device
-}  // namespace
-
 gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc* vd, int n_views,
                              const gr_render_opts& o, float* accum, cudaStream_t st, std::string& err) {
-  // --- per-device set-up: the host-side name of the array is not a device
-  // address; ask the runtime for it, with the calling thread's device current
+  // The host-side name of the array is not a device address: ask the runtime
+  // for it on every call, with the calling thread's device current (the
+  // lookup allocates nothing, and a module reloaded after cudaDeviceReset
+  // gets its new address).
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    err = "cannot determine the current device";
+  if (e != cudaSuccess) {
+    err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
     return GR_E_CUDA;
   }
-  if (!g_static_addr[dev]) {
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-    if (e != cudaSuccess || !ptr) {
-      err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-      return GR_E_CUDA;
-    }
-    g_static_addr[dev] = ptr;
+  void* sym = nullptr;
+  e = cudaGetSymbolAddress(&sym, g_static_scratch);
+  if (e != cudaSuccess || !sym) {
+    err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+    return GR_E_CUDA;
   }
-  unsigned char* base = (unsigned char*)g_static_addr[dev];
+  unsigned char* base = (unsigned char*)sym;
 
   const int NSv = vd[0].n_stokes;
   const size_t tsize = o.table_dtype == GR_TABLE_F32 ? 4 : 2;
@@ -2506,13 +2500,18 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   const size_t o_vals = take(tsize * (size_t)std::max(vals, 1));
   const size_t o_vals32 = o.table_dtype == GR_TABLE_F32 ? o_vals : take(sizeof(float) * (size_t)std::max(vals, 1));
   const size_t fixed = off;
+  // the slot pool's 6 arrays each start on a 256-byte boundary: up to 6 x 255
+  // bytes of padding, counted with the fixed part
   const size_t per_slot = sizeof(float4) * 14 + sizeof(float2) + sizeof(int4) + 2 * sizeof(int) + 1;
-  if (fixed + per_slot * 256 > (size_t)GR_STATIC_SCRATCH_BYTES) {
-    err = "views and order tables need " + std::to_string(fixed) + " bytes; the static scratch holds " +
-          std::to_string((size_t)GR_STATIC_SCRATCH_BYTES);
+  const size_t slack = 7 * 256;
+  const long long p_max = fixed + slack >= (size_t)GR_STATIC_SCRATCH_BYTES
+                              ? 0
+                              : (long long)(((size_t)GR_STATIC_SCRATCH_BYTES - fixed - slack) / per_slot) / 256 * 256;
+  if (p_max < 256) {
+    err = "views and order tables need " + std::to_string(fixed) + " bytes, which leaves fewer than 256 path slots "
+          "in the static scratch of " + std::to_string((size_t)GR_STATIC_SCRATCH_BYTES) + " bytes";
     return GR_E_INVALID;
   }
-  const long long p_max = (long long)(((size_t)GR_STATIC_SCRATCH_BYTES - fixed - 7 * 256) / per_slot) / 256 * 256;
   if (o.pool_size > p_max) {
     err = "pool_size " + std::to_string(o.pool_size) + " exceeds the static scratch capacity of " +
           std::to_string(p_max) + " slots";
