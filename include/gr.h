@@ -141,10 +141,14 @@ typedef struct {
 /* Render options (36 bytes).  flags: GR_FLAG_NEE next-event estimation toward emitters
  * with power-heuristic MIS; GR_FLAG_RR Russian roulette after 3 interactions;
  * GR_FLAG_NO_RENORM keeps raw grating order weights (no renormalisation over
- * propagating orders); GR_FLAG_WIDE_BVH traverses the 4-wide BVH with 8-bit
- * quantised child boxes instead of the default binary FP32 BVH (both give the
- * same closest hits; the wide tree halves node visits but needs more
- * registers per thread); GR_FLAG_HERO hero-wavelength spectral MIS (Sec. 7.2):
+ * propagating orders); the default tree is the binary BVH with its child
+ * boxes stored in FP16, rounded outward (32 bytes per node; used when every
+ * coordinate of every scene of the call is within +-16384); GR_FLAG_FP32_NODES
+ * walks the same tree with FP32 child boxes (64 bytes per node);
+ * GR_FLAG_WIDE_BVH traverses the 4-wide BVH with 8-bit quantised child boxes
+ * (all three give the same closest hits: a box that contains the FP32 box is
+ * entered whenever the FP32 box is; the wide tree halves node visits but needs
+ * more registers per thread); GR_FLAG_HERO hero-wavelength spectral MIS (Sec. 7.2):
  * with n_bins a multiple of 4, a path's bin is the hero of the class of bins
  * {c, c+Q, c+2Q, c+3Q} (Q = n_bins/4) and drives every sampling decision;
  * every connection to a light (escape, emitter hit, next-event estimate) is
@@ -165,7 +169,8 @@ typedef struct {
  * not available in gr_render_static).  table_dtype: storage of the grating order tables
  * (GR_TABLE_F32 / F16 / BF16); arithmetic is FP32 either way.  pool_size:
  * wavefront slots (0 = default); block: threads per block (0 = default). */
-enum { GR_FLAG_NEE = 1, GR_FLAG_RR = 2, GR_FLAG_NO_RENORM = 4, GR_FLAG_WIDE_BVH = 8, GR_FLAG_HERO = 16, GR_FLAG_ANISO = 32 };
+enum { GR_FLAG_NEE = 1, GR_FLAG_RR = 2, GR_FLAG_NO_RENORM = 4, GR_FLAG_WIDE_BVH = 8, GR_FLAG_HERO = 16, GR_FLAG_ANISO = 32,
+       GR_FLAG_FP32_NODES = 64 };
 enum { GR_TABLE_F32 = 0, GR_TABLE_F16 = 1, GR_TABLE_BF16 = 2 };
 typedef struct {
   uint32_t seed;

@@ -14,7 +14,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libgr.so")
 
 GR_OK, GR_E_INVALID, GR_E_OOM, GR_E_CUDA, GR_E_TIMEOUT, GR_E_BUSY = range(6)
-FLAG_NEE, FLAG_RR, FLAG_NO_RENORM, FLAG_WIDE_BVH, FLAG_HERO, FLAG_ANISO = 1, 2, 4, 8, 16, 32
+FLAG_NEE, FLAG_RR, FLAG_NO_RENORM, FLAG_WIDE_BVH, FLAG_HERO, FLAG_ANISO, FLAG_FP32_NODES = 1, 2, 4, 8, 16, 32, 64
 TABLE_DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
 
 EXPORTED = ["gr_scene_create", "gr_scene_destroy", "gr_frame_create", "gr_frame_wrap", "gr_frame_reset", "gr_frame_release",

@@ -257,6 +257,10 @@ gr_status gr_scene_create(const gr_scene_desc* desc, void* cuda_stream, gr_scene
   const size_t o_etri = take(sizeof(float4) * etris.size());
   const size_t o_keys = take(sizeof(unsigned long long) * (size_t)n);
   const size_t o_wide = take(sizeof(uint4) * 4 * (size_t)std::max(n - 1, 1));
+  // FP16 nodes only when every coordinate is within +-16384 (finite boxes)
+  bool half_ok = n >= 2;
+  for (size_t i = 0; half_ok && i < 9 * (size_t)n; ++i) half_ok = std::fabs(desc->verts[i]) <= 16384.0f;
+  const size_t o_half = take(half_ok ? sizeof(uint4) * 2 * (size_t)(n - 1) : 0);
   int n_wide = 0;
   cudaError_t e = cudaMallocAsync(&S->mem, off, st);
   if (e != cudaSuccess) {
@@ -285,6 +289,8 @@ gr_status gr_scene_create(const gr_scene_desc* desc, void* cuda_stream, gr_scene
       if (e != cudaSuccess) break;
       e = gr::build_wide((const float*)(b + o_nodes), (const float4*)(b + o_tri), n, (uint4*)(b + o_wide), &n_wide, st);
       if (e != cudaSuccess) break;
+      if (half_ok && (e = gr::build_half((const float*)(b + o_nodes), n, (uint4*)(b + o_half), st)) != cudaSuccess)
+        break;
     }
     // host arrays are pageable: make sure every copy has consumed them
     e = cudaStreamSynchronize(st);
@@ -306,6 +312,7 @@ gr_status gr_scene_create(const gr_scene_desc* desc, void* cuda_stream, gr_scene
   D.tri_mat = (const int*)(b + o_tmat);
   D.nodes = (const float4*)(b + o_nodes);
   D.wnodes = (const uint4*)(b + o_wide);
+  D.hnodes = half_ok ? (const uint4*)(b + o_half) : nullptr;
   D.n_wide = n_wide;
   D.pad_w = 0;
   D.mats = (const gr_material*)(b + o_mats);

@@ -14,6 +14,7 @@ namespace gr {
 cudaError_t build_lbvh(const float* verts, const int* tri_mat, int n, float4* tri, int* tmat, float* nodes,
                        unsigned long long* keys_out, cudaStream_t st);
 cudaError_t build_wide(const float* nodes, const float4* tri, int n, uint4* wn, int* n_wide, cudaStream_t st);
+cudaError_t build_half(const float* nodes, int n, uint4* hn, cudaStream_t st);
 
 // Wavefront slot pool: per-slot path state in structure-of-arrays form.
 struct Pool {

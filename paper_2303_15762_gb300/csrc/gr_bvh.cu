@@ -555,7 +555,43 @@ __global__ void k_collapse(const float* __restrict__ nodes, const float* __restr
   wn[4 * widx + 3] = d;
 }
 
+// 32-byte binary nodes: the two child boxes of node i in FP16, each lower
+// bound rounded toward -inf and each upper bound toward +inf (so the FP16 box
+// contains the FP32 one; values beyond the FP16 range become +-inf or the
+// largest finite value on the safe side), then the two child references.
+// Halves: [l.lo.x l.lo.y][l.lo.z l.hi.x][l.hi.y l.hi.z][r.lo.x r.lo.y]
+// [r.lo.z r.hi.x][r.hi.y r.hi.z], low half of each word first.
+__global__ void k_half_nodes(const float* __restrict__ nodes, int n, uint4* __restrict__ hn) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  const float* N = nodes + 16 * (size_t)i;
+  unsigned short h[12];
+  for (int c = 0; c < 2; ++c)
+    for (int a = 0; a < 3; ++a) {
+      h[6 * c + a] = __half_as_ushort(__float2half_rd(N[6 * c + a]));
+      h[6 * c + 3 + a] = __half_as_ushort(__float2half_ru(N[6 * c + 3 + a]));
+    }
+  uint4 q0, q1;
+  q0.x = (unsigned)h[0] | ((unsigned)h[1] << 16);
+  q0.y = (unsigned)h[2] | ((unsigned)h[3] << 16);
+  q0.z = (unsigned)h[4] | ((unsigned)h[5] << 16);
+  q0.w = (unsigned)h[6] | ((unsigned)h[7] << 16);
+  q1.x = (unsigned)h[8] | ((unsigned)h[9] << 16);
+  q1.y = (unsigned)h[10] | ((unsigned)h[11] << 16);
+  q1.z = (unsigned)__float_as_int(N[12]);
+  q1.w = (unsigned)__float_as_int(N[13]);
+  hn[2 * (size_t)i] = q0;
+  hn[2 * (size_t)i + 1] = q1;
+}
+
 }  // namespace
+
+// FP16 copy of the binary nodes (n >= 2 leaves): hn holds (n - 1) x 32 bytes.
+cudaError_t build_half(const float* nodes, int n, uint4* hn, cudaStream_t st) {
+  if (n < 2) return cudaSuccess;
+  k_half_nodes<<<(n - 1 + 255) / 256, 256, 0, st>>>(nodes, n, hn);
+  return cudaGetLastError();
+}
 
 // Collapse the binary LBVH (n >= 2 leaves) into 4-wide quantised nodes.  wn
 // must hold (n - 1) nodes (an upper bound); *n_wide receives the count.

@@ -21,6 +21,10 @@ constexpr float kGCont = 50.0f;
 // Largest grating order magnitude kept in the order tables.
 constexpr int kMaxOrder = 40;
 constexpr int kStackDepth = 64;
+// BVH layouts a traversal can walk: the binary tree with FP32 child boxes (64
+// bytes per node), the same tree with FP16 child boxes rounded outward (32
+// bytes per node, the default), or the 4-wide tree with 8-bit child boxes.
+enum Tree { kTreeF32 = 0, kTreeWide = 1, kTreeHalf = 2 };
 
 // Random-number uses at a path vertex (word 2 of the Philox counter is
 // (segment << 4) | call).
@@ -48,6 +52,8 @@ struct DevScene {
   const int* tri_mat;        // [n] material of leaf slot i
   const float4* nodes;       // [n-1][4] internal nodes (child boxes + child refs)
   const uint4* wnodes;       // [n_wide][4] 4-wide quantised nodes (root = 0)
+  const uint4* hnodes;       // [n-1][2] the binary nodes with FP16 child boxes rounded outward (32 bytes),
+                             // or null when the scene's coordinates exceed the FP16 range
   int n_wide;
   int pad_w;
   const gr_material* mats;   // [n_mats]
@@ -342,7 +348,16 @@ __device__ __forceinline__ bool bin_begin(int n_tris, const float4* __restrict__
   return false;
 }
 
-// One node visit; returns true when the traversal is complete.  Leaf
+// Two FP16 values packed in a 32-bit word (low half first), as floats.
+__device__ __forceinline__ float2 half2_bits_to_float2(unsigned w) {
+  __half2_raw r;
+  r.x = (unsigned short)(w & 0xffffu);
+  r.y = (unsigned short)(w >> 16);
+  return __half22float2(__half2(r));
+}
+
+// One node visit (HALF: the 32-byte FP16 node array, else the 64-byte FP32
+// one); returns true when the traversal is complete.  Leaf
 // children whose boxes the ray enters go to leaf(slot), which tests them at
 // once or queues them: the closest hit is the least (t, original id) over the
 // tested triangles whatever the order of the tests, and a test only ever
@@ -350,19 +365,36 @@ __device__ __forceinline__ bool bin_begin(int n_tris, const float4* __restrict__
 // bound trips, 1 if the stack would overflow (the traversal then drops the
 // farther child).  `stack` holds kStackDepth entries, kept outside BinTrav so
 // that the ray state stays in registers.
-template <class LeafFn>
-__device__ __forceinline__ bool bin_step(const float4* __restrict__ nodes, BinTrav& s, int* stack, int* visits,
+template <bool HALF, class LeafFn>
+__device__ __forceinline__ bool bin_step(const void* __restrict__ nodes, BinTrav& s, int* stack, int* visits,
                                          int* err, LeafFn&& leaf) {
   if (--s.guard < 0) {
     if (err) *err = 2;
     return true;
   }
   ++*visits;
-  const float4* N = nodes + 4 * s.node;
-  const float4 n0 = __ldg(N), n1 = __ldg(N + 1), n2 = __ldg(N + 2), n3 = __ldg(N + 3);
-  const int lref = __float_as_int(n3.x), rref = __float_as_int(n3.y);
-  const float tl = box_entry(s.r, f3(n0.x, n0.y, n0.z), f3(n0.w, n1.x, n1.y), s.t);
-  const float tr = box_entry(s.r, f3(n1.z, n1.w, n2.x), f3(n2.y, n2.z, n2.w), s.t);
+  float tl, tr;
+  int lref, rref;
+  if (HALF) {
+    // 32-byte node: halves [l.lo.x l.lo.y][l.lo.z l.hi.x][l.hi.y l.hi.z]
+    // [r.lo.x r.lo.y][r.lo.z r.hi.x][r.hi.y r.hi.z], then lref, rref; the
+    // boxes contain the FP32 ones, so a box the FP32 tree enters is entered
+    const uint4* N = (const uint4*)nodes + 2 * s.node;
+    const uint4 q0 = __ldg(N), q1 = __ldg(N + 1);
+    const float2 a = half2_bits_to_float2(q0.x), b = half2_bits_to_float2(q0.y), c = half2_bits_to_float2(q0.z);
+    const float2 d = half2_bits_to_float2(q0.w), e = half2_bits_to_float2(q1.x), f = half2_bits_to_float2(q1.y);
+    lref = (int)q1.z;
+    rref = (int)q1.w;
+    tl = box_entry(s.r, f3(a.x, a.y, b.x), f3(b.y, c.x, c.y), s.t);
+    tr = box_entry(s.r, f3(d.x, d.y, e.x), f3(e.y, f.x, f.y), s.t);
+  } else {
+    const float4* N = (const float4*)nodes + 4 * s.node;
+    const float4 n0 = __ldg(N), n1 = __ldg(N + 1), n2 = __ldg(N + 2), n3 = __ldg(N + 3);
+    lref = __float_as_int(n3.x);
+    rref = __float_as_int(n3.y);
+    tl = box_entry(s.r, f3(n0.x, n0.y, n0.z), f3(n0.w, n1.x, n1.y), s.t);
+    tr = box_entry(s.r, f3(n1.z, n1.w, n2.x), f3(n2.y, n2.z, n2.w), s.t);
+  }
   bool hl = tl >= 0.0f, hr = tr >= 0.0f;
   // leaves go to `leaf`; internal children are descended/pushed
   if (hl && lref < 0) {
@@ -400,6 +432,7 @@ __device__ __forceinline__ bool bin_step(const float4* __restrict__ nodes, BinTr
 // equal distances resolve to the lower original triangle id.  Stack-based
 // traversal of the binary BVH, nearer child first.  *err is set if the stack
 // would overflow (the traversal then stops early).
+template <bool HALF = false>
 __device__ __forceinline__ Hit closest_hit(const DevScene& S, float3 o, float3 d, int exclude, int* refined,
                                            int* visits, int* tests, int* err) {
   BinTrav s;
@@ -407,7 +440,8 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& S, float3 o, float3 d
   if (!bin_begin(S.n_tris, S.tri, s, o, d, exclude, refined, tests)) {
     const float4* tri = S.tri;
     auto test_now = [&](int leaf) { bin_leaf(tri, s, leaf, refined, tests); };
-    while (!bin_step(S.nodes, s, stack, visits, err, test_now)) {
+    const void* nodes = HALF ? (const void*)S.hnodes : (const void*)S.nodes;
+    while (!bin_step<HALF>(nodes, s, stack, visits, err, test_now)) {
     }
   }
   Hit h;

@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
 // enters); only the counts of visits and tests differ.
 //   entry(e) -> slot of queue entry e; ray(slot, o, d, exclude) gives the
 //   ray and returns its scene; done(slot, hit) consumes a finished ray.
-template <class Entry, class Ray, class Done>
+template <bool HALF, class Entry, class Ray, class Done>
 __device__ __forceinline__ void lane_trace(const RenderParams& p, int n, int* cursor, Entry&& entry, Ray&& ray,
                                            Done&& done, int& refined, int& visits, int& tests, int& err) {
   const int lane = threadIdx.x & 31;
@@ -453,7 +453,7 @@ __device__ __forceinline__ void lane_trace(const RenderParams& p, int n, int* cu
   s.t = 0.0f;
   s.slot = -1;
   int stack[kStackDepth];
-  const float4* nodes = nullptr;
+  const void* nodes = nullptr;
   const float4* tri = nullptr;
   int out = -1;
   bool live = false;     // the lane holds a ray
@@ -508,7 +508,7 @@ __device__ __forceinline__ void lane_trace(const RenderParams& p, int n, int* cu
         int x = -1;
         float3 o, d;
         const DevScene& S = ray(slot, o, d, x);
-        nodes = S.nodes;
+        nodes = HALF ? (const void*)S.hnodes : (const void*)S.nodes;
         tri = S.tri;
         out = slot;
         np = 0;
@@ -535,23 +535,25 @@ __device__ __forceinline__ void lane_trace(const RenderParams& p, int n, int* cu
       }
     }
     if (live && walking && np < 2) {
-      walking = !bin_step(nodes, s, stack, &visits, &err, queue_leaf);
+      walking = !bin_step<HALF>(nodes, s, stack, &visits, &err, queue_leaf);
       if (!walking && np == 0) finish();
     }
   }
 }
 
-// Trace-queue closest hits: the binary tree through lane_trace, the 4-wide
-// tree one ray per thread per pass.  The queue holds continuing segments from
-// the front of its array and camera rays from the back.
-template <bool WIDE>
-__global__ void __launch_bounds__(WIDE ? 256 : GR_TRACE_BLOCK, WIDE ? 3 : GR_TRACE_MIN_BLOCKS) k_trace(RenderParams p) {
+// Trace-queue closest hits: the binary tree (FP32 or FP16 child boxes)
+// through lane_trace, the 4-wide tree one ray per thread per pass.  The queue
+// holds continuing segments from the front of its array and camera rays from
+// the back.
+template <int TREE>
+__global__ void __launch_bounds__(TREE == kTreeWide ? 256 : GR_TRACE_BLOCK, TREE == kTreeWide ? 3 : GR_TRACE_MIN_BLOCKS)
+    k_trace(RenderParams p) {
   const Pool& P = p.pool;
   const int front = *(volatile int*)&p.ctr->tq_count;
   const int n = front + *(volatile int*)&p.ctr->tq_back;
   if (blockIdx.x == 0 && threadIdx.x == 0) p.ctr->segments += (unsigned long long)n;
   int err = 0, refined = 0, visits = 0, tests = 0;
-  if (WIDE) {
+  if (TREE == kTreeWide) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
       const int slot = tq_entry(p, i, front);
       const int4 m = P.meta[slot];
@@ -562,7 +564,7 @@ __global__ void __launch_bounds__(WIDE ? 256 : GR_TRACE_BLOCK, WIDE ? 3 : GR_TRA
       P.hit[slot] = make_float2(h.t, __int_as_float(h.slot));
     }
   } else {
-    lane_trace(
+    lane_trace<TREE == kTreeHalf>(
         p, n, &p.ctr->trace_next, [&](int e) { return tq_entry(p, e, front); },
         [&](int slot, float3& o, float3& d, int& exclude) -> const DevScene& {
           const int4 m = P.meta[slot];
@@ -1688,7 +1690,7 @@ __device__ __forceinline__ void shadow_finish_hero(const RenderParams& p, int sl
 // emitter direction, then shadow_finish, one ray per thread per pass (the
 // shadow queue is a third as long as the trace queue: too short for
 // lane_trace's refill schedule to pay for itself).
-template <int NS, bool WIDE, int MODE>
+template <int NS, int TREE, int MODE>
 __global__ void __launch_bounds__(256, GR_SHADOW_MIN_BLOCKS) k_shadow(RenderParams p) {
   const Pool& P = p.pool;
   const int n = *(volatile int*)&p.ctr->sq_count;
@@ -1698,8 +1700,8 @@ __global__ void __launch_bounds__(256, GR_SHADOW_MIN_BLOCKS) k_shadow(RenderPara
     const int4 m = P.meta[slot];
     const DevScene& S = p.scenes[p.views[m.x].scene_index];
     const float3 o = xyz(P.od0[slot]), d = xyz(P.shd[slot]);  // requested only if emitter_reachable
-    const Hit h = WIDE ? closest_hit_wide(S, o, d, m.w, &refined, &visits, &tests, &err)
-                       : closest_hit(S, o, d, m.w, &refined, &visits, &tests, &err);
+    const Hit h = TREE == kTreeWide ? closest_hit_wide(S, o, d, m.w, &refined, &visits, &tests, &err)
+                                    : closest_hit<TREE == kTreeHalf>(S, o, d, m.w, &refined, &visits, &tests, &err);
     if (MODE == 1)
       shadow_finish_hero<NS>(p, slot, h);
     else
@@ -1893,10 +1895,9 @@ int sm_count(int dev) {
 // Block size of the binary-tree trace kernel for a render's block size.
 int trace_block(int block) { return block < GR_TRACE_BLOCK ? block : GR_TRACE_BLOCK; }
 
-template <int NS, typename TT>
-cudaError_t launch_iteration(const RenderParams& p, int grid_regen, int grid_trace, int grid_shade, int grid_shadow,
-                             int block, size_t smem, cudaStream_t st, cudaEvent_t* ev) {
-  const bool wide = (p.flags & GR_FLAG_WIDE_BVH) != 0;
+template <int NS, typename TT, int TREE>
+cudaError_t launch_iteration_t(const RenderParams& p, int grid_regen, int grid_trace, int grid_shade, int grid_shadow,
+                               int block, size_t smem, cudaStream_t st, cudaEvent_t* ev) {
   const bool hero = (p.flags & GR_FLAG_HERO) != 0, aniso = (p.flags & GR_FLAG_ANISO) != 0;
   if (ev) cudaEventRecord(ev[0], st);
   if (hero)
@@ -1904,10 +1905,7 @@ cudaError_t launch_iteration(const RenderParams& p, int grid_regen, int grid_tra
   else
     k_regen<NS, false><<<grid_regen, block, 0, st>>>(p);
   if (ev) cudaEventRecord(ev[1], st);
-  if (wide)
-    k_trace<true><<<grid_trace, block, 0, st>>>(p);
-  else
-    k_trace<false><<<grid_trace, trace_block(block), 0, st>>>(p);
+  k_trace<TREE><<<grid_trace, TREE == kTreeWide ? block : trace_block(block), 0, st>>>(p);
   if (ev) cudaEventRecord(ev[2], st);
   if (hero)
     k_shade<NS, TT, 1><<<grid_shade, block, smem, st>>>(p);
@@ -1916,21 +1914,24 @@ cudaError_t launch_iteration(const RenderParams& p, int grid_regen, int grid_tra
   else
     k_shade<NS, TT, 0><<<grid_shade, block, smem, st>>>(p);
   if (ev) cudaEventRecord(ev[3], st);
-  const int mode = hero ? 1 : aniso ? 2 : 0;
-  if (wide && mode == 1)
-    k_shadow<NS, true, 1><<<grid_shadow, block, 0, st>>>(p);
-  else if (wide && mode == 2)
-    k_shadow<NS, true, 2><<<grid_shadow, block, 0, st>>>(p);
-  else if (wide)
-    k_shadow<NS, true, 0><<<grid_shadow, block, 0, st>>>(p);
-  else if (mode == 1)
-    k_shadow<NS, false, 1><<<grid_shadow, block, 0, st>>>(p);
-  else if (mode == 2)
-    k_shadow<NS, false, 2><<<grid_shadow, block, 0, st>>>(p);
+  if (hero)
+    k_shadow<NS, TREE, 1><<<grid_shadow, block, 0, st>>>(p);
+  else if (aniso)
+    k_shadow<NS, TREE, 2><<<grid_shadow, block, 0, st>>>(p);
   else
-    k_shadow<NS, false, 0><<<grid_shadow, block, 0, st>>>(p);
+    k_shadow<NS, TREE, 0><<<grid_shadow, block, 0, st>>>(p);
   if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError();
+}
+
+template <int NS, typename TT>
+cudaError_t launch_iteration(const RenderParams& p, int tree, int grid_regen, int grid_trace, int grid_shade,
+                             int grid_shadow, int block, size_t smem, cudaStream_t st, cudaEvent_t* ev) {
+  if (tree == kTreeWide)
+    return launch_iteration_t<NS, TT, kTreeWide>(p, grid_regen, grid_trace, grid_shade, grid_shadow, block, smem, st, ev);
+  if (tree == kTreeHalf)
+    return launch_iteration_t<NS, TT, kTreeHalf>(p, grid_regen, grid_trace, grid_shade, grid_shadow, block, smem, st, ev);
+  return launch_iteration_t<NS, TT, kTreeF32>(p, grid_regen, grid_trace, grid_shade, grid_shadow, block, smem, st, ev);
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -1952,12 +1953,32 @@ const void* shade_kernel(int ns, int dtype, int mode) {
   if (dtype == GR_TABLE_F16) return shade_kernel_t<4, __half>(mode);
   return shade_kernel_t<4, __nv_bfloat16>(mode);
 }
-const void* shadow_kernel(int ns, int mode) {
+template <int NS, int TREE>
+const void* shadow_kernel_t(int mode) {
+  return mode == 1 ? (const void*)k_shadow<NS, TREE, 1> : mode == 2 ? (const void*)k_shadow<NS, TREE, 2>
+                                                                    : (const void*)k_shadow<NS, TREE, 0>;
+}
+const void* shadow_kernel(int ns, int mode, int tree) {
   if (ns == 1)
-    return mode == 1 ? (const void*)k_shadow<1, false, 1> : mode == 2 ? (const void*)k_shadow<1, false, 2>
-                                                                      : (const void*)k_shadow<1, false, 0>;
-  return mode == 1 ? (const void*)k_shadow<4, false, 1> : mode == 2 ? (const void*)k_shadow<4, false, 2>
-                                                                    : (const void*)k_shadow<4, false, 0>;
+    return tree == kTreeWide ? shadow_kernel_t<1, kTreeWide>(mode)
+                             : tree == kTreeHalf ? shadow_kernel_t<1, kTreeHalf>(mode) : shadow_kernel_t<1, kTreeF32>(mode);
+  return tree == kTreeWide ? shadow_kernel_t<4, kTreeWide>(mode)
+                           : tree == kTreeHalf ? shadow_kernel_t<4, kTreeHalf>(mode) : shadow_kernel_t<4, kTreeF32>(mode);
+}
+const void* trace_kernel(int tree) {
+  return tree == kTreeWide ? (const void*)k_trace<kTreeWide>
+                           : tree == kTreeHalf ? (const void*)k_trace<kTreeHalf> : (const void*)k_trace<kTreeF32>;
+}
+// The tree a render walks: the 4-wide one on request, else the FP16 binary
+// nodes unless FP32 nodes are requested or a scene has no FP16 nodes (its
+// coordinates exceed the FP16 range; scenes of fewer than 2 triangles need no
+// nodes).
+int pick_tree(int flags, gr_scene* const* scenes, int n_scenes) {
+  if (flags & GR_FLAG_WIDE_BVH) return kTreeWide;
+  if (flags & GR_FLAG_FP32_NODES) return kTreeF32;
+  for (int i = 0; i < n_scenes; ++i)
+    if (scenes[i]->n_tris >= 2 && !scenes[i]->dev.hnodes) return kTreeF32;
+  return kTreeHalf;
 }
 const void* regen_kernel(int ns, bool hero) {
   if (ns == 1) return hero ? (const void*)k_regen<1, true> : (const void*)k_regen<1, false>;
@@ -2196,10 +2217,10 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   int g_regen, g_trace, g_shade, g_shadow;
   const void* shade_fn = shade_kernel(NSv, o.table_dtype, mode);
   g_regen = grid_for(regen_kernel(NSv, hero), 0);
-  g_shadow = grid_for(shadow_kernel(NSv, mode), 0);
-  const bool wide_bvh = (o.flags & GR_FLAG_WIDE_BVH) != 0;
-  const int tblk = wide_bvh ? block : trace_block(block);
-  g_trace = wide_bvh ? grid_for((const void*)k_trace<true>, 0) : grid_for((const void*)k_trace<false>, 0, tblk);
+  const int tree = pick_tree(o.flags, scenes, n_scenes);
+  g_shadow = grid_for(shadow_kernel(NSv, mode, tree), 0);
+  const int tblk = tree == kTreeWide ? block : trace_block(block);
+  g_trace = grid_for(trace_kernel(tree), 0, tblk);
   g_shade = grid_for(shade_fn, smem);
   // never more blocks than the pool needs
   const int gmax = (P + block - 1) / block;
@@ -2212,13 +2233,13 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   std::vector<cudaEvent_t> pev;
   auto launch_on = [&](cudaStream_t ls) -> cudaError_t {
     if (NSv == 1) {
-      if (o.table_dtype == GR_TABLE_F32) return launch_iteration<1, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
-      if (o.table_dtype == GR_TABLE_F16) return launch_iteration<1, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
-      return launch_iteration<1, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
+      if (o.table_dtype == GR_TABLE_F32) return launch_iteration<1, float>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
+      if (o.table_dtype == GR_TABLE_F16) return launch_iteration<1, __half>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
+      return launch_iteration<1, __nv_bfloat16>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
     }
-    if (o.table_dtype == GR_TABLE_F32) return launch_iteration<4, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
-    if (o.table_dtype == GR_TABLE_F16) return launch_iteration<4, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
-    return launch_iteration<4, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
+    if (o.table_dtype == GR_TABLE_F32) return launch_iteration<4, float>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
+    if (o.table_dtype == GR_TABLE_F16) return launch_iteration<4, __half>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
+    return launch_iteration<4, __nv_bfloat16>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, ls, nullptr);
   };
   auto launch = [&]() -> cudaError_t {
     cudaEvent_t* ev = nullptr;
@@ -2232,13 +2253,13 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
       ev = pev.data() + b;
     }
     if (NSv == 1) {
-      if (o.table_dtype == GR_TABLE_F32) return launch_iteration<1, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
-      if (o.table_dtype == GR_TABLE_F16) return launch_iteration<1, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
-      return launch_iteration<1, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
+      if (o.table_dtype == GR_TABLE_F32) return launch_iteration<1, float>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
+      if (o.table_dtype == GR_TABLE_F16) return launch_iteration<1, __half>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
+      return launch_iteration<1, __nv_bfloat16>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
     }
-    if (o.table_dtype == GR_TABLE_F32) return launch_iteration<4, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
-    if (o.table_dtype == GR_TABLE_F16) return launch_iteration<4, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
-    return launch_iteration<4, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
+    if (o.table_dtype == GR_TABLE_F32) return launch_iteration<4, float>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
+    if (o.table_dtype == GR_TABLE_F16) return launch_iteration<4, __half>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
+    return launch_iteration<4, __nv_bfloat16>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, st, ev);
   };
 
   // ---- iteration loop: batches of B iterations; the host watches the
@@ -2260,7 +2281,8 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   if (o.use_graph) {
     // ---- one graph launch: conditional while-node around one iteration
     std::vector<unsigned char> key(sizeof(RenderParams) + 8 * sizeof(long long));
-    long long shape[8] = {g_regen, g_trace, g_shade, g_shadow, block, (long long)smem, NSv * 16 + o.table_dtype, max_iter};
+    long long shape[8] = {g_regen, g_trace, g_shade, g_shadow, block, (long long)smem,
+                          (tree * 16 + NSv) * 16 + o.table_dtype, max_iter};
     std::memcpy(key.data(), &p, sizeof p);
     std::memcpy(key.data() + sizeof p, shape, sizeof shape);
     if (!f->graph_exec || f->graph_key != key) {
@@ -2611,14 +2633,12 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   const void* shade_fn = shade_kernel(NSv, o.table_dtype, 0);
   const int gmax = (int)((P + block - 1) / block);
   const int g_regen = std::min(gmax, grid_for(regen_kernel(NSv, false), 0));
-  const bool wide_bvh = (o.flags & GR_FLAG_WIDE_BVH) != 0;
-  const int tblk = wide_bvh ? block : trace_block(block);
-  const int g_trace =
-      std::min((int)((P + tblk - 1) / tblk), wide_bvh ? grid_for((const void*)k_trace<true>, 0)
-                                                       : grid_for((const void*)k_trace<false>, 0, tblk));
+  const int tree = pick_tree(o.flags, scenes, n_scenes);
+  const int tblk = tree == kTreeWide ? block : trace_block(block);
+  const int g_trace = std::min((int)((P + tblk - 1) / tblk), grid_for(trace_kernel(tree), 0, tblk));
   const int g_shade = std::min(gmax, grid_for(shade_fn, smem));
   const int g_shadow =
-      std::min(gmax, grid_for(shadow_kernel(NSv, 0), 0));
+      std::min(gmax, grid_for(shadow_kernel(NSv, 0, tree), 0));
   // --- iteration loop; the host reads the device counters into a stack copy
   // after every batch (no events, no pinned buffer)
   long long n_max = 1, d_max = 0;
@@ -2633,13 +2653,13 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   for (;;) {
     for (int i = 0; i < B; ++i) {
       if (NSv == 1) {
-        if (o.table_dtype == GR_TABLE_F32) e = launch_iteration<1, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
-        else if (o.table_dtype == GR_TABLE_F16) e = launch_iteration<1, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
-        else e = launch_iteration<1, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
+        if (o.table_dtype == GR_TABLE_F32) e = launch_iteration<1, float>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
+        else if (o.table_dtype == GR_TABLE_F16) e = launch_iteration<1, __half>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
+        else e = launch_iteration<1, __nv_bfloat16>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
       } else {
-        if (o.table_dtype == GR_TABLE_F32) e = launch_iteration<4, float>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
-        else if (o.table_dtype == GR_TABLE_F16) e = launch_iteration<4, __half>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
-        else e = launch_iteration<4, __nv_bfloat16>(p, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
+        if (o.table_dtype == GR_TABLE_F32) e = launch_iteration<4, float>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
+        else if (o.table_dtype == GR_TABLE_F16) e = launch_iteration<4, __half>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
+        else e = launch_iteration<4, __nv_bfloat16>(p, tree, g_regen, g_trace, g_shade, g_shadow, block, smem, st, nullptr);
       }
       if (e != cudaSuccess) {
         err = std::string("launch: ") + cudaGetErrorString(e);

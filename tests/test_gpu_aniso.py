@@ -9,6 +9,8 @@ import pytest
 
 from paper_2303_15762_gb300 import scenegen as sg
 
+from _parity import ELEM_TOL, assert_parity, elem_err
+
 pytestmark = pytest.mark.gpu
 TOL = 1e-3
 
@@ -50,6 +52,7 @@ def test_planar_grating_matches_oracle(gr, oracle):
     r = rel_l2(img, ref)
     print("aniso grating rel-L2 =", r)
     assert r <= TOL
+    assert elem_err(img, ref) <= ELEM_TOL
     assert rel_l2(gr.render_image(scene, v, seed=1), ref) > 1e-2  # the scalar model differs
 
 
@@ -66,6 +69,7 @@ def test_emitter_scene_matches_oracle(gr, oracle, ns, nee):
     print("aniso emitter scene ns=%d nee=%d rel-L2 = %.3g" % (ns, nee, r))
     assert np.linalg.norm(ref) > 1e-3
     assert r <= TOL
+    assert elem_err(img, ref) <= ELEM_TOL
 
 
 def test_procedural_stokes_nee_rr_matches_oracle(gr, oracle):
@@ -77,6 +81,7 @@ def test_procedural_stokes_nee_rr_matches_oracle(gr, oracle):
     r = rel_l2(img, ref)
     print("aniso procedural rel-L2 =", r)
     assert r <= TOL
+    assert elem_err(img, ref) <= ELEM_TOL
 
 
 @pytest.mark.parametrize("cauchy_b", [0.0, 0.0042])
@@ -90,6 +95,7 @@ def test_glass_slab_matches_oracle(gr, oracle, cauchy_b):
     r = rel_l2(img, ref)
     print("aniso glass b=%g rel-L2 = %.3g" % (cauchy_b, r))
     assert r <= TOL
+    assert elem_err(img, ref) <= ELEM_TOL
 
 
 def test_mirror_scene_equals_scalar_model(gr):

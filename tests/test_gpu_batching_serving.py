@@ -6,6 +6,8 @@ import pytest
 
 from paper_2303_15762_gb300 import scenegen as sg
 
+from _parity import ELEM_TOL, assert_parity, elem_err
+
 pytestmark = pytest.mark.gpu
 TOL = 1e-3
 
@@ -47,7 +49,7 @@ def test_batched_matches_oracle(gr, oracle):
     gr.render(S, views, f, seed=5, flags=gr.FLAG_NEE | gr.FLAG_RR, use_graph=True, table_dtype="f16")
     for i, v in enumerate(views):
         ref = oracle.Scene(scenes[v["scene_index"]]).render(v, 5, oracle.FLAG_NEE | oracle.FLAG_RR)
-        assert rel_l2(f.readback(i), ref) <= TOL, i
+        assert_parity(f.readback(i), ref, label=i)
 
 
 def test_render_multi_equals_render(gr):
@@ -101,4 +103,4 @@ def test_serving_mix_equals_alone_and_admission_by_memory(gr, oracle):
             gr.render([s], [dict(r.view, first_sample=k)], f, seed=1)
         assert np.array_equal(r.image, f.readback(0)), r.id
         ref = oracle.Scene(r.scene).render(dict(r.view, spp=r.frames), 1, 0)
-        assert rel_l2(r.image, ref) <= TOL, r.id
+        assert_parity(r.image, ref, label=r.id)

@@ -8,6 +8,8 @@ import pytest
 
 from paper_2303_15762_gb300 import scenegen as sg
 
+from _parity import ELEM_TOL, assert_parity, elem_err
+
 pytestmark = pytest.mark.gpu
 TOL = 1e-3
 
@@ -27,6 +29,7 @@ def test_slab_scene_matches_oracle(gr, oracle, n_stokes):
     print("dielectric slab, n_stokes", n_stokes, "rel-L2 =", r)
     assert np.linalg.norm(ref) > 0
     assert r <= TOL
+    assert elem_err(img, ref) <= ELEM_TOL
 
 
 def test_slab_white_furnace(gr):

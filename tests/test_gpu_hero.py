@@ -10,6 +10,8 @@ import pytest
 
 from paper_2303_15762_gb300 import scenegen as sg
 
+from _parity import ELEM_TOL, assert_parity, elem_err
+
 pytestmark = pytest.mark.gpu
 TOL = 1e-3
 
@@ -49,6 +51,7 @@ def test_rough_grating_matches_oracle(gr, oracle, ns, nee):
     r = rel_l2(img, ref)
     print("hero rough+grating ns=%d nee=%d rel-L2 = %.3g" % (ns, nee, r))
     assert r <= TOL
+    assert elem_err(img, ref) <= ELEM_TOL
     # the weights move contributions between the bins of a class: the image
     # differs from the plain estimator's
     plain = gr.render_image(scene, v, seed=3, flags=g_flags & ~gr.FLAG_HERO)
@@ -65,6 +68,7 @@ def test_procedural_stokes_nee_rr_matches_oracle(gr, oracle):
     r = rel_l2(img, ref)
     print("hero procedural rel-L2 =", r)
     assert r <= TOL
+    assert elem_err(img, ref) <= ELEM_TOL
 
 
 @pytest.mark.parametrize("cauchy_b", [0.0, 0.0042])
@@ -79,6 +83,7 @@ def test_glass_slab_matches_oracle(gr, oracle, cauchy_b):
     r = rel_l2(img, ref)
     print("hero glass b=%g rel-L2 = %.3g" % (cauchy_b, r))
     assert r <= TOL
+    assert elem_err(img, ref) <= ELEM_TOL
 
 
 def test_ragged_windows_match_oracle(gr, oracle):
@@ -96,6 +101,7 @@ def test_ragged_windows_match_oracle(gr, oracle):
         r = rel_l2(img, ref)
         print(c, "rel-L2 =", r)
         assert r <= TOL, c
+        assert elem_err(img, ref) <= ELEM_TOL, c
 
 
 def _emitter_scene():
@@ -132,6 +138,7 @@ def test_emitter_scene_matches_oracle(gr, oracle, ns, nee):
     print("hero emitters ns=%d nee=%d rel-L2 = %.3g" % (ns, nee, r))
     assert np.linalg.norm(ref) > 1e-3
     assert r <= TOL
+    assert elem_err(img, ref) <= ELEM_TOL
 
 
 def test_emitters_one_sample_per_class_is_plain(gr):

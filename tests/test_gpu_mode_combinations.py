@@ -8,6 +8,8 @@ import pytest
 
 from paper_2303_15762_gb300 import scenegen as sg
 
+from _parity import ELEM_TOL, assert_parity, elem_err
+
 pytestmark = pytest.mark.gpu
 TOL = 1e-3
 
@@ -47,6 +49,7 @@ def test_russian_roulette_matches_oracle(gr, oracle, mode, ns):
     print(mode, "ns", ns, "RR depth 7 rel-L2 =", r)
     assert np.linalg.norm(ref) > 0
     assert r <= TOL
+    assert elem_err(img, ref) <= ELEM_TOL
 
 
 @pytest.mark.parametrize("mode", ["hero", "aniso"])

@@ -6,6 +6,8 @@ import pytest
 
 from paper_2303_15762_gb300 import scenegen as sg
 
+from _parity import ELEM_TOL, assert_parity, elem_err
+
 pytestmark = pytest.mark.gpu
 TOL = 1e-3
 
@@ -24,6 +26,7 @@ def test_grating_workload_full_size(gr, oracle):
     r = rel_l2(img, ref)
     print("grating 64x64x16 @64spp rel-L2 =", r)
     assert r <= TOL
+    assert elem_err(img, ref) <= ELEM_TOL
 
 
 @pytest.mark.parametrize("dtype", ["f16", "bf16"])
@@ -39,6 +42,7 @@ def test_grating_workload_low_precision_tables(gr, oracle, dtype):
     r = rel_l2(img, ref)
     print(dtype, "rel-L2 =", r)
     assert r <= TOL
+    assert elem_err(img, ref) <= ELEM_TOL
     assert np.array_equal(img, gr.render_image(scene, view, seed=1, table_dtype="f32"))
     # the procedural scene's mix of gratings and rough conductors: the same
     # decisions, so the images agree to FP32 rounding (the kernels for each
@@ -64,6 +68,7 @@ def test_grating_stokes_conductor(gr, oracle):
     r = rel_l2(img, ref)
     print("stokes rel-L2 =", r)
     assert r <= TOL
+    assert elem_err(img, ref) <= ELEM_TOL
 
 
 def test_ragged_and_degenerate_shapes(gr, oracle):
@@ -85,7 +90,7 @@ def test_ragged_and_degenerate_shapes(gr, oracle):
             # values (~1e-118) underflow to 0 in FP32
             assert np.linalg.norm(img) < 1e-30
         else:
-            assert rel_l2(img, ref) <= TOL, c
+            assert_parity(img, ref, label=c)
 
 
 def test_zero_spp_and_empty_scene(gr, oracle):
@@ -97,7 +102,7 @@ def test_zero_spp_and_empty_scene(gr, oracle):
     v = sg.view(eye=(0, 0, 0), look_at=(0, 0, -1), vfov_deg=10, width=8, height=8, n_bins=2, spp=4, max_depth=2)
     img = gr.render_image(empty, v, seed=2)
     ref = oracle.Scene(empty).render(v, 2, 0)
-    assert rel_l2(img, ref) <= TOL
+    assert_parity(img, ref)
 
 
 def test_deterministic_and_progressive(gr):
@@ -150,13 +155,29 @@ def test_invalid_arguments_rejected(gr):
 
 
 def test_wide_quantised_bvh_equals_binary_bvh(gr, oracle):
-    """The 4-wide BVH with 8-bit quantised child boxes finds exactly the same
-    closest hits as the binary FP32 LBVH (images bit-identical), and both
+    """The 4-wide BVH with 8-bit quantised child boxes and the binary tree
+    with FP16 child boxes (the default) find exactly the same closest hits as
+    the binary tree with FP32 child boxes (images bit-identical), and all
     match the oracle."""
     scene = sg.procedural_scene(seed=13, n_objects=16, target_tris=24000, n_emitters=3)
     v = sg.procedural_view(width=96, height=72, spp=16, n_bins=8, n_stokes=4)
     wide = gr.render_image(scene, v, seed=6, flags=gr.FLAG_NEE | gr.FLAG_WIDE_BVH)
-    binary = gr.render_image(scene, v, seed=6, flags=gr.FLAG_NEE)
+    binary = gr.render_image(scene, v, seed=6, flags=gr.FLAG_NEE | gr.FLAG_FP32_NODES)
+    half = gr.render_image(scene, v, seed=6, flags=gr.FLAG_NEE)
     assert np.array_equal(wide, binary)
+    assert np.array_equal(half, binary)
     ref = oracle.Scene(scene).render(v, 6, oracle.FLAG_NEE)
-    assert rel_l2(wide, ref) <= TOL
+    assert_parity(wide, ref)
+
+
+def test_fp16_nodes_fall_back_beyond_their_range(gr):
+    """A scene with a coordinate beyond +-16384 has no FP16 nodes; it renders
+    with the FP32 ones, the same image as with FP32 nodes requested."""
+    scene = sg.grating_scene()
+    far = np.array([[[3.0e4, 0.0, -1.0], [3.0e4 + 1.0, 0.0, -1.0], [3.0e4, 1.0, -1.0]]], np.float32)
+    scene = dict(scene, verts=np.concatenate([scene["verts"], far]).astype(np.float32),
+                 tri_mat=np.concatenate([scene["tri_mat"], [0]]).astype(np.int32))
+    v = sg.grating_view(width=16, height=16, spp=16)
+    a = gr.render_image(scene, v, seed=3)
+    b = gr.render_image(scene, v, seed=3, flags=gr.FLAG_FP32_NODES)
+    assert np.array_equal(a, b)
