@@ -168,7 +168,12 @@ typedef struct {
  * mirror reflections renders as without the flag (not combined with GR_FLAG_HERO;
  * not available in gr_render_static).  table_dtype: storage of the grating order tables
  * (GR_TABLE_F32 / F16 / BF16); arithmetic is FP32 either way.  pool_size:
- * wavefront slots (0 = default); block: threads per block (0 = default). */
+ * wavefront slots, i.e. path samples in flight (0 = one slot per ticket -- a
+ * ticket is one pixel's samples of one wavelength bin, or of one class of 4
+ * bins with GR_FLAG_HERO -- capped at 2^25 slots and at a quarter of the
+ * device memory free at the call; a slot takes 257 bytes, plus 256 with
+ * GR_FLAG_HERO and 80 with GR_FLAG_ANISO; images do not depend on it);
+ * block: threads per block (0 = default). */
 enum { GR_FLAG_NEE = 1, GR_FLAG_RR = 2, GR_FLAG_NO_RENORM = 4, GR_FLAG_WIDE_BVH = 8, GR_FLAG_HERO = 16, GR_FLAG_ANISO = 32,
        GR_FLAG_FP32_NODES = 64 };
 enum { GR_TABLE_F32 = 0, GR_TABLE_F16 = 1, GR_TABLE_BF16 = 2 };

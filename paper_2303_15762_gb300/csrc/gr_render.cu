@@ -31,6 +31,11 @@ namespace gr {
 
 enum { ST_IDLE = 0, ST_ACTIVE = 1, ST_DONE = 2 };
 
+// Default slot pool bounds (slots; 257 bytes each without the hero and
+// anisotropic planes).
+constexpr long long kMaxDefaultPool = 1LL << 25;
+constexpr long long kMinDefaultPool = 1LL << 16;
+
 // Minimum resident 256-thread blocks per SM requested for the traversal
 // kernels (register budget 65536 / (256 x blocks)).
 // binary-tree trace kernel: 128-thread blocks, 7 per SM (<= 72 registers)
@@ -429,6 +434,10 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
 #ifndef GR_LEAF_BLOCKED
 #define GR_LEAF_BLOCKED 8
 #endif
+// node visits a lane makes between two looks at the warp's schedule
+#ifndef GR_TRACE_STEPS
+#define GR_TRACE_STEPS 6
+#endif
 // Closest hits for a queue of rays on the binary tree, one warp keeping its 32
 // lanes busy across rays.  Warps claim the queue in groups of 32 entries from
 // `cursor`; a lane whose ray has finished stays idle until GR_TRACE_REFILL
@@ -534,7 +543,8 @@ __device__ __forceinline__ void lane_trace(const RenderParams& p, int n, int* cu
         if (!walking) finish();
       }
     }
-    if (live && walking && np < 2) {
+#pragma unroll 1
+    for (int k = 0; k < GR_TRACE_STEPS && live && walking && np < 2; ++k) {
       walking = !bin_step<HALF>(nodes, s, stack, &visits, &err, queue_leaf);
       if (!walking && np == 0) finish();
     }
@@ -2074,8 +2084,24 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     plan.views.push_back(V);
   }
   // ---- scratch layout
-  int P = o.pool_size > 0 ? o.pool_size : 1 << 20;
-  if ((unsigned long long)P > plan.total_tickets) P = (int)std::max<unsigned long long>(plan.total_tickets, 1ull);
+  const bool hero = (o.flags & GR_FLAG_HERO) != 0, aniso = (o.flags & GR_FLAG_ANISO) != 0;
+  // Default pool: one slot per ticket (every ticket runs from the first
+  // iteration, so the render takes the fewest iterations and launch tails),
+  // capped at kMaxDefaultPool slots and at a quarter of the device memory
+  // free for this frame's scratch.  Images do not depend on the pool size.
+  long long P = o.pool_size;
+  if (P <= 0) {
+    const size_t per_slot = sizeof(float4) * 14 + sizeof(float2) + sizeof(int4) + 2 * sizeof(int) + 1 +
+                            (hero ? sizeof(float4) * 16 : 0) + (aniso ? sizeof(float4) * 5 : 0);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      free_b = 0;
+    }
+    const long long mem_cap = (long long)((free_b + f->scratch_bytes) / 4 / per_slot);
+    P = std::min<long long>(kMaxDefaultPool, std::max<long long>(mem_cap, kMinDefaultPool));
+  }
+  if ((unsigned long long)P > plan.total_tickets) P = (long long)std::max<unsigned long long>(plan.total_tickets, 1ull);
   P = (P + 255) / 256 * 256;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -2096,7 +2122,6 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const size_t o_tq = take(sizeof(int) * (size_t)P);
   const size_t o_sq = take(sizeof(int) * (size_t)P);
   const size_t o_st8 = take((size_t)P);
-  const bool hero = (o.flags & GR_FLAG_HERO) != 0, aniso = (o.flags & GR_FLAG_ANISO) != 0;
   const int mode = hero ? 1 : aniso ? 2 : 0;
   const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 16) : 0;  // hq, hqp, hfb, hfr, hpart/haccS/haccC[4]
   const size_t o_aniso = aniso ? take(sizeof(float4) * (size_t)P * 5) : 0;  // ak0, ak1, nk0, nk1, nkf
@@ -2160,7 +2185,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     p.pool.nk1 = a4 + (size_t)P * 3;
     p.pool.nkf = a4 + (size_t)P * 4;
   }
-  p.P = P;
+  p.P = (int)P;
   p.regen_thr = o.regen_threshold_pct;
   p.ctr = f->ctr;
   const size_t smem_table = sizeof(TableRow) * plan.rows.size() + tsize * plan.vals_count;
@@ -2223,9 +2248,9 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   g_trace = grid_for(trace_kernel(tree), 0, tblk);
   g_shade = grid_for(shade_fn, smem);
   // never more blocks than the pool needs
-  const int gmax = (P + block - 1) / block;
+  const int gmax = (int)((P + block - 1) / block);
   g_regen = std::min(g_regen, gmax);
-  g_trace = std::min(g_trace, (P + tblk - 1) / tblk);
+  g_trace = std::min(g_trace, (int)((P + tblk - 1) / tblk));
   g_shade = std::min(g_shade, gmax);
   g_shadow = std::min(g_shadow, gmax);
 
@@ -2637,8 +2662,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   const int tblk = tree == kTreeWide ? block : trace_block(block);
   const int g_trace = std::min((int)((P + tblk - 1) / tblk), grid_for(trace_kernel(tree), 0, tblk));
   const int g_shade = std::min(gmax, grid_for(shade_fn, smem));
-  const int g_shadow =
-      std::min(gmax, grid_for(shadow_kernel(NSv, 0, tree), 0));
+  const int g_shadow = std::min(gmax, grid_for(shadow_kernel(NSv, 0, tree), 0));
   // --- iteration loop; the host reads the device counters into a stack copy
   // after every batch (no events, no pinned buffer)
   long long n_max = 1, d_max = 0;
