@@ -10,8 +10,16 @@ interactions, next-event estimation with MIS.  One step renders all
 512*512*256 = 67.1M path samples.  Inputs are synthetic (seeded generator); the
 paper's own scenes are not available.
 
-Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-on a bounded crop of the same workload instead.
+Prints one JSON line (rank 0).  At N = 1 the line also carries, under
+`extras`, the other workloads' measurements, each run after the timed region
+and bounded to seconds (--no-extras skips them): the glass workload (f2) on a
+crop where the glass decides most pixel-bins, hero-wavelength MIS (f1) with its
+variance and efficiency, anisotropic footprints (f4), the batched form
+(config 4) against the plain per-view form with and without a graph, the
+progressive serving loop (config 5) with p50/p99 frame latency, the order-table
+precision form (configs 1 and 3) and the double slit at scale (f3), each
+against the FP64 oracle where it has an image.  `--impl reference` times the
+FP64 CPU oracle on a bounded crop of the same workload instead.
 """
 import argparse
 import hashlib
@@ -48,6 +56,11 @@ KERNELS = ["k_regen", "k_trace", "k_shade", "k_shadow"]
 # with the rays a launch processes.  Valid only for the traversal sources
 # whose hash (source_hash) is recorded with it (else reported null).
 NCU_TRAFFIC_PER_RAY = {("k_trace", "e3d10e75e5bd98aa"): (64.481792e6 + 1.645568e6) / 1048576}
+# the glass workload: a constant environment of this radiance lets paths
+# refracted through the glass reach a light, and the oracle crop (x0, y0,
+# side) is where the glass decides the most pixel-bins of the 512^2 view
+GLASS_ENV = 0.05
+GLASS_CROP = (0, 144, 96)
 
 
 def source_hash():
@@ -79,6 +92,9 @@ def parse():
     ap.add_argument("--pool", type=int, default=0)
     ap.add_argument("--wide", action="store_true", help="traverse the 4-wide quantised BVH")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' legs of the default run")
+    ap.add_argument("--extras", default="dielectric,hero,aniso,batched,serving,precision,doubleslit",
+                    help="legs of the default run (comma list)")
     ap.add_argument("--cpu-crop", type=int, default=128, help="side of the oracle's centre crop")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", choices=["procedural", "batched", "serving", "precision", "dielectric",
@@ -128,13 +144,14 @@ def workload(args, rank):
     from paper_2303_15762_gb300 import scenegen as sg
     scene = sg.procedural_scene(seed=2)
     if args.workload == "dielectric":
-        scene = sg.add_glass(scene)
+        scene = sg.add_glass(scene, env_radiance=GLASS_ENV)
     view = sg.procedural_view(width=args.size, height=args.size, spp=args.spp, view_index=rank)
     return scene, view
 
 
 def workload_name(args, scene):
-    glass = " with 8 dispersive glass slabs (n = 1.5 + 0.0042/lambda^2)" if args.workload == "dielectric" else ""
+    glass = (" with 8 dispersive glass slabs (n = 1.5 + 0.0042/lambda^2) and a constant environment of radiance %g"
+             % GLASS_ENV) if args.workload == "dielectric" else ""
     return ("procedural scene%s, %d tris, %dx%d, %d spp, 32 bins 400-700 nm, 4 Stokes, depth<=3, NEE+MIS"
             % (glass, len(scene["tri_mat"]), args.size, args.size, args.spp))
 
@@ -215,8 +232,23 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _timed(fn, flush, stream):
+    """Device time of fn() in ms (CUDA events on the render stream, L2 flushed first)."""
+    import torch
+    flush.zero_()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
 def run_batched(args):
-    """64 seeded views/scenes: plain per-view FP32 renders vs one autotuned
+    """64 seeded views/scenes: the plain per-view FP32 form (one gr_render per
+    view with the library's default pool, timed both with the host-driven
+    iteration loop and as one graph launch per view) against one autotuned
     render of all views as a single graph launch."""
     import numpy as np
     import torch
@@ -235,29 +267,21 @@ def run_batched(args):
     flags = gr.FLAG_NEE | gr.FLAG_RR
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-
-    def timed(fn):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        fn()
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1)
-
-    # plain form: one render per view, FP32 tables, host-driven iteration loop
+    steps, warmup = max(1, args.steps), max(1, args.warmup)
     plain_frames = [gr.Frame([dict(v, scene_index=0)]) for v in views]
 
-    def plain():
-        for i, v in enumerate(views):
-            plain_frames[i].reset()
-            gr.render([S[i]], [dict(v, scene_index=0)], plain_frames[i], seed=2, flags=flags, table_dtype="f32")
-    for _ in range(max(1, args.warmup)):
-        plain()
-    plain_ms = [timed(plain) for _ in range(args.steps)]
-    # batched form: autotuned (pool, block, threshold, table precision), one
-    # graph launch for all views
+    def plain(graph):
+        def run():
+            for i, v in enumerate(views):
+                plain_frames[i].reset()
+                gr.render([S[i]], [dict(v, scene_index=0)], plain_frames[i], seed=2, flags=flags, table_dtype="f32",
+                          use_graph=graph)
+        return run
+    res = {}
+    for name, graph in (("plain_host_loop", False), ("plain_graph", True)):
+        for _ in range(warmup):
+            plain(graph)()
+        res[name] = statistics.mean([_timed(plain(graph), flush, stream) for _ in range(steps)])
     best, trials = autotune.autotune(gr, S, views, dict(seed=2, flags=flags, table_dtype="f32", use_graph=True),
                                      probe_spp=max(1, views[0]["spp"] // 4))
     F = gr.Frame(views)
@@ -265,11 +289,10 @@ def run_batched(args):
     def batched():
         F.reset()
         gr.render(S, views, F, **best)
-    for _ in range(max(1, args.warmup)):
+    for _ in range(warmup):
         batched()
-    batched_ms = [timed(batched) for _ in range(args.steps)]
-    v_plain = samples / (statistics.mean(plain_ms) * 1e-3) / 1e6
-    v_batched = samples / (statistics.mean(batched_ms) * 1e-3) / 1e6
+    res["batched"] = statistics.mean([_timed(batched, flush, stream) for _ in range(steps)])
+    val = {k: samples / (ms * 1e-3) / 1e6 for k, ms in res.items()}
     # accuracy: batched vs the oracle on the four smallest views (full images;
     # an image whose oracle norm is below 1e-20 is dark -- FP32 cannot carry
     # the 1e-30-scale tails that remain there -- and is reported as null)
@@ -279,62 +302,76 @@ def run_batched(args):
         ref = orc.Scene(scenes[i]).render(views[i], 2, orc.FLAG_NEE | orc.FLAG_RR)
         nr = float(np.linalg.norm(ref))
         got = F.readback(i).astype(np.float64)
-        rels[i] = float(np.linalg.norm(got - ref) / nr) if nr >= 1e-20 else None
-    diff = max(float(np.max(np.abs(F.readback(i) - plain_frames[i].readback(0)))) for i in range(len(views)))
+        rels[i] = ({"rel_l2": float(np.linalg.norm(got - ref) / nr),
+                    "max_elem_err_over_max": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))}
+                   if nr >= 1e-20 else None)
+    identical = all(np.array_equal(F.readback(i), plain_frames[i].readback(0)) for i in range(len(views)))
     st = F.stats()
-    line = {"workload": "batched", "metric": METRIC, "unit": UNIT, "value": v_batched, "plain_fp32_value": v_plain,
-            "speedup_vs_plain": v_batched / v_plain, "ms_batched": statistics.mean(batched_ms),
-            "ms_plain": statistics.mean(plain_ms), "samples_per_step": samples, "n_views": len(views),
-            "tris": [len(s["tri_mat"]) for s in scenes], "sides": [v["width"] for v in views],
-            "depths": [v["max_depth"] for v in views], "bins": [v["n_bins"] for v in views],
+    for f in plain_frames:
+        f.close()
+    F.close()
+    for s_ in S:
+        s_.close()
+    tabs = {t[0]["table_dtype"] for t in trials}
+    return {"workload": "batched (config 4)", "metric": METRIC, "unit": UNIT, "value": val["batched"],
+            "plain_graph_value": val["plain_graph"], "plain_host_loop_value": val["plain_host_loop"],
+            "speedup_vs_plain_graph": val["batched"] / val["plain_graph"],
+            "speedup_vs_plain_host_loop": val["batched"] / val["plain_host_loop"],
+            "ms": res, "samples_per_step": samples, "n_views": len(views), "steps": steps, "warmup": warmup,
+            "plain_form": "one gr_render per view, FP32 tables, the library's default pool (one slot per ticket)",
+            "tris_range": [min(len(s["tri_mat"]) for s in scenes), max(len(s["tri_mat"]) for s in scenes)],
+            "side_range": [min(v["width"] for v in views), max(v["width"] for v in views)],
             "autotuned": {k: best[k] for k in ("pool_size", "block", "regen_threshold_pct", "table_dtype")},
+            "tables_tried": sorted(tabs),
             "autotune_trials": [[t[0]["pool_size"], t[0]["block"], t[0]["regen_threshold_pct"], t[0]["table_dtype"],
-                                 t[1]] for t in trials],
-            "rel_l2_full_views_vs_oracle": rels, "max_abs_diff_batched_vs_plain": diff,
+                                 round(t[1], 3)] for t in trials],
+            "oracle_four_smallest_views": rels, "batched_equals_per_view_bitwise": identical,
             "graph_launches_per_render": 1, "iterations": st["iterations"],
             "scene_gen_s": gen_s, "scene_build_s": build_s,
             "l2": "flushed before every timed step (256 MB write)"}
-    print(json.dumps(line))
 
 
-def run_serving(args):
+def run_serving(args, rates=None):
+    """Poisson-arriving progressive requests (config 5): p50/p99 inter-frame
+    and first-frame latency, throughput over wall time and over device-busy
+    time, at the headline arrival rate and optionally a sweep."""
     import numpy as np
-    import torch
     import paper_2303_15762_gb300 as gr
     from paper_2303_15762_gb300 import scenegen as sg
     from paper_2303_15762_gb300 import serving
     gr.load()
-    rng = np.random.default_rng(5)
 
-    def make():
+    def make(rng):
         return [serving.Request(k + 1, *sg.serving_request(rng, k + 1), args.frames) for k in range(args.requests)]
+    opts = dict(seed=1, flags=0, table_dtype="f32", use_graph=True)
     # warm-up pass (graph builds, allocator) on a few requests
-    srv = serving.ProgressiveServer(gr, render_opts=dict(seed=1, flags=0, table_dtype="f32", use_graph=True))
-    serving.run_poisson(gr, make()[:3], 1000.0, srv)
+    srv = serving.ProgressiveServer(gr, render_opts=opts)
+    serving.run_poisson(gr, make(np.random.default_rng(5))[:3], 1000.0, srv)
     srv.close()
-    # the headline rate, then the sweep (the same request stream at each rate)
-    rates = [args.rate] + [float(r) for r in args.rates.split(",") if r and float(r) != args.rate]
+    rates = [args.rate] if rates is None else rates
     runs = {}
     for rate in rates:
-        rng = np.random.default_rng(5)
-        srv = serving.ProgressiveServer(gr, render_opts=dict(seed=1, flags=0, table_dtype="f32", use_graph=True))
-        runs[rate] = serving.run_poisson(gr, make(), rate, srv, seed=6)
+        srv = serving.ProgressiveServer(gr, render_opts=opts)
+        runs[rate] = serving.run_poisson(gr, make(np.random.default_rng(5)), rate, srv, seed=6)
         srv.close()
-    res = dict(runs[args.rate])
-    keys = ("msamples_per_s", "p50_frame_ms", "p99_frame_ms", "p50_first_frame_ms", "p99_first_frame_ms",
-            "device_frames", "wall_s")
-    res.update({"workload": "serving", "metric": METRIC, "unit": UNIT, "value": res["msamples_per_s"],
-                "rate_req_per_s": args.rate, "frames_per_request": args.frames,
-                "resolutions": "256^2, 512^2, 1280x720, 1920x1080", "budget_bytes": srv.budget,
-                "rate_sweep": [dict(rate_req_per_s=r, **{k: runs[r][k] for k in keys}) for r in sorted(runs)]})
-    print(json.dumps(res))
+    res = dict(runs[rates[0]])
+    keys = ("msamples_per_s", "msamples_per_busy_s", "p50_frame_ms", "p99_frame_ms", "p50_first_frame_ms",
+            "p99_first_frame_ms", "p50_arrival_to_first_frame_ms", "p99_arrival_to_first_frame_ms", "device_frames",
+            "wall_s")
+    res.update({"workload": "serving (config 5)", "metric": METRIC, "unit": UNIT, "value": res["msamples_per_s"],
+                "value_basis": "samples over wall-clock time of the run (msamples_per_busy_s: over device-busy time)",
+                "rate_req_per_s": rates[0], "frames_per_request": args.frames, "requests_submitted": args.requests,
+                "resolutions": "256^2, 512^2, 1280x720, 1920x1080, 16 bins, 1 spp per frame"})
+    if len(rates) > 1:
+        res["rate_sweep"] = [dict(rate_req_per_s=r, **{k: runs[r][k] for k in keys}) for r in sorted(runs)]
+    return res
 
 
 def run_precision(args):
-    """Planar-grating workload with FP32 / FP16 / BF16 order tables: image
-    rel-L2 vs the FP64 oracle and vs the FP32-table image, and per-quantity
-    errors vs FP64 (stored order weights a_j; beta^2 and rho along
-    three-segment chains) through the library's inspection calls."""
+    """Planar-grating workload (config 1) with FP32 / FP16 / BF16 order tables
+    (config 3): image rel-L2 vs the FP64 oracle and vs the FP32-table image,
+    and per-quantity errors vs FP64 (stored order weights a_j; beta^2 and rho
+    along three-segment chains) through the library's inspection calls."""
     import math
     import numpy as np
     import torch
@@ -384,6 +421,7 @@ def run_precision(args):
             if (~nrm).any():
                 worst_abs = max(worst_abs, float(np.max(np.abs(got - a)[~nrm])))
         out[dt] = {"rel_l2_vs_oracle": float(np.linalg.norm(img - ref) / np.linalg.norm(ref)),
+                   "max_elem_err_over_max": float(np.max(np.abs(img - ref)) / np.max(np.abs(ref))),
                    "rel_l2_vs_f32_tables": float(np.linalg.norm(img - img32) / np.linalg.norm(img32)),
                    "max_rel_err_a_j_normal_range": worst_rel, "max_abs_err_a_j_below_normal": worst_abs,
                    "ms_per_render": statistics.mean(times),
@@ -399,7 +437,10 @@ def run_precision(args):
         st = gr.debug_footprint(np.stack([st[:, 0], st[:, 1], seg[:, k], kw], axis=1))
         rf = [orc.propagate(b, r, float(seg[i, k]) * 1e6 / float(kw[i])) for i, (b, r) in enumerate(rf)]
     rf = np.array(rf)
-    line = {"workload": "precision", "metric": METRIC, "unit": UNIT,
+    F.close()
+    S.close()
+    return {"workload": "precision (configs 1 and 3)", "metric": METRIC, "unit": UNIT,
+            "value": out["f32"]["msamples_per_s"],
             "config": "planar grating 64x64, 64 spp, 16 bins 400-700 nm, 1 interaction, S0",
             "tables": out,
             "cpu_baseline": {"value": samples / oracle_s / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -407,7 +448,6 @@ def run_precision(args):
             "footprint_fp32_vs_fp64_3_segments": {
                 "max_rel_err_beta2": float(np.max(np.abs(st[:, 0] - rf[:, 0]) / rf[:, 0])),
                 "max_rel_err_rho": float(np.max(np.abs(st[:, 1] - rf[:, 1]) / np.abs(rf[:, 1])))}}
-    print(json.dumps(line))
 
 
 def run_doubleslit(args):
@@ -443,8 +483,8 @@ def run_doubleslit(args):
     cpu_s = time.perf_counter() - t0
     cpu_rays = sum(th(x) for x in sub)
     err = float(np.max(np.abs(out[::1000] - ref)) / np.max(ref))
-    line = {"workload": "doubleslit", "metric": "generalized rays (element x direction) per second, each overlapped "
-            "with the aperture samples", "unit": "Mrays/s", "value": rays / (ms * 1e-3) / 1e6,
+    return {"workload": "doubleslit (f3)", "metric": "generalized rays (element x direction) per second, each "
+            "overlapped with the aperture samples", "unit": "Mrays/s", "value": rays / (ms * 1e-3) / 1e6,
             "ms_per_step": ms, "wall_ms_per_call": 1e3 * statistics.mean(walls), "steps": args.steps,
             "warmup": args.warmup, "config": {"elements": len(s["x0"]), "rays": rays, "aperture_samples": len(s["x_ap"]),
                                              "d": 400, "b": 40, "z": 1e4, "beta": s["beta"], "rho_cut": s["rho_cut"]},
@@ -452,15 +492,16 @@ def run_doubleslit(args):
             "max_err_vs_oracle_over_peak": err,
             "cpu_baseline": {"value": cpu_rays / cpu_s / 1e6, "unit": "Mrays/s", "cores": 1, "kind": "oracle",
                              "sample": "%d of the elements (%d rays), numpy FP64, %.1f s" % (len(sub), cpu_rays, cpu_s)}}
-    print(json.dumps(line))
 
 
-def time_modes(args, S, F, view, modes, clock_mode):
+def time_modes(args, S, F, view, modes, clock_mode, steps=None, warmup=None):
     """Device time per step (CUDA events, L2 flushed) and per-kernel time of
     each named flag set; nvidia-smi clocks are sampled during `clock_mode`.
     Returns ms, kernel ms per step, clocks and each mode's last image."""
     import torch
     import paper_2303_15762_gb300 as gr
+    steps = args.steps if steps is None else steps
+    warmup = max(3, args.warmup) if warmup is None else warmup
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
 
@@ -470,23 +511,16 @@ def time_modes(args, S, F, view, modes, clock_mode):
 
     ms, kernel_ms, clk, imgs = {}, {}, None, {}
     for name, flags in modes.items():
-        for _ in range(max(3, args.warmup)):
+        for _ in range(warmup):
             step(flags)
         torch.cuda.synchronize()
         clocks = ClockSampler(0) if name == clock_mode else None
         times, kms = [], [0.0] * 4
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step(flags, profile=True)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
+        for _ in range(steps):
+            times.append(_timed(lambda: step(flags, profile=True), flush, stream))
             st = F.stats()
             for k in range(4):
-                kms[k] += st["kernel_ms"][k] / args.steps
+                kms[k] += st["kernel_ms"][k] / steps
         if clocks is not None:
             clk = clocks.stop()
         ms[name] = statistics.mean(times)
@@ -495,7 +529,22 @@ def time_modes(args, S, F, view, modes, clock_mode):
     return ms, kernel_ms, clk, imgs
 
 
-def run_aniso(args):
+def _centre_crop(args, side):
+    c = min(side, args.size)
+    x0 = args.size // 2 - c // 2
+    return (x0, x0, x0 + c, x0 + c)
+
+
+def _crop_parity(img, ref, box):
+    import numpy as np
+    x0, y0, x1, y1 = box
+    got = img[y0:y1, x0:x1].astype(np.float64)
+    return {"rel_l2": float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)),
+            "max_elem_err_over_max": float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300)),
+            "crop": "x %d-%d, y %d-%d of the %dx%d view" % (x0, x1, y0, y1, img.shape[1], img.shape[0])}
+
+
+def run_aniso(args, steps=None, warmup=None, crop=128):
     """Anisotropic footprints (beta and rho as 2x2 matrices, Sec. 3.1) on the
     headline procedural workload: throughput with and without the flag,
     per-kernel device time, rel-L2 against the oracle's anisotropic model on
@@ -509,30 +558,30 @@ def run_aniso(args):
     S = gr.Scene(scene)
     F = gr.Frame([view])
     modes = {"scalar": gr.FLAG_NEE, "aniso": gr.FLAG_NEE | gr.FLAG_ANISO}
-    ms, kernel_ms, clk, imgs = time_modes(args, S, F, view, modes, "aniso")
+    ms, kernel_ms, clk, imgs = time_modes(args, S, F, view, modes, "aniso", steps, warmup)
     st = F.stats()
     a, b = imgs["aniso"].astype(np.float64), imgs["scalar"].astype(np.float64)
-    rel = None
+    par = None
     if not args.no_cpu_baseline:
         from oracle import oracle as orc
-        c = min(args.cpu_crop, args.size)
-        x0 = args.size // 2 - c // 2
-        ref = orc.Scene(scene).render(view, 2, orc.FLAG_NEE | orc.FLAG_ANISO, crop=(x0, x0, x0 + c, x0 + c))
-        rel = float(np.linalg.norm(a[x0:x0 + c, x0:x0 + c] - ref) / max(np.linalg.norm(ref), 1e-300))
-    line = {"workload": "aniso", "metric": METRIC, "unit": UNIT, "value": samples / (ms["aniso"] * 1e-3) / 1e6,
+        box = _centre_crop(args, crop)
+        ref = orc.Scene(scene).render(view, 2, orc.FLAG_NEE | orc.FLAG_ANISO, crop=box)
+        par = _crop_parity(imgs["aniso"], ref, box)
+    F.close()
+    S.close()
+    return {"workload": "aniso (f4)", "metric": METRIC, "unit": UNIT, "value": samples / (ms["aniso"] * 1e-3) / 1e6,
             "scalar_value": samples / (ms["scalar"] * 1e-3) / 1e6, "ms_aniso": ms["aniso"], "ms_scalar": ms["scalar"],
-            "kernel_ms_per_step": kernel_ms, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "kernel_ms_per_step": kernel_ms, "steps": steps or args.steps, "higher_is_better": True,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(args, scene) + ", anisotropic footprints",
                        "l2": "flushed before every timed step (256 MB write)"},
-            "rel_l2_vs_oracle_aniso": rel,
+            "vs_oracle_aniso": par,
             "rel_change_vs_scalar_model": float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)),
             "clocks": clk, "stats": {"iterations": st["iterations"], "segments": st["segments"],
                                      "shadow_rays": st["shadow_rays"]}}
-    print(json.dumps(line))
 
 
-def run_hero(args):
+def run_hero(args, steps=None, warmup=None, crop=128):
     """Hero-wavelength spectral MIS (Sec. 7.2) on the headline procedural
     workload: throughput with and without the flag, with per-kernel device
     time; rel-L2 of the hero image against the oracle's hero estimator on a
@@ -549,46 +598,105 @@ def run_hero(args):
     S = gr.Scene(scene)
     F = gr.Frame([view])
     modes = {"plain": gr.FLAG_NEE, "hero": gr.FLAG_NEE | gr.FLAG_HERO}
-    ms, kernel_ms, clk, _ = time_modes(args, S, F, view, modes, "hero")
-    img = F.readback(0)  # the last hero render
+    ms, kernel_ms, clk, imgs = time_modes(args, S, F, view, modes, "hero", steps, warmup)
     st = F.stats()
-    rel = None
+    par = None
     if not args.no_cpu_baseline:
         from oracle import oracle as orc
-        c = min(args.cpu_crop, args.size)
-        x0 = args.size // 2 - c // 2
-        ref = orc.Scene(scene).render(view, 2, orc.FLAG_NEE | orc.FLAG_HERO, crop=(x0, x0, x0 + c, x0 + c))
-        rel = float(np.linalg.norm(img[x0:x0 + c, x0:x0 + c].astype(np.float64) - ref) /
-                    max(np.linalg.norm(ref), 1e-300))
+        box = _centre_crop(args, crop)
+        ref = orc.Scene(scene).render(view, 2, orc.FLAG_NEE | orc.FLAG_HERO, crop=box)
+        par = _crop_parity(imgs["hero"], ref, box)
     # variance across seeds at equal samples (a smaller view of the same camera)
     vv = sg.procedural_view(width=128, height=128, spp=32)
     Fv = gr.Frame([vv])
     var = {}
     n_seeds = 8
     for name, flags in modes.items():
-        imgs = []
+        ims = []
         for sd in range(n_seeds):
             Fv.reset()
             gr.render([S], [vv], Fv, seed=100 + sd, flags=flags)
-            imgs.append(Fv.readback(0).astype(np.float64))
-        a = np.stack(imgs)
+            ims.append(Fv.readback(0).astype(np.float64))
+        a = np.stack(ims)
         v = np.var(a, axis=0, ddof=1)
         var[name] = {"total": float(v[..., 0].sum()), "mean_intensity": float(a[..., 0].mean())}
     vratio = var["plain"]["total"] / max(var["hero"]["total"], 1e-300)
-    line = {"workload": "hero", "metric": METRIC, "unit": UNIT, "value": samples / (ms["hero"] * 1e-3) / 1e6,
+    Fv.close()
+    F.close()
+    S.close()
+    return {"workload": "hero (f1)", "metric": METRIC, "unit": UNIT, "value": samples / (ms["hero"] * 1e-3) / 1e6,
             "plain_value": samples / (ms["plain"] * 1e-3) / 1e6, "ms_hero": ms["hero"], "ms_plain": ms["plain"],
-            "kernel_ms_per_step": kernel_ms, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "kernel_ms_per_step": kernel_ms, "steps": steps or args.steps, "higher_is_better": True,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(args, scene) + ", hero-wavelength MIS over classes of 4 bins",
                        "l2": "flushed before every timed step (256 MB write)"},
-            "rel_l2_vs_oracle_hero": rel,
+            "vs_oracle_hero": par,
             "variance_ratio_plain_over_hero": vratio,
             "efficiency_plain_over_hero": vratio * ms["plain"] / ms["hero"],
             "variance": {"view": "128x128, 32 spp, 32 bins, intensity (Stokes I), %d seeds per estimator" % n_seeds,
                          **var},
             "clocks": clk, "stats": {"iterations": st["iterations"], "segments": st["segments"],
                                      "shadow_rays": st["shadow_rays"]}}
-    print(json.dumps(line))
+
+
+def run_dielectric(args, steps=None, warmup=None):
+    """The glass workload (f2): throughput, and parity with the oracle on the
+    crop where the glass decides the most pixel-bins; the fraction of the
+    crop's pixel-bins whose oracle value depends on the glass (it differs from
+    the same render with the glass removed) says how much of the comparison
+    exercises refraction."""
+    import numpy as np
+    import paper_2303_15762_gb300 as gr
+    from paper_2303_15762_gb300 import scenegen as sg
+    gr.load()
+    a2 = argparse.Namespace(**dict(vars(args), workload="dielectric"))
+    scene, view = workload(a2, 0)
+    samples = view["width"] * view["height"] * view["spp"]
+    S = gr.Scene(scene)
+    F = gr.Frame([view])
+    ms, kernel_ms, clk, imgs = time_modes(a2, S, F, view, {"glass": gr.FLAG_NEE}, "glass", steps, warmup)
+    par = frac = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as orc
+        x0, y0, c = GLASS_CROP
+        box = (x0, y0, x0 + c, y0 + c)
+        cores = os.cpu_count() or 1
+        ref = orc.Scene(scene).render(view, 2, orc.FLAG_NEE, crop=box, n_threads=cores)
+        bare = orc.Scene(sg.env_only(sg.procedural_scene(seed=2), GLASS_ENV)).render(view, 2, orc.FLAG_NEE, crop=box,
+                                                                                     n_threads=cores)
+        par = _crop_parity(imgs["glass"], ref, box)
+        frac = float(np.any(ref != bare, axis=3).mean())
+    st = F.stats()
+    F.close()
+    S.close()
+    return {"workload": "dielectric (f2)", "metric": METRIC, "unit": UNIT, "value": samples / (ms["glass"] * 1e-3) / 1e6,
+            "ms_per_step": ms["glass"], "kernel_ms_per_step": kernel_ms["glass"], "steps": steps or args.steps,
+            "config": {"workload": workload_name(a2, scene), "l2": "flushed before every timed step (256 MB write)"},
+            "vs_oracle": par, "glass_fraction_of_crop_pixel_bins": frac,
+            "glass_fraction_note": "pixel-bins of the crop whose oracle value changes when the glass is removed",
+            "clocks": clk, "stats": {"iterations": st["iterations"], "segments": st["segments"]}}
+
+
+def run_extras(args):
+    """The other workloads' legs, after the headline's timed region: each
+    bounded (1 warm-up and 2 timed steps where it times a render) and isolated
+    (an error is reported in its place)."""
+    legs = {"dielectric": lambda: run_dielectric(args, steps=2, warmup=1),
+            "hero": lambda: run_hero(args, steps=2, warmup=1, crop=64),
+            "aniso": lambda: run_aniso(args, steps=2, warmup=1, crop=64),
+            "batched": lambda: run_batched(argparse.Namespace(**dict(vars(args), steps=1, warmup=1))),
+            "serving": lambda: run_serving(args),
+            "precision": lambda: run_precision(argparse.Namespace(**dict(vars(args), steps=3, warmup=2))),
+            "doubleslit": lambda: run_doubleslit(argparse.Namespace(**dict(vars(args), steps=3, warmup=1)))}
+    out = {}
+    for name in [x for x in args.extras.split(",") if x]:
+        t0 = time.perf_counter()
+        try:
+            out[name] = legs[name]()
+        except Exception as e:  # a failing leg must not lose the headline line
+            out[name] = {"error": repr(e)[:400]}
+        out[name]["leg_wall_s"] = round(time.perf_counter() - t0, 2)
+    return out
 
 
 def main():
@@ -596,23 +704,14 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.workload == "batched":
-        run_batched(args)
-        return
-    if args.workload == "serving":
-        run_serving(args)
-        return
-    if args.workload == "precision":
-        run_precision(args)
-        return
-    if args.workload == "doubleslit":
-        run_doubleslit(args)
-        return
-    if args.workload == "hero":
-        run_hero(args)
-        return
-    if args.workload == "aniso":
-        run_aniso(args)
+    legs = {"batched": lambda: run_batched(args),
+            "serving": lambda: run_serving(args, [args.rate] + [float(r) for r in args.rates.split(",")
+                                                              if r and float(r) != args.rate]),
+            "precision": lambda: run_precision(args), "doubleslit": lambda: run_doubleslit(args),
+            "hero": lambda: run_hero(args), "aniso": lambda: run_aniso(args),
+            "dielectric": lambda: run_dielectric(args)}
+    if args.workload in legs:
+        print(json.dumps(legs[args.workload]()))
         return
     world, rank, local = dist_setup()
     import numpy as np
@@ -671,6 +770,14 @@ def main():
     stats = F.stats()
     launches = stats["kernel_launches"] - launches0
     mean_ms = statistics.mean(step_ms)
+    # the same steps as one graph launch each (no per-kernel events), after the timed region
+    graph_ms = None
+    if world == 1:
+        def gstep():
+            F.reset()
+            gr.render([S], [view], F, seed=2, flags=flags, table_dtype=args.table, pool_size=args.pool, use_graph=True)
+        gstep()
+        graph_ms = statistics.mean([_timed(gstep, flush, stream) for _ in range(max(1, min(args.steps, 5)))])
     t_max = reduce_max(mean_ms, world)
     value = job_throughput(samples, t_max, world)
     img = F.readback(0)
@@ -763,7 +870,7 @@ def main():
 
     # ---- CPU oracle baseline on a centre crop, and the accuracy of this run there
     cpu = None
-    rel = None
+    rel = elem = None
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import oracle as orc
         c = min(args.cpu_crop, args.size)
@@ -778,6 +885,7 @@ def main():
                    c, c, view["spp"], c * c * view["spp"], dt)}
         crop = img[x0:x0 + c, x0:x0 + c].astype(np.float64)
         rel = float(np.linalg.norm(crop - ref) / max(np.linalg.norm(ref), 1e-300))
+        elem = float(np.max(np.abs(crop - ref)) / max(np.max(np.abs(ref)), 1e-300))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -786,14 +894,22 @@ def main():
                 "config": {"workload": workload_name(args, scene), "tables": args.table,
                            "parallelism": "replicas x%d" % world,
                            "l2": "flushed before every timed step (256 MB write)",
-                           "p50_frame_ms": float(np.percentile(step_ms, 50)),
-                           "p99_frame_ms": float(np.percentile(step_ms, 99))},
-                "rel_l2_vs_oracle": rel, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                           "pool": "library default (one slot per ticket)" if not args.pool else args.pool,
+                           "step_ms_p50": float(np.percentile(step_ms, 50)),
+                           "step_ms_p99": float(np.percentile(step_ms, 99))},
+                "rel_l2_vs_oracle": rel, "max_elem_err_over_max_vs_oracle": elem,
+                "oracle_crop": "%dx%d centre crop" % (min(args.cpu_crop, args.size), min(args.cpu_crop, args.size)),
+                "graph_value": samples / (graph_ms * 1e-3) / 1e6 if graph_ms else None,
+                "graph_value_note": "the same render as one CUDA graph launch per step (CUDA events, L2 flushed), "
+                                    "timed after the timed region",
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk,
                 "stats": {"iterations_per_step": stats["iterations"], "segments": stats["segments"],
                           "shadow_rays": stats["shadow_rays"], "refine64_hits": stats["refine64_hits"],
                           "refine64_lobes": stats["refine64_lobes"],
                           "node_visits_per_step": visits / args.steps, "tri_tests_per_step": tests / args.steps}}
+        if world == 1 and not args.no_extras:
+            line["extras"] = run_extras(args)
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -232,6 +232,9 @@ typedef struct {
  * unknown material or light type), GR_E_OOM, GR_E_CUDA. */
 gr_status gr_scene_create(const gr_scene_desc* desc, void* cuda_stream, gr_scene** out);
 gr_status gr_scene_destroy(gr_scene* scene);
+/* Device bytes the scene holds (triangles, BVH layouts, materials, lights,
+ * emitters); host-side bookkeeping, no CUDA call.  Errors: GR_E_INVALID. */
+gr_status gr_scene_bytes(const gr_scene* scene, size_t* bytes_out);
 
 /* Frame = the detector elements' accumulators for n_views views.  A view is
  * a detector (Sec. 3.2, Eq. wdf_coherent_states: each pixel a set of coherent
@@ -258,6 +261,11 @@ gr_status gr_frame_create(const gr_view_desc* views, int32_t n_views, void* cuda
  * must hold 2 * T floats).  Errors: GR_E_INVALID, GR_E_OOM, GR_E_CUDA. */
 gr_status gr_frame_wrap(const gr_view_desc* views, int32_t n_views, float* accum_device, void* cuda_stream,
                         gr_frame** out);
+/* Device bytes the frame holds now: its library-owned accumulators (none for
+ * a wrapped buffer), its counters and the wavefront scratch kept from its last
+ * render (a render grows it to gr_render_scratch_bytes when it is smaller).
+ * Host-side bookkeeping, no CUDA call.  Errors: GR_E_INVALID. */
+gr_status gr_frame_bytes(const gr_frame* frame, size_t* bytes_out);
 /* Zero the frame's accumulators (on stream) and its sample counts. */
 gr_status gr_frame_reset(gr_frame* frame, void* cuda_stream);
 /* Free the frame (library-owned accumulators included; a wrapped buffer stays
@@ -280,6 +288,14 @@ gr_status gr_frame_release(gr_frame* frame);
  * frame before rendering into it again). */
 gr_status gr_render(gr_scene* const* scenes, int32_t n_scenes, const gr_view_desc* views, int32_t n_views,
                     const gr_render_opts* opts, gr_frame* frame, void* cuda_stream);
+
+/* Device scratch bytes (slot pool, queues, view and order-table descriptors)
+ * that gr_render or gr_render_multi of these scenes, views and options would
+ * hold in the frame that serves the call; nothing is enqueued.  With
+ * opts.pool_size = 0 the default pool depends on the device memory free now
+ * (one cudaMemGetInfo).  Errors: as gr_render's argument checks. */
+gr_status gr_render_scratch_bytes(gr_scene* const* scenes, int32_t n_scenes, const gr_view_desc* views,
+                                  int32_t n_views, const gr_render_opts* opts, size_t* bytes_out);
 
 /* Continuous batching: one render over views whose accumulators live in
  * different frames (e.g. one resident frame per request of a progressive

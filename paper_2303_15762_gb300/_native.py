@@ -20,7 +20,8 @@ TABLE_DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
 EXPORTED = ["gr_scene_create", "gr_scene_destroy", "gr_frame_create", "gr_frame_wrap", "gr_frame_reset", "gr_frame_release",
             "gr_render", "gr_readback", "gr_frame_stats", "gr_scene_bvh", "gr_debug_rng", "gr_render_static", "gr_render_multi",
             "gr_last_error", "gr_abi_version", "gr_measure_fp32_peak", "gr_debug_order_table",
-            "gr_debug_footprint", "gr_aperture_backward_2d"]
+            "gr_debug_footprint", "gr_aperture_backward_2d", "gr_scene_bytes", "gr_frame_bytes",
+            "gr_render_scratch_bytes"]
 
 
 class GrError(RuntimeError):
@@ -105,6 +106,9 @@ def lib_handle(require_gpu=True):
     L.gr_debug_rng.argtypes = [U32, U32, U32, U32, I32, I32, I32, P, P]
     L.gr_render_static.argtypes = [P, I32, P, I32, P, P, P]
     L.gr_render_multi.argtypes = [P, I32, P, I32, P, P, P, P]
+    L.gr_scene_bytes.argtypes = [P, P]
+    L.gr_frame_bytes.argtypes = [P, P]
+    L.gr_render_scratch_bytes.argtypes = [P, I32, P, I32, P, P]
     L.gr_last_error.restype = ctypes.c_char_p
     L.gr_abi_version.restype = I32
     for name in EXPORTED:
@@ -195,6 +199,12 @@ class Scene:
     def handle(self):
         return self._h
 
+    def device_bytes(self):
+        """Device bytes the scene holds (gr_scene_bytes)."""
+        b = ctypes.c_size_t()
+        _check(_lib.gr_scene_bytes(self._h, ctypes.byref(b)))
+        return b.value
+
     def bvh(self):
         n = ctypes.c_int32()
         _check(_lib.gr_scene_bvh(self._h, ctypes.byref(n), None, None, None))
@@ -254,6 +264,12 @@ class Frame:
 
     def reset(self, stream=None):
         _check(_lib.gr_frame_reset(self._h, stream or current_stream()))
+
+    def device_bytes(self):
+        """Device bytes the frame holds now (gr_frame_bytes)."""
+        b = ctypes.c_size_t()
+        _check(_lib.gr_frame_bytes(self._h, ctypes.byref(b)))
+        return b.value
 
     def readback(self, view=0, out=None, stream=None):
         """Mean image float32 [H][W][n_bins][n_stokes]: a numpy array (host),
@@ -322,6 +338,18 @@ def render_multi(scenes, views, frames, frame_view, stream=None, **opts):
     fv = (ctypes.c_int32 * len(frame_view))(*[int(x) for x in frame_view])
     o = make_opts(**opts)
     _check(L.gr_render_multi(sc, len(scenes), arr, len(views), ctypes.byref(o), fr, fv, stream or current_stream()))
+
+
+def render_scratch_bytes(scenes, views, **opts):
+    """Device scratch bytes a render of these views would hold
+    (gr_render_scratch_bytes)."""
+    L = lib_handle()
+    sc = (ctypes.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    arr = pack_views(views)
+    o = make_opts(**opts)
+    b = ctypes.c_size_t()
+    _check(L.gr_render_scratch_bytes(sc, len(scenes), arr, len(views), ctypes.byref(o), ctypes.byref(b)))
+    return b.value
 
 
 def debug_rng(seed, view_index, pixel, sample, segment, call, n, stream=None):

@@ -14,7 +14,8 @@
 namespace gr {
 gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc* vd, int n_views,
                       const gr_render_opts& o, gr_frame* f, const std::vector<float*>& acc_sum,
-                      const std::vector<float*>& acc_comp, cudaStream_t st, std::string& err);
+                      const std::vector<float*>& acc_comp, cudaStream_t st, std::string& err,
+                      size_t* plan_bytes = nullptr);
 cudaError_t readback_impl(gr_frame* f, int v, float* dst_dev, const float* inv_count_dev, cudaStream_t st);
 cudaError_t debug_rng_impl(uint32_t seed, uint32_t view, uint32_t pixel, uint32_t sample, int seg, int call, int n,
                            uint32_t* host_out, cudaStream_t st);
@@ -321,7 +322,14 @@ gr_status gr_scene_create(const gr_scene_desc* desc, void* cuda_stream, gr_scene
   D.emitter_of_mat = (const int*)(b + o_eom);
   D.emitter_tris = (const float4*)(b + o_etri);
   S->keys = (unsigned long long*)(b + o_keys);
+  S->bytes = off;
   *out = S;
+  return GR_OK;
+}
+
+gr_status gr_scene_bytes(const gr_scene* scene, size_t* bytes_out) {
+  if (!scene || !bytes_out) return fail(GR_E_INVALID, "gr_scene_bytes: null argument");
+  *bytes_out = scene->bytes;
   return GR_OK;
 }
 
@@ -363,6 +371,12 @@ gr_status gr_frame_create(const gr_view_desc* views, int32_t n_views, void* cuda
 gr_status gr_frame_wrap(const gr_view_desc* views, int32_t n_views, float* accum_device, void* cuda_stream,
                         gr_frame** out) {
   return frame_make("gr_frame_wrap", views, n_views, accum_device, (cudaStream_t)cuda_stream, out);
+}
+
+gr_status gr_frame_bytes(const gr_frame* f, size_t* bytes_out) {
+  if (!f || !bytes_out) return fail(GR_E_INVALID, "gr_frame_bytes: null argument");
+  *bytes_out = (f->owns_acc ? sizeof(float) * f->acc_floats * 2 : 0) + sizeof(gr::Counters) + f->scratch_bytes;
+  return GR_OK;
 }
 
 gr_status gr_frame_reset(gr_frame* f, void* cuda_stream) {
@@ -511,6 +525,33 @@ gr_status gr_render_multi(gr_scene* const* scenes, int32_t n_scenes, const gr_vi
   s = gr::render_impl(scenes, n_scenes, views, n_views, *opts, frames[0], as, ac, (cudaStream_t)cuda_stream, err);
   if (s != GR_OK) return fail(s, "gr_render_multi: " + err);
   for (int v = 0; v < n_views; ++v) add_counts(frames[v], frame_view[v], views[v]);
+  return GR_OK;
+}
+
+gr_status gr_render_scratch_bytes(gr_scene* const* scenes, int32_t n_scenes, const gr_view_desc* views,
+                                  int32_t n_views, const gr_render_opts* opts, size_t* bytes_out) {
+  if (!bytes_out || !views || n_views <= 0) return fail(GR_E_INVALID, "gr_render_scratch_bytes: null or empty argument");
+  // the views' shapes are checked as a frame over them would check them
+  std::vector<gr_view_shape> shapes;
+  gr_frame probe;
+  for (int v = 0; v < n_views; ++v) {
+    const gr_view_desc& d = views[v];
+    if (d.width <= 0 || d.height <= 0 || d.n_bins <= 0 || d.n_bins > 4096 || (d.n_stokes != 1 && d.n_stokes != 4))
+      return fail(GR_E_INVALID, "gr_render_scratch_bytes: bad view shape " + std::to_string(v));
+    probe.shapes.push_back(gr_view_shape{d.width, d.height, d.n_bins, d.n_stokes});
+    probe.offsets.push_back(0);
+  }
+  probe.n_views = n_views;
+  std::vector<gr_frame*> frames(n_views, &probe);
+  gr_status s = check_render_args("gr_render_scratch_bytes", scenes, n_scenes, views, n_views, opts, frames.data(),
+                                  nullptr);
+  if (s != GR_OK) return s;
+  std::vector<float*> none;
+  std::string err;
+  size_t bytes = 0;
+  s = gr::render_impl(scenes, n_scenes, views, n_views, *opts, nullptr, none, none, nullptr, err, &bytes);
+  if (s != GR_OK) return fail(s, "gr_render_scratch_bytes: " + err);
+  *bytes_out = bytes;
   return GR_OK;
 }
 

@@ -107,6 +107,7 @@ struct gr_scene {
   int n_tris = 0;
   std::vector<gr_material> mats;  // host copy (order tables)
   int device = 0;
+  size_t bytes = 0;               // size of `mem`
 };
 
 struct gr_view_shape {

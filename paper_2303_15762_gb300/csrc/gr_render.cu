@@ -2009,9 +2009,12 @@ struct RenderPlan {
 // Called by gr_render after argument validation.
 // acc_sum[v] / acc_comp[v]: view v's accumulator planes; f supplies the
 // scratch, counters and graph cache of the call.
+// With plan_bytes != nullptr nothing is enqueued: the scratch size the render
+// would hold is written there (f may then be null; acc_sum/acc_comp unused).
 gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc* vd_in, int n_views,
                       const gr_render_opts& o, gr_frame* f, const std::vector<float*>& acc_sum,
-                      const std::vector<float*>& acc_comp, cudaStream_t st, std::string& err) {
+                      const std::vector<float*>& acc_comp, cudaStream_t st, std::string& err,
+                      size_t* plan_bytes) {
   // Tickets are numbered over the views in order of decreasing path depth, so
   // that the paths still running once every ticket is claimed (the render's
   // tail) belong to the shallowest views.  Results do not depend on the
@@ -2052,8 +2055,8 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     V.nbu = std::min(d.spp, V.Q);
     V.n_tickets = (long long)V.nbu * d.width * d.height;
     plan.total_tickets += (unsigned long long)V.n_tickets;
-    V.acc_sum = acc_sum[order[v]];
-    V.acc_comp = acc_comp[order[v]];
+    V.acc_sum = plan_bytes ? nullptr : acc_sum[order[v]];
+    V.acc_comp = plan_bytes ? nullptr : acc_comp[order[v]];
     // grating order table rows for every (material, bin) of this view
     const gr_scene* sc = scenes[d.scene_index];
     V.table_base = (int)plan.rows.size();
@@ -2098,7 +2101,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
       cudaGetLastError();
       free_b = 0;
     }
-    const long long mem_cap = (long long)((free_b + f->scratch_bytes) / 4 / per_slot);
+    const long long mem_cap = (long long)((free_b + (f ? f->scratch_bytes : 0)) / 4 / per_slot);
     P = std::min<long long>(kMaxDefaultPool, std::max<long long>(mem_cap, kMinDefaultPool));
   }
   if ((unsigned long long)P > plan.total_tickets) P = (long long)std::max<unsigned long long>(plan.total_tickets, 1ull);
@@ -2126,6 +2129,10 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 16) : 0;  // hq, hqp, hfb, hfr, hpart/haccS/haccC[4]
   const size_t o_aniso = aniso ? take(sizeof(float4) * (size_t)P * 5) : 0;  // ak0, ak1, nk0, nk1, nkf
   const size_t total = off;
+  if (plan_bytes) {
+    *plan_bytes = total;
+    return GR_OK;
+  }
   if (f->scratch_bytes < total) {
     if (f->scratch) cudaFreeAsync(f->scratch, st);
     f->scratch = nullptr;

@@ -284,10 +284,12 @@ def dielectric_scene(n_re=1.5, cauchy_b_um2=0.0042, slab_half=(0.15, 0.1, 0.01),
                   np.asarray(lights, dtype=np.float32).reshape(-1, 8))
 
 
-def add_glass(scene, n_glass=8, seed=12, n_re=1.5, cauchy_b_um2=0.0042, extent_m=2.0):
+def add_glass(scene, n_glass=8, seed=12, n_re=1.5, cauchy_b_um2=0.0042, extent_m=2.0, env_radiance=0.0):
     """The scene with n_glass closed glass slabs (dielectric, outward faces,
     random size, height and rotation about the vertical) added among its
-    objects; the original triangles, materials and lights are unchanged."""
+    objects; the original triangles, materials and lights are unchanged, and
+    with env_radiance > 0 a constant environment of that radiance is added to
+    the lights (so that paths refracted through the glass reach a light)."""
     rng = np.random.default_rng(seed)
     mats = np.concatenate([scene["mats"], material(MAT_DIELECTRIC, n_re=n_re, cauchy_b_um2=cauchy_b_um2)[None]])
     gm = len(mats) - 1
@@ -298,7 +300,19 @@ def add_glass(scene, n_glass=8, seed=12, n_re=1.5, cauchy_b_um2=0.0042, extent_m
         boxes.append(_box(c, half, rng.uniform(0, 180)))
     verts = np.concatenate([scene["verts"], np.concatenate(boxes).astype(np.float32)])
     tri_mat = np.concatenate([scene["tri_mat"], np.full(12 * n_glass, gm, dtype=np.int32)])
-    return _scene(verts, tri_mat, mats, scene["lights"])
+    lights = np.asarray(scene["lights"], np.float32).reshape(-1, 8)
+    if env_radiance > 0.0:
+        lights = np.concatenate([lights, light(LIGHT_ENV, (0, 0, 1), env_radiance, 0.0)[None]])
+    return _scene(verts, tri_mat, mats, lights)
+
+
+def env_only(scene, env_radiance):
+    """The scene's geometry and materials with a constant environment of the
+    given radiance added to its lights (the glass workload's reference without
+    glass)."""
+    lights = np.asarray(scene["lights"], np.float32).reshape(-1, 8)
+    lights = np.concatenate([lights, light(LIGHT_ENV, (0, 0, 1), env_radiance, 0.0)[None]])
+    return _scene(scene["verts"], scene["tri_mat"], scene["mats"], lights)
 
 
 def dielectric_view(width=48, height=40, spp=32, n_bins=8, n_stokes=4, max_depth=8, first_sample=0):
