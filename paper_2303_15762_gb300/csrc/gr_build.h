@@ -43,6 +43,10 @@ struct Pool {
   float4* hpart; // [4] the current sample's contributions to member g (g != hero)
   float4* haccS; // [4] ticket sums of member g (Kahan)
   float4* haccC; // [4] ticket compensations of member g
+  float4* hd0;   // a rough vertex's class lobe-density inputs, deferred to k_density: g_j
+  float4* hd1;   // (|k_j| l)^2
+  float4* hd2;   // squared offset of the sampled direction, the wanted members (bits) | hero member << 4
+  int* dq;       // the density queue (slots whose ratios k_density completes)
   // anisotropic footprints only (null otherwise): K = Kr + i Ki in the ray's
   // frame (xf), as (Kr11, Kr12, Kr22, Ki11), (Ki12, Ki22, -, -); the same for
   // a next-event request in the frame nkf of its direction
@@ -62,6 +66,7 @@ struct Counters {
   int err;
   int trace_next;  // next unclaimed trace-queue entry (claimed in groups of 32)
   int tq_back;     // trace-queue entries filled from the end of the array (camera rays)
+  int dq_count;    // hero-wavelength MIS: rough vertices queued for k_density
   unsigned long long samples, segments, shadow, ref_hit, ref_lobe, iters, node_visits, tri_tests;
 };
 

@@ -291,6 +291,7 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
   const int stride = gridDim.x * blockDim.x;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     p.ctr->sq_count = 0;
+    p.ctr->dq_count = 0;
     p.ctr->iters += 1;
   }
   int finished = 0;
@@ -1048,6 +1049,7 @@ __global__ void __launch_bounds__(256, MODE != 0 ? GR_SHADE_MIN_BLOCKS_EXT
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int i = base + threadIdx.x;
     bool want_shadow = false;
+    bool want_density = false;  // hero: the class lobe densities are deferred to k_density
     int slot = -1;
     if (i < n) {
       slot = tq_entry(p, i, front);
@@ -1454,24 +1456,28 @@ __global__ void __launch_bounds__(256, MODE != 0 ? GR_SHADE_MIN_BLOCKS_EXT
                 // specular e^-g, or the m >= 1 density at the sampled offset
                 // (the cosine factor is common to all wavelengths)
                 // (g and (k l)^2 scale with k^2 across the class)
-                float gq[4], klq[4], dens[4];
-                bool want[4];
+                float gq[4], klq[4];
+                unsigned want = 0u;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                   const float r = j == gh ? 1.0f : lambda * __frcp_rn(step_lambda(V, cstep, cls + j * Qv));
                   const float sc = r * r;  // (k_j / k)^2
                   gq[j] = g_r * sc;
                   klq[j] = mis_rec.z * sc;
-                  want[j] = mreal != 0.0f && (j == gh || hq[j] != 0.0f);
+                  if (mreal != 0.0f && (j == gh || hq[j] != 0.0f)) want |= 1u << j;
                 }
-                if (mreal != 0.0f) rough_density_class(gq, klq, want, mis_rec.x, dens);
+                if (mreal == 0.0f) {
 #pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                  if (g == gh || hq[g] == 0.0f) continue;
-                  if (mreal == 0.0f)
-                    hq[g] *= gq[g] > kGCont ? 0.0f : expf(g_r - gq[g]);
-                  else
-                    hq[g] = dens[gh] > 0.0f ? hq[g] * (dens[g] / dens[gh]) : 0.0f;
+                  for (int g = 0; g < 4; ++g)
+                    if (g != gh && hq[g] != 0.0f) hq[g] *= gq[g] > kGCont ? 0.0f : expf(g_r - gq[g]);
+                } else {
+                  // the m >= 1 series over the four wavelengths runs in
+                  // k_density on a compacted queue of such vertices (here
+                  // only a fraction of a warp's lanes would run it)
+                  P.hd0[slot] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+                  P.hd1[slot] = make_float4(klq[0], klq[1], klq[2], klq[3]);
+                  P.hd2[slot] = make_float4(mis_rec.x, __int_as_float((int)(want | ((unsigned)gh << 4))), 0.0f, 0.0f);
+                  want_density = true;
                 }
               }
             }
@@ -1545,6 +1551,37 @@ __global__ void __launch_bounds__(256, MODE != 0 ? GR_SHADE_MIN_BLOCKS_EXT
     }
     const int q = block_reserve<int>(&p.ctr->sq_count, want_shadow);
     if (want_shadow) P.sq[q] = slot;
+    if (HERO) {
+      const int qd = block_reserve<int>(&p.ctr->dq_count, want_density);
+      if (want_density) P.dq[qd] = slot;
+    }
+  }
+}
+
+// Hero-wavelength MIS: completes the density ratios q_j of the rough
+// vertices k_shade queued, with the lobe's m >= 1 density at the four class
+// wavelengths (rough_density_class) -- the same arithmetic on the same inputs
+// as inline, on a dense queue.  Runs after k_shade and before k_shadow.
+__global__ void __launch_bounds__(256) k_density(RenderParams p) {
+  const Pool& P = p.pool;
+  const int n = *(volatile int*)&p.ctr->dq_count;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int slot = P.dq[i];
+    const float4 a = P.hd0[slot], b = P.hd1[slot], c = P.hd2[slot];
+    const float gq[4] = {a.x, a.y, a.z, a.w}, klq[4] = {b.x, b.y, b.z, b.w};
+    const unsigned bits = (unsigned)__float_as_int(c.y);
+    const int gh = (int)(bits >> 4);
+    const bool want[4] = {(bits & 1u) != 0, (bits & 2u) != 0, (bits & 4u) != 0, (bits & 8u) != 0};
+    float dens[4];
+    rough_density_class(gq, klq, want, c.x, dens);
+    const float4 q4 = P.hq[slot];
+    float hq[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      if (g == gh || hq[g] == 0.0f) continue;
+      hq[g] = dens[gh] > 0.0f ? hq[g] * (dens[g] / dens[gh]) : 0.0f;
+    }
+    P.hq[slot] = make_float4(hq[0], hq[1], hq[2], hq[3]);
   }
 }
 
@@ -1917,9 +1954,10 @@ cudaError_t launch_iteration_t(const RenderParams& p, int grid_regen, int grid_t
   if (ev) cudaEventRecord(ev[1], st);
   k_trace<TREE><<<grid_trace, TREE == kTreeWide ? block : trace_block(block), 0, st>>>(p);
   if (ev) cudaEventRecord(ev[2], st);
-  if (hero)
+  if (hero) {
     k_shade<NS, TT, 1><<<grid_shade, block, smem, st>>>(p);
-  else if (aniso)
+    k_density<<<grid_shade, 256, 0, st>>>(p);  // counted with shading
+  } else if (aniso)
     k_shade<NS, TT, 2><<<grid_shade, block, smem, st>>>(p);
   else
     k_shade<NS, TT, 0><<<grid_shade, block, smem, st>>>(p);
@@ -2095,7 +2133,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   long long P = o.pool_size;
   if (P <= 0) {
     const size_t per_slot = sizeof(float4) * 14 + sizeof(float2) + sizeof(int4) + 2 * sizeof(int) + 1 +
-                            (hero ? sizeof(float4) * 16 : 0) + (aniso ? sizeof(float4) * 5 : 0);
+                            (hero ? sizeof(float4) * 19 + sizeof(int) : 0) + (aniso ? sizeof(float4) * 5 : 0);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
       cudaGetLastError();
@@ -2126,7 +2164,9 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const size_t o_sq = take(sizeof(int) * (size_t)P);
   const size_t o_st8 = take((size_t)P);
   const int mode = hero ? 1 : aniso ? 2 : 0;
-  const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 16) : 0;  // hq, hqp, hfb, hfr, hpart/haccS/haccC[4]
+  // hq, hqp, hfb, hfr, hpart/haccS/haccC[4], hd0..hd2, then the density queue
+  const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 19) : 0;
+  const size_t o_dq = hero ? take(sizeof(int) * (size_t)P) : 0;
   const size_t o_aniso = aniso ? take(sizeof(float4) * (size_t)P * 5) : 0;  // ak0, ak1, nk0, nk1, nkf
   const size_t total = off;
   if (plan_bytes) {
@@ -2183,6 +2223,10 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     p.pool.hpart = h4 + (size_t)P * 4;
     p.pool.haccS = h4 + (size_t)P * 8;
     p.pool.haccC = h4 + (size_t)P * 12;
+    p.pool.hd0 = h4 + (size_t)P * 16;
+    p.pool.hd1 = h4 + (size_t)P * 17;
+    p.pool.hd2 = h4 + (size_t)P * 18;
+    p.pool.dq = (int*)(base + o_dq);
   }
   if (aniso) {
     float4* a4 = (float4*)(base + o_aniso);
@@ -2361,7 +2405,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     GR_CK(cudaMemcpyAsync(hc, f->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     GR_CK(cudaStreamSynchronize(st));
     f->iterations += (long long)hc->iters;
-    f->launches += 5LL * (long long)hc->iters + 1;
+    f->launches += (5LL + (hero ? 1 : 0)) * (long long)hc->iters + 1;
     if (hc->err == 3) {
       err = "render exceeded its iteration bound";
       return GR_E_TIMEOUT;
@@ -2387,7 +2431,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
       break;
     }
     it += B;
-    f->launches += 4LL * B;
+    f->launches += (4LL + (hero ? 1 : 0)) * B;
     // copy the counters of this batch into pinned slot (batch & 1)
     e = cudaMemcpyAsync(hc + (batch & 1), f->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[batch & 1], st);
