@@ -135,6 +135,9 @@ __device__ __forceinline__ int find_view(const RenderParams& p, unsigned long lo
   return lo;
 }
 // views whose first tickets k_regen stages in shared memory (4 KB)
+#ifndef GR_REGEN_SLOTS
+#define GR_REGEN_SLOTS 4
+#endif
 #ifndef GR_REGEN_SMEM_VIEWS
 #define GR_REGEN_SMEM_VIEWS 512
 #endif
@@ -220,6 +223,37 @@ __device__ __forceinline__ CT block_reserve(CT* counter, bool want) {
   return off;
 }
 
+// Block-wide reservation of n entries per thread (n >= 0) with one atomic per
+// block: returns the first of this thread's n entries (exclusive scan over the
+// block).  Uniform control flow, as block_reserve.
+template <typename CT>
+__device__ __forceinline__ CT block_reserve_n(CT* counter, int n) {
+  __shared__ int s_warp[8];
+  __shared__ CT s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  int incl = n;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += v;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int c = s_warp[w];
+      s_warp[w] = tot;
+      tot += c;
+    }
+    s_base = tot ? atomicAdd(counter, (CT)tot) : (CT)0;
+  }
+  __syncthreads();
+  const CT off = s_base + (CT)(s_warp[warp] + incl - n);
+  __syncthreads();
+  return off;
+}
+
 // Block-wide sum of a per-thread count added with one atomic per block.
 __device__ __forceinline__ void block_count(unsigned long long* ctr, int v) {
   __shared__ int s_sum[8];
@@ -288,7 +322,6 @@ __device__ __forceinline__ bool fold_class(const RenderParams& p, int slot, cons
 template <int NS, bool HERO>
 __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
   const Pool& P = p.pool;
-  const int stride = gridDim.x * blockDim.x;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     p.ctr->sq_count = 0;
     p.ctr->dq_count = 0;
@@ -307,100 +340,120 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
     for (int i = threadIdx.x; i < p.n_views; i += blockDim.x) s_base[i] = p.views[i].ticket_base;
     __syncthreads();
   }
-  for (int base = blockIdx.x * blockDim.x; base < p.P; base += stride) {
-    const int slot = base + threadIdx.x;
-    const bool valid = slot < p.P;
-    bool need = false, active = false, fresh = false;
-    // one byte of state per slot; the meta record only for finished samples
-    const int st = valid ? P.st8[slot] : ST_IDLE;
-    const int4 m = valid && st == ST_DONE ? P.meta[slot] : make_int4(0, 0, 0, 0);
-    if (valid && st == ST_DONE && HERO) {
-      ++finished;
-      if (fold_class<NS>(p, slot, m)) {
-        start_sample<NS, true>(p, slot, m.x, m.y, meta_k(m.z) + 1);
-        active = fresh = true;
-      } else {
-        need = true;
-      }
-    } else if (valid && st == ST_DONE) {
-      ++finished;
-      const DevView& V = p.views[m.x];
-      const int WH = V.W * V.H;
-      const int bin = m.y / WH;
-      const int k = meta_k(m.z) + 1;
-      const int n_smp = bin_samples(V, bin);
-      // a one-sample ticket's sum is its sample: no slot accumulator is kept
-      // (the same bits as a Kahan sum of one term)
-      float4 s = n_smp == 1 ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : P.accS[slot];
-      float4 c = n_smp == 1 ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : P.accC[slot];
-      const float4 v = P.part[slot];
-      kahan_add(s.x, c.x, v.x);
-      if (NS == 4) {
-        kahan_add(s.y, c.y, v.y);
-        kahan_add(s.z, c.z, v.z);
-        kahan_add(s.w, c.w, v.w);
-      }
-      if (k < n_smp) {
-        P.accS[slot] = s;
-        P.accC[slot] = c;
-        start_sample<NS, false>(p, slot, m.x, m.y, k);
-        active = fresh = true;
-      } else {
-        // ticket complete: add its sum into the frame accumulator (Kahan)
-        const size_t idx = (size_t)m.y * NS;
-        float tot[4] = {s.x - c.x, s.y - c.y, s.z - c.z, s.w - c.w};
-        for (int q = 0; q < NS; ++q) {
-          float a = V.acc_sum[idx + q], e = V.acc_comp[idx + q];
-          kahan_add(a, e, tot[q]);
-          V.acc_sum[idx + q] = a;
-          V.acc_comp[idx + q] = e;
-        }
-        need = true;
-      }
-    } else if (valid && st == ST_IDLE) {
-      need = true;
-    } else if (valid && st == ST_ACTIVE) {
-      active = true;
-    }
-    if (need && !may_claim) {
-      need = false;
-      if (st != ST_IDLE) P.st8[slot] = ST_IDLE;
-    }
-    // claim tickets, one atomic per block (tickets without samples in this
-    // render are skipped by claiming again)
-    while (__syncthreads_or(need)) {
-      const unsigned long long t = block_reserve<unsigned long long>(&p.ctr->next_ticket, need);
-      if (need) {
-        if (t >= p.ctr->total_tickets) {
-          need = false;
-          if (st != ST_IDLE) P.st8[slot] = ST_IDLE;
+  // each thread takes GR_REGEN_SLOTS slots per round (coalesced: slot j of a
+  // round is base + j * blockDim.x + threadIdx.x), so the block's ticket
+  // claims and queue reservations cost one barrier round and one atomic per
+  // GR_REGEN_SLOTS slots
+  constexpr int R = GR_REGEN_SLOTS;
+  const int chunk = blockDim.x * R;
+  for (int base = blockIdx.x * chunk; base < p.P; base += gridDim.x * chunk) {
+    unsigned need_m = 0u, active_m = 0u, fresh_m = 0u, busy_m = 0u;  // per slot j: bit j
+#pragma unroll 1
+    for (int j = 0; j < R; ++j) {
+      const int slot = base + j * blockDim.x + threadIdx.x;
+      if (slot >= p.P) break;
+      bool need = false, active = false, fresh = false;
+      // one byte of state per slot; the meta record only for finished samples
+      const int st = P.st8[slot];
+      const int4 m = st == ST_DONE ? P.meta[slot] : make_int4(0, 0, 0, 0);
+      if (st == ST_DONE && HERO) {
+        ++finished;
+        if (fold_class<NS>(p, slot, m)) {
+          start_sample<NS, true>(p, slot, m.x, m.y, meta_k(m.z) + 1);
+          active = fresh = true;
         } else {
-          int view = find_view(p, t, staged ? s_base : nullptr);
-          const DevView& V = p.views[view];
-          // tickets run pixel-major, sample class fastest: neighbouring
-          // slots start the same pixel at neighbouring wavelengths, so a warp's
-          // camera rays (and grating orders) stay coherent.  Only classes that
-          // receive samples have tickets: sample s goes to class s mod Q, so
-          // with spp < Q they are the nbu = spp classes from first_sample mod Q
-          // on.  The ticket's element is class * W*H + pixel, whatever the
-          // claim order (with Q = nb the class is the bin).
-          const int local = (int)(t - (unsigned long long)V.ticket_base);
-          const int pix = local / V.nbu;
-          const int cls = (V.first_sample + (local - pix * V.nbu)) % V.Q;
-          if (class_samples(V, cls, V.Q) > 0) {
-            if (HERO) {
-              for (int g = 0; g < 4; ++g) {
-                P.haccS[(size_t)g * p.P + slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                P.haccC[(size_t)g * p.P + slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-              }
-            } else if (class_samples(V, cls, V.Q) > 1) {
-              P.accS[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-              P.accC[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            }
-            start_sample<NS, HERO>(p, slot, view, cls * (V.W * V.H) + pix, 0);
-            active = fresh = true;
-            need = false;
+          need = true;
+        }
+      } else if (st == ST_DONE) {
+        ++finished;
+        const DevView& V = p.views[m.x];
+        const int WH = V.W * V.H;
+        const int bin = m.y / WH;
+        const int k = meta_k(m.z) + 1;
+        const int n_smp = bin_samples(V, bin);
+        // a one-sample ticket's sum is its sample: no slot accumulator is kept
+        // (the same bits as a Kahan sum of one term)
+        float4 s = n_smp == 1 ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : P.accS[slot];
+        float4 c = n_smp == 1 ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : P.accC[slot];
+        const float4 v = P.part[slot];
+        kahan_add(s.x, c.x, v.x);
+        if (NS == 4) {
+          kahan_add(s.y, c.y, v.y);
+          kahan_add(s.z, c.z, v.z);
+          kahan_add(s.w, c.w, v.w);
+        }
+        if (k < n_smp) {
+          P.accS[slot] = s;
+          P.accC[slot] = c;
+          start_sample<NS, false>(p, slot, m.x, m.y, k);
+          active = fresh = true;
+        } else {
+          // ticket complete: add its sum into the frame accumulator (Kahan)
+          const size_t idx = (size_t)m.y * NS;
+          float tot[4] = {s.x - c.x, s.y - c.y, s.z - c.z, s.w - c.w};
+          for (int q = 0; q < NS; ++q) {
+            float a = V.acc_sum[idx + q], e = V.acc_comp[idx + q];
+            kahan_add(a, e, tot[q]);
+            V.acc_sum[idx + q] = a;
+            V.acc_comp[idx + q] = e;
           }
+          need = true;
+        }
+      } else if (st == ST_IDLE) {
+        need = true;
+      } else if (st == ST_ACTIVE) {
+        active = true;
+      }
+      if (need && !may_claim) {
+        need = false;
+        if (st != ST_IDLE) P.st8[slot] = ST_IDLE;
+      }
+      need_m |= (unsigned)need << j;
+      active_m |= (unsigned)active << j;
+      fresh_m |= (unsigned)fresh << j;
+      busy_m |= (unsigned)(st != ST_IDLE) << j;
+    }
+    // claim tickets, one atomic per block per pass (tickets without samples
+    // in this render are skipped by claiming again)
+    while (__syncthreads_or(need_m != 0u)) {
+      const unsigned long long t0 = block_reserve_n<unsigned long long>(&p.ctr->next_ticket, __popc(need_m));
+      unsigned long long t = t0;
+#pragma unroll 1
+      for (int j = 0; j < R; ++j) {
+        if (!((need_m >> j) & 1u)) continue;
+        const int slot = base + j * blockDim.x + threadIdx.x;
+        const unsigned long long tk = t++;
+        if (tk >= p.ctr->total_tickets) {
+          need_m &= ~(1u << j);
+          if ((busy_m >> j) & 1u) P.st8[slot] = ST_IDLE;
+          continue;
+        }
+        int view = find_view(p, tk, staged ? s_base : nullptr);
+        const DevView& V = p.views[view];
+        // tickets run pixel-major, sample class fastest: neighbouring
+        // slots start the same pixel at neighbouring wavelengths, so a warp's
+        // camera rays (and grating orders) stay coherent.  Only classes that
+        // receive samples have tickets: sample s goes to class s mod Q, so
+        // with spp < Q they are the nbu = spp classes from first_sample mod Q
+        // on.  The ticket's element is class * W*H + pixel, whatever the
+        // claim order (with Q = nb the class is the bin).
+        const int local = (int)(tk - (unsigned long long)V.ticket_base);
+        const int pix = local / V.nbu;
+        const int cls = (V.first_sample + (local - pix * V.nbu)) % V.Q;
+        if (class_samples(V, cls, V.Q) > 0) {
+          if (HERO) {
+            for (int g = 0; g < 4; ++g) {
+              P.haccS[(size_t)g * p.P + slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+              P.haccC[(size_t)g * p.P + slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+          } else if (class_samples(V, cls, V.Q) > 1) {
+            P.accS[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            P.accC[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          }
+          start_sample<NS, HERO>(p, slot, view, cls * (V.W * V.H) + pix, 0);
+          active_m |= 1u << j;
+          fresh_m |= 1u << j;
+          need_m &= ~(1u << j);
         }
       }
     }
@@ -408,12 +461,16 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
     // part: continuing segments (incoherent, longer traversals) from the front
     // of the array, camera rays from the back, so that the queue is traced
     // longest-first and the end of the trace launch waits on short rays
-    const int qf = block_reserve<int>(&p.ctr->tq_count, active && !fresh);
-    const int qb = block_reserve<int>(&p.ctr->tq_back, fresh);
-    if (fresh) {
-      P.tq[p.P - 1 - qb] = slot;
-    } else if (active) {
-      P.tq[qf] = slot;
+    const unsigned cont_m = active_m & ~fresh_m;
+    int qf = block_reserve_n<int>(&p.ctr->tq_count, __popc(cont_m));
+    int qb = block_reserve_n<int>(&p.ctr->tq_back, __popc(fresh_m));
+#pragma unroll 1
+    for (int j = 0; j < R; ++j) {
+      const int slot = base + j * blockDim.x + threadIdx.x;
+      if ((fresh_m >> j) & 1u)
+        P.tq[p.P - 1 - qb++] = slot;
+      else if ((cont_m >> j) & 1u)
+        P.tq[qf++] = slot;
     }
   }
   block_count(&p.ctr->samples, finished);
@@ -2300,7 +2357,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   g_shade = grid_for(shade_fn, smem);
   // never more blocks than the pool needs
   const int gmax = (int)((P + block - 1) / block);
-  g_regen = std::min(g_regen, gmax);
+  g_regen = std::min(g_regen, (int)((P + (long long)block * GR_REGEN_SLOTS - 1) / ((long long)block * GR_REGEN_SLOTS)));
   g_trace = std::min(g_trace, (int)((P + tblk - 1) / tblk));
   g_shade = std::min(g_shade, gmax);
   g_shadow = std::min(g_shadow, gmax);
@@ -2708,7 +2765,8 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   };
   const void* shade_fn = shade_kernel(NSv, o.table_dtype, 0);
   const int gmax = (int)((P + block - 1) / block);
-  const int g_regen = std::min(gmax, grid_for(regen_kernel(NSv, false), 0));
+  const int g_regen = std::min((int)((P + (long long)block * GR_REGEN_SLOTS - 1) / ((long long)block * GR_REGEN_SLOTS)),
+                               grid_for(regen_kernel(NSv, false), 0));
   const int tree = pick_tree(o.flags, scenes, n_scenes);
   const int tblk = tree == kTreeWide ? block : trace_block(block);
   const int g_trace = std::min((int)((P + tblk - 1) / tblk), grid_for(trace_kernel(tree), 0, tblk));
