@@ -93,12 +93,12 @@ def parse():
     ap.add_argument("--wide", action="store_true", help="traverse the 4-wide quantised BVH")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' legs of the default run")
-    ap.add_argument("--extras", default="dielectric,hero,aniso,batched,serving,precision,doubleslit",
+    ap.add_argument("--extras", default="dielectric,hero,aniso,batched,serving,precision,doubleslit,aperture3d",
                     help="legs of the default run (comma list)")
     ap.add_argument("--cpu-crop", type=int, default=128, help="side of the oracle's centre crop")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", choices=["procedural", "batched", "serving", "precision", "dielectric",
-                                           "doubleslit", "hero", "aniso"],
+                                           "doubleslit", "hero", "aniso", "aperture3d"],
                     default="procedural",
                     help="procedural: the headline single-view workload; batched: 64 views/scenes, plain "
                          "per-view FP32 form vs the autotuned single-graph form; serving: "
@@ -494,6 +494,50 @@ def run_doubleslit(args):
                              "sample": "%d of the elements (%d rays), numpy FP64, %.1f s" % (len(sub), cpu_rays, cpu_s)}}
 
 
+def run_aperture3d(args):
+    """Footprint-resolved generalized rays through a disk aperture in a 3D
+    world onto a 48 x 48 screen of detector elements (the double-slit
+    validation of Sec. 5.1-5.2 taken to a plane aperture, with the Sec. 6
+    truncation): generalized rays (element x direction) per second, and one
+    element against the oracle's FP64 sums and against exact 3D
+    Rayleigh-Sommerfeld diffraction."""
+    import numpy as np
+    import paper_2303_15762_gb300 as gr
+    from paper_2303_15762_gb300 import scenegen as sg
+    from oracle import aperture3d as a3
+    gr.load()
+    s = sg.aperture3d_setup("disk")
+    n_t = int(np.ceil(2 * s["reach"] / (s["z"] * s["dt"])))
+    rays = len(s["x0"]) * n_t * n_t
+    args_ = (s["x0"], s["x_ap"], s["w_ap"], s["beta"], s["z"], s["k"], s["reach"], s["dt"], s["rho_cut"])
+    for _ in range(max(1, args.warmup)):
+        gr.aperture_backward_3d(*args_)
+    times = []
+    for _ in range(max(1, args.steps)):
+        out, ms = gr.aperture_backward_3d(*args_)
+        times.append(ms)
+    ms = statistics.mean(times)
+    i0 = int(np.argmin(np.abs(s["x0"][:, 0] - 30.0) + np.abs(s["x0"][:, 1] + 30.0)))
+    x0 = s["x0"][i0:i0 + 1]
+    t0 = time.perf_counter()
+    ref = a3.backward_generalized_rays(x0, s["z"], s["k"], s["x_ap"], s["w_ap"], s["beta"], s["reach"], s["dt"],
+                                       s["rho_cut"])
+    cpu_s = time.perf_counter() - t0
+    exact = a3.forward_exact(x0, s["z"], s["k"], s["x_ap"], s["w_ap"], s["beta"])
+    return {"workload": "aperture3d (f3, plane aperture in a 3D world)",
+            "metric": "generalized rays (element x direction) per second, each overlapped with the aperture samples",
+            "unit": "Mrays/s", "value": rays / (ms * 1e-3) / 1e6, "ms_per_step": ms, "steps": max(1, args.steps),
+            "config": {"aperture": "disk of radius 12 wavelengths, %d samples" % len(s["x_ap"]),
+                       "elements": len(s["x0"]), "screen": "48 x 48 over +-240", "directions_per_element": n_t * n_t,
+                       "z": s["z"], "beta": s["beta"], "beta_at_aperture": s["beta_ap"], "rho_cut": s["rho_cut"]},
+            "overlaps_per_s": rays * len(s["x_ap"]) / (ms * 1e-3),
+            "element": [float(v) for v in x0[0]],
+            "rel_err_vs_oracle_sums": float(abs(out[i0] - ref[0]) / ref[0]),
+            "rel_err_vs_exact_rayleigh_sommerfeld": float(abs(out[i0] - exact[0]) / exact[0]),
+            "cpu_baseline": {"value": n_t * n_t / cpu_s / 1e6, "unit": "Mrays/s", "cores": 1, "kind": "oracle",
+                             "sample": "one element (%d rays), numpy FP64, %.1f s" % (n_t * n_t, cpu_s)}}
+
+
 def time_modes(args, S, F, view, modes, clock_mode, steps=None, warmup=None):
     """Device time per step (CUDA events, L2 flushed) and per-kernel time of
     each named flag set; nvidia-smi clocks are sampled during `clock_mode`.
@@ -687,7 +731,8 @@ def run_extras(args):
             "batched": lambda: run_batched(argparse.Namespace(**dict(vars(args), steps=1, warmup=1))),
             "serving": lambda: run_serving(args),
             "precision": lambda: run_precision(argparse.Namespace(**dict(vars(args), steps=3, warmup=2))),
-            "doubleslit": lambda: run_doubleslit(argparse.Namespace(**dict(vars(args), steps=3, warmup=1)))}
+            "doubleslit": lambda: run_doubleslit(argparse.Namespace(**dict(vars(args), steps=3, warmup=1))),
+            "aperture3d": lambda: run_aperture3d(argparse.Namespace(**dict(vars(args), steps=2, warmup=1)))}
     out = {}
     for name in [x for x in args.extras.split(",") if x]:
         t0 = time.perf_counter()
@@ -708,6 +753,7 @@ def main():
             "serving": lambda: run_serving(args, [args.rate] + [float(r) for r in args.rates.split(",")
                                                               if r and float(r) != args.rate]),
             "precision": lambda: run_precision(args), "doubleslit": lambda: run_doubleslit(args),
+            "aperture3d": lambda: run_aperture3d(args),
             "hero": lambda: run_hero(args), "aniso": lambda: run_aniso(args),
             "dielectric": lambda: run_dielectric(args)}
     if args.workload in legs:

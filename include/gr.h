@@ -381,6 +381,38 @@ gr_status gr_aperture_backward_2d(int32_t n_det, const double* x0, int32_t n_ap,
                                   const double* w_ap, double beta, double z, double k, double reach, double dtheta,
                                   double rho_cut, double* out, float* kernel_ms, void* cuda_stream);
 
+/* Footprint-resolved generalized rays through a plane aperture in a 3D world:
+ * the double-slit validation of Sec. 5.1-5.2 taken to a 2D aperture (any
+ * sampled shape, e.g. a rectangle or a disk) and a 2D screen of detector
+ * elements, with the accurate propagation and truncation of Sec. 6.  All
+ * lengths in one unit (that of the wavelength); k = 2 pi / lambda; the
+ * aperture lies in the plane z = 0, lit at normal incidence, the screen in the
+ * plane at distance z.
+ *   x0[n_det][2]       detector element centres (x, y) on the screen; each is a
+ *                      coherent state of width beta (Eq. wdf_coherent_states)
+ *   x_ap[n_ap][2], w_ap[n_ap]
+ *                      aperture samples: positions and field weights
+ *                      (quadrature weight x real field amplitude), n_ap <= 12288
+ *   reach, dt          each element's directions t = (s_x, s_y) / s_z form the
+ *                      grid (x0 - reach) / z + i dt per axis (i < ceil(2 reach /
+ *                      (z dt)) <= 8192), i.e. rays landing on a square grid of
+ *                      step z dt over +-reach around the aperture centre; reach
+ *                      must cover the aperture plus rho_cut beta'
+ *   rho_cut            truncation radius in units of the propagated width beta'
+ * Each direction is a generalized ray propagated back over z / s_z in closed
+ * form (Eq. K_free_space_propagation from rho = 0), whose footprint is
+ * projected obliquely onto the aperture plane (|P d|^2 = |d|^2 - s_z^2 (t.d)^2
+ * for an offset d from its landing point), truncated at rho_cut beta' and
+ * overlapped with the aperture field; out[n_det] (host) receives
+ * sum_t |A|^2 s_z / (pi beta'^2) k^2 s_z^4 dt^2 / (2 pi)^2.  Per-direction terms
+ * in FP64, the aperture sums in FP32, the per-element sum in FP64 in a fixed
+ * order.  *kernel_ms (may be NULL) receives the kernel's device time.  Host
+ * buffers; the call synchronises the stream.  GR_E_INVALID for bad sizes or
+ * non-positive lengths. */
+gr_status gr_aperture_backward_3d(int32_t n_det, const double* x0, int32_t n_ap, const double* x_ap,
+                                  const double* w_ap, double beta, double z, double k, double reach, double dt,
+                                  double rho_cut, double* out, float* kernel_ms, void* cuda_stream);
+
 /* ---- Rendering without device allocation (no counterpart in the paper).
  *
  * For callers that must not allocate device memory while rendering: a

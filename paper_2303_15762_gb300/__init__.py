@@ -11,7 +11,7 @@ from . import scenegen  # noqa: F401
 _NATIVE_NAMES = ("Scene", "Frame", "render", "render_image", "make_opts", "GrError", "lib_handle",
                  "FLAG_NEE", "FLAG_RR", "FLAG_NO_RENORM", "FLAG_WIDE_BVH", "FLAG_HERO", "FLAG_ANISO", "FLAG_FP32_NODES", "pack_views", "current_stream", "debug_rng",
                  "render_multi", "measure_fp32_peak", "debug_order_table", "debug_footprint",
-                 "aperture_backward_2d", "accum_floats",
+                 "aperture_backward_2d", "aperture_backward_3d", "accum_floats",
                  "render_scratch_bytes")
 
 

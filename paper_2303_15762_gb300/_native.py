@@ -21,7 +21,7 @@ EXPORTED = ["gr_scene_create", "gr_scene_destroy", "gr_frame_create", "gr_frame_
             "gr_render", "gr_readback", "gr_frame_stats", "gr_scene_bvh", "gr_debug_rng", "gr_render_static", "gr_render_multi",
             "gr_last_error", "gr_abi_version", "gr_measure_fp32_peak", "gr_debug_order_table",
             "gr_debug_footprint", "gr_aperture_backward_2d", "gr_scene_bytes", "gr_frame_bytes",
-            "gr_render_scratch_bytes"]
+            "gr_render_scratch_bytes", "gr_aperture_backward_3d"]
 
 
 class GrError(RuntimeError):
@@ -406,6 +406,26 @@ def debug_footprint(quads):
     out = np.zeros((q.shape[0], 2), dtype=np.float32)
     _check(fn(q.shape[0], _ptr(q), _ptr(out), current_stream()))
     return out
+
+
+def aperture_backward_3d(x0, x_ap, w_ap, beta, z, k, reach, dt, rho_cut=2.5):
+    """Footprint-resolved generalized rays through a plane aperture in a 3D
+    world (gr_aperture_backward_3d): x0 [n][2] detector element centres, x_ap
+    [m][2] aperture samples with weights w_ap [m]; returns (intensity per
+    detector element, kernel ms)."""
+    L = lib_handle()
+    fn = L.gr_aperture_backward_3d
+    D = ctypes.c_double
+    fn.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, D, D, D, D, D,
+                   D, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    x0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(-1, 2)
+    xa = np.ascontiguousarray(x_ap, dtype=np.float64).reshape(-1, 2)
+    wa = np.ascontiguousarray(w_ap, dtype=np.float64).reshape(-1)
+    out = np.zeros(len(x0), dtype=np.float64)
+    ms = ctypes.c_float()
+    _check(fn(len(x0), _ptr(x0), len(xa), _ptr(xa), _ptr(wa), beta, z, k, reach, dt, rho_cut, _ptr(out),
+              ctypes.byref(ms), current_stream()))
+    return out, ms.value
 
 
 def aperture_backward_2d(x0, x_ap, w_ap, beta, z, k, reach, dtheta, rho_cut=2.5):

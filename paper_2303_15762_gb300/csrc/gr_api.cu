@@ -691,4 +691,19 @@ gr_status gr_aperture_backward_2d(int32_t n_det, const double* x0, int32_t n_ap,
   return GR_OK;
 }
 
+gr_status gr_aperture_backward_3d(int32_t n_det, const double* x0, int32_t n_ap, const double* x_ap,
+                                  const double* w_ap, double beta, double z, double k, double reach, double dt,
+                                  double rho_cut, double* out, float* kernel_ms, void* cuda_stream) {
+  if (!x0 || !x_ap || !w_ap || !out || n_det <= 0 || n_ap <= 0 || n_ap > 12288 || !(beta > 0.0) || !(z > 0.0) ||
+      !(k > 0.0) || !(reach > 0.0) || !(dt > 0.0) || !(rho_cut > 0.0))
+    return fail(GR_E_INVALID, "gr_aperture_backward_3d: bad arguments");
+  // bound the direction grid: at most 2^13 directions per axis
+  if (2.0 * reach / (z * dt) > (double)(1 << 13))
+    return fail(GR_E_INVALID, "gr_aperture_backward_3d: direction grid too fine");
+  cudaError_t e = gr::aperture_backward_3d_impl(n_det, x0, n_ap, x_ap, w_ap, beta, z, k, reach, dt, rho_cut, out,
+                                                (cudaStream_t)cuda_stream, kernel_ms);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_aperture_backward_3d");
+  return GR_OK;
+}
+
 }  // extern "C"

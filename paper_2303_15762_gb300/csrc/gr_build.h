@@ -102,6 +102,9 @@ cudaError_t debug_footprint_impl(int n, const float* host_in, float* host_out, c
 cudaError_t aperture_backward_impl(int n_det, const double* x0_host, int n_ap, const double* xa_host,
                                    const double* wa_host, double beta, double z, double k, double reach,
                                    double dtheta, double rho_cut, double* out_host, cudaStream_t st, float* ms);
+cudaError_t aperture_backward_3d_impl(int n_det, const double* x0_host, int n_ap, const double* xa_host,
+                                      const double* wa_host, double beta, double z, double k, double reach,
+                                      double dt, double rho_cut, double* out_host, cudaStream_t st, float* ms);
 
 }  // namespace gr
 

@@ -351,6 +351,55 @@ def double_slit_setup(d=400.0, b=40.0, z=1e4, wavelength=1.0, sigma_at_slits=100
                 reach=d / 2 + b + 8 * 150.0, dtheta=dkappa / k, rho_cut=rho_cut, d=d, b=b)
 
 
+def aperture_nodes(shape, size, n):
+    """Quadrature of a unit field over a plane aperture: nodes [N][2] and
+    weights [N].  shape 'rect': size = (a, b) full side lengths, n x n
+    Gauss-Legendre nodes; 'disk': size = radius, n Gauss-Legendre radii x 2n
+    equally spaced angles."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    if shape == "rect":
+        a, b = size
+        X, Y = np.meshgrid(0.5 * a * x, 0.5 * b * x, indexing="ij")
+        W = np.outer(0.5 * a * w, 0.5 * b * w)
+        return np.stack([X.ravel(), Y.ravel()], axis=1), W.ravel()
+    if shape == "disk":
+        R = float(size)
+        r, wr = 0.5 * R * (x + 1), 0.5 * R * w
+        m = 2 * n
+        ph = 2 * math.pi * (np.arange(m) + 0.5) / m
+        rr, pp = np.meshgrid(r, ph, indexing="ij")
+        W = np.outer(wr * r, np.full(m, 2 * math.pi / m))
+        return np.stack([(rr * np.cos(pp)).ravel(), (rr * np.sin(pp)).ravel()], axis=1), W.ravel()
+    raise ValueError(shape)
+
+
+def aperture3d_setup(shape="disk", size=12.0, z=2000.0, sigma_ap=30.0, n_nodes=24, rho_cut=2.5, dt=5e-4,
+                     x0=None, wavelength=1.0):
+    """Inputs of the aperture experiment in a 3D world (the double slit of
+    Sec. 5.1-5.2 taken to a plane aperture and a 2D screen), in units of the
+    wavelength: a disk of radius `size` (or a square of side `size`) lit at
+    normal incidence, the screen at z, detector states of the width beta whose
+    footprint at the aperture has spatial std sigma_ap (the smaller root of
+    beta^2 + zbar^2 / beta^2 = 2 sigma^2; the footprint width there is then
+    beta' = sqrt(2) sigma_ap), the aperture quadrature, the detector centres
+    (default: a 48 x 48 screen over +-240) and the direction grid (rays
+    landing within +-reach of the aperture centre, reach = the aperture's
+    half-diagonal + 1.05 rho_cut beta', one landing step = z dt)."""
+    k = 2 * math.pi / wavelength
+    zb = z / k
+    s2 = 2 * sigma_ap ** 2
+    beta = math.sqrt((s2 - math.sqrt(s2 * s2 - 4 * zb * zb)) / 2)
+    nodes, w = aperture_nodes(shape, size if shape == "disk" else (size, size), n_nodes)
+    half = float(np.max(np.hypot(nodes[:, 0], nodes[:, 1])))
+    if x0 is None:
+        g = np.linspace(-240.0, 240.0, 48)
+        X, Y = np.meshgrid(g, g, indexing="ij")
+        x0 = np.stack([X.ravel(), Y.ravel()], axis=1)
+    return dict(shape=shape, size=size, x0=np.asarray(x0, np.float64).reshape(-1, 2), x_ap=nodes, w_ap=w,
+                beta=beta, beta_ap=math.sqrt(2.0) * sigma_ap, z=z, k=k,
+                reach=half + 1.05 * rho_cut * math.sqrt(2.0) * sigma_ap, dt=dt, rho_cut=rho_cut)
+
+
 # ---------------------------------------------------------------- batched workload
 def batch_views(seed=4, n_views=64, spp=16, tris_range=(5_000, 200_000), side_range=(128, 1024)):
     """64 views, each with its own seeded procedural scene; returns (scenes, views)."""

@@ -1,0 +1,91 @@
+"""Pins of the 3D aperture oracle (oracle/aperture3d.py): generalized rays
+through a plane aperture (disk or rectangle) onto a 2D screen of detector
+elements, the extension of the double-slit validation of Sec. 5.1-5.2.
+
+* The exact Rayleigh-Sommerfeld integral is checked against closed forms that
+  do not share its quadrature: the on-axis field of a uniformly lit disk
+  (exact), and the Fraunhofer patterns of a rectangle (sinc^2) and a disk
+  (Airy) far from the aperture.
+* Backward generalized rays (closed-form propagation, oblique footprint,
+  tangent-plane direction grid) reproduce the exact forward computation:
+  within 1e-3 of the peak without truncation and 1e-2 with the Sec. 6
+  truncation at 2.5 beta', and element by element at a steep direction, where
+  the grid's measure k^2 s_z^4 d^2t departs from k^2 d^2t by 15%.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import aperture3d as a3
+from paper_2303_15762_gb300 import scenegen as sg
+
+K = 2 * math.pi
+
+
+@pytest.mark.parametrize("z", [50.0, 200.0, 2000.0])
+def test_rs_on_axis_disk_closed_form(z):
+    nodes, w = sg.aperture_nodes("disk", 12.0, 48)
+    U = a3.rs_field([[0.0, 0.0]], z, K, nodes, w)[0]
+    ex = a3.on_axis_disk(z, K, 12.0)
+    assert abs(U - ex) <= 1e-10 * abs(ex)
+
+
+def test_rs_far_field_is_fraunhofer():
+    z = 1e5
+    xs = np.stack([np.linspace(0, 3e4, 40), np.linspace(0, 2e4, 40)], axis=1)
+    nodes, w = sg.aperture_nodes("rect", (8.0, 6.0), 32)
+    I = np.abs(a3.rs_field(xs, z, K, nodes, w)) ** 2
+    F = a3.fraunhofer_rect(xs, z, K, 8.0, 6.0)
+    assert np.max(np.abs(I - F)) <= 1e-6 * F.max()
+    # the sinc^2 zeros are where the far field vanishes: x = 2 pi r / (k a)
+    nodes, w = sg.aperture_nodes("disk", 5.0, 32)
+    I = np.abs(a3.rs_field(xs, z, K, nodes, w)) ** 2
+    F = a3.fraunhofer_disk(xs, z, K, 5.0)
+    assert np.max(np.abs(I - F)) <= 1e-6 * F.max()
+
+
+def test_rs_rejects_wrong_kernels():
+    """A dropped obliquity factor or the wrong sign of the phase fails the
+    on-axis closed form (the pin is sensitive to both)."""
+    nodes, w = sg.aperture_nodes("disk", 12.0, 48)
+    z = 50.0
+    r = np.sqrt(nodes[:, 0] ** 2 + nodes[:, 1] ** 2 + z * z)
+    no_obl = np.sum(w * (1.0 / r) * (1.0 / r - 1j * K) * np.exp(1j * K * r)) / (2 * math.pi)
+    conj = np.sum(w * (z / r ** 2) * (1.0 / r + 1j * K) * np.exp(-1j * K * r)) / (2 * math.pi)
+    ex = a3.on_axis_disk(z, K, 12.0)
+    assert abs(no_obl - ex) > 1e-3 * abs(ex)
+    assert abs(conj - ex) > 1e-3 * abs(ex)
+
+
+def test_screen_beta_spreads_to_sigma():
+    b = a3.screen_beta(30.0, 2000.0, K)
+    zb = 2000.0 / K
+    assert abs(math.sqrt((b * b + zb * zb / (b * b)) / 2) - 30.0) < 1e-9
+    assert abs(sg.aperture3d_setup()["beta"] - b) < 1e-12
+
+
+@pytest.mark.parametrize("shape", ["rect", "disk"])
+def test_backward_truncated_matches_exact(shape):
+    s = sg.aperture3d_setup(shape, size=12.0 if shape == "disk" else 24.0)
+    x0s = np.array([[0.0, 0.0], [60.0, -25.0]])
+    fw = a3.forward_exact(x0s, s["z"], s["k"], s["x_ap"], s["w_ap"], s["beta"])
+    bw = a3.backward_generalized_rays(x0s, s["z"], s["k"], s["x_ap"], s["w_ap"], s["beta"], s["reach"], s["dt"],
+                                      s["rho_cut"])
+    assert np.max(np.abs(bw - fw)) <= 1e-2 * fw.max()
+
+
+def test_backward_untruncated_matches_exact_and_the_measure():
+    """Without truncation the agreement is within 1e-3 of the peak; at an
+    element 400 wavelengths off axis (directions with s_z^4 ~ 0.92) each
+    element agrees to 2% of its own value, which a grid measure without the
+    s_z^4 factor would miss by 7%."""
+    s = sg.aperture3d_setup("rect", size=24.0, n_nodes=16)
+    x0s = np.array([[0.0, 0.0], [400.0, 0.0]])
+    fw = a3.forward_exact(x0s, s["z"], s["k"], s["x_ap"], s["w_ap"], s["beta"])
+    reach = s["reach"] * 2.0
+    bw = a3.backward_generalized_rays(x0s, s["z"], s["k"], s["x_ap"], s["w_ap"], s["beta"], reach, 1e-3, 5.5)
+    assert abs(bw[0] - fw[0]) <= 1e-3 * fw[0]
+    assert abs(bw[1] - fw[1]) <= 2e-2 * fw[1]
+    t = 400.0 / s["z"]
+    assert (1 + t * t) ** -2 < 0.93  # the element is steep enough for the measure to matter
