@@ -828,19 +828,62 @@ def main():
     value = job_throughput(samples, t_max, world)
     img = F.readback(0)
 
+    # ---- CPU oracle baseline on a centre crop, the accuracy of this run there,
+    # and the traversal work per closest-hit query of the oracle's SAH tree
+    cpu = None
+    rel = elem = None
+    ref_work = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import oracle as orc
+        c = min(args.cpu_crop, args.size)
+        x0 = args.size // 2 - c // 2
+        O = orc.Scene(scene)
+        cores = os.cpu_count() or 1
+        orc.work_reset()
+        t0 = time.perf_counter()
+        ref = O.render(view, 2, orc.FLAG_NEE, crop=(x0, x0, x0 + c, x0 + c), n_threads=cores)
+        dt = time.perf_counter() - t0
+        ref_work = orc.work_counters()
+        cpu = {"value": c * c * view["spp"] / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%dx%d centre crop of the same view, %d spp (%d samples), %.1f s" % (
+                   c, c, view["spp"], c * c * view["spp"], dt)}
+        crop = img[x0:x0 + c, x0:x0 + c].astype(np.float64)
+        rel = float(np.linalg.norm(crop - ref) / max(np.linalg.norm(ref), 1e-300))
+        elem = float(np.max(np.abs(crop - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
     # ---- roofline of the dominant kernel (device time share from live events)
     dom = int(np.argmax(kms))
     per_launch_ms = kms[dom] / max(1, kcnt[dom])
     if dom in (1, 3):
-        # traversal kernels: ALU-bound; counts of node visits / triangle tests
-        # are summed over trace and shadow, so attribute by time share
+        # traversal kernels, ALU/latency-bound.  Work = closest-hit queries of
+        # this step (segments + next-event rays) x the FLOPs a query needs
+        # through the oracle's binned-SAH reference tree (its node visits and
+        # triangle tests per query, counted on the oracle's crop), so that the
+        # work does not depend on the GPU's own tree; the kernels' own counts
+        # are reported beside it.
         per_node = FLOP_PER_WNODE if args.wide else FLOP_PER_NODE
-        flops = (visits * per_node + tests * FLOP_PER_TRI) / args.steps
         trav_ms = (kms[1] + kms[3]) / args.steps
+        queries = (stats["segments"] + stats["shadow_rays"])
+        flops_kernel = (visits * per_node + tests * FLOP_PER_TRI) / args.steps
+        achieved_kernel = flops_kernel / (trav_ms * 1e-3) / 1e12
+        if ref_work and ref_work["queries"] > 0:
+            vq = ref_work["node_visits"] / ref_work["queries"]
+            tq = ref_work["tri_tests"] / ref_work["queries"]
+            flops = queries * (vq * FLOP_PER_NODE + tq * FLOP_PER_TRI)
+            basis = ("closest-hit queries per step (%d segments + next-event rays) x (%.2f node visits x %d + %.2f "
+                     "triangle tests x %d FLOP) per query of the oracle's binned-SAH binary tree (ordered traversal, "
+                     "counted over its %d queries on the centre crop)" % (queries, vq, FLOP_PER_NODE, tq, FLOP_PER_TRI,
+                                                                         ref_work["queries"]))
+        else:
+            flops = flops_kernel
+            basis = "the kernels' own node visits and triangle tests (no oracle run)"
         achieved = flops / (trav_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": KERNELS[dom] + "+k_shadow" if dom == 1 else KERNELS[dom],
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops,
+                "frac": achieved / peak_tflops, "work_basis": basis,
+                "achieved_kernel_counts": achieved_kernel,
+                "kernel_counts": "%.2f node visits and %.2f triangle tests per query in the GPU's PLOC tree" % (
+                    visits / args.steps / max(queries, 1), tests / args.steps / max(queries, 1)),
                 "peak_source": "measured: FP32 FMA-chain microbenchmark, gr_measure_fp32_peak (best of 3, %.2f ms); "
                                "nominal 152 SM x 128 lanes x 2 FLOP x 2070 MHz = %.1f" % (peak_ms, FP32_PEAK_TFLOPS),
                 "traffic": None, "per_launch_ms": per_launch_ms}
@@ -852,11 +895,9 @@ def main():
     else:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
-        # slot state read and written by regen / shade per processed slot
-        bytes_per_launch = None
         roof = {"bound": "hbm", "kernel": KERNELS[dom], "achieved": None, "peak": peaks.get("hbm_gbs", 6800.0),
                 "unit": "GB/s", "frac": None, "traffic": None,
-                "per_launch_ms": per_launch_ms, "note": "bytes per launch not yet derived", "bytes": bytes_per_launch}
+                "per_launch_ms": per_launch_ms, "note": "bytes per launch not yet derived"}
     roof["kernel_ms_share"] = {KERNELS[k]: kms[k] / max(sum(kms), 1e-9) for k in range(4)}
 
     # ---- end to end through the C ABI with pinned host buffers
@@ -913,25 +954,6 @@ def main():
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
                "includes": "scene upload + BVH build, frame alloc, render, readback to pinned host",
                "phases": {k: statistics.mean(v) for k, v in ph.items()}}
-
-    # ---- CPU oracle baseline on a centre crop, and the accuracy of this run there
-    cpu = None
-    rel = elem = None
-    if rank == 0 and not args.no_cpu_baseline:
-        from oracle import oracle as orc
-        c = min(args.cpu_crop, args.size)
-        x0 = args.size // 2 - c // 2
-        O = orc.Scene(scene)
-        cores = os.cpu_count() or 1
-        t0 = time.perf_counter()
-        ref = O.render(view, 2, orc.FLAG_NEE, crop=(x0, x0, x0 + c, x0 + c), n_threads=cores)
-        dt = time.perf_counter() - t0
-        cpu = {"value": c * c * view["spp"] / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%dx%d centre crop of the same view, %d spp (%d samples), %.1f s" % (
-                   c, c, view["spp"], c * c * view["spp"], dt)}
-        crop = img[x0:x0 + c, x0:x0 + c].astype(np.float64)
-        rel = float(np.linalg.norm(crop - ref) / max(np.linalg.norm(ref), 1e-300))
-        elem = float(np.max(np.abs(crop - ref)) / max(np.max(np.abs(ref)), 1e-300))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -231,49 +231,112 @@ Box tri_box(const Tri& t) {
   return b;
 }
 
-// Plain median-split bounding-volume hierarchy over triangle centroids
-// (longest axis of the centroid bounds, leaves of at most 4 triangles).  It is
-// only an accelerator for the oracle's own closest-hit query, checked against
-// an exhaustive scan by the tests.
+// Binary bounding-volume hierarchy built top-down by the surface area
+// heuristic (MacDonald & Booth 1990) over 16 centroid bins per axis, one
+// triangle per leaf.  It is only an accelerator for the oracle's closest-hit
+// query (checked against an exhaustive scan by the tests) and the reference
+// tree whose node visits and triangle tests per query define the traversal
+// work the benchmark reports, independently of the GPU's tree.
+double box_half_area(const Box& b) {
+  V3 e = b.hi - b.lo;
+  return e.x * e.y + e.y * e.z + e.z * e.x;
+}
+
+Box box_union(const Box& a, const Box& b) {
+  Box r;
+  r.lo = v3(std::min(a.lo.x, b.lo.x), std::min(a.lo.y, b.lo.y), std::min(a.lo.z, b.lo.z));
+  r.hi = v3(std::max(a.hi.x, b.hi.x), std::max(a.hi.y, b.hi.y), std::max(a.hi.z, b.hi.z));
+  return r;
+}
+
 int build_bvh(Scene& S, int first, int count) {
-  BvhNode node;
   Box b = tri_box(S.tris[S.order[first]]);
-  for (int i = first + 1; i < first + count; ++i) {
-    Box t = tri_box(S.tris[S.order[i]]);
-    b.lo = v3(std::min(b.lo.x, t.lo.x), std::min(b.lo.y, t.lo.y), std::min(b.lo.z, t.lo.z));
-    b.hi = v3(std::max(b.hi.x, t.hi.x), std::max(b.hi.y, t.hi.y), std::max(b.hi.z, t.hi.z));
-  }
+  for (int i = first + 1; i < first + count; ++i) b = box_union(b, tri_box(S.tris[S.order[i]]));
+  BvhNode node;
   node.box = b;
   node.left = node.right = -1;
   node.first = first;
   node.count = count;
-  int idx = (int)S.nodes.size();
+  const int idx = (int)S.nodes.size();
   S.nodes.push_back(node);
-  if (count <= 4) return idx;
+  if (count <= 1) return idx;
   auto centroid = [&](int t) {
     const Tri& tr = S.tris[t];
     return (1.0 / 3.0) * (tr.v0 + tr.v1 + tr.v2);
   };
+  auto comp = [](V3 v, int a) { return a == 0 ? v.x : (a == 1 ? v.y : v.z); };
   V3 clo = centroid(S.order[first]), chi = clo;
   for (int i = first; i < first + count; ++i) {
     V3 c = centroid(S.order[i]);
     clo = v3(std::min(clo.x, c.x), std::min(clo.y, c.y), std::min(clo.z, c.z));
     chi = v3(std::max(chi.x, c.x), std::max(chi.y, c.y), std::max(chi.z, c.z));
   }
-  V3 ext = chi - clo;
-  int axis = (ext.x >= ext.y && ext.x >= ext.z) ? 0 : (ext.y >= ext.z ? 1 : 2);
-  auto key = [&](int t) {
-    V3 c = centroid(t);
-    return axis == 0 ? c.x : (axis == 1 ? c.y : c.z);
-  };
-  int mid = first + count / 2;
-  std::nth_element(S.order.begin() + first, S.order.begin() + mid, S.order.begin() + first + count,
-                   [&](int a, int b2) {
-                     double ka = key(a), kb = key(b2);
-                     return ka < kb || (ka == kb && a < b2);
-                   });
-  int l = build_bvh(S, first, mid - first);
-  int r = build_bvh(S, mid, first + count - mid);
+  // best (axis, bin boundary) by SAH cost A_left n_left + A_right n_right
+  const int NB = 16;
+  int best_axis = -1, best_split = -1;
+  double best_cost = 1e300;
+  for (int a = 0; a < 3; ++a) {
+    const double lo = comp(clo, a), ext = comp(chi, a) - lo;
+    if (!(ext > 0.0)) continue;
+    int cnt[NB] = {0};
+    Box bb[NB];
+    bool has[NB] = {false};
+    for (int i = first; i < first + count; ++i) {
+      int k = (int)(NB * (comp(centroid(S.order[i]), a) - lo) / ext);
+      k = std::min(NB - 1, std::max(0, k));
+      const Box t = tri_box(S.tris[S.order[i]]);
+      bb[k] = has[k] ? box_union(bb[k], t) : t;
+      has[k] = true;
+      ++cnt[k];
+    }
+    // suffix areas, then sweep the boundaries left to right
+    double right_area[NB];
+    int right_cnt[NB];
+    Box acc;
+    bool any = false;
+    int c = 0;
+    for (int k = NB - 1; k >= 1; --k) {
+      if (has[k]) {
+        acc = any ? box_union(acc, bb[k]) : bb[k];
+        any = true;
+      }
+      c += cnt[k];
+      right_area[k] = any ? box_half_area(acc) : 0.0;
+      right_cnt[k] = c;
+    }
+    any = false;
+    c = 0;
+    for (int k = 0; k < NB - 1; ++k) {
+      if (has[k]) {
+        acc = any ? box_union(acc, bb[k]) : bb[k];
+        any = true;
+      }
+      c += cnt[k];
+      if (c == 0 || right_cnt[k + 1] == 0) continue;
+      const double cost = box_half_area(acc) * c + right_area[k + 1] * right_cnt[k + 1];
+      if (cost < best_cost) {
+        best_cost = cost;
+        best_axis = a;
+        best_split = k + 1;
+      }
+    }
+  }
+  int mid;
+  if (best_axis < 0) {
+    mid = first + count / 2;  // coincident centroids: split the range in half
+  } else {
+    const double lo = comp(clo, best_axis), ext = comp(chi, best_axis) - lo;
+    auto left_of = [&](int t) {
+      int k = (int)(NB * (comp(centroid(t), best_axis) - lo) / ext);
+      k = std::min(NB - 1, std::max(0, k));
+      return k < best_split;
+    };
+    mid = (int)(std::stable_partition(S.order.begin() + first, S.order.begin() + first + count, left_of) -
+                S.order.begin());
+    if (mid == first || mid == first + count) mid = first + count / 2;
+  }
+  const int l = build_bvh(S, first, mid - first);
+  const int r = build_bvh(S, mid, first + count - mid);
   S.nodes[idx].left = l;
   S.nodes[idx].right = r;
   S.nodes[idx].count = 0;
@@ -301,13 +364,15 @@ double intersect_tri(const Tri& T, V3 o, V3 d) {
 // hits closer than T_MIN metres, and the primitive just left, are ignored.
 const double T_MIN = 1e-5;
 
-bool box_hit(const Box& b, V3 o, V3 d, double tmax) {
+// Entry distance of the ray into the box (>= 0), or -1 when it misses the box
+// or enters beyond tmax.
+double box_entry(const Box& b, V3 o, V3 d, double tmax) {
   double t0 = 0.0, t1 = tmax;
   double oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
   double lo[3] = {b.lo.x, b.lo.y, b.lo.z}, hi[3] = {b.hi.x, b.hi.y, b.hi.z};
   for (int a = 0; a < 3; ++a) {
     if (dd[a] == 0.0) {
-      if (oo[a] < lo[a] || oo[a] > hi[a]) return false;
+      if (oo[a] < lo[a] || oo[a] > hi[a]) return -1.0;
       continue;
     }
     double ta = (lo[a] - oo[a]) / dd[a], tb = (hi[a] - oo[a]) / dd[a];
@@ -318,18 +383,25 @@ bool box_hit(const Box& b, V3 o, V3 d, double tmax) {
     tb += pad;
     t0 = std::max(t0, ta);
     t1 = std::min(t1, tb);
-    if (t0 > t1) return false;
+    if (t0 > t1) return -1.0;
   }
-  return true;
+  return t0;
 }
+
+// Traversal work of the closest-hit queries made since the last reset, over
+// every thread: queries, internal node visits (two child boxes tested each)
+// and ray-triangle tests.
+std::atomic<long long> g_work_queries{0}, g_work_visits{0}, g_work_tests{0};
 
 // Closest hit with t > T_MIN, excluding one primitive; equal distances resolve
 // to the lower primitive id.
 bool closest_hit(const Scene& S, V3 o, V3 d, int exclude, bool use_bvh, double* t_out, int* prim_out) {
   double best = 1e300;
   int bi = -1;
+  long long visits = 0, tests = 0;
   auto test = [&](int i) {
     if (i == exclude) return;
+    ++tests;
     double t = intersect_tri(S.tris[i], o, d);
     if (t > T_MIN && (t < best || (t == best && i < bi))) {
       best = t;
@@ -338,22 +410,57 @@ bool closest_hit(const Scene& S, V3 o, V3 d, int exclude, bool use_bvh, double* 
   };
   if (!use_bvh || S.nodes.empty()) {
     for (int i = 0; i < (int)S.tris.size(); ++i) test(i);
+  } else if (S.nodes[0].left < 0) {
+    test(S.order[S.nodes[0].first]);
   } else {
+    // nearer child first, the farther one stacked; leaf children tested at once
     std::vector<int> stack;
-    stack.push_back(0);
-    while (!stack.empty()) {
-      int ni = stack.back();
-      stack.pop_back();
+    int ni = 0;
+    for (;;) {
+      ++visits;
       const BvhNode& n = S.nodes[ni];
-      if (!box_hit(n.box, o, d, best)) continue;
-      if (n.left < 0) {
-        for (int k = n.first; k < n.first + n.count; ++k) test(S.order[k]);
-      } else {
-        stack.push_back(n.left);
-        stack.push_back(n.right);
+      int next[2];
+      double tn[2];
+      int m = 0;
+      for (int c = 0; c < 2; ++c) {
+        const int ch = c == 0 ? n.left : n.right;
+        const BvhNode& cn = S.nodes[ch];
+        const double te = box_entry(cn.box, o, d, best);
+        if (te < 0.0) continue;
+        if (cn.left < 0) {
+          test(S.order[cn.first]);
+        } else {
+          next[m] = ch;
+          tn[m] = te;
+          ++m;
+        }
       }
+      if (m == 2) {
+        const bool swap = tn[1] < tn[0];
+        stack.push_back(swap ? next[0] : next[1]);
+        ni = swap ? next[1] : next[0];
+        continue;
+      }
+      if (m == 1) {
+        ni = next[0];
+        continue;
+      }
+      // pop, skipping subtrees now beyond the best hit
+      ni = -1;
+      while (!stack.empty()) {
+        const int cand = stack.back();
+        stack.pop_back();
+        if (box_entry(S.nodes[cand].box, o, d, best) >= 0.0) {
+          ni = cand;
+          break;
+        }
+      }
+      if (ni < 0) break;
     }
   }
+  g_work_queries.fetch_add(1, std::memory_order_relaxed);
+  g_work_visits.fetch_add(visits, std::memory_order_relaxed);
+  g_work_tests.fetch_add(tests, std::memory_order_relaxed);
   if (bi < 0) return false;
   *t_out = best;
   *prim_out = bi;
@@ -1487,6 +1594,20 @@ void* oracle_scene_create(int n_tris, const float* verts, const int* tri_mat, in
 }
 
 void oracle_scene_destroy(void* s) { delete (Scene*)s; }
+
+// Traversal work since the last reset: out[0] closest-hit queries, out[1]
+// internal node visits, out[2] ray-triangle tests (summed over threads).
+void oracle_work_counters(long long* out) {
+  out[0] = g_work_queries.load();
+  out[1] = g_work_visits.load();
+  out[2] = g_work_tests.load();
+}
+
+void oracle_work_reset(void) {
+  g_work_queries = 0;
+  g_work_visits = 0;
+  g_work_tests = 0;
+}
 
 int oracle_closest_hit(void* s, const double* o, const double* d, int exclude, int use_bvh, double* t, int* prim) {
   Scene* S = (Scene*)s;

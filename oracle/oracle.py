@@ -95,6 +95,8 @@ def lib():
     L.oracle_aniso_propagate.argtypes = [P, D, P]
     L.oracle_aniso_interaction.argtypes = [P, P, P, P, P, P, P]
     L.oracle_aniso_emitter.argtypes = [P, P, P, D, D, P, D, D, P]
+    L.oracle_work_counters.argtypes = [P]
+    L.oracle_work_reset.argtypes = []
     _lib = L
     return L
 
@@ -105,6 +107,20 @@ def _p(a):
 
 def _d3(v):
     return np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(3))
+
+
+# ------------------------------------------------------------------ traversal work
+def work_reset():
+    """Zero the oracle's traversal-work counters."""
+    lib().oracle_work_reset()
+
+
+def work_counters():
+    """Closest-hit queries, internal node visits and ray-triangle tests of the
+    oracle's SAH reference tree since the last reset."""
+    o = np.zeros(3, dtype=np.int64)
+    lib().oracle_work_counters(_p(o))
+    return {"queries": int(o[0]), "node_visits": int(o[1]), "tri_tests": int(o[2])}
 
 
 # ------------------------------------------------------------------ primitives
