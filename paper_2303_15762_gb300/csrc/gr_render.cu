@@ -635,15 +635,17 @@ __global__ void __launch_bounds__(TREE == kTreeWide ? 256 : GR_TRACE_BLOCK, TREE
     lane_trace<TREE == kTreeHalf>(
         p, n, &p.ctr->trace_next, [&](int e) { return tq_entry(p, e, front); },
         [&](int slot, float3& o, float3& d, int& exclude) -> const DevScene& {
-          const int4 m = P.meta[slot];
-          const float4 a = P.od0[slot], b = P.od1[slot];
+          // the slot state is read once per segment: evict-first loads keep
+          // it from displacing the BVH and triangles in L2
+          const int4 m = __ldcs(&P.meta[slot]);
+          const float4 a = __ldcs(&P.od0[slot]), b = __ldcs(&P.od1[slot]);
           o = xyz(a);
           d = xyz(b);
           exclude = m.w;
           return p.scenes[p.views[m.x].scene_index];
         },
-        [&](int slot, const Hit& h) { P.hit[slot] = make_float2(h.t, __int_as_float(h.slot)); }, refined, visits,
-        tests, err);
+        [&](int slot, const Hit& h) { __stcs(&P.hit[slot], make_float2(h.t, __int_as_float(h.slot))); }, refined,
+        visits, tests, err);
   }
   block_count(&p.ctr->ref_hit, refined);
   block_count(&p.ctr->node_visits, visits);

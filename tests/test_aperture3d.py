@@ -10,7 +10,7 @@ elements, the extension of the double-slit validation of Sec. 5.1-5.2.
   tangent-plane direction grid) reproduce the exact forward computation:
   within 1e-3 of the peak without truncation and 1e-2 with the Sec. 6
   truncation at 2.5 beta', and element by element at a steep direction, where
-  the grid's measure k^2 s_z^4 d^2t departs from k^2 d^2t by 15%.
+  the grid's measure k^2 s_z^4 d^2t departs from k^2 d^2t by 7%.
 """
 import math
 
