@@ -331,6 +331,11 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
   // regeneration threshold: new tickets are claimed only while enough of the
   // pool was idle after the previous iteration (or when nothing is active)
   const int active_prev = *(volatile int*)&p.ctr->last_active;
+  // the render is complete (no slot was live in the previous iteration and no
+  // ticket is left): nothing to fold, claim or queue -- the iterations the
+  // host loop runs past the end (it reads the counters a batch late) cost a
+  // launch, not a scan of every slot
+  if (active_prev == 0 && *(volatile unsigned long long*)&p.ctr->next_ticket >= p.ctr->total_tickets) return;
   const bool may_claim = p.regen_thr <= 0 || active_prev == 0 ||
                          (long long)(p.P - active_prev) * 100 >= (long long)p.regen_thr * p.P;
   // the views' first tickets, for the claims' view search (batches of views)
