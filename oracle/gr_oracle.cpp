@@ -978,25 +978,81 @@ void throughput_column(const PathState& P, int ns, double* out) {
   for (int i = 0; i < 4; ++i) out[i] = P.T.m[i][0];
 }
 
-void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
-  const Scene& S = *C.S;
-  const View& V = *C.V;
-  const int ns = V.n_stokes;
-  for (int i = 0; i < 16; ++i) result[i] = 0.0;
-  Rng rng = C.rng;
-  rng.pixel = (uint32_t)(py * V.W + px);
-  rng.sample = (uint32_t)sample;
+// The state one path sample carries (Algorithm 1): the generalized ray and
+// its throughput, the anisotropic footprint (FLAG_ANISO, R25) and the
+// hero-wavelength class (FLAG_HERO, R24), with the sample's result.
+//
+// Hero-wavelength spectral MIS (Sec. 7.2, after Wilkie et al. 2014): the
+// path's bin is the hero of the class of G = 4 bins {c, c+Q, c+2Q, c+3Q}
+// (Q = n_bins / 4) and drives every sampling decision.  q[g] is the
+// probability density of the path sampled so far at class bin g's
+// wavelength divided by its density at the hero's; it stays 1 through
+// wavelength-independent decisions and drops to 0 at a dispersive delta
+// (a grating order j != 0, a dispersive dielectric), where no other
+// wavelength could have made the same path.  Every connection to a light is
+// measured at each class wavelength (with that wavelength's footprint,
+// carried along the path in b2/rho) and weighted by multiple importance
+// sampling over the techniques that could have made the path, with
+// cf_j = share of the class's samples whose hero is bin j:
+//  - an escape, or an emitter hit whose last direction only the lobe could
+//    have sampled: balance heuristic over the class wavelengths,
+//    T M_g cf_g q_g / sum_j cf_j q_j;
+//  - an emitter hit after a diffuse rough vertex, and next-event estimation,
+//    with NEE on: power heuristic over the eight (wavelength j, technique t
+//    = lobe or emitter sampling) pairs with full path densities
+//    cf_j P_j p_{j,t}; with one hero per class it is the plain estimator's
+//    power heuristic between lobe and emitter sampling.
+// result[4 g + k] is class bin g's Stokes component k.
+struct HeroClass {
+  bool on = false;
+  int G = 1, gh = 0, c0 = 0;
+  double lam[4], k[4], cf[4];
+  double q[4];        // path density at class wavelength g over the hero's
+  double qpre[4];     // q before the latest interaction
+  double b2[4], rho[4];  // the footprint the path has at class wavelength g
+  void drop_companions() {
+    for (int g = 0; g < G; ++g)
+      if (g != gh) q[g] = 0.0;
+  }
+};
 
-  // --- sourcing (Eq. MC_sourcing; Sec. 7.2): position uniform on the pixel,
-  // rho = 0, beta = f_beta * pixel pitch, alpha = 1, wavelength of bin s mod B.
-  double u[4];
-  rng.draw(0, CALL_JITTER, u);
-  int bin = (int)(sample % V.n_bins);
+struct Sample {
+  const Ctx& C;
+  const Scene& S;
+  const View& V;
+  int ns;
+  Rng rng;
+  double* result;
   PathState P;
+  bool aniso;
+  CS2 K;          // anisotropic footprint (FLAG_ANISO)
+  HeroClass H;
+  double beta0;
+  int n_emit;
+  Sample(const Ctx& c, double* res)
+      : C(c), S(*c.S), V(*c.V), ns(c.V->n_stokes), rng(c.rng), result(res), aniso((c.flags & FLAG_ANISO) != 0) {}
+  // the vMF density of emitter sampling toward w at class wavelength g
+  double nee_density(int g, V3 w, V3 ne, double coh_len_um) const {
+    const double s2g = 1.0 / (2.0 * beta0 * beta0 * H.k[g] * H.k[g]);
+    return vmf(w, neg(ne), 1.0 / (s2g + source_spread2(H.lam[g], coh_len_um))) / n_emit;
+  }
+};
+
+// --- sourcing (Eq. MC_sourcing; Sec. 7.2): position uniform on the pixel,
+// rho = 0, beta = f_beta * pixel pitch, alpha = 1, wavelength of bin s mod B.
+void source(Sample& W, int px, int py, long sample) {
+  const View& V = W.V;
+  for (int i = 0; i < 16; ++i) W.result[i] = 0.0;
+  W.rng.pixel = (uint32_t)(py * V.W + px);
+  W.rng.sample = (uint32_t)sample;
+  double u[4];
+  W.rng.draw(0, CALL_JITTER, u);
+  const int bin = (int)(sample % V.n_bins);
+  PathState& P = W.P;
   P.lambda = bin_lambda(V, bin);
   P.k = 2.0 * PI / P.lambda;
-  double beta0 = V.f_beta * V.p_pix_um;
-  P.beta2 = beta0 * beta0;
+  W.beta0 = V.f_beta * V.p_pix_um;
+  P.beta2 = W.beta0 * W.beta0;
   P.rho = 0.0;
   P.s_ray2 = (1.0 + P.rho * P.rho) / (2.0 * P.beta2) / (P.k * P.k);
   V3 fw = normalize(V.look - V.eye);
@@ -1021,407 +1077,470 @@ void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
   P.xf = normalize(right - dot(right, P.d) * P.d);
   P.prev_delta = true;
   P.prev_pdf = 0.0;
-  const int n_emit = (int)S.emitters.size();
-  // anisotropic footprint (FLAG_ANISO): the camera state is isotropic,
-  // K = beta0^2 I (rho = 0)
-  const bool aniso = (C.flags & FLAG_ANISO) != 0;
-  CS2 K{cplx(P.beta2, 0.0), cplx(0.0, 0.0), cplx(P.beta2, 0.0)};
+  W.n_emit = (int)W.S.emitters.size();
+  // anisotropic footprint: the camera state is isotropic, K = beta0^2 I (rho = 0)
+  W.K = CS2{cplx(P.beta2, 0.0), cplx(0.0, 0.0), cplx(P.beta2, 0.0)};
+  // the hero's class: its wavelengths, sample shares and footprints
+  HeroClass& H = W.H;
+  H.on = (W.C.flags & FLAG_HERO) != 0;
+  H.G = H.on ? 4 : 1;
+  const int Qb = V.n_bins / H.G;
+  H.gh = H.on ? bin / Qb : 0;
+  H.c0 = bin - H.gh * Qb;
+  long ncls = 0, nb_g[4];
+  for (int g = 0; g < H.G; ++g) {
+    H.lam[g] = bin_lambda(V, H.c0 + g * Qb);
+    H.q[g] = 1.0;
+    nb_g[g] = H.on ? bin_count(V, H.c0 + g * Qb) : 1;
+    ncls += nb_g[g];
+  }
+  for (int g = 0; g < H.G; ++g) H.cf[g] = (double)nb_g[g] / (double)ncls;
+  for (int g = 0; g < H.G; ++g) {
+    H.qpre[g] = 1.0;
+    H.b2[g] = P.beta2;
+    H.rho[g] = P.rho;
+    H.k[g] = 2.0 * PI / H.lam[g];
+  }
+}
 
-  // Hero-wavelength spectral MIS (Sec. 7.2, after Wilkie et al. 2014): the
-  // path's bin is the hero of the class of G = 4 bins {c, c+Q, c+2Q, c+3Q}
-  // (Q = n_bins / 4) and drives every sampling decision.  q[g] is the
-  // probability density of the path sampled so far at class bin g's
-  // wavelength divided by its density at the hero's; it stays 1 through
-  // wavelength-independent decisions and drops to 0 at a dispersive delta
-  // (a grating order j != 0, a dispersive dielectric), where no other
-  // wavelength could have made the same path.  Every connection to a light is
-  // measured at each class wavelength (with that wavelength's footprint,
-  // carried along the path in fb2/frho) and weighted by multiple importance
-  // sampling over the techniques that could have made the path, with
-  // cf_j = share of the class's samples whose hero is bin j:
-  //  - an escape, or an emitter hit whose last direction only the lobe could
-  //    have sampled: balance heuristic over the class wavelengths,
-  //    T M_g cf_g q_g / sum_j cf_j q_j;
-  //  - an emitter hit after a diffuse rough vertex, and next-event estimation,
-  //    with NEE on: power heuristic over the eight (wavelength j, technique t
-  //    = lobe or emitter sampling) pairs with full path densities
-  //    cf_j P_j p_{j,t}; with one hero per class it is the plain estimator's
-  //    power heuristic between lobe and emitter sampling.
-  // result[4 g + k] is class bin g's Stokes component k.
-  const bool hero = (C.flags & FLAG_HERO) != 0;
-  const int G = hero ? 4 : 1, Qb = V.n_bins / G;
-  const int gh = hero ? bin / Qb : 0;
-  const int c0 = bin - gh * Qb;
-  double lam_g[4], q[4], cf[4];
-  {
-    long ncls = 0, nb_g[4];
-    for (int g = 0; g < G; ++g) {
-      lam_g[g] = bin_lambda(V, c0 + g * Qb);
-      q[g] = 1.0;
-      nb_g[g] = hero ? bin_count(V, c0 + g * Qb) : 1;
-      ncls += nb_g[g];
+// --- measurement of distant sources on escape (Eq. measurement_operator);
+// col is the throughput column of the path
+void measure_escape(Sample& W, const double* col) {
+  const PathState& P = W.P;
+  const HeroClass& H = W.H;
+  if (!H.on) {
+    double m = 0.0;
+    for (const Light& L : W.S.lights)
+      m += W.aniso ? measure_distant_aniso(L, P.d, P.lambda, P.k, W.K, P.xf) : measure_distant(L, P.d, P.lambda, P.s_ray2);
+    add_vec(W.result, W.ns, col, m);
+    return;
+  }
+  // every class wavelength, balance heuristic over the class
+  double den = 0.0;
+  for (int g = 0; g < H.G; ++g) den += H.cf[g] * H.q[g];
+  for (int g = 0; g < H.G; ++g) {
+    if (H.cf[g] * H.q[g] == 0.0) continue;
+    const double kg = 2.0 * PI / H.lam[g];
+    const double s2g = 1.0 / (2.0 * W.beta0 * W.beta0 * kg * kg);  // the invariant spread at lambda_g
+    double m = 0.0;
+    for (const Light& L : W.S.lights) m += measure_distant(L, P.d, H.lam[g], s2g);
+    add_vec(W.result + 4 * g, W.ns, col, m * H.cf[g] * H.q[g] / den);
+  }
+}
+
+// --- measurement of an emissive triangle hit at x (Eq. measurement_operator,
+// footprint-sampled), weighted against next-event estimation by MIS when the
+// last direction came from a diffuse rough lobe
+void measure_emitter_hit(Sample& W, int seg, int prim, V3 x, const double* col) {
+  const PathState& P = W.P;
+  const HeroClass& H = W.H;
+  const Tri& T = W.S.tris[prim];
+  const Material& M = W.S.mats[T.mat];
+  double u[4];
+  W.rng.draw(seg, CALL_EMIT_FOOT, u);
+  const bool two = (W.C.flags & FLAG_NEE) && !P.prev_delta && W.n_emit > 0;
+  if (H.on) {
+    const V3 ne = tri_normal(T);
+    const double pb = P.prev_pdf;  // the hero's lobe density of the last direction
+    // with two techniques, cf_j qpre_j p_{j,lobe} = cf_j q_j pb (q = qpre times
+    // the lobe density ratio of the last vertex)
+    double den = 0.0;
+    for (int j = 0; j < H.G; ++j) {
+      if (two) {
+        const double a = H.cf[j] * H.q[j] * pb, b = H.cf[j] * H.qpre[j] * W.nee_density(j, P.d, ne, M.coh_len_um);
+        den += a * a + b * b;
+      } else {
+        den += H.cf[j] * H.q[j];
+      }
     }
-    for (int g = 0; g < G; ++g) cf[g] = (double)nb_g[g] / (double)ncls;
+    for (int g = 0; g < H.G; ++g) {
+      if (H.cf[g] * H.q[g] == 0.0 || den == 0.0) continue;
+      const double m = measure_emitter(W.S, prim, x, P.d, H.b2[g], H.rho[g], H.k[g], H.lam[g], u[0], u[1]);
+      const double w = two ? H.cf[g] * H.cf[H.gh] * H.q[g] * pb * pb / den : H.cf[g] * H.q[g] / den;
+      add_vec(W.result + 4 * g, W.ns, col, m * w);
+    }
+    return;
   }
-  auto drop_companions = [&]() {
-    for (int g = 0; g < G; ++g)
-      if (g != gh) q[g] = 0.0;
-  };
-  // qpre: q before the latest interaction (the density ratio of the path up
-  // to the vertex whose outgoing direction is being weighted); fb2/frho: the
-  // footprint (beta^2, rho) the path has at class wavelength g
-  double qpre[4], fb2[4], frho[4], kcls[4];
-  for (int g = 0; g < G; ++g) {
-    qpre[g] = 1.0;
-    fb2[g] = P.beta2;
-    frho[g] = P.rho;
-    kcls[g] = 2.0 * PI / lam_g[g];
+  double m = W.aniso ? measure_emitter_aniso(W.S, prim, x, P.d, W.K, P.xf, P.k, P.lambda, u[0], u[1])
+                     : measure_emitter(W.S, prim, x, P.d, P.beta2, P.rho, P.k, P.lambda, u[0], u[1]);
+  double w = 1.0;
+  if (two) {
+    V3 ne = tri_normal(T);
+    double kap = 1.0 / (P.s_ray2 + source_spread2(P.lambda, M.coh_len_um));
+    double pn = vmf(neg(P.d), ne, kap) / W.n_emit;
+    double pb = P.prev_pdf;
+    w = pb * pb / (pb * pb + pn * pn);  // power heuristic
   }
-  // the vMF density of emitter sampling toward w at class wavelength g
-  auto nee_density = [&](int g, V3 w, V3 ne, double coh_len_um) {
-    const double s2g = 1.0 / (2.0 * beta0 * beta0 * kcls[g] * kcls[g]);
-    return vmf(w, neg(ne), 1.0 / (s2g + source_spread2(lam_g[g], coh_len_um))) / n_emit;
-  };
+  add_vec(W.result, W.ns, col, m * w);
+}
 
+// --- Russian roulette before interaction seg+1 once 3 interactions are done
+// (R14); false ends the path
+bool russian_roulette(Sample& W, int seg) {
+  if (!(W.C.flags & FLAG_RR) || seg < 3) return true;
+  PathState& P = W.P;
+  double q = std::min(1.0, std::max(0.05, W.ns == 1 ? P.t : P.T.m[0][0]));
+  double u[4];
+  W.rng.draw(seg, CALL_RR, u);
+  if (u[0] >= q) return false;
+  if (W.ns == 1)
+    P.t /= q;
+  else
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) P.T.m[i][j] /= q;
+  return true;
+}
+
+// A surface vertex of the path, as the interaction sees it (wavevector
+// reversed, Eq. action_time_reversal): the normal oriented against the
+// arriving direction, the Fresnel weight and the throughput it gives.
+struct Vertex {
+  int prim;
+  const Tri* T;
+  const Material* M;
+  V3 x, n, d_in, t_mir, s_o;
+  double cos_i;
+  V3 d_dielectric;   // a dielectric's chosen direction (reflected or refracted)
+  double eta_next;   // the medium index after the vertex
+  M4 TRM;            // throughput x frame rotation x Fresnel weight
+  double t_new;      // the scalar throughput after the vertex
+  double c_nee[4];   // the throughput column a next-event estimate carries
+};
+
+// Fresnel weight (Eq. K_reflection_refraction), as a Mueller matrix in the
+// s-p frames at the incidence angle of the arriving ray; diffractive lobes are
+// scaled by the same matrix (reading R12).  A dielectric chooses reflection or
+// refraction with the unpolarised reflectance R (R23).
+void interaction_weight(Sample& W, int seg, Vertex& X) {
+  const PathState& P = W.P;
+  const Material& M = *X.M;
+  M4 MF = m4_identity();
+  X.d_dielectric = X.d_in;
+  X.eta_next = P.eta;
+  if (M.type == MAT_DIELECTRIC) {
+    // the front (counter-clockwise) face looks out into air; reflection or
+    // refraction is chosen with the unpolarised reflectance R, and the
+    // Mueller weight divided by the choice's probability; a refracted
+    // radiance carries (eta_a / eta_b)^2 (camera side over light side)
+    const double eta_m = M.n_re + M.cauchy_b_um2 / (P.lambda * P.lambda);
+    const bool entering = dot(P.d, tri_normal(*X.T)) < 0.0;
+    const double eta_a = entering ? 1.0 : eta_m, eta_b = entering ? eta_m : 1.0;
+    const double n_rel = eta_b / eta_a;
+    Dielectric D;
+    fresnel_dielectric(X.cos_i, n_rel, &D);
+    double u[4];
+    W.rng.draw(seg, CALL_LOBE, u);
+    if (u[0] < D.R) {
+      MF = mueller_diag(D.rs, D.rp);
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) MF.m[i][j] /= D.R;
+      X.d_dielectric = X.d_in + (2.0 * X.cos_i) * X.n;
+    } else {
+      MF = mueller_diag(cplx(D.ts, 0.0), cplx(D.tp, 0.0));
+      const double f = (n_rel * D.cos_t / X.cos_i) * (eta_a / eta_b) * (eta_a / eta_b) / (1.0 - D.R);
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) MF.m[i][j] *= f;
+      X.d_dielectric = refract_dir(X.d_in, X.n, n_rel, X.cos_i, D.cos_t);
+      X.eta_next = eta_b;
+    }
+  } else if (M.fresnel == 1) {
+    cplx rs, rp;
+    fresnel_conductor(X.cos_i, M.n_re, M.n_im, &rs, &rp);
+    MF = mueller_diag(rs, rp);
+  }
+  // frame of the outgoing light of the forward problem (propagation -d_in)
+  V3 k_o = neg(X.d_in);
+  X.s_o = s_vector(X.n, k_o, P.xf);
+  V3 p_o = cross(k_o, X.s_o);
+  M4 Rot = stokes_rotation(frame_angle(X.s_o, p_o, P.xf));  // frame o -> current frame
+  X.TRM = m4_mul(m4_mul(P.T, Rot), MF);
+  X.t_new = P.t * MF.m[0][0];
+  if (W.ns == 1)
+    X.c_nee[0] = X.t_new;
+  else
+    for (int i = 0; i < 4; ++i) X.c_nee[i] = X.TRM.m[i][0];
+}
+
+// The sampled child ray of a vertex.
+struct Lobe {
+  V3 d_out;
+  bool delta = true;   // a delta lobe (grating order, mirror, specular term, dielectric)
+  double pdf = 0.0;    // the diffuse lobe's density of d_out (solid angle)
+  bool alive = true;   // false: the sample landed on an evanescent direction
+  double g_r = 0.0;    // rough surface: roughness g = (2 k sigma_h cos)^2
+  double m_rough = -1.0;           // rough surface: the Poisson term drawn
+  V3 delta_rough = v3(0.0, 0.0, 0.0);  // rough surface: the tangential offset drawn
+};
+
+// --- sample the scattered distribution (Eq. MC_light_transport_Q1): one
+// grating order (Eq. K_grating), the mirror direction, the dielectric's
+// choice, or a rough-surface term and offset (R11).  Returns false where no
+// order carries energy (the path ends).  With hero MIS a grating order
+// updates the class's density ratios here (R24).
+bool sample_lobe(Sample& W, int seg, const Vertex& X, Lobe& L) {
+  const PathState& P = W.P;
+  const Material& M = *X.M;
+  HeroClass& H = W.H;
+  double u[4];
+  W.rng.draw(seg, CALL_LOBE, u);
+  if (M.type == MAT_GRATING) {
+    Lobes O;
+    grating_lobes(M, X.d_in, X.n, P.lambda, !(W.C.flags & FLAG_NO_RENORM), &O);
+    if (O.n == 0) return false;
+    // first order (ascending j) whose cumulative weight exceeds u * total
+    double target = u[0] * O.total;
+    double cum = 0.0;
+    int pick = -1;
+    for (int i = 0; i < O.n; ++i) {
+      cum += O.w[i];
+      if (cum > target) {
+        pick = i;
+        break;
+      }
+    }
+    if (pick < 0) return false;  // only possible without renormalisation
+    L.d_out = O.dir[pick];
+    if (H.on) {
+      if (O.order[pick] != 0) {
+        H.drop_companions();  // the order's direction depends on lambda
+      } else {
+        // specular order: same direction at every wavelength, probability
+        // a_0 / total there
+        const double ph = O.w[pick] / O.total;
+        for (int g = 0; g < H.G; ++g) {
+          if (g == H.gh || H.q[g] == 0.0) continue;
+          Lobes Lg;
+          grating_lobes(M, X.d_in, X.n, H.lam[g], !(W.C.flags & FLAG_NO_RENORM), &Lg);
+          double p0 = 0.0;
+          for (int i = 0; i < Lg.n; ++i)
+            if (Lg.order[i] == 0) p0 = Lg.w[i] / Lg.total;
+          H.q[g] *= p0 / ph;
+        }
+      }
+    }
+  } else if (M.type == MAT_MIRROR) {
+    L.d_out = X.d_in + (2.0 * X.cos_i) * X.n;
+  } else if (M.type == MAT_DIELECTRIC) {
+    L.d_out = X.d_dielectric;  // chosen by interaction_weight with the same uniform
+  } else {  // MAT_ROUGH
+    L.g_r = std::pow(2.0 * P.k * M.sigma_h_um * X.cos_i, 2);
+    double m;
+    if (L.g_r > G_CONT) {
+      m = L.g_r;
+    } else {
+      // Poisson(g) by sequential inversion: first m with CDF(m) > u
+      double p = std::exp(-L.g_r), cdf = p;
+      int mi = 0;
+      while (u[0] >= cdf && mi < 1000) {
+        ++mi;
+        p *= L.g_r / mi;
+        cdf += p;
+      }
+      m = mi;
+    }
+    L.m_rough = m;
+    if (m == 0.0) {
+      L.d_out = X.d_in + (2.0 * X.cos_i) * X.n;
+    } else {
+      L.delta = false;
+      double kl = P.k * M.corr_len_um;
+      double sig = std::sqrt(2.0 * m / (kl * kl));
+      double z0, z1;
+      box_muller(u[1], u[2], &z0, &z1);
+      V3 e1, e2;
+      onb(X.n, &e1, &e2);
+      V3 delta_t = (sig * z0) * e1 + (sig * z1) * e2;
+      L.delta_rough = delta_t;
+      V3 t_out = X.t_mir + delta_t;
+      double tt = dot(t_out, t_out);
+      if (tt >= 1.0) {
+        L.alive = false;  // evanescent: no propagating energy
+      } else {
+        L.d_out = t_out + std::sqrt(1.0 - tt) * X.n;
+        L.pdf = rough_diffuse_density(L.g_r, P.k, M.corr_len_um, delta_t) * std::sqrt(1.0 - tt);
+      }
+    }
+  }
+  return true;
+}
+
+// --- hero MIS: the class wavelengths' densities of the rough-lobe term just
+// sampled (the specular term's probability e^-g, or the diffuse density at the
+// sampled offset; the cosine factor is common), and the companions dropped at
+// a dispersive dielectric (R24)
+void hero_vertex_ratios(Sample& W, const Vertex& X, const Lobe& L) {
+  const PathState& P = W.P;
+  const Material& M = *X.M;
+  HeroClass& H = W.H;
+  if (L.alive && M.type == MAT_ROUGH) {
+    for (int g = 0; g < H.G; ++g) {
+      if (g == H.gh || H.q[g] == 0.0) continue;
+      const double kg = 2.0 * PI / H.lam[g];
+      const double gg = std::pow(2.0 * kg * M.sigma_h_um * X.cos_i, 2);
+      if (L.m_rough == 0.0)  // specular term: probability e^{-g} (none in the continuous limit)
+        H.q[g] *= gg > G_CONT ? 0.0 : std::exp(L.g_r - gg);
+      else  // diffuse terms: density at the sampled offset (the cos factor is common)
+        H.q[g] *= rough_diffuse_density(gg, kg, M.corr_len_um, L.delta_rough) /
+                  rough_diffuse_density(L.g_r, P.k, M.corr_len_um, L.delta_rough);
+    }
+  }
+  if (M.type == MAT_DIELECTRIC && M.cauchy_b_um2 != 0.0) H.drop_companions();
+}
+
+// --- next-event estimation toward an emissive triangle (rough lobes only:
+// grating orders and mirror reflection are delta lobes; R21): a direction from
+// the vMF of the chosen emitter's measured lobe, a shadow ray that must reach
+// that emitter first, and the power heuristic against the rough lobe
+void next_event(Sample& W, int seg, const Vertex& X, const Lobe& L) {
+  const Material& M = *X.M;
+  if (M.type != MAT_ROUGH || !(W.C.flags & FLAG_NEE) || W.n_emit <= 0) return;
+  const PathState& P = W.P;
+  const HeroClass& H = W.H;
+  const Scene& S = W.S;
+  const int n_emit = W.n_emit;
+  double un[4], uf[4];
+  W.rng.draw(seg, CALL_NEE_DIR, un);
+  int ei = std::min(n_emit - 1, (int)(un[0] * n_emit));
+  const Tri& ET = S.tris[S.emitters[ei][0]];
+  const int emat = ET.mat;
+  const Material& EM = S.mats[emat];
+  V3 ne = tri_normal(ET);
+  double kap = 1.0 / (P.s_ray2 + source_spread2(P.lambda, EM.coh_len_um));
+  V3 w = vmf_sample(neg(ne), kap, un[1], un[2]);
+  double cos_o = dot(w, X.n);
+  if (cos_o <= 0.0) return;
+  double ts;
+  int sp;
+  if (!(closest_hit(S, X.x, w, X.prim, true, &ts, &sp) && S.tris[sp].mat == emat)) return;
+  V3 delta_t = (w - dot(w, X.n) * X.n) - X.t_mir;
+  double f = (L.g_r > 0.0 ? rough_diffuse_density(L.g_r, P.k, M.corr_len_um, delta_t) : 0.0) * cos_o;
+  double pn = vmf(w, neg(ne), kap) / n_emit;
+  if (H.on && pn > 0.0) {
+    // joint power heuristic over (class wavelength, technique); the lobe
+    // density toward w at wavelength j (the cos factor included)
+    double pbw[4], den = 0.0;
+    for (int j = 0; j < H.G; ++j) {
+      pbw[j] = 0.0;
+      if (H.cf[j] * H.qpre[j] == 0.0) continue;
+      const double gj = std::pow(2.0 * H.k[j] * M.sigma_h_um * X.cos_i, 2);
+      pbw[j] = (gj > 0.0 ? rough_diffuse_density(gj, H.k[j], M.corr_len_um, delta_t) : 0.0) * cos_o;
+      const double a = H.cf[j] * H.qpre[j] * pbw[j], b = H.cf[j] * H.qpre[j] * W.nee_density(j, w, ne, EM.coh_len_um);
+      den += a * a + b * b;
+    }
+    W.rng.draw(seg, CALL_NEE_FOOT, uf);
+    for (int g = 0; g < H.G; ++g) {
+      if (pbw[g] == 0.0 || den == 0.0) continue;
+      double b2 = H.b2[g], r = H.rho[g];
+      propagate(&b2, &r, ts * 1e6 / (H.k[g] * P.eta));
+      double m = measure_emitter(S, sp, X.x + ts * w, w, b2, r, H.k[g], H.lam[g], uf[0], uf[1]);
+      add_vec(W.result + 4 * g, W.ns, X.c_nee, m * H.cf[g] * H.cf[H.gh] * H.qpre[g] * pn * pbw[g] / den);
+    }
+  } else if (f > 0.0 && pn > 0.0 && W.aniso) {
+    // the vertex's footprint mapped to the emitter direction's frame
+    const V3 xf_w = s_vector(X.n, neg(w), X.s_o);
+    CS2 Kw = aniso_interaction(W.K, P.xf, X.d_in, xf_w, w, X.n);
+    aniso_propagate(&Kw, ts * 1e6 / (P.k * P.eta));
+    W.rng.draw(seg, CALL_NEE_FOOT, uf);
+    double m = measure_emitter_aniso(S, sp, X.x + ts * w, w, Kw, xf_w, P.k, P.lambda, uf[0], uf[1]);
+    double wmis = pn * pn / (pn * pn + f * f);
+    add_vec(W.result, W.ns, X.c_nee, m * f / pn * wmis);
+  } else if (f > 0.0 && pn > 0.0) {
+    double b2 = P.beta2, r = P.rho;
+    propagate(&b2, &r, ts * 1e6 / (P.k * P.eta));
+    W.rng.draw(seg, CALL_NEE_FOOT, uf);
+    double m = measure_emitter(S, sp, X.x + ts * w, w, b2, r, P.k, P.lambda, uf[0], uf[1]);
+    double wmis = pn * pn / (pn * pn + f * f);
+    add_vec(W.result, W.ns, X.c_nee, m * f / pn * wmis);
+  }
+}
+
+// --- continue the path with the sampled generalized ray: position and
+// (beta, rho) unchanged by the interaction (Eq. K_reflection_refraction; rho
+// growth at the grating ignored, Eq. K_grating); the anisotropic footprint is
+// mapped onto the outgoing direction's frame (R25)
+void continue_path(Sample& W, const Vertex& X, const Lobe& L) {
+  PathState& P = W.P;
+  if (W.aniso) {
+    const V3 xf_out = s_vector(X.n, neg(L.d_out), X.s_o);
+    W.K = aniso_interaction(W.K, P.xf, X.d_in, xf_out, L.d_out, X.n);
+    P.xf = xf_out;
+  }
+  if (W.ns == 1) {
+    P.t = X.t_new;
+  } else {
+    P.T = X.TRM;
+    V3 k_i = neg(L.d_out);
+    P.xf = s_vector(X.n, k_i, X.s_o);
+  }
+  P.o = X.x;
+  P.d = L.d_out;
+  P.eta = X.eta_next;
+  P.prev_prim = X.prim;
+  P.prev_delta = L.delta;
+  P.prev_pdf = L.pdf;
+}
+
+// One path sample of pixel (px, py), Algorithm 1 with the interactive
+// simplifications of Sec. 7.2: source, then per segment propagate (closest
+// hit, footprint update), measure (escape or emitter hit: the path ends),
+// Russian roulette, interact (weight, sampled child ray), next-event estimate,
+// continue.  result: the sample's contribution [Stokes] (with hero MIS
+// [class bin][Stokes]).
+void trace_sample(const Ctx& C, int px, int py, long sample, double* result) {
+  Sample W(C, result);
+  source(W, px, py, sample);
+  PathState& P = W.P;
+  HeroClass& H = W.H;
   for (int seg = 0;; ++seg) {
     // --- propagation: closest hit along d (point-hit assumption, Sec. 7.2)
     double th;
     int prim;
-    bool hit = closest_hit(S, P.o, P.d, P.prev_prim, true, &th, &prim);
+    bool hit = closest_hit(W.S, P.o, P.d, P.prev_prim, true, &th, &prim);
     double col[4];
-    throughput_column(P, ns, col);
+    throughput_column(P, W.ns, col);
     if (!hit) {
-      // --- measurement of distant sources on escape
-      if (!hero) {
-        double m = 0.0;
-        for (const Light& L : S.lights)
-          m += aniso ? measure_distant_aniso(L, P.d, P.lambda, P.k, K, P.xf) : measure_distant(L, P.d, P.lambda, P.s_ray2);
-        add_vec(result, ns, col, m);
-        return;
-      }
-      double den = 0.0;
-      for (int g = 0; g < G; ++g) den += cf[g] * q[g];
-      for (int g = 0; g < G; ++g) {
-        if (cf[g] * q[g] == 0.0) continue;
-        const double kg = 2.0 * PI / lam_g[g];
-        const double s2g = 1.0 / (2.0 * beta0 * beta0 * kg * kg);  // the invariant spread at lambda_g
-        double m = 0.0;
-        for (const Light& L : S.lights) m += measure_distant(L, P.d, lam_g[g], s2g);
-        add_vec(result + 4 * g, ns, col, m * cf[g] * q[g] / den);
-      }
+      measure_escape(W, col);
       return;
     }
-    // footprint update over the segment (z in um; |k| = eta k0 in a medium)
+    // footprint update over the segment (z in um; |k| = eta k0 in a medium;
+    // Eq. K_free_space_propagation)
     propagate(&P.beta2, &P.rho, th * 1e6 / (P.k * P.eta));
-    if (aniso) aniso_propagate(&K, th * 1e6 / (P.k * P.eta));
-    if (hero)
-      for (int g = 0; g < G; ++g) propagate(&fb2[g], &frho[g], th * 1e6 / (kcls[g] * P.eta));
+    if (W.aniso) aniso_propagate(&W.K, th * 1e6 / (P.k * P.eta));
+    if (H.on)
+      for (int g = 0; g < H.G; ++g) propagate(&H.b2[g], &H.rho[g], th * 1e6 / (H.k[g] * P.eta));
     V3 x = P.o + th * P.d;
-    const Tri& T = S.tris[prim];
-    const Material& M = S.mats[T.mat];
-    if (M.type == MAT_EMITTER && hero) {
-      rng.draw(seg, CALL_EMIT_FOOT, u);
-      const V3 ne = tri_normal(T);
-      const bool two = (C.flags & FLAG_NEE) && !P.prev_delta && n_emit > 0;
-      const double pb = P.prev_pdf;  // the hero's lobe density of the last direction
-      // with two techniques, cf_j qpre_j p_{j,lobe} = cf_j q_j pb (q = qpre times
-      // the lobe density ratio of the last vertex)
-      double den = 0.0;
-      for (int j = 0; j < G; ++j) {
-        if (two) {
-          const double a = cf[j] * q[j] * pb, b = cf[j] * qpre[j] * nee_density(j, P.d, ne, M.coh_len_um);
-          den += a * a + b * b;
-        } else {
-          den += cf[j] * q[j];
-        }
-      }
-      for (int g = 0; g < G; ++g) {
-        if (cf[g] * q[g] == 0.0 || den == 0.0) continue;
-        const double m = measure_emitter(S, prim, x, P.d, fb2[g], frho[g], kcls[g], lam_g[g], u[0], u[1]);
-        const double w = two ? cf[g] * cf[gh] * q[g] * pb * pb / den : cf[g] * q[g] / den;
-        add_vec(result + 4 * g, ns, col, m * w);
-      }
-      return;
-    }
+    const Tri& T = W.S.tris[prim];
+    const Material& M = W.S.mats[T.mat];
     if (M.type == MAT_EMITTER) {
-      rng.draw(seg, CALL_EMIT_FOOT, u);
-      double m = aniso ? measure_emitter_aniso(S, prim, x, P.d, K, P.xf, P.k, P.lambda, u[0], u[1])
-                       : measure_emitter(S, prim, x, P.d, P.beta2, P.rho, P.k, P.lambda, u[0], u[1]);
-      double w = 1.0;
-      if ((C.flags & FLAG_NEE) && !P.prev_delta && n_emit > 0) {
-        V3 ne = tri_normal(T);
-        double kap = 1.0 / (P.s_ray2 + source_spread2(P.lambda, M.coh_len_um));
-        double pn = vmf(neg(P.d), ne, kap) / n_emit;
-        double pb = P.prev_pdf;
-        w = pb * pb / (pb * pb + pn * pn);
-      }
-      add_vec(result, ns, col, m * w);
+      measure_emitter_hit(W, seg, prim, x, col);
       return;
     }
     if (M.type == MAT_ABSORBER) return;
-    if (seg >= V.max_depth) return;  // no interactions left
-    // Russian roulette before interaction seg+1 once 3 interactions are done
-    if ((C.flags & FLAG_RR) && seg >= 3) {
-      double q = std::min(1.0, std::max(0.05, ns == 1 ? P.t : P.T.m[0][0]));
-      rng.draw(seg, CALL_RR, u);
-      if (u[0] >= q) return;
-      if (ns == 1)
-        P.t /= q;
-      else
-        for (int i = 0; i < 4; ++i)
-          for (int j = 0; j < 4; ++j) P.T.m[i][j] /= q;
-    }
+    if (seg >= W.V.max_depth) return;  // no interactions left
+    if (!russian_roulette(W, seg)) return;
 
     // --- light-matter interaction with the wavevector reversed (Eq.
     // action_time_reversal): the surface normal is oriented against d.
-    V3 n = tri_normal(T);
-    if (dot(n, P.d) > 0.0) n = neg(n);
-    double cos_i = -dot(P.d, n);
-    V3 d_in = P.d;
-    for (int g = 0; g < G; ++g) qpre[g] = q[g];
-
-    // Fresnel weight (Eq. K_reflection_refraction), as a Mueller matrix in the
-    // s-p frames at the incidence angle of the arriving ray; diffractive lobes
-    // are scaled by the same matrix (reading).
-    M4 MF = m4_identity();
-    V3 d_dielectric = d_in;
-    double eta_next = P.eta;
-    if (M.type == MAT_DIELECTRIC) {
-      // the front (counter-clockwise) face looks out into air; reflection or
-      // refraction is chosen with the unpolarised reflectance R, and the
-      // Mueller weight divided by the choice's probability; a refracted
-      // radiance carries (eta_a / eta_b)^2 (camera side over light side)
-      const double eta_m = M.n_re + M.cauchy_b_um2 / (P.lambda * P.lambda);
-      const bool entering = dot(P.d, tri_normal(T)) < 0.0;
-      const double eta_a = entering ? 1.0 : eta_m, eta_b = entering ? eta_m : 1.0;
-      const double n_rel = eta_b / eta_a;
-      Dielectric D;
-      fresnel_dielectric(cos_i, n_rel, &D);
-      rng.draw(seg, CALL_LOBE, u);
-      if (u[0] < D.R) {
-        MF = mueller_diag(D.rs, D.rp);
-        for (int i = 0; i < 4; ++i)
-          for (int j = 0; j < 4; ++j) MF.m[i][j] /= D.R;
-        d_dielectric = d_in + (2.0 * cos_i) * n;
-      } else {
-        MF = mueller_diag(cplx(D.ts, 0.0), cplx(D.tp, 0.0));
-        const double f = (n_rel * D.cos_t / cos_i) * (eta_a / eta_b) * (eta_a / eta_b) / (1.0 - D.R);
-        for (int i = 0; i < 4; ++i)
-          for (int j = 0; j < 4; ++j) MF.m[i][j] *= f;
-        d_dielectric = refract_dir(d_in, n, n_rel, cos_i, D.cos_t);
-        eta_next = eta_b;
-      }
-    } else if (M.fresnel == 1) {
-      cplx rs, rp;
-      fresnel_conductor(cos_i, M.n_re, M.n_im, &rs, &rp);
-      MF = mueller_diag(rs, rp);
-    }
-    // frame of the outgoing light of the forward problem (propagation -d_in)
-    V3 k_o = neg(d_in);
-    V3 s_o = s_vector(n, k_o, P.xf);
-    V3 p_o = cross(k_o, s_o);
-    V3 y_cur = cross(k_o, P.xf);
-    M4 Rot = stokes_rotation(frame_angle(s_o, p_o, P.xf));  // frame o -> current frame
-    (void)y_cur;
-    M4 TRM = m4_mul(m4_mul(P.T, Rot), MF);
-    double t_new = P.t * MF.m[0][0];
-    double c_nee[4];
-    if (ns == 1)
-      c_nee[0] = t_new;
-    else
-      for (int i = 0; i < 4; ++i) c_nee[i] = TRM.m[i][0];
-
-    // --- sample the scattered distribution (Eq. MC_light_transport_Q1)
-    rng.draw(seg, CALL_LOBE, u);
-    V3 d_out;
-    bool delta = true;
-    double pdf = 0.0;
-    bool alive = true;
-    double g_r = 0.0;
-    double m_rough = -1.0;
-    V3 delta_rough = v3(0.0, 0.0, 0.0);
-    V3 t_mir = d_in - dot(d_in, n) * n;
-    if (M.type == MAT_GRATING) {
-      Lobes L;
-      grating_lobes(M, d_in, n, P.lambda, !(C.flags & FLAG_NO_RENORM), &L);
-      if (L.n == 0) return;
-      // first order (ascending j) whose cumulative weight exceeds u * total
-      double target = u[0] * L.total;
-      double cum = 0.0;
-      int pick = -1;
-      for (int i = 0; i < L.n; ++i) {
-        cum += L.w[i];
-        if (cum > target) {
-          pick = i;
-          break;
-        }
-      }
-      if (pick < 0) return;  // only possible without renormalisation
-      d_out = L.dir[pick];
-      if (hero) {
-        if (L.order[pick] != 0) {
-          drop_companions();  // the order's direction depends on lambda
-        } else {
-          // specular order: same direction at every wavelength, probability
-          // a_0 / total there
-          const double ph = L.w[pick] / L.total;
-          for (int g = 0; g < G; ++g) {
-            if (g == gh || q[g] == 0.0) continue;
-            Lobes Lg;
-            grating_lobes(M, d_in, n, lam_g[g], !(C.flags & FLAG_NO_RENORM), &Lg);
-            double p0 = 0.0;
-            for (int i = 0; i < Lg.n; ++i)
-              if (Lg.order[i] == 0) p0 = Lg.w[i] / Lg.total;
-            q[g] *= p0 / ph;
-          }
-        }
-      }
-    } else if (M.type == MAT_MIRROR) {
-      d_out = d_in + (2.0 * cos_i) * n;
-    } else if (M.type == MAT_DIELECTRIC) {
-      d_out = d_dielectric;  // chosen above with the same uniform
-    } else {  // MAT_ROUGH
-      g_r = std::pow(2.0 * P.k * M.sigma_h_um * cos_i, 2);
-      double m;
-      if (g_r > G_CONT) {
-        m = g_r;
-      } else {
-        // Poisson(g) by sequential inversion: first m with CDF(m) > u
-        double p = std::exp(-g_r), cdf = p;
-        int mi = 0;
-        while (u[0] >= cdf && mi < 1000) {
-          ++mi;
-          p *= g_r / mi;
-          cdf += p;
-        }
-        m = mi;
-      }
-      m_rough = m;
-      if (m == 0.0) {
-        d_out = d_in + (2.0 * cos_i) * n;
-      } else {
-        delta = false;
-        double kl = P.k * M.corr_len_um;
-        double sig = std::sqrt(2.0 * m / (kl * kl));
-        double z0, z1;
-        box_muller(u[1], u[2], &z0, &z1);
-        V3 e1, e2;
-        onb(n, &e1, &e2);
-        V3 delta_t = (sig * z0) * e1 + (sig * z1) * e2;
-        delta_rough = delta_t;
-        V3 t_out = t_mir + delta_t;
-        double tt = dot(t_out, t_out);
-        if (tt >= 1.0) {
-          alive = false;  // evanescent: no propagating energy
-        } else {
-          d_out = t_out + std::sqrt(1.0 - tt) * n;
-          pdf = rough_diffuse_density(g_r, P.k, M.corr_len_um, delta_t) * std::sqrt(1.0 - tt);
-        }
-      }
-    }
-
-    // --- the class wavelengths' densities of the direction just sampled
-    if (hero && alive && M.type == MAT_ROUGH) {
-      for (int g = 0; g < G; ++g) {
-        if (g == gh || q[g] == 0.0) continue;
-        const double kg = 2.0 * PI / lam_g[g];
-        const double gg = std::pow(2.0 * kg * M.sigma_h_um * cos_i, 2);
-        if (m_rough == 0.0)  // specular term: probability e^{-g} (none in the continuous limit)
-          q[g] *= gg > G_CONT ? 0.0 : std::exp(g_r - gg);
-        else  // diffuse terms: density at the sampled offset (the cos factor is common)
-          q[g] *= rough_diffuse_density(gg, kg, M.corr_len_um, delta_rough) /
-                  rough_diffuse_density(g_r, P.k, M.corr_len_um, delta_rough);
-      }
-    }
-    if (hero && M.type == MAT_DIELECTRIC && M.cauchy_b_um2 != 0.0) drop_companions();
-
-    // --- next-event estimation toward an emissive triangle (rough lobes only:
-    // grating orders and mirror reflection are delta lobes)
-    if (M.type == MAT_ROUGH && (C.flags & FLAG_NEE) && n_emit > 0) {
-      double un[4], uf[4];
-      rng.draw(seg, CALL_NEE_DIR, un);
-      int ei = std::min(n_emit - 1, (int)(un[0] * n_emit));
-      const Tri& ET = S.tris[S.emitters[ei][0]];
-      const int emat = ET.mat;
-      const Material& EM = S.mats[emat];
-      V3 ne = tri_normal(ET);
-      double kap = 1.0 / (P.s_ray2 + source_spread2(P.lambda, EM.coh_len_um));
-      V3 w = vmf_sample(neg(ne), kap, un[1], un[2]);
-      double cos_o = dot(w, n);
-      if (cos_o > 0.0) {
-        double ts;
-        int sp;
-        if (closest_hit(S, x, w, prim, true, &ts, &sp) && S.tris[sp].mat == emat) {
-          V3 delta_t = (w - dot(w, n) * n) - t_mir;
-          double f = (g_r > 0.0 ? rough_diffuse_density(g_r, P.k, M.corr_len_um, delta_t) : 0.0) * cos_o;
-          double pn = vmf(w, neg(ne), kap) / n_emit;
-          if (hero && pn > 0.0) {
-            // joint power heuristic over (class wavelength, technique); the
-            // lobe density toward w at wavelength j (the cos factor included)
-            double pbw[4], den = 0.0;
-            for (int j = 0; j < G; ++j) {
-              pbw[j] = 0.0;
-              if (cf[j] * qpre[j] == 0.0) continue;
-              const double gj = std::pow(2.0 * kcls[j] * M.sigma_h_um * cos_i, 2);
-              pbw[j] = (gj > 0.0 ? rough_diffuse_density(gj, kcls[j], M.corr_len_um, delta_t) : 0.0) * cos_o;
-              const double a = cf[j] * qpre[j] * pbw[j], b = cf[j] * qpre[j] * nee_density(j, w, ne, EM.coh_len_um);
-              den += a * a + b * b;
-            }
-            rng.draw(seg, CALL_NEE_FOOT, uf);
-            for (int g = 0; g < G; ++g) {
-              if (pbw[g] == 0.0 || den == 0.0) continue;
-              double b2 = fb2[g], r = frho[g];
-              propagate(&b2, &r, ts * 1e6 / (kcls[g] * P.eta));
-              double m = measure_emitter(S, sp, x + ts * w, w, b2, r, kcls[g], lam_g[g], uf[0], uf[1]);
-              add_vec(result + 4 * g, ns, c_nee, m * cf[g] * cf[gh] * qpre[g] * pn * pbw[g] / den);
-            }
-          } else if (f > 0.0 && pn > 0.0 && aniso) {
-            // the vertex's footprint mapped to the emitter direction's frame
-            const V3 xf_w = s_vector(n, neg(w), s_o);
-            CS2 Kw = aniso_interaction(K, P.xf, d_in, xf_w, w, n);
-            aniso_propagate(&Kw, ts * 1e6 / (P.k * P.eta));
-            rng.draw(seg, CALL_NEE_FOOT, uf);
-            double m = measure_emitter_aniso(S, sp, x + ts * w, w, Kw, xf_w, P.k, P.lambda, uf[0], uf[1]);
-            double wmis = pn * pn / (pn * pn + f * f);
-            add_vec(result, ns, c_nee, m * f / pn * wmis);
-          } else if (f > 0.0 && pn > 0.0) {
-            double b2 = P.beta2, r = P.rho;
-            propagate(&b2, &r, ts * 1e6 / (P.k * P.eta));
-            rng.draw(seg, CALL_NEE_FOOT, uf);
-            double m = measure_emitter(S, sp, x + ts * w, w, b2, r, P.k, P.lambda, uf[0], uf[1]);
-            double wmis = pn * pn / (pn * pn + f * f);
-            add_vec(result, ns, c_nee, m * f / pn * wmis);
-          }
-        }
-      }
-    }
-    if (!alive) return;
-
-    // --- continue the path with the sampled generalized ray: position and
-    // (beta, rho) unchanged by the interaction (Eq. K_reflection_refraction;
-    // rho growth at the grating ignored, Eq. K_grating).
-    if (aniso) {
-      // the footprint mapped onto the outgoing direction's transverse frame
-      const V3 xf_out = s_vector(n, neg(d_out), s_o);
-      K = aniso_interaction(K, P.xf, d_in, xf_out, d_out, n);
-      P.xf = xf_out;
-    }
-    if (ns == 1) {
-      P.t = t_new;
-    } else {
-      P.T = TRM;
-      V3 k_i = neg(d_out);
-      P.xf = s_vector(n, k_i, s_o);
-    }
-    P.o = x;
-    P.d = d_out;
-    P.eta = eta_next;
-    P.prev_prim = prim;
-    P.prev_delta = delta;
-    P.prev_pdf = pdf;
+    Vertex X;
+    X.prim = prim;
+    X.T = &T;
+    X.M = &M;
+    X.x = x;
+    X.n = tri_normal(T);
+    if (dot(X.n, P.d) > 0.0) X.n = neg(X.n);
+    X.cos_i = -dot(P.d, X.n);
+    X.d_in = P.d;
+    X.t_mir = X.d_in - dot(X.d_in, X.n) * X.n;
+    for (int g = 0; g < H.G; ++g) H.qpre[g] = H.q[g];
+    interaction_weight(W, seg, X);
+    Lobe L;
+    if (!sample_lobe(W, seg, X, L)) return;
+    if (H.on) hero_vertex_ratios(W, X, L);
+    next_event(W, seg, X, L);
+    if (!L.alive) return;
+    continue_path(W, X, L);
   }
 }
-
 }  // namespace
 
 // ======================================================================= C ABI

@@ -83,3 +83,25 @@ def test_iteration_bound_returns_timeout_and_frame_recovers(gr, use_graph):
     gr.render(S, views, fresh, seed=2, flags=gr.FLAG_NEE, use_graph=use_graph)
     for i in range(len(views)):
         assert np.array_equal(f.readback(i), fresh.readback(i)), i
+
+
+def test_size_queries_match_what_a_render_holds(gr):
+    """gr_render_scratch_bytes predicts the scratch a render keeps in its
+    frame, and gr_frame_bytes / gr_scene_bytes report the allocations: the
+    accumulators (library-owned only), the counters and that scratch."""
+    scenes, views = _views()
+    S = [gr.Scene(s) for s in scenes]
+    opts = dict(seed=1, flags=gr.FLAG_NEE, pool_size=4096)
+    predicted = gr.render_scratch_bytes(S, views, **opts)
+    own = gr.Frame(views)
+    before = own.device_bytes()
+    assert before >= 4 * gr.accum_floats(views)
+    gr.render(S, views, own, **opts)
+    assert own.device_bytes() - before == predicted
+    import torch
+    buf = torch.zeros(gr.accum_floats(views), dtype=torch.float32, device="cuda")
+    wrapped = gr.Frame(views, accum=buf)
+    assert wrapped.device_bytes() == before - 4 * gr.accum_floats(views)  # counters only
+    for sc, s in zip(scenes, S):
+        n = len(sc["tri_mat"])
+        assert 0 < s.device_bytes() < 400 * n + (1 << 16)
