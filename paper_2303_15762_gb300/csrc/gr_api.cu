@@ -415,8 +415,9 @@ gr_status check_render_args(const char* who, gr_scene* const* scenes, int32_t n_
     if (!scenes[i]) return fail(GR_E_INVALID, w + ": null scene " + std::to_string(i));
   if (opts->table_dtype < GR_TABLE_F32 || opts->table_dtype > GR_TABLE_BF16)
     return fail(GR_E_INVALID, w + ": bad table dtype");
-  if (opts->pool_size < 0 || opts->block < 0 || (opts->block && (opts->block % 32 || opts->block > 256)))
-    return fail(GR_E_INVALID, w + ": bad pool size or block (block must be a multiple of 32, <= 256)");
+  if (opts->pool_size < 0 || opts->pool_size > gr::kMaxPool || opts->block < 0 ||
+      (opts->block && (opts->block % 32 || opts->block > 256)))
+    return fail(GR_E_INVALID, w + ": bad pool size (0 to 2^30 - 256) or block (a multiple of 32, <= 256)");
   if (opts->regen_threshold_pct < 0 || opts->regen_threshold_pct > 100)
     return fail(GR_E_INVALID, w + ": regen_threshold_pct out of [0, 100]");
   const int ns = views[0].n_stokes;
@@ -614,8 +615,9 @@ gr_status gr_render_static(gr_scene* const* scenes, int32_t n_scenes, const gr_v
     if (!scenes[i]) return fail(GR_E_INVALID, "gr_render_static: null scene " + std::to_string(i));
   if (opts->table_dtype < GR_TABLE_F32 || opts->table_dtype > GR_TABLE_BF16)
     return fail(GR_E_INVALID, "gr_render_static: bad table dtype");
-  if (opts->pool_size < 0 || opts->block < 0 || (opts->block && (opts->block % 32 || opts->block > 256)))
-    return fail(GR_E_INVALID, "gr_render_static: bad pool size or block (block must be a multiple of 32, <= 256)");
+  if (opts->pool_size < 0 || opts->pool_size > gr::kMaxPool || opts->block < 0 ||
+      (opts->block && (opts->block % 32 || opts->block > 256)))
+    return fail(GR_E_INVALID, "gr_render_static: bad pool size (0 to 2^30 - 256) or block (a multiple of 32, <= 256)");
   if (opts->regen_threshold_pct < 0 || opts->regen_threshold_pct > 100)
     return fail(GR_E_INVALID, "gr_render_static: regen_threshold_pct out of [0, 100]");
   const int ns = views[0].n_stokes;

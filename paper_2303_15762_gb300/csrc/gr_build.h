@@ -16,6 +16,10 @@ cudaError_t build_lbvh(const float* verts, const int* tri_mat, int n, float4* tr
 cudaError_t build_wide(const float* nodes, const float4* tri, int n, uint4* wn, int* n_wide, cudaStream_t st);
 cudaError_t build_half(const float* nodes, int n, uint4* hn, cudaStream_t st);
 
+// Largest slot pool (the trace launch tags next-event entries with bit 30 of
+// the slot index).
+constexpr int kMaxPool = (1 << 30) - 256;
+
 // Wavefront slot pool: per-slot path state in structure-of-arrays form.
 struct Pool {
   float4* od0;   // o.xyz, beta^2 (um^2)
@@ -30,10 +34,11 @@ struct Pool {
   float4* shm;   // NEE lobe terms: squared offset, g, (k l)^2, cos
   float4* mis;   // lobe terms of the vertex that sampled the current direction
   float2* hit;   // t, leaf slot
+  float2* shh;   // the next-event ray's closest hit: t, leaf slot
   int4* meta;    // view, local ticket, (sample k | seg << 16 | state << 24 | delta << 26), previous leaf slot
   int* tq;       // trace queue
   int* sq;       // shadow queue
-  unsigned char* st8;  // slot state (idle / active / done): the one field k_regen scans for every slot
+  unsigned char* st8;  // slot state (idle / active / done / waiting): the one field k_regen scans for every slot
   // hero-wavelength MIS only (null otherwise); planes [g * P + slot] for the
   // class member g (bin c + g Q)
   float4* hq;    // path density ratios q_g of the class wavelengths to the hero's
@@ -67,7 +72,10 @@ struct Counters {
   int trace_next;  // next unclaimed trace-queue entry (claimed in groups of 32)
   int tq_back;     // trace-queue entries filled from the end of the array (camera rays)
   int dq_count;    // hero-wavelength MIS: rough vertices queued for k_density
+  int sq_done;     // k_shadow blocks finished (the last one closes the queues)
+  int tq_front, tq_n;  // the iteration's trace queue as k_shade reads it
   unsigned long long samples, segments, shadow, ref_hit, ref_lobe, iters, node_visits, tri_tests;
+  unsigned long long held;  // finished samples k_regen held back for their next-event ray
 };
 
 struct RenderParams {

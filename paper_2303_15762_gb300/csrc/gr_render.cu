@@ -9,7 +9,13 @@
 //            generalized ray, Eq. MC_sourcing), or claim new tickets with one
 //            warp-aggregated atomic per warp; compact live slots into the
 //            trace queue (ballot + popc)
-//   trace  : closest hit of every queued ray (BVH, stack traversal)
+//   trace  : closest hit of every queued ray and of the previous shade's
+//            next-event rays, in one load-balanced launch (BVH, stack
+//            traversal)
+//   shadow : measure the emitter each next-event ray reached and add the
+//            MIS-weighted contribution (before the segment's own shading, so
+//            the sample's terms are added in path order); close the
+//            iteration's queues
 //   shade  : footprint update (Eq. K_free_space_propagation), measurement on
 //            escape / emitter hit (Eq. measurement_operator), interaction with
 //            the reversed wavevector (Eq. action_time_reversal) and sampling of
@@ -17,8 +23,8 @@
 //            (Eq. K_grating, order tables staged in shared memory), rough lobe
 //            (Eq. K_surface_HS), smooth reflection (Eq. K_reflection_refraction)
 //            with Fresnel Mueller weights; NEE shadow requests are queued
-//   shadow : trace NEE shadow rays, measure the emitter, add the MIS-weighted
-//            contribution
+// A sample that ends at a vertex with a next-event request waits (ST_WAIT)
+// one regen pass for its ray, so its fold still follows its last term.
 // All launches have fixed shapes (grid-stride loops over device-side queue
 // counts), so a batch of iterations can be replayed as one CUDA graph.
 #include <algorithm>
@@ -29,9 +35,14 @@
 
 namespace gr {
 
-enum { ST_IDLE = 0, ST_ACTIVE = 1, ST_DONE = 2 };
+// slot states; ST_WAIT: the sample has ended, but its last vertex's
+// next-event ray is traced and measured in the next iteration (the slot is
+// folded one regen pass later)
+enum { ST_IDLE = 0, ST_ACTIVE = 1, ST_DONE = 2, ST_WAIT = 3 };
+// trace-launch entries that are next-event rays carry this bit on the slot
+constexpr int kShadowEntry = 1 << 30;
 
-// Default slot pool bounds (slots; 257 bytes each without the hero and
+// Default slot pool bounds (slots; 265 bytes each without the hero and
 // anisotropic planes).
 constexpr long long kMaxDefaultPool = 1LL << 25;
 constexpr long long kMinDefaultPool = 1LL << 16;
@@ -44,9 +55,6 @@ constexpr long long kMinDefaultPool = 1LL << 16;
 #endif
 #ifndef GR_TRACE_BLOCK
 #define GR_TRACE_BLOCK 128
-#endif
-#ifndef GR_SHADOW_MIN_BLOCKS
-#define GR_SHADOW_MIN_BLOCKS 3
 #endif
 // shading: 4 blocks/SM (64 registers) for both Stokes counts.  The spills
 // this costs the 4-Stokes kernel are cheaper than the latency left exposed
@@ -323,11 +331,10 @@ template <int NS, bool HERO>
 __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
   const Pool& P = p.pool;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    p.ctr->sq_count = 0;
     p.ctr->dq_count = 0;
     p.ctr->iters += 1;
   }
-  int finished = 0;
+  int finished = 0, held = 0;
   // regeneration threshold: new tickets are claimed only while enough of the
   // pool was idle after the previous iteration (or when nothing is active)
   const int active_prev = *(volatile int*)&p.ctr->last_active;
@@ -335,7 +342,12 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
   // ticket is left): nothing to fold, claim or queue -- the iterations the
   // host loop runs past the end (it reads the counters a batch late) cost a
   // launch, not a scan of every slot
-  if (active_prev == 0 && *(volatile unsigned long long*)&p.ctr->next_ticket >= p.ctr->total_tickets) return;
+  // (decided once per block: other blocks' claims move next_ticket meanwhile)
+  __shared__ int s_complete;
+  if (threadIdx.x == 0)
+    s_complete = active_prev == 0 && *(volatile unsigned long long*)&p.ctr->next_ticket >= p.ctr->total_tickets;
+  __syncthreads();
+  if (s_complete) return;
   const bool may_claim = p.regen_thr <= 0 || active_prev == 0 ||
                          (long long)(p.P - active_prev) * 100 >= (long long)p.regen_thr * p.P;
   // the views' first tickets, for the claims' view search (batches of views)
@@ -408,6 +420,11 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
         need = true;
       } else if (st == ST_ACTIVE) {
         active = true;
+      } else if (st == ST_WAIT) {
+        // the sample's next-event ray is traced and measured in this
+        // iteration: it is folded by the next regen pass
+        P.st8[slot] = ST_DONE;
+        ++held;
       }
       if (need && !may_claim) {
         need = false;
@@ -479,6 +496,7 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
     }
   }
   block_count(&p.ctr->samples, finished);
+  block_count(&p.ctr->held, held);
 }
 
 // ------------------------------------------------------------------ trace
@@ -614,43 +632,71 @@ __device__ __forceinline__ void lane_trace(const RenderParams& p, int n, int* cu
   }
 }
 
-// Trace-queue closest hits: the binary tree (FP32 or FP16 child boxes)
-// through lane_trace, the 4-wide tree one ray per thread per pass.  The queue
-// holds continuing segments from the front of its array and camera rays from
-// the back.
+// Closest hits of the trace queue and of the next-event rays the previous
+// k_shade requested, in one launch: the binary tree (FP32 or FP16 child boxes)
+// through lane_trace, the 4-wide tree one ray per thread per pass.  Entries
+// [0, ns) are the next-event rays (origin: the vertex, direction: the sampled
+// emitter direction; their hits go to shh), then the trace queue, which holds
+// continuing segments from the front of its array and camera rays from the
+// back.  The few next-event rays ride on the launch's load balancing instead
+// of a launch of their own, where the slowest of them set its length.
+__device__ __forceinline__ int trace_entry(const RenderParams& p, int e, int ns, int front) {
+  return e < ns ? (p.pool.sq[e] | kShadowEntry) : tq_entry(p, e - ns, front);
+}
+
 template <int TREE>
 __global__ void __launch_bounds__(TREE == kTreeWide ? 256 : GR_TRACE_BLOCK, TREE == kTreeWide ? 3 : GR_TRACE_MIN_BLOCKS)
     k_trace(RenderParams p) {
   const Pool& P = p.pool;
   const int front = *(volatile int*)&p.ctr->tq_count;
-  const int n = front + *(volatile int*)&p.ctr->tq_back;
-  if (blockIdx.x == 0 && threadIdx.x == 0) p.ctr->segments += (unsigned long long)n;
+  const int nt = front + *(volatile int*)&p.ctr->tq_back;
+  const int ns = *(volatile int*)&p.ctr->sq_count;
+  const int n = ns + nt;
+  if (blockIdx.x == 0 && threadIdx.x == 0) p.ctr->segments += (unsigned long long)nt;
   int err = 0, refined = 0, visits = 0, tests = 0;
   if (TREE == kTreeWide) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-      const int slot = tq_entry(p, i, front);
+      const int es = trace_entry(p, i, ns, front);
+      const int slot = es & ~kShadowEntry;
       const int4 m = P.meta[slot];
       const DevView& V = p.views[m.x];
       const DevScene& S = p.scenes[V.scene_index];
-      const float4 a = P.od0[slot], b = P.od1[slot];
+      const float4 a = P.od0[slot], b = (es & kShadowEntry) ? P.shd[slot] : P.od1[slot];
       const Hit h = closest_hit_wide(S, xyz(a), xyz(b), m.w, &refined, &visits, &tests, &err);
-      P.hit[slot] = make_float2(h.t, __int_as_float(h.slot));
+      (es & kShadowEntry ? P.shh : P.hit)[slot] = make_float2(h.t, __int_as_float(h.slot));
     }
   } else {
     lane_trace<TREE == kTreeHalf>(
-        p, n, &p.ctr->trace_next, [&](int e) { return tq_entry(p, e, front); },
-        [&](int slot, float3& o, float3& d, int& exclude) -> const DevScene& {
-          // the slot state is read once per segment: evict-first loads keep
-          // it from displacing the BVH and triangles in L2
-          const int4 m = __ldcs(&P.meta[slot]);
-          const float4 a = __ldcs(&P.od0[slot]), b = __ldcs(&P.od1[slot]);
+        p, n, &p.ctr->trace_next, [&](int e) { return trace_entry(p, e, ns, front); },
+        [&](int es, float3& o, float3& d, int& exclude) -> const DevScene& {
+          const int slot = es & ~kShadowEntry;
+          int4 m;
+          float4 a, b;
+          if (es & kShadowEntry) {
+            // read again by k_shadow and k_shade: cached loads
+            m = P.meta[slot];
+            a = P.od0[slot];
+            b = P.shd[slot];
+          } else {
+            // the slot state is read once per segment: evict-first loads
+            // keep it from displacing the BVH and triangles in L2
+            m = __ldcs(&P.meta[slot]);
+            a = __ldcs(&P.od0[slot]);
+            b = __ldcs(&P.od1[slot]);
+          }
           o = xyz(a);
           d = xyz(b);
           exclude = m.w;
           return p.scenes[p.views[m.x].scene_index];
         },
-        [&](int slot, const Hit& h) { __stcs(&P.hit[slot], make_float2(h.t, __int_as_float(h.slot))); }, refined,
-        visits, tests, err);
+        [&](int es, const Hit& h) {
+          const float2 r = make_float2(h.t, __int_as_float(h.slot));
+          if (es & kShadowEntry)
+            P.shh[es & ~kShadowEntry] = r;
+          else
+            __stcs(&P.hit[es], r);
+        },
+        refined, visits, tests, err);
   }
   block_count(&p.ctr->ref_hit, refined);
   block_count(&p.ctr->node_visits, visits);
@@ -1108,8 +1154,10 @@ __global__ void __launch_bounds__(256, MODE != 0 ? GR_SHADE_MIN_BLOCKS_EXT
     tvals = svals;
   }
   const Pool& P = p.pool;
-  const int front = *(volatile int*)&p.ctr->tq_count;
-  const int n = front + *(volatile int*)&p.ctr->tq_back;
+  // the iteration's trace queue, as k_shadow recorded it when it reset the
+  // queue counters for the next regen pass
+  const int front = *(volatile int*)&p.ctr->tq_front;
+  const int n = *(volatile int*)&p.ctr->tq_n;
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int i = base + threadIdx.x;
     bool want_shadow = false;
@@ -1602,7 +1650,9 @@ __global__ void __launch_bounds__(256, MODE != 0 ? GR_SHADE_MIN_BLOCKS_EXT
             } else {
               P.od1[slot] = make_float4(d.x, d.y, d.z, rho);
               P.meta[slot] = make_int4(m.x, m.y, meta_pack(kk, seg, ST_DONE, 0), hslot);
-              P.st8[slot] = ST_DONE;
+              // a pending next-event ray is measured in the next iteration:
+              // the fold waits for it
+              P.st8[slot] = want_shadow ? ST_WAIT : ST_DONE;
             }
           }
         }
@@ -1625,7 +1675,8 @@ __global__ void __launch_bounds__(256, MODE != 0 ? GR_SHADE_MIN_BLOCKS_EXT
 // Hero-wavelength MIS: completes the density ratios q_j of the rough
 // vertices k_shade queued, with the lobe's m >= 1 density at the four class
 // wavelengths (rough_density_class) -- the same arithmetic on the same inputs
-// as inline, on a dense queue.  Runs after k_shade and before k_shadow.
+// as inline, on a dense queue.  Runs after k_shade, before the next
+// iteration's k_shadow measures the vertices' next-event rays.
 __global__ void __launch_bounds__(256) k_density(RenderParams p) {
   const Pool& P = p.pool;
   const int n = *(volatile int*)&p.ctr->dq_count;
@@ -1797,37 +1848,51 @@ __device__ __forceinline__ void shadow_finish_hero(const RenderParams& p, int sl
   }
 }
 
-// NEE shadow rays: closest hit from the interaction point toward the sampled
-// emitter direction, then shadow_finish, one ray per thread per pass (the
-// shadow queue is a third as long as the trace queue: too short for
-// lane_trace's refill schedule to pay for itself).
-template <int NS, int TREE, int MODE>
-__global__ void __launch_bounds__(256, GR_SHADOW_MIN_BLOCKS) k_shadow(RenderParams p) {
+// Next-event measurement of the shadow rays the previous k_shade requested,
+// whose closest hits this iteration's k_trace launch found: each ray that
+// reached its emitter adds its MIS-weighted measurement to its slot's sample,
+// before k_shade adds the sample's next segment (path order).  The last block
+// to finish closes the iteration's queues: it records the trace queue for
+// k_shade, the live count (traced rays and held samples) for the next regen
+// pass and the loop's exit test, and empties the trace and shadow queues.
+template <int NS, int MODE>
+__global__ void __launch_bounds__(256) k_shadow(RenderParams p) {
   const Pool& P = p.pool;
-  const int n = *(volatile int*)&p.ctr->sq_count;
-  int err = 0, refined = 0, visits = 0, tests = 0;
+  __shared__ int s_n;
+  if (threadIdx.x == 0) s_n = *(volatile int*)&p.ctr->sq_count;
+  __syncthreads();
+  const int n = s_n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int slot = P.sq[i];
-    const int4 m = P.meta[slot];
-    const DevScene& S = p.scenes[p.views[m.x].scene_index];
-    const float3 o = xyz(P.od0[slot]), d = xyz(P.shd[slot]);  // requested only if emitter_reachable
-    const Hit h = TREE == kTreeWide ? closest_hit_wide(S, o, d, m.w, &refined, &visits, &tests, &err)
-                                    : closest_hit<TREE == kTreeHalf>(S, o, d, m.w, &refined, &visits, &tests, &err);
+    const float2 hh = P.shh[slot];
+    Hit h;
+    h.t = hh.x;
+    h.slot = __float_as_int(hh.y);
     if (MODE == 1)
       shadow_finish_hero<NS>(p, slot, h);
     else
       shadow_finish<NS, MODE == 2>(p, slot, h);
   }
-  block_count(&p.ctr->ref_hit, refined);
-  block_count(&p.ctr->node_visits, visits);
-  block_count(&p.ctr->tri_tests, tests);
-  if (err) atomicOr(&p.ctr->err, err);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    p.ctr->shadow += (unsigned long long)n;
-    p.ctr->last_active = p.ctr->tq_count + p.ctr->tq_back;
-    p.ctr->tq_count = 0;
-    p.ctr->tq_back = 0;
-    p.ctr->trace_next = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // every block has read sq_count before it counts itself here
+    __threadfence();
+    if (atomicAdd(&p.ctr->sq_done, 1) == (int)gridDim.x - 1) {
+      __threadfence();
+      Counters* c = p.ctr;
+      const int front = *(volatile int*)&c->tq_count;
+      const int nt = front + *(volatile int*)&c->tq_back;
+      c->shadow += (unsigned long long)n;
+      c->tq_front = front;
+      c->tq_n = nt;
+      c->last_active = nt + (int)c->held;
+      c->tq_count = 0;
+      c->tq_back = 0;
+      c->trace_next = 0;
+      c->held = 0;
+      c->sq_count = 0;
+      c->sq_done = 0;
+    }
   }
 }
 
@@ -2000,11 +2065,18 @@ int sm_count(int dev) {
   return n > 0 ? n : 1;
 }
 
-// One wavefront iteration.  With `ev` (profiling) an event is recorded before
-// each kernel and after the last, so each kernel's device time is measured on
-// the stream it runs on.
 // Block size of the binary-tree trace kernel for a render's block size.
 int trace_block(int block) { return block < GR_TRACE_BLOCK ? block : GR_TRACE_BLOCK; }
+
+// Blocks of k_shadow: its queue is the few next-event rays of one iteration
+// (two blocks per SM cover the usual case in one pass), and every block takes
+// part in closing the queues, so the grid stays small.
+int shadow_grid(long long P, int sms) { return (int)std::min<long long>((P + 255) / 256, 2LL * sms); }
+
+// One wavefront iteration: regen, trace (with the previous shade's next-event
+// rays), shadow (their measurement), shade.  With `ev` (profiling) an event
+// is recorded before each kernel and after the last, so each kernel's device
+// time is measured on the stream it runs on.
 
 template <int NS, typename TT, int TREE>
 cudaError_t launch_iteration_t(const RenderParams& p, int grid_regen, int grid_trace, int grid_shade, int grid_shadow,
@@ -2018,6 +2090,13 @@ cudaError_t launch_iteration_t(const RenderParams& p, int grid_regen, int grid_t
   if (ev) cudaEventRecord(ev[1], st);
   k_trace<TREE><<<grid_trace, TREE == kTreeWide ? block : trace_block(block), 0, st>>>(p);
   if (ev) cudaEventRecord(ev[2], st);
+  if (hero)
+    k_shadow<NS, 1><<<grid_shadow, 256, 0, st>>>(p);
+  else if (aniso)
+    k_shadow<NS, 2><<<grid_shadow, 256, 0, st>>>(p);
+  else
+    k_shadow<NS, 0><<<grid_shadow, 256, 0, st>>>(p);
+  if (ev) cudaEventRecord(ev[3], st);
   if (hero) {
     k_shade<NS, TT, 1><<<grid_shade, block, smem, st>>>(p);
     k_density<<<grid_shade, 256, 0, st>>>(p);  // counted with shading
@@ -2025,13 +2104,6 @@ cudaError_t launch_iteration_t(const RenderParams& p, int grid_regen, int grid_t
     k_shade<NS, TT, 2><<<grid_shade, block, smem, st>>>(p);
   else
     k_shade<NS, TT, 0><<<grid_shade, block, smem, st>>>(p);
-  if (ev) cudaEventRecord(ev[3], st);
-  if (hero)
-    k_shadow<NS, TREE, 1><<<grid_shadow, block, 0, st>>>(p);
-  else if (aniso)
-    k_shadow<NS, TREE, 2><<<grid_shadow, block, 0, st>>>(p);
-  else
-    k_shadow<NS, TREE, 0><<<grid_shadow, block, 0, st>>>(p);
   if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError();
 }
@@ -2064,18 +2136,6 @@ const void* shade_kernel(int ns, int dtype, int mode) {
   if (dtype == GR_TABLE_F32) return shade_kernel_t<4, float>(mode);
   if (dtype == GR_TABLE_F16) return shade_kernel_t<4, __half>(mode);
   return shade_kernel_t<4, __nv_bfloat16>(mode);
-}
-template <int NS, int TREE>
-const void* shadow_kernel_t(int mode) {
-  return mode == 1 ? (const void*)k_shadow<NS, TREE, 1> : mode == 2 ? (const void*)k_shadow<NS, TREE, 2>
-                                                                    : (const void*)k_shadow<NS, TREE, 0>;
-}
-const void* shadow_kernel(int ns, int mode, int tree) {
-  if (ns == 1)
-    return tree == kTreeWide ? shadow_kernel_t<1, kTreeWide>(mode)
-                             : tree == kTreeHalf ? shadow_kernel_t<1, kTreeHalf>(mode) : shadow_kernel_t<1, kTreeF32>(mode);
-  return tree == kTreeWide ? shadow_kernel_t<4, kTreeWide>(mode)
-                           : tree == kTreeHalf ? shadow_kernel_t<4, kTreeHalf>(mode) : shadow_kernel_t<4, kTreeF32>(mode);
 }
 const void* trace_kernel(int tree) {
   return tree == kTreeWide ? (const void*)k_trace<kTreeWide>
@@ -2196,7 +2256,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   // free for this frame's scratch.  Images do not depend on the pool size.
   long long P = o.pool_size;
   if (P <= 0) {
-    const size_t per_slot = sizeof(float4) * 14 + sizeof(float2) + sizeof(int4) + 2 * sizeof(int) + 1 +
+    const size_t per_slot = sizeof(float4) * 14 + 2 * sizeof(float2) + sizeof(int4) + 2 * sizeof(int) + 1 +
                             (hero ? sizeof(float4) * 19 + sizeof(int) : 0) + (aniso ? sizeof(float4) * 5 : 0);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
@@ -2222,7 +2282,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const size_t o_vals = take(tsize * std::max(plan.vals_count, 1));
   const size_t o_vals32 = o.table_dtype == GR_TABLE_F32 ? o_vals : take(sizeof(float) * std::max(plan.vals_count, 1));
   const size_t o_f4 = take(sizeof(float4) * (size_t)P * 14);
-  const size_t o_hit = take(sizeof(float2) * (size_t)P);
+  const size_t o_hit = take(sizeof(float2) * (size_t)P * 2);  // hit, shh
   const size_t o_meta = take(sizeof(int4) * (size_t)P);
   const size_t o_tq = take(sizeof(int) * (size_t)P);
   const size_t o_sq = take(sizeof(int) * (size_t)P);
@@ -2274,6 +2334,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   p.pool.shm = f4 + (size_t)P * 12;
   p.pool.mis = f4 + (size_t)P * 13;
   p.pool.hit = (float2*)(base + o_hit);
+  p.pool.shh = p.pool.hit + (size_t)P;
   p.pool.meta = (int4*)(base + o_meta);
   p.pool.tq = (int*)(base + o_tq);
   p.pool.sq = (int*)(base + o_sq);
@@ -2358,7 +2419,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const void* shade_fn = shade_kernel(NSv, o.table_dtype, mode);
   g_regen = grid_for(regen_kernel(NSv, hero), 0);
   const int tree = pick_tree(o.flags, scenes, n_scenes);
-  g_shadow = grid_for(shadow_kernel(NSv, mode, tree), 0);
+  g_shadow = shadow_grid(P, sms);
   const int tblk = tree == kTreeWide ? block : trace_block(block);
   g_trace = grid_for(trace_kernel(tree), 0, tblk);
   g_shade = grid_for(shade_fn, smem);
@@ -2367,7 +2428,6 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   g_regen = std::min(g_regen, (int)((P + (long long)block * GR_REGEN_SLOTS - 1) / ((long long)block * GR_REGEN_SLOTS)));
   g_trace = std::min(g_trace, (int)((P + tblk - 1) / tblk));
   g_shade = std::min(g_shade, gmax);
-  g_shadow = std::min(g_shadow, gmax);
 
   const bool profile = o.profile && !o.use_graph;
   std::vector<cudaEvent_t> pev;
@@ -2535,12 +2595,15 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
       f->kernel_launches[k] = 0;
     }
     if (status == GR_OK && !pev.empty()) cudaEventSynchronize(pev.back());
+    // launch order regen, trace, shadow, shade; reported as 0 regen, 1 trace,
+    // 2 shade, 3 shadow
+    const int slot_of[4] = {0, 1, 3, 2};
     for (size_t i = 0; i + 4 < pev.size(); i += 5) {
       for (int k = 0; k < 4; ++k) {
         float ms = 0.0f;
         if (status == GR_OK && cudaEventElapsedTime(&ms, pev[i + k], pev[i + k + 1]) == cudaSuccess) {
-          f->kernel_ms[k] += ms;
-          f->kernel_launches[k] += 1;
+          f->kernel_ms[slot_of[k]] += ms;
+          f->kernel_launches[slot_of[k]] += 1;
         }
       }
     }
@@ -2664,7 +2727,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   const size_t fixed = off;
   // the slot pool's 6 arrays each start on a 256-byte boundary: up to 6 x 255
   // bytes of padding, counted with the fixed part
-  const size_t per_slot = sizeof(float4) * 14 + sizeof(float2) + sizeof(int4) + 2 * sizeof(int) + 1;
+  const size_t per_slot = sizeof(float4) * 14 + 2 * sizeof(float2) + sizeof(int4) + 2 * sizeof(int) + 1;
   const size_t slack = 7 * 256;
   const long long p_max = fixed + slack >= (size_t)GR_STATIC_SCRATCH_BYTES
                               ? 0
@@ -2684,7 +2747,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   P = (P + 255) / 256 * 256;
   if (P > p_max) P = p_max;
   const size_t o_f4 = take(sizeof(float4) * (size_t)P * 14);
-  const size_t o_hit = take(sizeof(float2) * (size_t)P);
+  const size_t o_hit = take(sizeof(float2) * (size_t)P * 2);  // hit, shh
   const size_t o_meta = take(sizeof(int4) * (size_t)P);
   const size_t o_tq = take(sizeof(int) * (size_t)P);
   const size_t o_sq = take(sizeof(int) * (size_t)P);
@@ -2719,6 +2782,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   p.pool.shm = f4 + (size_t)P * 12;
   p.pool.mis = f4 + (size_t)P * 13;
   p.pool.hit = (float2*)(base + o_hit);
+  p.pool.shh = p.pool.hit + (size_t)P;
   p.pool.meta = (int4*)(base + o_meta);
   p.pool.tq = (int*)(base + o_tq);
   p.pool.sq = (int*)(base + o_sq);
@@ -2778,7 +2842,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
   const int tblk = tree == kTreeWide ? block : trace_block(block);
   const int g_trace = std::min((int)((P + tblk - 1) / tblk), grid_for(trace_kernel(tree), 0, tblk));
   const int g_shade = std::min(gmax, grid_for(shade_fn, smem));
-  const int g_shadow = std::min(gmax, grid_for(shadow_kernel(NSv, 0, tree), 0));
+  const int g_shadow = shadow_grid(P, sms);
   // --- iteration loop; the host reads the device counters into a stack copy
   // after every batch (no events, no pinned buffer)
   long long n_max = 1, d_max = 0;

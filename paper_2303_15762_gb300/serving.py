@@ -36,7 +36,7 @@ import numpy as np
 
 # device bytes per slot of the wavefront pool (the render's slot state, queues
 # and state byte), and an allowance for the view and order-table descriptors
-SLOT_BYTES = 257
+SLOT_BYTES = 265
 DESCRIPTOR_ALLOWANCE = 1 << 20
 
 

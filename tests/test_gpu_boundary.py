@@ -105,3 +105,16 @@ def test_size_queries_match_what_a_render_holds(gr):
     for sc, s in zip(scenes, S):
         n = len(sc["tri_mat"])
         assert 0 < s.device_bytes() < 400 * n + (1 << 16)
+
+
+def test_pool_beyond_the_largest_is_rejected(gr):
+    """Pools above 2^30 - 256 slots are refused before any launch (the trace
+    launch tags next-event entries with bit 30 of the slot index)."""
+    from paper_2303_15762_gb300 import _native as nat
+    scenes, views = _views()
+    S = [gr.Scene(s) for s in scenes]
+    f = gr.Frame(views)
+    with pytest.raises(nat.GrError) as exc:
+        gr.render(S, views, f, seed=2, flags=gr.FLAG_NEE, pool_size=(1 << 30) - 255)
+    assert exc.value.status == nat.GR_E_INVALID
+    assert "bad pool size" in str(exc.value)

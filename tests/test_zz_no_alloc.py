@@ -75,8 +75,11 @@ def test_static_rejects_pool_beyond_capacity(gr):
     S = [gr.Scene(sg.grating_scene())]
     v = sg.grating_view(width=8, height=8, spp=4)
     accum = torch.zeros(2 * 8 * 8 * 16, dtype=torch.float32, device="cuda")
-    assert _static_render(S, [v], accum.data_ptr(), pool_size=1 << 30) == nat.GR_E_INVALID
+    assert _static_render(S, [v], accum.data_ptr(), pool_size=1 << 24) == nat.GR_E_INVALID
     assert b"static scratch" in _last_error()
+    # beyond the largest pool of any render
+    assert _static_render(S, [v], accum.data_ptr(), pool_size=1 << 30) == nat.GR_E_INVALID
+    assert b"bad pool size" in _last_error()
     assert _static_render(S, [v], accum.data_ptr(), regen_threshold_pct=101) == nat.GR_E_INVALID
     assert b"regen_threshold_pct" in _last_error()
 
