@@ -917,17 +917,22 @@ __device__ __forceinline__ float3 emitter_normal(const DevScene& S, int ei) {
 // cosines at squared offset r2 from the mirror direction, kl2 = (|k| l)^2.
 // Evaluated only where it is needed (MIS weights of paths that actually reach
 // an emitter), not at every rough vertex.
+// Term m of the sum is e^-g g^m / m! * kl2 / (4 pi m) * exp(-r2 kl2 / (4 m)):
+// one reciprocal per term and no division; the sum stops once m has passed g
+// and the Poisson weight is below 1e-13 (as rough_density_class).
 __device__ float rough_density(float g, float kl2, float r2) {
   if (g > kGCont) {
     const float var = 2.0f * g / kl2;
     return __expf(-0.5f * r2 / var) / (2.0f * kPi * var);
   }
+  const float c = 0.25f * r2 * kl2, a = kl2 * (0.25f / kPi);
   float pm = __expf(-g), sum = 0.0f;
   const int mmax = (int)(g + 12.0f * sqrtf(g) + 20.0f);
   for (int m = 1; m <= mmax; ++m) {
-    pm *= g / (float)m;
-    const float var = 2.0f * (float)m / kl2;
-    sum += pm * __expf(-0.5f * r2 / var) / (2.0f * kPi * var);
+    const float inv = __frcp_rn((float)m);
+    pm *= g * inv;
+    sum += pm * (a * inv) * __expf(-c * inv);
+    if ((float)m > g && pm < 1e-13f) break;
   }
   return sum;
 }
@@ -2071,7 +2076,12 @@ int trace_block(int block) { return block < GR_TRACE_BLOCK ? block : GR_TRACE_BL
 // Blocks of k_shadow: its queue is the few next-event rays of one iteration
 // (two blocks per SM cover the usual case in one pass), and every block takes
 // part in closing the queues, so the grid stays small.
-int shadow_grid(long long P, int sms) { return (int)std::min<long long>((P + 255) / 256, 2LL * sms); }
+#ifndef GR_SHADOW_BLOCKS_PER_SM
+#define GR_SHADOW_BLOCKS_PER_SM 2
+#endif
+int shadow_grid(long long P, int sms) {
+  return (int)std::min<long long>((P + 255) / 256, (long long)GR_SHADOW_BLOCKS_PER_SM * sms);
+}
 
 // One wavefront iteration: regen, trace (with the previous shade's next-event
 // rays), shadow (their measurement), shade.  With `ev` (profiling) an event

@@ -43,3 +43,26 @@ def test_images_independent_of_schedule(gr):
         gr.render(S, [v], f, seed=12, flags=gr.FLAG_NEE | gr.FLAG_RR)
         assert np.array_equal(f.readback(0), images[0][i]), i
         f.close()
+
+
+@pytest.mark.parametrize("mode", ["hero", "aniso"])
+def test_hero_and_aniso_images_independent_of_schedule(gr, mode):
+    """Hero-wavelength MIS and anisotropic footprints with next-event rays and
+    4 Stokes components: pool size, regeneration threshold, block size and the
+    host loop or the graph leave every element bit-identical."""
+    scene = sg.procedural_scene(seed=31, n_objects=6, target_tris=6000, n_emitters=2)
+    view = sg.procedural_view(width=96, height=80, spp=64, n_bins=16, n_stokes=4, max_depth=4)
+    flags = gr.FLAG_NEE | gr.FLAG_RR | (gr.FLAG_HERO if mode == "hero" else gr.FLAG_ANISO)
+    S = [gr.Scene(scene)]
+    schedules = [dict(), dict(pool_size=4096, regen_threshold_pct=25),
+                 dict(pool_size=1 << 16, block=128, use_graph=True)]
+    images = []
+    for sch in schedules:
+        f = gr.Frame([view])
+        gr.render(S, [view], f, seed=5, flags=flags, **sch)
+        images.append(f.readback(0))
+        assert f.stats()["shadow_rays"] > 0
+        f.close()
+    assert np.linalg.norm(images[0]) > 0
+    for k in (1, 2):
+        assert np.array_equal(images[0], images[k]), schedules[k]
