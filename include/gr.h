@@ -169,9 +169,12 @@ typedef struct {
  * not available in gr_render_static).  table_dtype: storage of the grating order tables
  * (GR_TABLE_F32 / F16 / BF16); arithmetic is FP32 either way.  pool_size:
  * wavefront slots, i.e. path samples in flight (0 = one slot per ticket -- a
- * ticket is one pixel's samples of one wavelength bin, or of one class of 4
- * bins with GR_FLAG_HERO -- capped at 2^25 slots and at a quarter of the
- * device memory free at the call; at most 2^30 - 256; a slot takes 265 bytes,
+ * ticket is one pixel's samples of one wavelength bin, or with GR_FLAG_HERO
+ * one of min(4, spp / Q) consecutive ranges (1 if spp < 2 Q) of one pixel's
+ * samples of one class of 4 bins (Q = n_bins / 4; split ranges' sums meet in
+ * a 260-byte record per class and pixel and are added in range order) --
+ * capped at 2^25 slots and at a quarter of the device memory free at the
+ * call; at most 2^30 - 256; a slot takes 265 bytes,
  * plus 308 with GR_FLAG_HERO and 80 with GR_FLAG_ANISO; images do not depend on it);
  * block: threads per block (0 = default). */
 enum { GR_FLAG_NEE = 1, GR_FLAG_RR = 2, GR_FLAG_NO_RENORM = 4, GR_FLAG_WIDE_BVH = 8, GR_FLAG_HERO = 16, GR_FLAG_ANISO = 32,

@@ -52,6 +52,8 @@ struct Pool {
   float4* hd1;   // (|k_j| l)^2
   float4* hd2;   // squared offset of the sampled direction, the wanted members (bits) | hero member << 4
   int* dq;       // the density queue (slots whose ratios k_density completes)
+  float* hsub;   // per class record (views with hs > 1): [range][member][Stokes] totals
+  int* hsub_n;   // per class record: ranges folded so far (the last one adds all)
   // anisotropic footprints only (null otherwise): K = Kr + i Ki in the ray's
   // frame (xf), as (Kr11, Kr12, Kr22, Ki11), (Ki12, Ki22, -, -); the same for
   // a next-event request in the frame nkf of its direction

@@ -77,6 +77,9 @@ struct DevView {
   int nbu;                // sample classes that receive samples: min(spp, Q), from first_sample mod Q on
   int Q;                  // class modulus: a ticket owns the samples s with s mod Q == its class
                           // (Q = nb: one bin per ticket; Q = nb/4 with hero-wavelength MIS)
+  int hs;                 // hero-wavelength MIS: tickets per class (its samples in hs
+                          // consecutive ranges, combined in range order); 1 otherwise
+  long long hbase;        // first class record of this view in the range-sum buffer (hs > 1)
 };
 
 // Per-(view, material, bin) row of the grating order table: J_j(h k/2)^2 for

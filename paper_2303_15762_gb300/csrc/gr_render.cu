@@ -291,6 +291,19 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
 // next-event estimates) into theirs.  On the ticket's last sample every
 // member's total goes to its bin's frame accumulator.  Returns true if the
 // ticket has more samples.
+// Sample ranges of a class ticket under hero-wavelength MIS: with hs > 1 the
+// n samples k of a class are split into hs tickets, range j holding
+// k in [floor(j n / hs), floor((j + 1) n / hs)) (never empty: n >= hs).
+__device__ __forceinline__ int range_of(int k, int n, int hs) { return ((k + 1) * hs - 1) / n; }
+__device__ __forceinline__ int range_begin(int j, int n, int hs) { return (j * n) / hs; }
+
+// Fold a finished hero sample into its ticket's sums (Kahan, per class member
+// and Stokes component); at the end of the ticket's range, add the range's
+// totals into the frame.  With hs > 1 the ranges of a class finish in any
+// order: each stores its totals in the class record, and the last to finish
+// adds all of them, in range order, so every frame element still receives
+// its terms in sample order whatever the schedule.  Returns true if the
+// ticket has another sample.
 template <int NS>
 __device__ __forceinline__ bool fold_class(const RenderParams& p, int slot, const int4& m) {
   const Pool& P = p.pool;
@@ -299,8 +312,11 @@ __device__ __forceinline__ bool fold_class(const RenderParams& p, int slot, cons
   const int cls = m.y / WH;
   const int k = meta_k(m.z);
   const int gh = ((class_first_sample(V, cls, V.Q) + k * V.Q) % V.nb) / V.Q;
-  const bool more = k + 1 < class_samples(V, cls, V.Q);
+  const int n = class_samples(V, cls, V.Q), hs = V.hs;
+  const int j = hs > 1 ? range_of(k, n, hs) : 0;
+  const bool more = k + 1 < (hs > 1 ? range_begin(j + 1, n, hs) : n);
   const size_t Ps = (size_t)p.P;
+  float* rec = hs > 1 ? P.hsub + (size_t)(V.hbase + m.y) * 64 : nullptr;
   for (int g = 0; g < 4; ++g) {
     const float4 v = g == gh ? P.part[slot] : P.hpart[g * Ps + slot];
     float4 sm = P.haccS[g * Ps + slot], c = P.haccC[g * Ps + slot];
@@ -313,6 +329,8 @@ __device__ __forceinline__ bool fold_class(const RenderParams& p, int slot, cons
     if (more) {
       P.haccS[g * Ps + slot] = sm;
       P.haccC[g * Ps + slot] = c;
+    } else if (hs > 1) {
+      *(float4*)(rec + j * 16 + g * 4) = make_float4(sm.x - c.x, sm.y - c.y, sm.z - c.z, sm.w - c.w);
     } else {
       const size_t idx = ((size_t)m.y + (size_t)g * V.Q * WH) * NS;
       const float tot[4] = {sm.x - c.x, sm.y - c.y, sm.z - c.z, sm.w - c.w};
@@ -321,6 +339,23 @@ __device__ __forceinline__ bool fold_class(const RenderParams& p, int slot, cons
         kahan_add(a, e, tot[q]);
         V.acc_sum[idx + q] = a;
         V.acc_comp[idx + q] = e;
+      }
+    }
+  }
+  if (!more && hs > 1) {
+    // publish this range's totals, then count it; the last range reads the
+    // others' from L2
+    __threadfence();
+    if (atomicAdd(P.hsub_n + V.hbase + m.y, 1) == hs - 1) {
+      __threadfence();
+      for (int g = 0; g < 4; ++g) {
+        const size_t idx = ((size_t)m.y + (size_t)g * V.Q * WH) * NS;
+        for (int q = 0; q < NS; ++q) {
+          float a = V.acc_sum[idx + q], e = V.acc_comp[idx + q];
+          for (int r = 0; r < hs; ++r) kahan_add(a, e, __ldcg(rec + r * 16 + g * 4 + q));
+          V.acc_sum[idx + q] = a;
+          V.acc_comp[idx + q] = e;
+        }
       }
     }
   }
@@ -459,9 +494,13 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
         // with spp < Q they are the nbu = spp classes from first_sample mod Q
         // on.  The ticket's element is class * W*H + pixel, whatever the
         // claim order (with Q = nb the class is the bin).
+        // (with hero-wavelength MIS and hs > 1, the class's sample ranges
+        // come next: ticket = (pixel * hs + range) * nbu + class offset)
         const int local = (int)(tk - (unsigned long long)V.ticket_base);
-        const int pix = local / V.nbu;
-        const int cls = (V.first_sample + (local - pix * V.nbu)) % V.Q;
+        const int t = local / V.nbu;
+        const int cls = (V.first_sample + (local - t * V.nbu)) % V.Q;
+        const int pix = HERO ? t / V.hs : t;
+        const int rng_j = HERO ? t - pix * V.hs : 0;
         if (class_samples(V, cls, V.Q) > 0) {
           if (HERO) {
             for (int g = 0; g < 4; ++g) {
@@ -472,7 +511,8 @@ __global__ void __launch_bounds__(256) k_regen(RenderParams p) {
             P.accS[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             P.accC[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
           }
-          start_sample<NS, HERO>(p, slot, view, cls * (V.W * V.H) + pix, 0);
+          const int k0 = HERO && V.hs > 1 ? range_begin(rng_j, class_samples(V, cls, V.Q), V.hs) : 0;
+          start_sample<NS, HERO>(p, slot, view, cls * (V.W * V.H) + pix, k0);
           active_m |= 1u << j;
           fresh_m |= 1u << j;
           need_m &= ~(1u << j);
@@ -2176,6 +2216,7 @@ struct RenderPlan {
   std::vector<TableBuildRow> build_rows;
   int vals_count = 0;
   unsigned long long total_tickets = 0;
+  long long hero_classes = 0;  // class records of views whose classes are split (hs > 1)
 };
 
 // Called by gr_render after argument validation.
@@ -2225,7 +2266,20 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     V.ticket_base = (long long)plan.total_tickets;
     V.Q = (o.flags & GR_FLAG_HERO) ? d.n_bins / 4 : d.n_bins;
     V.nbu = std::min(d.spp, V.Q);
-    V.n_tickets = (long long)V.nbu * d.width * d.height;
+    // hero-wavelength MIS: a class with n samples is split into hs = min(4,
+    // n) tickets of consecutive sample ranges (every class has at least
+    // floor(spp / Q) samples), so the pool holds as many paths in flight as
+    // the plain form's one-bin tickets; the ranges' sums meet in a class
+    // record (fold_class).  hs depends on the view alone, so images do not
+    // depend on the pool or on the other views.
+    V.hs = 1;
+    V.hbase = 0;
+    if ((o.flags & GR_FLAG_HERO) && d.spp / V.Q >= 2) {
+      V.hs = std::min(4, d.spp / V.Q);
+      V.hbase = plan.hero_classes;
+      plan.hero_classes += (long long)V.Q * d.width * d.height;
+    }
+    V.n_tickets = (long long)V.nbu * d.width * d.height * V.hs;
     plan.total_tickets += (unsigned long long)V.n_tickets;
     V.acc_sum = plan_bytes ? nullptr : acc_sum[order[v]];
     V.acc_comp = plan_bytes ? nullptr : acc_comp[order[v]];
@@ -2301,6 +2355,10 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   // hq, hqp, hfb, hfr, hpart/haccS/haccC[4], hd0..hd2, then the density queue
   const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 19) : 0;
   const size_t o_dq = hero ? take(sizeof(int) * (size_t)P) : 0;
+  // range totals of split classes: 4 ranges x 4 members x 4 Stokes floats per
+  // class record, and the count of ranges folded
+  const size_t o_hsub = plan.hero_classes ? take(sizeof(float) * 64 * (size_t)plan.hero_classes) : 0;
+  const size_t o_hsubn = plan.hero_classes ? take(sizeof(int) * (size_t)plan.hero_classes) : 0;
   const size_t o_aniso = aniso ? take(sizeof(float4) * (size_t)P * 5) : 0;  // ak0, ak1, nk0, nk1, nkf
   const size_t total = off;
   if (plan_bytes) {
@@ -2362,6 +2420,10 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     p.pool.hd1 = h4 + (size_t)P * 17;
     p.pool.hd2 = h4 + (size_t)P * 18;
     p.pool.dq = (int*)(base + o_dq);
+    if (plan.hero_classes) {
+      p.pool.hsub = (float*)(base + o_hsub);
+      p.pool.hsub_n = (int*)(base + o_hsubn);
+    }
   }
   if (aniso) {
     float4* a4 = (float4*)(base + o_aniso);
@@ -2409,6 +2471,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   }
   GR_CK(cudaMemsetAsync(p.pool.meta, 0, sizeof(int4) * (size_t)P, st));
   GR_CK(cudaMemsetAsync(p.pool.st8, ST_IDLE, (size_t)P, st));
+  if (plan.hero_classes) GR_CK(cudaMemsetAsync(p.pool.hsub_n, 0, sizeof(int) * (size_t)plan.hero_classes, st));
   Counters c0;
   std::memset(&c0, 0, sizeof c0);
   c0.total_tickets = plan.total_tickets;
@@ -2687,6 +2750,7 @@ gr_status render_static_impl(gr_scene* const* scenes, int n_scenes, const gr_vie
     V.beta0 = d.f_beta * d.p_pix_um;
     V.ticket_base = (long long)total_tickets;
     V.Q = d.n_bins;  // no hero-wavelength MIS here
+    V.hs = 1;
     V.nbu = std::min(d.spp, d.n_bins);
     V.n_tickets = (long long)V.nbu * d.width * d.height;
     total_tickets += (unsigned long long)V.n_tickets;
