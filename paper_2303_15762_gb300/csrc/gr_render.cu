@@ -1171,6 +1171,34 @@ __device__ __forceinline__ float order0_prob(const TableRow& row, float3 t_mir, 
   return total > 0.0f ? a0 / total : 0.0f;
 }
 
+// An out-of-line copy of the emitter measurement for the hero-wavelength
+// paths, which evaluate it once per class member: inlined four times over,
+// the hero shading kernel outgrew the instruction cache (no-instruction
+// stalls were 7.9 warps per issue in ncu); out of line, the kernel takes 50.1
+// instead of 52.1 ms per headline step.  The plain paths keep the inlined
+// form (out of line it cost them 0.25 ms).  Making the order-0 probability
+// and the escape measurement out-of-line too gained nothing more.
+__device__ __noinline__ float hero_measure_emitter(const DevScene& S, int ei, float3 hit, float3 d, float beta2,
+                                                   float rho, float k, float lambda, float u0, float u1) {
+  return measure_emitter(S, ei, hit, d, beta2, rho, k, lambda, u0, u1);
+}
+// Distant sources measured at class wavelength lg (escape, hero MIS).
+__device__ __forceinline__ float hero_escape_measure(const DevScene& S, float3 d, float lg, float beta0) {
+  const float kg = 2.0f * kPi * __frcp_rn(lg);
+  const float s2g = 1.0f / (2.0f * beta0 * beta0 * kg * kg);
+  float mg = 0.0f;
+  for (int l = 0; l < S.n_lights; ++l) {
+    const gr_light L = S.lights[l];
+    if (L.type == GR_LIGHT_ENV) {
+      mg += L.E;
+    } else {
+      const float kap = 1.0f / (s2g + src_spread2(lg, L.coh_len_um));
+      mg += L.E * vmf(d, f3(L.dir[0], L.dir[1], L.dir[2]), kap);
+    }
+  }
+  return mg;
+}
+
 // HERO: hero-wavelength spectral MIS (Sec. 7.2).  The path's bin is the hero
 // of its class {c, c+Q, c+2Q, c+3Q} and makes every decision; hq[g] holds the
 // path's density at class wavelength g divided by its density at the hero's
@@ -1336,19 +1364,7 @@ __global__ void __launch_bounds__(256, MODE == 1   ? GR_SHADE_MIN_BLOCKS_HERO
           const float wq = cf[g] * hq[g];
           float val = 0.0f;
           if (wq > 0.0f) {
-            const float lg = step_lambda(V, cstep, cls + g * Qv);
-            const float kg = 2.0f * kPi * __frcp_rn(lg);
-            const float s2g = 1.0f / (2.0f * V.beta0 * V.beta0 * kg * kg);
-            float mg = 0.0f;
-            for (int l = 0; l < S.n_lights; ++l) {
-              const gr_light L = S.lights[l];
-              if (L.type == GR_LIGHT_ENV) {
-                mg += L.E;
-              } else {
-                const float kap = 1.0f / (s2g + src_spread2(lg, L.coh_len_um));
-                mg += L.E * vmf(d, f3(L.dir[0], L.dir[1], L.dir[2]), kap);
-              }
-            }
+            const float mg = hero_escape_measure(S, d, step_lambda(V, cstep, cls + g * Qv), V.beta0);
             val = mg * (wq / den);
           }
           add_member(g, val);
@@ -1421,7 +1437,7 @@ __global__ void __launch_bounds__(256, MODE == 1   ? GR_SHADE_MIN_BLOCKS_HERO
           for (int g = 0; g < 4; ++g) {
             if (!(cf[g] * hq[g] > 0.0f) || !(den > 0.0f)) continue;
             const float lg = step_lambda(V, cstep, cls + g * Qv);
-            const float mg = measure_emitter(S, ei, x, d, fb[g], fr[g], 2.0f * kPi * __frcp_rn(lg), lg, u.x, u.y);
+            const float mg = hero_measure_emitter(S, ei, x, d, fb[g], fr[g], 2.0f * kPi * __frcp_rn(lg), lg, u.x, u.y);
             const float w = two ? cf[g] * cf[gh] * hq[g] * pb * pb / den : cf[g] * hq[g] / den;
             add_member(g, mg * w);
           }
@@ -1883,7 +1899,7 @@ __device__ __forceinline__ void shadow_finish_hero(const RenderParams& p, int sl
     const float lg = step_lambda(V, cstep, cls + g * Qv), kg = 2.0f * kPi * __frcp_rn(lg);
     float b2 = fb[g], ro = fr[g];
     footprint_update_ik(h.t, lg * kInv2Pi * __frcp_rn(eta), b2, ro);
-    const float mg = measure_emitter(S, ei, x + h.t * w, w, b2, ro, kg, lg, u.x, u.y);
+    const float mg = hero_measure_emitter(S, ei, x + h.t * w, w, b2, ro, kg, lg, u.x, u.y);
     const float val = mg * cf[g] * cf[gh] * qp[g] * pn_h * pbw[g] / den;
     if (val == 0.0f) continue;
     float4* dst = g == gh ? P.part + slot : P.hpart + (size_t)g * p.P + slot;
