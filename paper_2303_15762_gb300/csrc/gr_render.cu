@@ -323,6 +323,10 @@ __device__ __forceinline__ bool fold_class(const RenderParams& p, int slot, cons
   float* rec = hs > 1 ? P.hsub + (size_t)(V.hbase + m.y) * 64 : nullptr;
   for (int g = 0; g < 4; ++g) {
     const float4 v = g == gh ? P.part[slot] : P.hpart[g * Ps + slot];
+    // nothing to add (a member whose density ratio is zero, or a sample that
+    // measured nothing): the sums are not touched until the range ends (a
+    // Kahan step with a zero term would only move compensation into the sum)
+    if (more && v.x == 0.0f && (NS == 1 || (v.y == 0.0f && v.z == 0.0f && v.w == 0.0f))) continue;
     float4 sm = P.haccS[g * Ps + slot], c = P.haccC[g * Ps + slot];
     kahan_add(sm.x, c.x, v.x);
     if (NS == 4) {
