@@ -235,6 +235,38 @@ __device__ __forceinline__ CT block_reserve(CT* counter, bool want) {
   return off;
 }
 
+// Two block-wide queue reservations with one set of barriers: this thread's
+// entries in queue a (for want_a) and in queue b (for want_b).  Uniform
+// control flow, as block_reserve.
+__device__ __forceinline__ int2 block_reserve2(int* counter_a, bool want_a, int* counter_b, bool want_b) {
+  __shared__ int s_wa[8], s_wb[8];
+  __shared__ int s_base[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const unsigned ma = __ballot_sync(0xffffffffu, want_a), mb = __ballot_sync(0xffffffffu, want_b);
+  if (lane == 0) {
+    s_wa[warp] = __popc(ma);
+    s_wb[warp] = __popc(mb);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ta = 0, tb = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int ca = s_wa[w], cb = s_wb[w];
+      s_wa[w] = ta;
+      s_wb[w] = tb;
+      ta += ca;
+      tb += cb;
+    }
+    s_base[0] = ta ? atomicAdd(counter_a, ta) : 0;
+    s_base[1] = tb ? atomicAdd(counter_b, tb) : 0;
+  }
+  __syncthreads();
+  const unsigned below = (1u << lane) - 1u;
+  const int2 off = make_int2(s_base[0] + s_wa[warp] + __popc(ma & below), s_base[1] + s_wb[warp] + __popc(mb & below));
+  __syncthreads();
+  return off;
+}
+
 // Block-wide reservation of n entries per thread (n >= 0) with one atomic per
 // block: returns the first of this thread's n entries (exclusive scan over the
 // block).  Uniform control flow, as block_reserve.
@@ -1733,11 +1765,14 @@ __global__ void __launch_bounds__(256, MODE == 1   ? GR_SHADE_MIN_BLOCKS_HERO
         P.st8[slot] = ST_DONE;
       }
     }
-    const int q = block_reserve<int>(&p.ctr->sq_count, want_shadow);
-    if (want_shadow) P.sq[q] = slot;
     if (HERO) {
-      const int qd = block_reserve<int>(&p.ctr->dq_count, want_density);
-      if (want_density) P.dq[qd] = slot;
+      // the next-event and density queues with one set of barriers
+      const int2 q = block_reserve2(&p.ctr->sq_count, want_shadow, &p.ctr->dq_count, want_density);
+      if (want_shadow) P.sq[q.x] = slot;
+      if (want_density) P.dq[q.y] = slot;
+    } else {
+      const int q = block_reserve<int>(&p.ctr->sq_count, want_shadow);
+      if (want_shadow) P.sq[q] = slot;
     }
   }
 }
