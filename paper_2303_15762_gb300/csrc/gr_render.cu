@@ -1403,7 +1403,9 @@ __global__ void __launch_bounds__(256, MODE == 1   ? GR_SHADE_MIN_BLOCKS_HERO
             const float mg = hero_escape_measure(S, d, step_lambda(V, cstep, cls + g * Qv), V.beta0);
             val = mg * (wq / den);
           }
-          add_member(g, val);
+          // a zero term leaves the member's sum as it is (the sums start at
+          // +0 and a zero product cannot change them): no read-modify-write
+          if (val != 0.0f) add_member(g, val);
         }
         done = true;
       } else if (hslot < 0 && ANISO) {
@@ -1514,7 +1516,9 @@ __global__ void __launch_bounds__(256, MODE == 1   ? GR_SHADE_MIN_BLOCKS_HERO
               // the density ratios before this vertex's decision and the
               // footprints at the vertex, for its next-event estimate and for
               // an emitter hit by the direction it samples
-              P.hqp[slot] = make_float4(hq[0], hq[1], hq[2], hq[3]);
+              // (the ratios are read only at a rough vertex's next-event
+              // estimate and at an emitter hit after a diffuse rough lobe)
+              if (M.type == GR_MAT_ROUGH) P.hqp[slot] = make_float4(hq[0], hq[1], hq[2], hq[3]);
               P.hfb[slot] = make_float4(fb[0], fb[1], fb[2], fb[3]);
               P.hfr[slot] = make_float4(fr[0], fr[1], fr[2], fr[3]);
             }
