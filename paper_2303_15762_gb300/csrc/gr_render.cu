@@ -807,6 +807,21 @@ __device__ __forceinline__ void footprint_update_ik(float t_m, float ik, float& 
   beta2 = b2;
 }
 
+// The path's footprint at a class wavelength of hero-wavelength MIS, from the
+// hero's: interactions leave (beta, rho) unchanged (Eq.
+// K_reflection_refraction, Eq. K_grating) and a free segment adds zbar = z /
+// |k| to the footprint's complex parameter (Eq. K_free_space_propagation
+// composes additively: rho grows by zbar / Kr with Kr = beta^2 / (1 + rho^2)
+// fixed), so from the camera's (beta0^2, 0), the same at every wavelength,
+// rho = Zbar / beta0^2 and beta^2 = beta0^2 (1 + rho^2), where Zbar, the sum
+// of the path's zbar, scales with the wavelength (every member's segments use
+// the hero's medium index; a dispersive medium drops the companions).
+// ratio = lambda_g / lambda_hero.
+__device__ __forceinline__ void member_footprint(float rho_hero, float ratio, float beta02, float& beta2, float& rho) {
+  rho = rho_hero * ratio;
+  beta2 = beta02 * (1.0f + rho * rho);
+}
+
 // ------------------------------------------------------------------ measurement
 // Emitter measurement (Eq. measurement_operator on an emissive triangle set):
 // one footprint point x ~ N(0, beta^2/2) transverse to d, projected along d
@@ -1344,19 +1359,6 @@ __global__ void __launch_bounds__(256, MODE == 1   ? GR_SHADE_MIN_BLOCKS_HERO
         hq[2] = q4.z;
         hq[3] = q4.w;
       }
-      // the path's footprint at each class wavelength (camera footprint on
-      // the first segment)
-      float fb[4], fr[4];
-      if (HERO) {
-        if (seg > 0) {
-          const float4 b4 = P.hfb[slot], r4 = P.hfr[slot];
-          fb[0] = b4.x, fb[1] = b4.y, fb[2] = b4.z, fb[3] = b4.w;
-          fr[0] = r4.x, fr[1] = r4.y, fr[2] = r4.z, fr[3] = r4.w;
-        } else {
-#pragma unroll
-          for (int g = 0; g < 4; ++g) fb[g] = beta2, fr[g] = rho;
-        }
-      }
       auto drop_companions = [&]() {
 #pragma unroll
         for (int g = 0; g < 4; ++g)
@@ -1435,11 +1437,6 @@ __global__ void __launch_bounds__(256, MODE == 1   ? GR_SHADE_MIN_BLOCKS_HERO
           K.i11 += zb;
           K.i22 += zb;
         }
-        if (HERO) {
-#pragma unroll
-          for (int g = 0; g < 4; ++g)
-            footprint_update_ik(t, step_lambda(V, cstep, cls + g * Qv) * kInv2Pi * __frcp_rn(eta), fb[g], fr[g]);
-        }
         const float3 x = o + t * d;
         const int mat = S.tri_mat[hslot];
         const gr_material M = S.mats[mat];
@@ -1475,7 +1472,9 @@ __global__ void __launch_bounds__(256, MODE == 1   ? GR_SHADE_MIN_BLOCKS_HERO
           for (int g = 0; g < 4; ++g) {
             if (!(cf[g] * hq[g] > 0.0f) || !(den > 0.0f)) continue;
             const float lg = step_lambda(V, cstep, cls + g * Qv);
-            const float mg = hero_measure_emitter(S, ei, x, d, fb[g], fr[g], 2.0f * kPi * __frcp_rn(lg), lg, u.x, u.y);
+            float fbg = beta2, frg = rho;  // the member's footprint at the hit
+            if (g != gh) member_footprint(rho, lg * __frcp_rn(lambda), V.beta0 * V.beta0, fbg, frg);
+            const float mg = hero_measure_emitter(S, ei, x, d, fbg, frg, 2.0f * kPi * __frcp_rn(lg), lg, u.x, u.y);
             const float w = two ? cf[g] * cf[gh] * hq[g] * pb * pb / den : cf[g] * hq[g] / den;
             add_member(g, mg * w);
           }
@@ -1519,8 +1518,6 @@ __global__ void __launch_bounds__(256, MODE == 1   ? GR_SHADE_MIN_BLOCKS_HERO
               // (the ratios are read only at a rough vertex's next-event
               // estimate and at an emitter hit after a diffuse rough lobe)
               if (M.type == GR_MAT_ROUGH) P.hqp[slot] = make_float4(hq[0], hq[1], hq[2], hq[3]);
-              P.hfb[slot] = make_float4(fb[0], fb[1], fb[2], fb[3]);
-              P.hfr[slot] = make_float4(fr[0], fr[1], fr[2], fr[3]);
             }
             const float4 v0 = __ldg(&S.tri[3 * hslot]), v1 = __ldg(&S.tri[3 * hslot + 1]),
                          v2 = __ldg(&S.tri[3 * hslot + 2]);
@@ -1932,15 +1929,17 @@ __device__ __forceinline__ void shadow_finish_hero(const RenderParams& p, int sl
     den += cq * cq * (pbw[j] * pbw[j] + pn * pn);
   }
   if (!(pn_h > 0.0f) || !(den > 0.0f)) return;
-  const float4 b4 = P.hfb[slot], r4 = P.hfr[slot];
-  const float fb[4] = {b4.x, b4.y, b4.z, b4.w}, fr[4] = {r4.x, r4.y, r4.z, r4.w};
+  // the vertex's footprint: the hero's (rho stored with the ray; beta^2 with
+  // its origin) and the members' from it (member_footprint)
+  const float rho_v = P.od1[slot].w, b2_v = P.od0[slot].w;
   const float4 u = rng4(p.seed, V.view_index, pixel, smp, seg, kCallNeeFoot);
   const float4 c = P.shc[slot];
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     if (!(pbw[g] > 0.0f)) continue;
     const float lg = step_lambda(V, cstep, cls + g * Qv), kg = 2.0f * kPi * __frcp_rn(lg);
-    float b2 = fb[g], ro = fr[g];
+    float b2 = b2_v, ro = rho_v;
+    if (g != gh) member_footprint(rho_v, lg * __frcp_rn(lambda), V.beta0 * V.beta0, b2, ro);
     footprint_update_ik(h.t, lg * kInv2Pi * __frcp_rn(eta), b2, ro);
     const float mg = hero_measure_emitter(S, ei, x + h.t * w, w, b2, ro, kg, lg, u.x, u.y);
     const float val = mg * cf[g] * cf[gh] * qp[g] * pn_h * pbw[g] / den;
@@ -2385,7 +2384,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   long long P = o.pool_size;
   if (P <= 0) {
     const size_t per_slot = sizeof(float4) * 14 + 2 * sizeof(float2) + sizeof(int4) + 2 * sizeof(int) + 1 +
-                            (hero ? sizeof(float4) * 19 + sizeof(int) : 0) + (aniso ? sizeof(float4) * 5 : 0);
+                            (hero ? sizeof(float4) * 17 + sizeof(int) : 0) + (aniso ? sizeof(float4) * 5 : 0);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
       cudaGetLastError();
@@ -2416,8 +2415,8 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const size_t o_sq = take(sizeof(int) * (size_t)P);
   const size_t o_st8 = take((size_t)P);
   const int mode = hero ? 1 : aniso ? 2 : 0;
-  // hq, hqp, hfb, hfr, hpart/haccS/haccC[4], hd0..hd2, then the density queue
-  const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 19) : 0;
+  // hq, hqp, hpart/haccS/haccC[4], hd0..hd2, then the density queue
+  const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 17) : 0;
   const size_t o_dq = hero ? take(sizeof(int) * (size_t)P) : 0;
   // range totals of split classes: 4 ranges x 4 members x 4 Stokes floats per
   // class record, and the count of ranges folded
@@ -2475,14 +2474,12 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     float4* h4 = (float4*)(base + o_hero);
     p.pool.hq = h4;
     p.pool.hqp = h4 + (size_t)P;
-    p.pool.hfb = h4 + (size_t)P * 2;
-    p.pool.hfr = h4 + (size_t)P * 3;
-    p.pool.hpart = h4 + (size_t)P * 4;
-    p.pool.haccS = h4 + (size_t)P * 8;
-    p.pool.haccC = h4 + (size_t)P * 12;
-    p.pool.hd0 = h4 + (size_t)P * 16;
-    p.pool.hd1 = h4 + (size_t)P * 17;
-    p.pool.hd2 = h4 + (size_t)P * 18;
+    p.pool.hpart = h4 + (size_t)P * 2;
+    p.pool.haccS = h4 + (size_t)P * 6;
+    p.pool.haccC = h4 + (size_t)P * 10;
+    p.pool.hd0 = h4 + (size_t)P * 14;
+    p.pool.hd1 = h4 + (size_t)P * 15;
+    p.pool.hd2 = h4 + (size_t)P * 16;
     p.pool.dq = (int*)(base + o_dq);
     if (plan.hero_classes) {
       p.pool.hsub = (float*)(base + o_hsub);

@@ -166,3 +166,31 @@ def test_emitters_lower_error_at_equal_samples(oracle):
     print("emitters: rms error plain %.4g hero %.4g (reference rms %.4g)" % (ep, eh, np.sqrt(np.mean(ref ** 2))))
     assert np.sqrt(np.mean(ref ** 2)) > 1e-3
     assert eh < 0.8 * ep
+
+
+def test_member_footprints_follow_from_the_heros():
+    """The kernels do not carry a footprint per class member: they derive it
+    from the hero's rho.  Free propagation (Eq. K_free_space_propagation, the
+    oracle's `propagate`) chained over a path's segments, at each class
+    wavelength from the same camera footprint (beta0^2, 0), gives rho_g =
+    rho_hero lambda_g / lambda_hero and beta_g^2 = beta0^2 (1 + rho_g^2) to
+    FP64 rounding, for any segment lengths and media (zbar = z lambda /
+    (2 pi eta))."""
+    from oracle import oracle as orc
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        beta0 = rng.uniform(0.5, 30.0)
+        lam = np.sort(rng.uniform(0.4, 0.7, 4))
+        hero = int(rng.integers(4))
+        segs = [(rng.uniform(1e-4, 2.0), rng.choice([1.0, 1.33, 1.5])) for _ in range(int(rng.integers(1, 6)))]
+        fp = []
+        for lg in lam:
+            b2, r = beta0 * beta0, 0.0
+            for t_m, eta in segs:
+                b2, r = orc.propagate(b2, r, t_m * 1e6 * lg / (2 * np.pi * eta))
+            fp.append((b2, r))
+        rho_h = fp[hero][1]
+        for g in range(4):
+            rho_g = rho_h * lam[g] / lam[hero]
+            assert fp[g][1] == pytest.approx(rho_g, rel=1e-12)
+            assert fp[g][0] == pytest.approx(beta0 * beta0 * (1.0 + rho_g * rho_g), rel=1e-12)
