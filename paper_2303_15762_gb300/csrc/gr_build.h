@@ -46,9 +46,6 @@ struct Pool {
   float4* hpart; // [4] the current sample's contributions to member g (g != hero)
   float4* haccS; // [4] ticket sums of member g (Kahan)
   float4* haccC; // [4] ticket compensations of member g
-  float4* hd0;   // a rough vertex's class lobe-density inputs, deferred to k_density: g_j
-  float4* hd1;   // (|k_j| l)^2
-  float4* hd2;   // squared offset of the sampled direction, the wanted members (bits) | hero member << 4
   int* dq;       // the density queue (slots whose ratios k_density completes)
   float* hsub;   // per class record (views with hs > 1): [range][member][Stokes] totals
   int* hsub_n;   // per class record: ranges folded so far (the last one adds all)

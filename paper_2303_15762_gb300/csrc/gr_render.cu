@@ -1667,31 +1667,23 @@ __global__ void __launch_bounds__(256, MODE == 1   ? GR_SHADE_MIN_BLOCKS_HERO
                 }
               }
               if (HERO && alive) {
-                // the class wavelengths' densities of the lobe term just sampled:
-                // specular e^-g, or the m >= 1 density at the sampled offset
-                // (the cosine factor is common to all wavelengths)
-                // (g and (k l)^2 scale with k^2 across the class)
-                float gq[4], klq[4];
-                unsigned want = 0u;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                  const float r = j == gh ? 1.0f : lambda * __frcp_rn(step_lambda(V, cstep, cls + j * Qv));
-                  const float sc = r * r;  // (k_j / k)^2
-                  gq[j] = g_r * sc;
-                  klq[j] = mis_rec.z * sc;
-                  if (mreal != 0.0f && (j == gh || hq[j] != 0.0f)) want |= 1u << j;
-                }
+                // the class wavelengths' densities of the lobe term just
+                // sampled (the cosine factor is common to all of them; g
+                // scales with k^2 across the class): the specular term's
+                // probability e^-g here; the m >= 1 density at the sampled
+                // offset by k_density, on a compacted queue of such vertices
+                // (here only a fraction of a warp's lanes would run the
+                // series), from the lobe terms stored for MIS, the ratios and
+                // the sample
                 if (mreal == 0.0f) {
 #pragma unroll
-                  for (int g = 0; g < 4; ++g)
-                    if (g != gh && hq[g] != 0.0f) hq[g] *= gq[g] > kGCont ? 0.0f : expf(g_r - gq[g]);
+                  for (int g = 0; g < 4; ++g) {
+                    if (g == gh || hq[g] == 0.0f) continue;
+                    const float r = lambda * __frcp_rn(step_lambda(V, cstep, cls + g * Qv));
+                    const float gqg = g_r * (r * r);  // g at class wavelength g
+                    hq[g] *= gqg > kGCont ? 0.0f : expf(g_r - gqg);
+                  }
                 } else {
-                  // the m >= 1 series over the four wavelengths runs in
-                  // k_density on a compacted queue of such vertices (here
-                  // only a fraction of a warp's lanes would run it)
-                  P.hd0[slot] = make_float4(gq[0], gq[1], gq[2], gq[3]);
-                  P.hd1[slot] = make_float4(klq[0], klq[1], klq[2], klq[3]);
-                  P.hd2[slot] = make_float4(mis_rec.x, __int_as_float((int)(want | ((unsigned)gh << 4))), 0.0f, 0.0f);
                   want_density = true;
                 }
               }
@@ -1788,15 +1780,31 @@ __global__ void __launch_bounds__(256) k_density(RenderParams p) {
   const int n = *(volatile int*)&p.ctr->dq_count;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int slot = P.dq[i];
-    const float4 a = P.hd0[slot], b = P.hd1[slot], c = P.hd2[slot];
-    const float gq[4] = {a.x, a.y, a.z, a.w}, klq[4] = {b.x, b.y, b.z, b.w};
-    const unsigned bits = (unsigned)__float_as_int(c.y);
-    const int gh = (int)(bits >> 4);
-    const bool want[4] = {(bits & 1u) != 0, (bits & 2u) != 0, (bits & 4u) != 0, (bits & 8u) != 0};
-    float dens[4];
-    rough_density_class(gq, klq, want, c.x, dens);
+    // the vertex's lobe terms (squared offset, g, (k l)^2 at the hero's
+    // wavelength), its ratios, and the sample's class and hero member
+    const float4 mi = P.mis[slot];
     const float4 q4 = P.hq[slot];
     float hq[4] = {q4.x, q4.y, q4.z, q4.w};
+    const int4 m = P.meta[slot];
+    const DevView& V = p.views[m.x];
+    const int cls = m.y / (V.W * V.H);
+    const int Qv = V.Q;
+    const int bin = (class_first_sample(V, cls, Qv) + meta_k(m.z) * Qv) % V.nb;
+    const int gh = (bin - cls) / Qv;
+    const float lambda = bin_lambda(V, bin), cstep = bin_step(V);
+    // g and (k l)^2 scale with k^2 across the class (as k_shade forms them)
+    float gq[4], klq[4];
+    bool want[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float r = j == gh ? 1.0f : lambda * __frcp_rn(step_lambda(V, cstep, cls + j * Qv));
+      const float sc = r * r;
+      gq[j] = mi.y * sc;
+      klq[j] = mi.z * sc;
+      want[j] = j == gh || hq[j] != 0.0f;
+    }
+    float dens[4];
+    rough_density_class(gq, klq, want, mi.x, dens);
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
       if (g == gh || hq[g] == 0.0f) continue;
@@ -2384,7 +2392,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   long long P = o.pool_size;
   if (P <= 0) {
     const size_t per_slot = sizeof(float4) * 14 + 2 * sizeof(float2) + sizeof(int4) + 2 * sizeof(int) + 1 +
-                            (hero ? sizeof(float4) * 17 + sizeof(int) : 0) + (aniso ? sizeof(float4) * 5 : 0);
+                            (hero ? sizeof(float4) * 14 + sizeof(int) : 0) + (aniso ? sizeof(float4) * 5 : 0);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
       cudaGetLastError();
@@ -2415,8 +2423,8 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const size_t o_sq = take(sizeof(int) * (size_t)P);
   const size_t o_st8 = take((size_t)P);
   const int mode = hero ? 1 : aniso ? 2 : 0;
-  // hq, hqp, hpart/haccS/haccC[4], hd0..hd2, then the density queue
-  const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 17) : 0;
+  // hq, hqp, hpart/haccS/haccC[4], then the density queue
+  const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 14) : 0;
   const size_t o_dq = hero ? take(sizeof(int) * (size_t)P) : 0;
   // range totals of split classes: 4 ranges x 4 members x 4 Stokes floats per
   // class record, and the count of ranges folded
@@ -2477,9 +2485,6 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     p.pool.hpart = h4 + (size_t)P * 2;
     p.pool.haccS = h4 + (size_t)P * 6;
     p.pool.haccC = h4 + (size_t)P * 10;
-    p.pool.hd0 = h4 + (size_t)P * 14;
-    p.pool.hd1 = h4 + (size_t)P * 15;
-    p.pool.hd2 = h4 + (size_t)P * 16;
     p.pool.dq = (int*)(base + o_dq);
     if (plan.hero_classes) {
       p.pool.hsub = (float*)(base + o_hsub);
