@@ -1684,7 +1684,10 @@ __global__ void __launch_bounds__(256, MODE == 1   ? GR_SHADE_MIN_BLOCKS_HERO
                     hq[g] *= gqg > kGCont ? 0.0f : expf(g_r - gqg);
                   }
                 } else {
-                  want_density = true;
+                  // (only a living companion's ratio needs the series)
+#pragma unroll
+                  for (int g = 0; g < 4; ++g)
+                    if (g != gh && hq[g] != 0.0f) want_density = true;
                 }
               }
             }
