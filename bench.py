@@ -51,13 +51,13 @@ FLOP_PER_WNODE = 109
 KERNELS = ["k_regen", "k_trace", "k_shade", "k_shadow"]
 # DRAM traffic of the dominant kernel per unit (ray) from one ncu capture:
 # dram__bytes_read.sum + dram__bytes_write.sum of the second k_trace launch of
-# the 256x256 x 64 spp case (162.99 + 7.56 MB), divided by the rays it traced
+# the 256x256 x 64 spp case (162.71 + 7.10 MB), divided by the rays it traced
 # (the full default pool: one slot per ticket, 2,097,152 slots, all live in
 # the second iteration, plus about a thousand next-event rays, not counted);
 # traffic grows with the rays a launch processes.  Valid only for the
 # traversal sources whose hash (source_hash) is recorded with it (else
 # reported null).
-NCU_TRAFFIC_PER_RAY = {("k_trace", "0764fd6448540c6a"): (162.99136e6 + 7.563264e6) / 2097152}
+NCU_TRAFFIC_PER_RAY = {("k_trace", "15075b81b78d8b16"): (162.713856e6 + 7.096832e6) / 2097152}
 # the glass workload: a constant environment of this radiance lets paths
 # refracted through the glass reach a light, and the oracle crop (x0, y0,
 # side) is where the glass decides the most pixel-bins of the 512^2 view
