@@ -560,8 +560,11 @@ __global__ void k_collapse(const float* __restrict__ nodes, const float* __restr
 // contains the FP32 one; values beyond the FP16 range become +-inf or the
 // largest finite value on the safe side), then the two child references.
 // Halves: [l.lo.x l.lo.y][l.lo.z l.hi.x][l.hi.y l.hi.z][r.lo.x r.lo.y]
-// [r.lo.z r.hi.x][r.hi.y r.hi.z], low half of each word first.
-__global__ void k_half_nodes(const float* __restrict__ nodes, int n, uint4* __restrict__ hn) {
+// [r.lo.z r.hi.x][r.hi.y r.hi.z], low half of each word first.  Node i is
+// stored at position pos[i] and its internal child references are renumbered
+// the same way (leaf references are triangle slots and stay).
+__global__ void k_half_nodes(const float* __restrict__ nodes, int n, const int* __restrict__ pos,
+                             uint4* __restrict__ hn) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
   const float* N = nodes + 16 * (size_t)i;
@@ -578,19 +581,64 @@ __global__ void k_half_nodes(const float* __restrict__ nodes, int n, uint4* __re
   q0.w = (unsigned)h[6] | ((unsigned)h[7] << 16);
   q1.x = (unsigned)h[8] | ((unsigned)h[9] << 16);
   q1.y = (unsigned)h[10] | ((unsigned)h[11] << 16);
-  q1.z = (unsigned)__float_as_int(N[12]);
-  q1.w = (unsigned)__float_as_int(N[13]);
-  hn[2 * (size_t)i] = q0;
-  hn[2 * (size_t)i + 1] = q1;
+  const int l = __float_as_int(N[12]), r = __float_as_int(N[13]);
+  q1.z = (unsigned)(l >= 0 ? pos[l] : l);
+  q1.w = (unsigned)(r >= 0 ? pos[r] : r);
+  const size_t d = (size_t)pos[i];
+  hn[2 * d] = q0;
+  hn[2 * d + 1] = q1;
 }
 
 }  // namespace
 
-// FP16 copy of the binary nodes (n >= 2 leaves): hn holds (n - 1) x 32 bytes.
+// FP16 copy of the binary nodes (n >= 2 leaves): hn holds (n - 1) x 32 bytes,
+// in depth-first order from the root (left child first), so that a node and
+// its left internal child are neighbours in memory and a subtree occupies one
+// contiguous range: a traversal's consecutive node fetches then often fall in
+// a cache line already read.  The order is computed on the host from the
+// nodes' child references (8 bytes per node copied back), before the
+// conversion kernel writes each node at its new position.  The tree, its
+// boxes and its closest hits are those of the FP32 nodes.
 cudaError_t build_half(const float* nodes, int n, uint4* hn, cudaStream_t st) {
   if (n < 2) return cudaSuccess;
-  k_half_nodes<<<(n - 1 + 255) / 256, 256, 0, st>>>(nodes, n, hn);
-  return cudaGetLastError();
+  const int m = n - 1;
+  std::vector<int2> refs((size_t)m);
+  cudaError_t e = cudaMemcpy2DAsync(refs.data(), sizeof(int2), nodes + 12, 16 * sizeof(float), sizeof(int2), (size_t)m,
+                                    cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  std::vector<int> pos((size_t)m, -1), stack;
+  stack.reserve(128);
+  stack.push_back(0);
+  int next = 0;
+  while (!stack.empty()) {
+    const int x = stack.back();
+    stack.pop_back();
+    // a malformed tree (a node reached twice, an index out of range) keeps
+    // the identity order; the traversal's own bounds then report it
+    if (x < 0 || x >= m || pos[(size_t)x] >= 0 || next >= m) {
+      next = -1;
+      break;
+    }
+    pos[(size_t)x] = next++;
+    const int2 c = refs[(size_t)x];
+    if (c.y >= 0) stack.push_back(c.y);
+    if (c.x >= 0) stack.push_back(c.x);
+  }
+  if (next != m)
+    for (int i = 0; i < m; ++i) pos[(size_t)i] = i;
+  int* pos_d = nullptr;
+  e = cudaMallocAsync(&pos_d, sizeof(int) * (size_t)m, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(pos_d, pos.data(), sizeof(int) * (size_t)m, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    k_half_nodes<<<(m + 255) / 256, 256, 0, st>>>(nodes, n, pos_d, hn);
+    e = cudaGetLastError();
+  }
+  // the host order must outlive its copy
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  cudaFreeAsync(pos_d, st);
+  return e != cudaSuccess ? e : e2;
 }
 
 // Collapse the binary LBVH (n >= 2 leaves) into 4-wide quantised nodes.  wn
