@@ -51,13 +51,13 @@ FLOP_PER_WNODE = 109
 KERNELS = ["k_regen", "k_trace", "k_shade", "k_shadow"]
 # DRAM traffic of the dominant kernel per unit (ray) from one ncu capture:
 # dram__bytes_read.sum + dram__bytes_write.sum of the second k_trace launch of
-# the 256x256 x 64 spp case (162.71 + 7.10 MB), divided by the rays it traced
+# the 256x256 x 64 spp case (162.24 + 7.20 MB), divided by the rays it traced
 # (the full default pool: one slot per ticket, 2,097,152 slots, all live in
 # the second iteration, plus about a thousand next-event rays, not counted);
 # traffic grows with the rays a launch processes.  Valid only for the
 # traversal sources whose hash (source_hash) is recorded with it (else
 # reported null).
-NCU_TRAFFIC_PER_RAY = {("k_trace", "15075b81b78d8b16"): (162.713856e6 + 7.096832e6) / 2097152}
+NCU_TRAFFIC_PER_RAY = {("k_trace", "e5e574ad5b3bb949"): (162.242048e6 + 7.202048e6) / 2097152}
 # the glass workload: a constant environment of this radiance lets paths
 # refracted through the glass reach a light, and the oracle crop (x0, y0,
 # side) is where the glass decides the most pixel-bins of the 512^2 view
@@ -67,11 +67,12 @@ GLASS_CROP = (0, 144, 96)
 
 def source_hash():
     """Hash of what k_trace's DRAM bytes per ray depend on: the device header
-    (traversal, BVH layout), the slot-pool layout and the trace section of the
-    render source (the queue schedule and the kernel)."""
+    (traversal, BVH layout), the slot-pool layout, the BVH builder (node
+    order) and the trace section of the render source (the queue schedule and
+    the kernel)."""
     csrc = os.path.join(ROOT, "paper_2303_15762_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ["gr_device.cuh", "gr_build.h"]:
+    for f in ["gr_device.cuh", "gr_build.h", "gr_bvh.cu"]:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     with open(os.path.join(csrc, "gr_render.cu"), "rb") as fh:
