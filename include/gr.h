@@ -213,7 +213,8 @@ typedef struct {
   int64_t node_visits;    /* BVH internal nodes visited (trace + shadow) */
   int64_t tri_tests;      /* ray-triangle tests (trace + shadow) */
   /* last render with profile = 1: device ms and launches per kernel
-     (0 regen, 1 trace, 2 shade, 3 shadow) */
+     (0 regen, 1 trace: the trace queue and the next-event rays, 2 shade,
+     3 shadow: the next-event measurement) */
   double kernel_ms[4];
   int64_t kernel_count[4];
 } gr_stats;
