@@ -175,7 +175,7 @@ typedef struct {
  * a 260-byte record per class and pixel and are added in range order) --
  * capped at 2^25 slots and at a quarter of the device memory free at the
  * call; at most 2^30 - 256; a slot takes 265 bytes,
- * plus 228 with GR_FLAG_HERO and 80 with GR_FLAG_ANISO; images do not depend on it);
+ * plus 164 with GR_FLAG_HERO and 80 with GR_FLAG_ANISO; images do not depend on it);
  * block: threads per block (0 = default). */
 enum { GR_FLAG_NEE = 1, GR_FLAG_RR = 2, GR_FLAG_NO_RENORM = 4, GR_FLAG_WIDE_BVH = 8, GR_FLAG_HERO = 16, GR_FLAG_ANISO = 32,
        GR_FLAG_FP32_NODES = 64 };

@@ -43,7 +43,6 @@ struct Pool {
   // class member g (bin c + g Q)
   float4* hq;    // path density ratios q_g of the class wavelengths to the hero's
   float4* hqp;   // the same ratios before the latest interaction
-  float4* hpart; // [4] the current sample's contributions to member g (g != hero)
   float4* haccS; // [4] ticket sums of member g (Kahan)
   float4* haccC; // [4] ticket compensations of member g
   int* dq;       // the density queue (slots whose ratios k_density completes)

@@ -198,8 +198,6 @@ __device__ __forceinline__ void start_sample(const RenderParams& p, int slot, in
   // forms them instead of reading them
   P.meta[slot] = make_int4(view, local, meta_pack(k, 0, ST_ACTIVE, 1), -1);
   P.st8[slot] = ST_ACTIVE;
-  if (HERO)  // the sample's contributions to the other bins of its class
-    for (int g = 0; g < 4; ++g) P.hpart[(size_t)g * p.P + slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
 // Sum a per-thread count over the warp and add it with one atomic.
@@ -327,14 +325,33 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
 // next-event estimates) into theirs.  On the ticket's last sample every
 // member's total goes to its bin's frame accumulator.  Returns true if the
 // ticket has more samples.
+// A term of class member g's range sum (hero-wavelength MIS, g not the
+// sample's hero): Kahan-added to the slot's sum as soon as it is measured,
+// in path order (the hero's own terms go through the sample's contribution
+// and are folded when the sample ends).  col: the throughput column.
+template <int NS>
+__device__ __forceinline__ void member_add(const Pool& P, size_t Ps, int g, int slot, float c0, float c1, float c2,
+                                           float c3, float val) {
+  float4 sm = P.haccS[g * Ps + slot], c = P.haccC[g * Ps + slot];
+  kahan_add(sm.x, c.x, c0 * val);
+  if (NS == 4) {
+    kahan_add(sm.y, c.y, c1 * val);
+    kahan_add(sm.z, c.z, c2 * val);
+    kahan_add(sm.w, c.w, c3 * val);
+  }
+  P.haccS[g * Ps + slot] = sm;
+  P.haccC[g * Ps + slot] = c;
+}
+
 // Sample ranges of a class ticket under hero-wavelength MIS: with hs > 1 the
 // n samples k of a class are split into hs tickets, range j holding
 // k in [floor(j n / hs), floor((j + 1) n / hs)) (never empty: n >= hs).
 __device__ __forceinline__ int range_of(int k, int n, int hs) { return ((k + 1) * hs - 1) / n; }
 __device__ __forceinline__ int range_begin(int j, int n, int hs) { return (j * n) / hs; }
 
-// Fold a finished hero sample into its ticket's sums (Kahan, per class member
-// and Stokes component); at the end of the ticket's range, add the range's
+// Fold a finished hero sample's own total into its member's range sum
+// (Kahan, per Stokes component; the companions' terms are already in theirs,
+// member_add); at the end of the ticket's range, add the four members' range
 // totals into the frame.  With hs > 1 the ranges of a class finish in any
 // order: each stores its totals in the class record, and the last to finish
 // adds all of them, in range order, so every frame element still receives
@@ -353,32 +370,41 @@ __device__ __forceinline__ bool fold_class(const RenderParams& p, int slot, cons
   const bool more = k + 1 < (hs > 1 ? range_begin(j + 1, n, hs) : n);
   const size_t Ps = (size_t)p.P;
   float* rec = hs > 1 ? P.hsub + (size_t)(V.hbase + m.y) * 64 : nullptr;
-  for (int g = 0; g < 4; ++g) {
-    const float4 v = g == gh ? P.part[slot] : P.hpart[g * Ps + slot];
-    // nothing to add (a member whose density ratio is zero, or a sample that
-    // measured nothing): the sums are not touched until the range ends (a
-    // Kahan step with a zero term would only move compensation into the sum)
-    if (more && v.x == 0.0f && (NS == 1 || (v.y == 0.0f && v.z == 0.0f && v.w == 0.0f))) continue;
-    float4 sm = P.haccS[g * Ps + slot], c = P.haccC[g * Ps + slot];
-    kahan_add(sm.x, c.x, v.x);
+  // the hero member's sample total (the companions' terms went straight into
+  // their range sums as they were measured); nothing to add leaves the sums
+  // untouched until the range ends (a Kahan step with a zero term would only
+  // move compensation into the sum)
+  const float4 v = P.part[slot];
+  const bool zero = v.x == 0.0f && (NS == 1 || (v.y == 0.0f && v.z == 0.0f && v.w == 0.0f));
+  float4 sh = make_float4(0.0f, 0.0f, 0.0f, 0.0f), ch = sh;
+  if (!more || !zero) {
+    sh = P.haccS[gh * Ps + slot];
+    ch = P.haccC[gh * Ps + slot];
+    kahan_add(sh.x, ch.x, v.x);
     if (NS == 4) {
-      kahan_add(sm.y, c.y, v.y);
-      kahan_add(sm.z, c.z, v.z);
-      kahan_add(sm.w, c.w, v.w);
+      kahan_add(sh.y, ch.y, v.y);
+      kahan_add(sh.z, ch.z, v.z);
+      kahan_add(sh.w, ch.w, v.w);
     }
     if (more) {
-      P.haccS[g * Ps + slot] = sm;
-      P.haccC[g * Ps + slot] = c;
-    } else if (hs > 1) {
-      *(float4*)(rec + j * 16 + g * 4) = make_float4(sm.x - c.x, sm.y - c.y, sm.z - c.z, sm.w - c.w);
-    } else {
-      const size_t idx = ((size_t)m.y + (size_t)g * V.Q * WH) * NS;
-      const float tot[4] = {sm.x - c.x, sm.y - c.y, sm.z - c.z, sm.w - c.w};
-      for (int q = 0; q < NS; ++q) {
-        float a = V.acc_sum[idx + q], e = V.acc_comp[idx + q];
-        kahan_add(a, e, tot[q]);
-        V.acc_sum[idx + q] = a;
-        V.acc_comp[idx + q] = e;
+      P.haccS[gh * Ps + slot] = sh;
+      P.haccC[gh * Ps + slot] = ch;
+    }
+  }
+  if (!more) {
+    for (int g = 0; g < 4; ++g) {
+      const float4 sm = g == gh ? sh : P.haccS[g * Ps + slot], c = g == gh ? ch : P.haccC[g * Ps + slot];
+      if (hs > 1) {
+        *(float4*)(rec + j * 16 + g * 4) = make_float4(sm.x - c.x, sm.y - c.y, sm.z - c.z, sm.w - c.w);
+      } else {
+        const size_t idx = ((size_t)m.y + (size_t)g * V.Q * WH) * NS;
+        const float tot[4] = {sm.x - c.x, sm.y - c.y, sm.z - c.z, sm.w - c.w};
+        for (int q = 0; q < NS; ++q) {
+          float a = V.acc_sum[idx + q], e = V.acc_comp[idx + q];
+          kahan_add(a, e, tot[q]);
+          V.acc_sum[idx + q] = a;
+          V.acc_comp[idx + q] = e;
+        }
       }
     }
   }
@@ -1375,21 +1401,14 @@ __global__ void __launch_bounds__(256, MODE == 1   ? GR_SHADE_MIN_BLOCKS_HERO
         }
       };
       // a contribution to class member g: the hero's into the sample's own
-      // sum, the others' into their planes
+      // sum, the others' straight into their range sums
       auto add_member = [&](int g, float val) {
         if (g == gh) {
           add_col(val);
           return;
         }
-        float4* hp = P.hpart + (size_t)g * p.P + slot;
-        float4 c = *hp;
-        c.x += T[0][0] * val;
-        if (NS == 4) {
-          c.y += T[1][0] * val;
-          c.z += T[2][0] * val;
-          c.w += T[3][0] * val;
-        }
-        *hp = c;
+        member_add<NS>(P, (size_t)p.P, g, slot, T[0][0], NS == 4 ? T[1][0] : 0.0f, NS == 4 ? T[2][0] : 0.0f,
+                       NS == 4 ? T[3][0] : 0.0f, val);
       };
       if (hslot < 0 && HERO) {
         // escape measured at every class wavelength, balance-heuristic weights
@@ -1955,15 +1974,18 @@ __device__ __forceinline__ void shadow_finish_hero(const RenderParams& p, int sl
     const float mg = hero_measure_emitter(S, ei, x + h.t * w, w, b2, ro, kg, lg, u.x, u.y);
     const float val = mg * cf[g] * cf[gh] * qp[g] * pn_h * pbw[g] / den;
     if (val == 0.0f) continue;
-    float4* dst = g == gh ? P.part + slot : P.hpart + (size_t)g * p.P + slot;
-    float4 pt = *dst;
+    if (g != gh) {
+      member_add<NS>(P, (size_t)p.P, g, slot, c.x, c.y, c.z, c.w, val);
+      continue;
+    }
+    float4 pt = P.part[slot];
     pt.x += c.x * val;
     if (NS == 4) {
       pt.y += c.y * val;
       pt.z += c.z * val;
       pt.w += c.w * val;
     }
-    *dst = pt;
+    P.part[slot] = pt;
   }
 }
 
@@ -2395,7 +2417,7 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   long long P = o.pool_size;
   if (P <= 0) {
     const size_t per_slot = sizeof(float4) * 14 + 2 * sizeof(float2) + sizeof(int4) + 2 * sizeof(int) + 1 +
-                            (hero ? sizeof(float4) * 14 + sizeof(int) : 0) + (aniso ? sizeof(float4) * 5 : 0);
+                            (hero ? sizeof(float4) * 10 + sizeof(int) : 0) + (aniso ? sizeof(float4) * 5 : 0);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
       cudaGetLastError();
@@ -2426,8 +2448,8 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
   const size_t o_sq = take(sizeof(int) * (size_t)P);
   const size_t o_st8 = take((size_t)P);
   const int mode = hero ? 1 : aniso ? 2 : 0;
-  // hq, hqp, hpart/haccS/haccC[4], then the density queue
-  const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 14) : 0;
+  // hq, hqp, haccS/haccC[4], then the density queue
+  const size_t o_hero = hero ? take(sizeof(float4) * (size_t)P * 10) : 0;
   const size_t o_dq = hero ? take(sizeof(int) * (size_t)P) : 0;
   // range totals of split classes: 4 ranges x 4 members x 4 Stokes floats per
   // class record, and the count of ranges folded
@@ -2485,9 +2507,8 @@ gr_status render_impl(gr_scene* const* scenes, int n_scenes, const gr_view_desc*
     float4* h4 = (float4*)(base + o_hero);
     p.pool.hq = h4;
     p.pool.hqp = h4 + (size_t)P;
-    p.pool.hpart = h4 + (size_t)P * 2;
-    p.pool.haccS = h4 + (size_t)P * 6;
-    p.pool.haccC = h4 + (size_t)P * 10;
+    p.pool.haccS = h4 + (size_t)P * 2;
+    p.pool.haccC = h4 + (size_t)P * 6;
     p.pool.dq = (int*)(base + o_dq);
     if (plan.hero_classes) {
       p.pool.hsub = (float*)(base + o_hsub);
