@@ -51,13 +51,13 @@ FLOP_PER_WNODE = 109
 KERNELS = ["k_regen", "k_trace", "k_shade", "k_shadow"]
 # DRAM traffic of the dominant kernel per unit (ray) from one ncu capture:
 # dram__bytes_read.sum + dram__bytes_write.sum of the second k_trace launch of
-# the 256x256 x 64 spp case (162.24 + 7.20 MB), divided by the rays it traced
+# the 256x256 x 64 spp case (162.50 + 7.37 MB), divided by the rays it traced
 # (the full default pool: one slot per ticket, 2,097,152 slots, all live in
 # the second iteration, plus about a thousand next-event rays, not counted);
 # traffic grows with the rays a launch processes.  Valid only for the
 # traversal sources whose hash (source_hash) is recorded with it (else
 # reported null).
-NCU_TRAFFIC_PER_RAY = {("k_trace", "e5e574ad5b3bb949"): (162.242048e6 + 7.202048e6) / 2097152}
+NCU_TRAFFIC_PER_RAY = {("k_trace", "374dc2e6c0ef425d"): (162.498816e6 + 7.366912e6) / 2097152}
 # the glass workload: a constant environment of this radiance lets paths
 # refracted through the glass reach a light, and the oracle crop (x0, y0,
 # side) is where the glass decides the most pixel-bins of the 512^2 view
